@@ -1,0 +1,208 @@
+/*
+ * panache.h -- C ABI of the B300 Panache pan-motif engine.
+ *
+ * Problem (Sec. 2, "Problem statement"): given a series T = (t_0..t_{n-1}),
+ * a length interval [m_min, m_max] and a fixed exclusion zone excl, return
+ * top-k pan-motifs: cells (m, i) of the pan matrix profile with a valid
+ * neighbour j (|i - j| >= excl) and the exact z-normalised distance
+ *   d_m(i, j) = || (T_{i,m} - mu_i) / sigma_i - (T_{j,m} - mu_j) / sigma_j ||_2,
+ * ranked by distance, skipping any cell within m/2 (2|i - i'| <= m) of an
+ * already accepted cell of the same length.  Distances below eps0 are
+ * reported as 0 (Sec. 3.6).  Constant windows (max == min) are ignored.
+ *
+ * Method (Sec. 3, Algorithms 1-2): per anchor length a in
+ * A = {m_min + r s} U {m_max}, every window's normalised non-DC spectrum
+ * F = (X_1..X_K')/sigma is kept by a sliding DFT, hashed by SimHash into a
+ * global-depth prefix directory with occupancy target alpha, searched with
+ * multi-probe under the budget R = gamma alpha, filtered by the Parseval
+ * bound LB <= d (Lemma 2) with a (1 - lambda) shrink, and verified exactly;
+ * an emit stage runs the hot-class sieve and local completion before the
+ * top-k.  Every reported distance is recomputed in FP64 from two-pass
+ * moments.
+ *
+ * Conventions of every entry point:
+ *  - Return 0 on success, a negative PANACHE_E* code on failure;
+ *    panache_strerror() names it.  On failure no output is written except
+ *    where stated (PANACHE_ETRUNC sets *out_len).
+ *  - Ownership: the caller owns every input and output buffer; the library
+ *    copies what it needs before returning and owns all device state behind
+ *    a context or stream handle.
+ *  - Series pointers are host memory unless the dtype carries
+ *    PANACHE_DEVICE, in which case they are device pointers on the context's
+ *    device and are read on the context's stream.
+ *  - A context is not thread-safe: use one per host thread.  Calls on one
+ *    context are serialised on its CUDA stream and are synchronous (they
+ *    return after the results are on the host).
+ *  - Results are deterministic for a given input, configuration and seed
+ *    (Prop. 6): the profile each call builds is the minimum over the pairs
+ *    its candidate rules admit, independent of the GPU schedule.
+ *  - Limits: 3 <= m_min <= m_max <= 1024; n <= 2^26 - 1 samples per series;
+ *    1 <= k; 1 <= excl; k * (m_max + 1) <= 3500 (selection pool).
+ */
+#ifndef PANACHE_H
+#define PANACHE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define PANACHE_OK 0
+#define PANACHE_EINVAL (-1)   /* bad argument (sizes, lengths, null pointers) */
+#define PANACHE_ENOMEM (-2)   /* device or host allocation failed */
+#define PANACHE_EBUDGET (-3)  /* request footprint above the context's HBM budget (admission refused) */
+#define PANACHE_ECUDA (-4)    /* a CUDA call failed; the context should be destroyed */
+#define PANACHE_ETRUNC (-5)   /* output capacity too small; *out_len holds the size needed */
+#define PANACHE_ESTATE (-6)   /* call not valid in the handle's current state */
+#define PANACHE_EPOOL (-7)    /* top-k pool overflow (massive exact ties); results withheld */
+#define PANACHE_ENODEV (-8)   /* no CUDA device, or the device is not sm_103 */
+
+/* ---- sample types (low byte) and pointer location flag ---- */
+#define PANACHE_F32 1
+#define PANACHE_F64 2
+#define PANACHE_DEVICE 0x100
+
+/* ---- precision forms ---- */
+#define PANACHE_PLAIN_FP64 0  /* FP64 sliding-DFT state and FP64 in-stream distances */
+#define PANACHE_MIXED 1       /* FP32 recurrence from FP64 anchors, FP32 in-stream distances */
+
+/* ---- top-k modes ---- */
+#define PANACHE_TOPK_GLOBAL 0      /* k cells over the whole stack */
+#define PANACHE_TOPK_PER_LENGTH 1  /* k cells for every length, ascending m */
+
+/* ---- flags ---- */
+#define PANACHE_FLAG_EXHAUSTIVE_SIEVE 0x1  /* every valid pair of a hot class, not only w sort-neighbours */
+#define PANACHE_FLAG_NO_SIEVE 0x2          /* skip the hot-class sieve (S_hot) */
+#define PANACHE_FLAG_NO_COMPLETION 0x4     /* skip local completion (S_local) */
+
+/* Tunables.  A zero field takes the paper's default (Sec. 4):
+ * alpha 16, gamma 8 (R = 128), stride 2, K 16, B 24, d0 12, probe cap 8,
+ * sieve width 8, (dm, dp) = (6, 4), 8 completion rounds, lambda 1e-4,
+ * eps0 1e-6, batch beta = excl, chunk 256 slides per direct-DFT anchor. */
+typedef struct {
+    uint32_t alpha;       /* occupancy target, the analyst's one knob ("budget") */
+    uint32_t gamma;       /* R = gamma * alpha candidate inspections per query (R <= 512) */
+    uint32_t stride;      /* anchor stride s */
+    uint32_t K;           /* spectral width, 2..16 (bins 1..K-1 kept) */
+    uint32_t B;           /* signature bits, 1..24 */
+    uint32_t d0;          /* probe reference depth */
+    uint32_t probe_cap;   /* cap on Hamming-1 probes, 1..8 */
+    uint32_t sieve_w;     /* sieve width w */
+    uint32_t dm, dp;      /* completion radii */
+    uint32_t rounds;      /* completion rounds P_max */
+    uint32_t precision;   /* PANACHE_PLAIN_FP64 or PANACHE_MIXED */
+    uint32_t topk_mode;   /* PANACHE_TOPK_GLOBAL or PANACHE_TOPK_PER_LENGTH */
+    uint32_t flags;       /* PANACHE_FLAG_* */
+    uint32_t chunk;       /* slides per direct-DFT re-anchor (power of two, 16..4096) */
+    uint32_t beta;        /* batch length of the streaming schedule (0: excl; capped at excl) */
+    uint64_t seed;        /* seed of the Gaussian projections */
+    uint64_t hbm_budget_bytes; /* admission limit on a request's device footprint (0: none) */
+    double lambda;        /* bound shrink */
+    double eps0;          /* zero-snap threshold */
+} panache_config;
+
+/* One motif: cell (m, i) with neighbour j and its FP64 distance d. */
+typedef struct {
+    int32_t m;
+    int32_t _pad;
+    int64_t i;
+    int64_t j;
+    double d;
+} panache_motif;
+
+/* One series of a batched request.  Its motifs use the context's top-k mode. */
+typedef struct {
+    const void *series;
+    int32_t dtype;
+    int32_t _pad;
+    int64_t n;
+    int32_t m_min, m_max, k, excl;
+} panache_request;
+
+/* Counters of the last request (Sec. 3.7 cost terms). */
+typedef struct {
+    uint64_t queries;            /* windows searched at anchor lengths */
+    uint64_t candidates;         /* candidates inspected (<= R per query) */
+    uint64_t exact_stream;       /* exact evaluations in the streaming pass (bound survivors) */
+    uint64_t exact_sieve;        /* exact evaluations of the hot-class sieve */
+    uint64_t exact_completion;   /* exact evaluations of local completion */
+    uint64_t hot_classes;        /* buckets larger than R at the final depth */
+    uint64_t completion_rounds;  /* rounds run (stops early when nothing improves) */
+    uint64_t device_bytes;       /* device footprint of the request (admission estimate) */
+    uint64_t kernel_launches;    /* kernels launched by the request */
+} panache_stats;
+
+typedef struct panache_ctx panache_ctx;
+typedef struct panache_stream panache_stream;
+
+/* Fills *cfg with the paper's defaults. */
+int panache_default_config(panache_config *cfg);
+
+/* Creates a context on the current CUDA device (which must be sm_103).
+ * cfg may be null (defaults).  `panache_create(budget)` of the paper's
+ * statement is a config with only alpha set.  Errors: EINVAL, ENODEV, ECUDA. */
+int panache_create(const panache_config *cfg, panache_ctx **out);
+
+/* Releases every device buffer of the context.  Null is ignored. */
+void panache_destroy(panache_ctx *ctx);
+
+/* Runs the context's work on `cuda_stream` (a cudaStream_t; null: the
+ * context's own stream). */
+int panache_set_stream(panache_ctx *ctx, void *cuda_stream);
+
+/* One series: top-k pan-motifs into out[0..out_cap).  *out_len receives the
+ * number written (fewer than k when fewer cells exist; k per length in
+ * per-length mode).  ETRUNC when out_cap is too small (with *out_len set to
+ * the count needed).  Errors: EINVAL, ENOMEM, EBUDGET, ECUDA, EPOOL. */
+int panache_pmp(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min, int32_t m_max,
+                int32_t k, int32_t excl, panache_motif *out, int64_t out_cap, int64_t *out_len);
+
+/* Many independent series in one set of launches (the batched form).  The
+ * motifs of request r go to out[r * out_cap_per_req ...], their count to
+ * out_len[r].  Errors as panache_pmp; EBUDGET when the whole batch exceeds
+ * the budget (split it and retry). */
+int panache_pmp_batch(panache_ctx *ctx, const panache_request *reqs, int32_t nreq, panache_motif *out,
+                      int64_t out_cap_per_req, int64_t *out_len);
+
+/* Streaming handles (Sec. 3.1): samples arrive by panache_append in chunks
+ * of any size; windows complete when their last sample arrives; the emit
+ * stage runs when panache_stream_topk is called.  A stream's samples and
+ * index stay resident on the device until panache_stream_close. */
+int panache_stream_open(panache_ctx *ctx, int32_t m_min, int32_t m_max, int32_t k, int32_t excl,
+                        panache_stream **out);
+int panache_append(panache_stream *h, const void *chunk, int32_t dtype, int64_t len);
+int panache_stream_topk(panache_stream *h, panache_motif *out, int64_t out_cap, int64_t *out_len);
+int64_t panache_stream_length(const panache_stream *h);
+void panache_stream_close(panache_stream *h);
+
+/* Counters of the context's last request. */
+int panache_last_stats(const panache_ctx *ctx, panache_stats *out);
+
+/* Copies the last request's profile rows of series `series_index`
+ * (packed keys, layout [m_max - m_min + 1][n]: the IEEE-754 bits of the
+ * in-stream distance with the low 26 bits replaced by the neighbour index;
+ * 0xFFFFFFFFFFFFFFFF for an empty cell) into keys[0..cap).  ETRUNC when cap
+ * is smaller than the row block.  The state is kept until the next request. */
+int panache_profile_rows(const panache_ctx *ctx, int32_t series_index, uint64_t *keys, int64_t cap);
+
+/* Copies anchor `anchor_index` (0-based in A of series `series_index`) of
+ * the last request: its length, the FP32 feature rows [nw][32] (bins
+ * re, im interleaved / sigma, zero padded) and the B-bit keys [nw].  Either
+ * output may be null.  Used by the parity tests. */
+int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *a_out,
+                         float *features, uint32_t *keys, int64_t cap_windows);
+
+/* Writes the FP32 Gaussian projections g_{a,l} (l = 1..B+1, row-major
+ * [B+1][32], dimensions >= 2(K-1) zero) that a context with configuration
+ * cfg (null: defaults) draws for anchor length a (Sec. 3.4).  Host-only: no
+ * device is needed.  ETRUNC when cap < (B+1)*32. */
+int panache_projections(const panache_config *cfg, int32_t a, float *g, int64_t cap);
+
+const char *panache_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PANACHE_H */

@@ -1,0 +1,10 @@
+"""B300-native Panache pan-motif engine (one-pass z-normalised PMP motif search).
+
+The compute path is the CUDA library ``libpanache.so`` (sources in
+``csrc/``, C ABI in ``include/panache.h``); ``native`` is its thin ctypes
+binding.  Importing the package does not load the library; the first call
+that needs it does, and fails loudly if it has not been built.
+"""
+from .native import (DEVICE, F32, F64, FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_COMPLETION, FLAG_NO_SIEVE,  # noqa: F401
+                     MIXED, PLAIN_FP64, TOPK_GLOBAL, TOPK_PER_LENGTH, Context, PanacheError, Stream,
+                     default_config, unpack_keys)

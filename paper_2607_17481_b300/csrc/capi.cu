@@ -1,0 +1,804 @@
+// Host runtime and C ABI: planning, admission, device buffers and the
+// order of the steps (Algorithm 1 over all anchors, then Algorithm 2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "emit.cuh"
+#include "kernels.cuh"
+#include "panache.h"
+#include "philox.h"
+#include "prims.cuh"
+
+namespace {
+
+struct SeriesIn {
+    const void *ptr;
+    int32_t dtype;
+    int64_t n;
+    int32_t m_min, m_max, k, excl;
+};
+
+int from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return PANACHE_OK;
+    if (e == cudaErrorMemoryAllocation) return PANACHE_ENOMEM;
+    return PANACHE_ECUDA;
+}
+
+#define PN_TRY(expr)                         \
+    do {                                     \
+        int rc_ = (expr);                    \
+        if (rc_ != PANACHE_OK) return rc_;   \
+    } while (0)
+#define PN_CU(expr) PN_TRY(from_cuda(expr))
+
+int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Sample conversion: raw host/device series -> FP64 and (hi, lo) float pairs.
+struct PnConv {
+    const void *src;
+    int64_t n;
+    int64_t x_off;
+    int32_t dtype;
+    int32_t _pad;
+};
+
+__global__ void k_convert(const PnConv *cv, int32_t ncv, int64_t total, double *x, float2 *xs) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int c = pn_find(cv, ncv, t, [](const PnConv &e) { return e.x_off; });
+    const PnConv &e = cv[c];
+    int64_t i = t - e.x_off;
+    double v = (e.dtype & 0xFF) == PANACHE_F32 ? (double)((const float *)e.src)[i] : ((const double *)e.src)[i];
+    float hi = (float)v;
+    x[t] = v;
+    xs[t] = make_float2(hi, (float)(v - (double)hi));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// One request: tables, device buffers and results.
+// ---------------------------------------------------------------------------
+struct PnRequest {
+    std::vector<PnSeries> ser;
+    std::vector<PnAnchor> anc;
+    std::vector<PnLevel> lev;
+    std::vector<int32_t> blk_anchor, blk_chunk0;
+    std::vector<int64_t> slot_off;
+    int64_t total_samples = 0, total_windows = 0, total_rows = 0, total_items = 0, total_buckets = 0;
+    int64_t total_cells = 0, total_slots = 0;
+    int a_max = 0;
+    size_t footprint = 0;
+
+    std::vector<void *> allocs;
+    cudaStream_t st = nullptr;
+    PnSeries *d_ser = nullptr;
+    PnAnchor *d_anc = nullptr;
+    PnLevel *d_lev = nullptr;
+    int32_t *d_blk_anchor = nullptr, *d_blk_chunk0 = nullptr;
+    int64_t *d_slot_off = nullptr;
+    double *x = nullptr;
+    float2 *xs = nullptr;
+    double2 *sq = nullptr;
+    double *shift = nullptr;
+    int32_t *runlen = nullptr;
+    float *F = nullptr;
+    uint32_t *sig = nullptr, *cnt = nullptr, *nclist = nullptr;
+    float *g = nullptr;
+    uint32_t *dir_keys = nullptr, *dir_vals = nullptr, *bstart = nullptr;
+    unsigned long long *prof = nullptr, *stats = nullptr;
+    int *flagbuf = nullptr;
+
+    ~PnRequest() {
+        for (void *p : allocs) cudaFree(p);
+    }
+
+    template <class T>
+    cudaError_t alloc(T *&p, int64_t count) {
+        p = nullptr;
+        if (count <= 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)&p, sizeof(T) * (size_t)count);
+        if (e == cudaSuccess) allocs.push_back(p);
+        return e;
+    }
+};
+
+struct panache_ctx {
+    panache_config cfg;
+    int device = 0;
+    int sm_count = 148;
+    cudaStream_t own = nullptr;
+    cudaStream_t st = nullptr;
+    PnRequest *last = nullptr;
+    panache_stats stats;
+    std::map<int, std::vector<float>> gcache;
+    uint64_t launches = 0;
+
+    const std::vector<float> &proj(int a) {
+        auto it = gcache.find(a);
+        if (it != gcache.end()) return it->second;
+        std::vector<float> g((size_t)(cfg.B + 1) * PN_FEAT);
+        pn::projections(a, cfg.seed, (int)cfg.B, (int)cfg.K, g.data());
+        return gcache.emplace(a, std::move(g)).first->second;
+    }
+};
+
+struct panache_stream {
+    panache_ctx *ctx;
+    int32_t m_min, m_max, k, excl;
+    double *dev = nullptr;  // resident samples (FP64)
+    int64_t len = 0, cap = 0;
+};
+
+namespace {
+
+void fill_defaults(panache_config &c) {
+    if (!c.alpha) c.alpha = 16;
+    if (!c.gamma) c.gamma = 8;
+    if (!c.stride) c.stride = 2;
+    if (!c.K) c.K = 16;
+    if (!c.B) c.B = 24;
+    if (!c.d0) c.d0 = 12;
+    if (!c.probe_cap) c.probe_cap = 8;
+    if (!c.sieve_w) c.sieve_w = 8;
+    if (!c.dm) c.dm = 6;
+    if (!c.dp) c.dp = 4;
+    if (!c.rounds) c.rounds = 8;
+    if (!c.chunk) c.chunk = 256;
+    if (c.lambda == 0.0) c.lambda = 1e-4;
+    if (c.eps0 == 0.0) c.eps0 = 1e-6;
+}
+
+int check_config(const panache_config &c) {
+    if (c.K < 2 || c.K > PN_MAXK || c.B < 1 || c.B > PN_MAXB) return PANACHE_EINVAL;
+    if ((int)(c.gamma * c.alpha) > pn::search_max_budget() || c.alpha > (1u << 20)) return PANACHE_EINVAL;
+    if (c.probe_cap < 1 || c.probe_cap > 8 || c.precision > 1 || c.topk_mode > 1) return PANACHE_EINVAL;
+    if (c.chunk < 16 || c.chunk > 4096 || (c.chunk & (c.chunk - 1))) return PANACHE_EINVAL;
+    if (!(c.lambda > 0.0 && c.lambda < 1.0) || !(c.eps0 >= 0.0)) return PANACHE_EINVAL;
+    return PANACHE_OK;
+}
+
+int check_series(const SeriesIn &s) {
+    const int dt = s.dtype & 0xFF;
+    if (!s.ptr && s.n > 0) return PANACHE_EINVAL;
+    if ((dt != PANACHE_F32 && dt != PANACHE_F64) || (s.dtype & ~0x1FF)) return PANACHE_EINVAL;
+    if (s.n < 0 || s.n > PN_MAX_SERIES_LEN) return PANACHE_EINVAL;
+    if (s.m_min < 3 || s.m_max < s.m_min || s.m_max > 1024) return PANACHE_EINVAL;
+    if (s.k < 1 || s.excl < 1) return PANACHE_EINVAL;
+    return PANACHE_OK;
+}
+
+// Builds every table of a request and its device footprint.
+int plan(panache_ctx *ctx, const std::vector<SeriesIn> &in, PnRequest &R) {
+    const panache_config &c = ctx->cfg;
+    const int C = (int)c.chunk;
+    int64_t x_off = 0, row_off = 0;
+    for (size_t s = 0; s < in.size(); ++s) {
+        const SeriesIn &si = in[s];
+        PnSeries S;
+        memset(&S, 0, sizeof(S));
+        S.x_off = x_off;
+        S.n = si.n;
+        S.row_off = row_off;
+        S.m_min = si.m_min;
+        S.m_max = si.m_max;
+        S.excl = si.excl;
+        S.k = si.k;
+        S.mode = (int32_t)c.topk_mode;
+        S.anchor_begin = (int32_t)R.anc.size();
+        std::vector<int> al;
+        for (int a = si.m_min; a <= si.m_max; a += (int)c.stride) al.push_back(a);
+        if (al.back() != si.m_max) al.push_back(si.m_max);
+        for (int a : al) {
+            const int64_t nw = si.n - a + 1;
+            if (nw <= 0) continue;
+            PnAnchor A;
+            memset(&A, 0, sizeof(A));
+            A.series = (int32_t)s;
+            A.a = a;
+            A.kp = pn_kprime(a, (int)c.K);
+            A.nw = nw;
+            A.dmax = pn_depth(nw, (int)c.alpha, (int)c.B);
+            A.win_off = R.total_windows;
+            A.nchunk = (nw + C - 1) / C;
+            A.row_off = R.total_rows;
+            A.item_off = R.total_items;
+            A.bucket_base = R.total_buckets;
+            A.level_begin = (int32_t)R.lev.size();
+            A.nlevels = A.dmax + 1;
+            for (int d = 0; d <= A.dmax; ++d) {
+                PnLevel L;
+                L.anchor = (int32_t)R.anc.size();
+                L.d = d;
+                L.cap = std::min<int64_t>(nw, (int64_t)c.alpha << d);
+                L.item_off = R.total_items;
+                L.bucket_base = R.total_buckets;
+                R.total_items += L.cap;
+                R.total_buckets += (int64_t)1 << d;
+                R.lev.push_back(L);
+            }
+            for (int64_t b = 0; b < A.nchunk; b += 128) {
+                R.blk_anchor.push_back((int32_t)R.anc.size());
+                R.blk_chunk0.push_back((int32_t)b);
+            }
+            R.slot_off.push_back(R.total_slots);
+            R.total_slots += (int64_t)1 << A.dmax;
+            R.total_windows += nw;
+            R.total_rows += A.nchunk * C;
+            R.a_max = std::max(R.a_max, a);
+            R.anc.push_back(A);
+        }
+        S.anchor_count = (int32_t)R.anc.size() - S.anchor_begin;
+        R.ser.push_back(S);
+        x_off += si.n;
+        row_off += (int64_t)(si.m_max - si.m_min + 1) * si.n;
+    }
+    R.total_samples = x_off;
+    R.total_cells = row_off;
+    if (R.total_items >= 0xFFFFFFFFll || R.total_buckets >= 0xFFFFFFFEll || R.total_windows >= 0xFFFFFFFFll)
+        return PANACHE_EBUDGET;
+    // device footprint: resident arrays plus the largest transient (radix sort of the directory)
+    size_t b = 0;
+    b += (size_t)R.total_samples * (8 + 8 + 16 + 4 + 8);   // x, xs, sq, runlen, staging
+    b += (size_t)R.total_rows * PN_FEAT * 4;                // features
+    b += (size_t)R.total_windows * 12;                      // sig, cnt, nclist
+    b += (size_t)R.total_items * 8 * 2;                     // directory + sort scratch
+    b += (size_t)R.total_buckets * 4 + (size_t)R.total_items / 4096 * 1024;
+    b += (size_t)R.total_cells * 8;                         // profile rows
+    b += (size_t)R.anc.size() * (c.B + 1) * PN_FEAT * 4;
+    R.footprint = b;
+    if (c.hbm_budget_bytes && b > c.hbm_budget_bytes) return PANACHE_EBUDGET;
+    return PANACHE_OK;
+}
+
+PnView make_view(panache_ctx *ctx, PnRequest &R) {
+    const panache_config &c = ctx->cfg;
+    PnView v;
+    memset(&v, 0, sizeof(v));
+    v.series = R.d_ser;
+    v.anchors = R.d_anc;
+    v.levels = R.d_lev;
+    v.nseries = (int32_t)R.ser.size();
+    v.nanchors = (int32_t)R.anc.size();
+    v.nlevels = (int32_t)R.lev.size();
+    v.B = (int32_t)c.B;
+    v.K = (int32_t)c.K;
+    v.C = (int32_t)c.chunk;
+    v.alpha = (int32_t)c.alpha;
+    v.R = (int32_t)(c.gamma * c.alpha);
+    v.d0 = (int32_t)c.d0;
+    v.probe_cap = (int32_t)c.probe_cap;
+    v.beta = (int32_t)c.beta;
+    v.lam = (float)c.lambda;
+    v.precision = (int32_t)c.precision;
+    v.x = R.x;
+    v.xs = R.xs;
+    v.sq = R.sq;
+    v.shift = R.shift;
+    v.runlen = R.runlen;
+    v.F = R.F;
+    v.sig = R.sig;
+    v.cnt = R.cnt;
+    v.nclist = R.nclist;
+    v.g = R.g;
+    v.dir_keys = R.dir_keys;
+    v.dir_vals = R.dir_vals;
+    v.bstart = R.bstart;
+    v.prof = R.prof;
+    v.stats = R.stats;
+    return v;
+}
+
+struct GroupSet {
+    std::vector<PnSelGroup> g;
+    std::vector<int32_t> owner;  // series of each group
+};
+
+GroupSet make_groups(const PnRequest &R, int mode, const std::vector<int> &k_of_series) {
+    GroupSet gs;
+    for (size_t s = 0; s < R.ser.size(); ++s) {
+        const PnSeries &S = R.ser[s];
+        const int L = S.m_max - S.m_min + 1;
+        if (mode == PANACHE_TOPK_GLOBAL) {
+            PnSelGroup G;
+            memset(&G, 0, sizeof(G));
+            G.cell_off = S.row_off;
+            G.ncell = (int64_t)L * S.n;
+            G.series = (int32_t)s;
+            G.k = k_of_series[s];
+            G.need = (uint32_t)((int64_t)G.k * (S.m_max + 1));
+            gs.g.push_back(G);
+            gs.owner.push_back((int32_t)s);
+        } else {
+            for (int r = 0; r < L; ++r) {
+                PnSelGroup G;
+                memset(&G, 0, sizeof(G));
+                G.cell_off = S.row_off + (int64_t)r * S.n;
+                G.ncell = S.n;
+                G.series = (int32_t)s;
+                G.k = k_of_series[s];
+                G.need = (uint32_t)((int64_t)G.k * (S.m_min + r + 1));
+                gs.g.push_back(G);
+                gs.owner.push_back((int32_t)s);
+            }
+        }
+    }
+    return gs;
+}
+
+// Runs the selection of `gs` and returns the picks per group on the host.
+int run_select(panache_ctx *ctx, PnRequest &R, const GroupSet &gs, bool strict,
+               std::vector<std::vector<PnPick>> &picks) {
+    picks.assign(gs.g.size(), {});
+    if (gs.g.empty()) return PANACHE_OK;
+    uint32_t need_max = 0;
+    int32_t kmax = 1;
+    for (auto &G : gs.g) {
+        need_max = std::max(need_max, G.need);
+        kmax = std::max(kmax, G.k);
+    }
+    int64_t cap = next_pow2((int64_t)need_max + need_max / 4 + 256);
+    if (cap > 8192) {
+        if (strict) return PANACHE_EINVAL;
+        cap = 8192;
+    }
+    const int32_t ng = (int32_t)gs.g.size();
+    PnSelGroup *dg = nullptr;
+    PnPick *dout = nullptr;
+    int32_t *dcnt = nullptr;
+    cudaStream_t st = ctx->st;
+    PN_CU(cudaMallocAsync((void **)&dg, sizeof(PnSelGroup) * ng, st));
+    PN_CU(cudaMallocAsync((void **)&dout, sizeof(PnPick) * (size_t)ng * kmax, st));
+    PN_CU(cudaMallocAsync((void **)&dcnt, sizeof(int32_t) * ng, st));
+    PN_CU(cudaMemcpyAsync(dg, gs.g.data(), sizeof(PnSelGroup) * ng, cudaMemcpyHostToDevice, st));
+    PN_CU(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
+    PnView v = make_view(ctx, R);
+    PN_CU(pn::launch_select(v, dg, ng, 0, R.total_cells, (int32_t)cap, ctx->cfg.eps0, kmax, dout, dcnt, R.flagbuf,
+                            ctx->sm_count * 8, st));
+    ctx->launches += 10;
+    std::vector<PnPick> hout((size_t)ng * kmax);
+    std::vector<int32_t> hcnt(ng);
+    int overflow = 0;
+    PN_CU(cudaMemcpyAsync(hout.data(), dout, sizeof(PnPick) * hout.size(), cudaMemcpyDeviceToHost, st));
+    PN_CU(cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int32_t) * ng, cudaMemcpyDeviceToHost, st));
+    PN_CU(cudaMemcpyAsync(&overflow, R.flagbuf, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PN_CU(cudaFreeAsync(dg, st));
+    PN_CU(cudaFreeAsync(dout, st));
+    PN_CU(cudaFreeAsync(dcnt, st));
+    PN_CU(cudaStreamSynchronize(st));
+    if (overflow && strict) return PANACHE_EPOOL;
+    for (int32_t gi = 0; gi < ng; ++gi)
+        picks[gi].assign(hout.begin() + (size_t)gi * kmax, hout.begin() + (size_t)gi * kmax + hcnt[gi]);
+    return PANACHE_OK;
+}
+
+// The whole path for a list of series; results per series.
+int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<std::vector<panache_motif>> &res) {
+    const panache_config &c = ctx->cfg;
+    for (auto &s : in) PN_TRY(check_series(s));
+    delete ctx->last;
+    ctx->last = nullptr;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->launches = 0;
+    PnRequest *Rp = new (std::nothrow) PnRequest();
+    if (!Rp) return PANACHE_ENOMEM;
+    ctx->last = Rp;
+    PnRequest &R = *Rp;
+    PN_TRY(plan(ctx, in, R));
+    ctx->stats.device_bytes = R.footprint;
+    cudaStream_t st = ctx->st;
+    R.st = st;
+    const int64_t nser = (int64_t)R.ser.size(), nanc = (int64_t)R.anc.size();
+
+    PN_CU(R.alloc(R.d_ser, nser));
+    PN_CU(R.alloc(R.d_anc, nanc));
+    PN_CU(R.alloc(R.d_lev, (int64_t)R.lev.size()));
+    PN_CU(R.alloc(R.d_blk_anchor, (int64_t)R.blk_anchor.size()));
+    PN_CU(R.alloc(R.d_blk_chunk0, (int64_t)R.blk_chunk0.size()));
+    PN_CU(R.alloc(R.d_slot_off, nanc));
+    PN_CU(R.alloc(R.x, R.total_samples));
+    PN_CU(R.alloc(R.xs, R.total_samples));
+    PN_CU(R.alloc(R.sq, R.total_samples + nser));
+    PN_CU(R.alloc(R.shift, nser));
+    PN_CU(R.alloc(R.runlen, R.total_samples));
+    PN_CU(R.alloc(R.F, R.total_rows * PN_FEAT));
+    PN_CU(R.alloc(R.sig, R.total_windows));
+    PN_CU(R.alloc(R.cnt, R.total_windows));
+    PN_CU(R.alloc(R.nclist, R.total_windows));
+    PN_CU(R.alloc(R.g, nanc * (c.B + 1) * PN_FEAT));
+    PN_CU(R.alloc(R.dir_keys, R.total_items));
+    PN_CU(R.alloc(R.dir_vals, R.total_items));
+    PN_CU(R.alloc(R.bstart, R.total_buckets + 1));
+    PN_CU(R.alloc(R.prof, R.total_cells));
+    PN_CU(R.alloc(R.stats, PN_ST_COUNT));
+    PN_CU(R.alloc(R.flagbuf, 4));
+
+    // tables and projections
+    std::vector<float> hg((size_t)nanc * (c.B + 1) * PN_FEAT);
+    for (int64_t a = 0; a < nanc; ++a) {
+        const std::vector<float> &g = ctx->proj(R.anc[a].a);
+        std::copy(g.begin(), g.end(), hg.begin() + a * (c.B + 1) * PN_FEAT);
+    }
+    PN_CU(cudaMemcpyAsync(R.d_ser, R.ser.data(), sizeof(PnSeries) * nser, cudaMemcpyHostToDevice, st));
+    if (nanc) {
+        PN_CU(cudaMemcpyAsync(R.d_anc, R.anc.data(), sizeof(PnAnchor) * nanc, cudaMemcpyHostToDevice, st));
+        PN_CU(cudaMemcpyAsync(R.d_lev, R.lev.data(), sizeof(PnLevel) * R.lev.size(), cudaMemcpyHostToDevice, st));
+        PN_CU(cudaMemcpyAsync(R.d_blk_anchor, R.blk_anchor.data(), 4 * R.blk_anchor.size(), cudaMemcpyHostToDevice,
+                              st));
+        PN_CU(cudaMemcpyAsync(R.d_blk_chunk0, R.blk_chunk0.data(), 4 * R.blk_chunk0.size(), cudaMemcpyHostToDevice,
+                              st));
+        PN_CU(cudaMemcpyAsync(R.d_slot_off, R.slot_off.data(), 8 * nanc, cudaMemcpyHostToDevice, st));
+        PN_CU(cudaMemcpyAsync(R.g, hg.data(), 4 * hg.size(), cudaMemcpyHostToDevice, st));
+    }
+    PN_CU(cudaMemsetAsync(R.prof, 0xFF, sizeof(unsigned long long) * std::max<int64_t>(1, R.total_cells), st));
+    PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
+
+    // samples: host inputs go through one staging buffer; device inputs are read in place
+    {
+        std::vector<PnConv> cv(nser);
+        int64_t stage_bytes = 0;
+        for (int64_t s = 0; s < nser; ++s) {
+            const int es = (in[s].dtype & 0xFF) == PANACHE_F32 ? 4 : 8;
+            if (!(in[s].dtype & PANACHE_DEVICE)) stage_bytes += ((in[s].n * es + 15) / 16) * 16;
+        }
+        unsigned char *stage = nullptr;
+        if (stage_bytes) PN_CU(cudaMallocAsync((void **)&stage, stage_bytes, st));
+        int64_t off = 0;
+        for (int64_t s = 0; s < nser; ++s) {
+            const int es = (in[s].dtype & 0xFF) == PANACHE_F32 ? 4 : 8;
+            cv[s].n = in[s].n;
+            cv[s].x_off = R.ser[s].x_off;
+            cv[s].dtype = in[s].dtype;
+            if (in[s].dtype & PANACHE_DEVICE) {
+                cv[s].src = in[s].ptr;
+            } else {
+                cv[s].src = stage + off;
+                if (in[s].n) PN_CU(cudaMemcpyAsync(stage + off, in[s].ptr, in[s].n * es, cudaMemcpyHostToDevice, st));
+                off += ((in[s].n * es + 15) / 16) * 16;
+            }
+        }
+        PnConv *dcv = nullptr;
+        PN_CU(cudaMallocAsync((void **)&dcv, sizeof(PnConv) * std::max<int64_t>(1, nser), st));
+        PN_CU(cudaMemcpyAsync(dcv, cv.data(), sizeof(PnConv) * nser, cudaMemcpyHostToDevice, st));
+        if (R.total_samples > 0) {
+            k_convert<<<(unsigned)((R.total_samples + 255) / 256), 256, 0, st>>>(dcv, (int32_t)nser, R.total_samples,
+                                                                                R.x, R.xs);
+            PN_CU(cudaGetLastError());
+            ctx->launches += 1;
+        }
+        PN_CU(cudaFreeAsync(dcv, st));
+        if (stage) PN_CU(cudaFreeAsync(stage, st));
+    }
+
+    PnView v = make_view(ctx, R);
+    const int grid = ctx->sm_count * 8;
+    // Algorithm 1 over every anchor of every series
+    PN_CU(pn::launch_runlen(v, R.total_samples, st));
+    PN_CU(pn::launch_moments(v, R.total_samples, R.sq, st));
+    PN_CU(pn::launch_features(v, R.d_blk_anchor, R.d_blk_chunk0, (int32_t)R.blk_anchor.size(), R.a_max, st));
+    PN_CU(pn::launch_ranks(v, R.total_windows, st));
+    PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
+    PN_CU(pn::launch_search(v, R.total_windows, grid, st));
+    ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3 + 1;
+    // Algorithm 2: sieve, completion rounds, final selection
+    int32_t ncls = 0;
+    if (!(c.flags & PANACHE_FLAG_NO_SIEVE)) {
+        PN_CU(pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w,
+                               (c.flags & PANACHE_FLAG_EXHAUSTIVE_SIEVE) ? 1 : 0, grid, st, &ncls));
+        ctx->launches += 6 + (ncls ? 4 + 2 * 12 : 0);
+    }
+    ctx->stats.hot_classes = (uint64_t)ncls;
+    std::vector<int> kser(nser), kseed(nser);
+    for (int64_t s = 0; s < nser; ++s) {
+        kser[s] = R.ser[s].k;
+        kseed[s] = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)R.ser[s].k, 6000 / (R.ser[s].m_max + 1)));
+    }
+    const GroupSet out_groups = make_groups(R, (int)c.topk_mode, kser);
+    if (!(c.flags & PANACHE_FLAG_NO_COMPLETION)) {
+        const GroupSet seed_global = make_groups(R, PANACHE_TOPK_GLOBAL, kseed);
+        PnSeed *dseeds = nullptr;
+        size_t seeds_cap = 0;
+        for (uint32_t round = 0; round < c.rounds; ++round) {
+            std::vector<PnSeed> seeds;
+            std::vector<std::vector<PnPick>> picks;
+            PN_TRY(run_select(ctx, R, out_groups, false, picks));
+            for (auto &gp : picks)
+                for (auto &p : gp) seeds.push_back(PnSeed{p.series, p.m, p.i, p.j});
+            if (c.topk_mode == PANACHE_TOPK_PER_LENGTH) {
+                PN_TRY(run_select(ctx, R, seed_global, false, picks));
+                for (auto &gp : picks)
+                    for (auto &p : gp) seeds.push_back(PnSeed{p.series, p.m, p.i, p.j});
+            }
+            if (seeds.empty()) break;
+            if (seeds.size() > seeds_cap) {
+                if (dseeds) PN_CU(cudaFreeAsync(dseeds, st));
+                seeds_cap = seeds.size();
+                PN_CU(cudaMallocAsync((void **)&dseeds, sizeof(PnSeed) * seeds_cap, st));
+            }
+            PN_CU(cudaMemcpyAsync(dseeds, seeds.data(), sizeof(PnSeed) * seeds.size(), cudaMemcpyHostToDevice, st));
+            PN_CU(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
+            PN_CU(pn::launch_complete(v, dseeds, (int32_t)seeds.size(), (int)c.dm, (int)c.dp, R.flagbuf, grid, st));
+            ctx->launches += 1;
+            int improved = 0;
+            PN_CU(cudaMemcpyAsync(&improved, R.flagbuf, sizeof(int), cudaMemcpyDeviceToHost, st));
+            PN_CU(cudaStreamSynchronize(st));
+            ctx->stats.completion_rounds = round + 1;
+            if (!improved) break;
+        }
+        if (dseeds) PN_CU(cudaFreeAsync(dseeds, st));
+    }
+    std::vector<std::vector<PnPick>> picks;
+    PN_TRY(run_select(ctx, R, out_groups, true, picks));
+    res.assign(nser, {});
+    for (size_t gi = 0; gi < picks.size(); ++gi) {
+        for (auto &p : picks[gi]) {
+            panache_motif mo;
+            mo.m = p.m;
+            mo._pad = 0;
+            mo.i = p.i;
+            mo.j = p.j;
+            mo.d = p.d;
+            res[out_groups.owner[gi]].push_back(mo);
+        }
+    }
+    unsigned long long hs[PN_ST_COUNT];
+    PN_CU(cudaMemcpyAsync(hs, R.stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    PN_CU(cudaStreamSynchronize(st));
+    ctx->stats.queries = hs[PN_ST_QUERIES];
+    ctx->stats.candidates = hs[PN_ST_CANDIDATES];
+    ctx->stats.exact_stream = hs[PN_ST_LB_PASSED];
+    ctx->stats.exact_sieve = hs[PN_ST_EXACT_SIEVE];
+    ctx->stats.exact_completion = hs[PN_ST_EXACT_COMPLETION];
+    ctx->stats.kernel_launches = ctx->launches;
+    return PANACHE_OK;
+}
+
+int copy_out(const std::vector<panache_motif> &m, panache_motif *out, int64_t cap, int64_t *out_len) {
+    if (out_len) *out_len = (int64_t)m.size();
+    if ((int64_t)m.size() > cap) return PANACHE_ETRUNC;
+    if (!m.empty()) {
+        if (!out) return PANACHE_EINVAL;
+        memcpy(out, m.data(), sizeof(panache_motif) * m.size());
+    }
+    return PANACHE_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int panache_default_config(panache_config *cfg) {
+    if (!cfg) return PANACHE_EINVAL;
+    memset(cfg, 0, sizeof(*cfg));
+    fill_defaults(*cfg);
+    return PANACHE_OK;
+}
+
+int panache_create(const panache_config *cfg, panache_ctx **out) {
+    if (!out) return PANACHE_EINVAL;
+    *out = nullptr;
+    panache_config c;
+    if (cfg) c = *cfg; else memset(&c, 0, sizeof(c));
+    fill_defaults(c);
+    PN_TRY(check_config(c));
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PANACHE_ENODEV;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return PANACHE_ENODEV;
+    if (prop.major != 10 || prop.minor != 3) return PANACHE_ENODEV;
+    panache_ctx *ctx = new (std::nothrow) panache_ctx();
+    if (!ctx) return PANACHE_ENOMEM;
+    ctx->cfg = c;
+    ctx->device = dev;
+    ctx->sm_count = prop.multiProcessorCount;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    if (cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return PANACHE_ECUDA;
+    }
+    ctx->st = ctx->own;
+    *out = ctx;
+    return PANACHE_OK;
+}
+
+void panache_destroy(panache_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    delete ctx->last;
+    if (ctx->own) cudaStreamDestroy(ctx->own);
+    delete ctx;
+}
+
+int panache_set_stream(panache_ctx *ctx, void *stream) {
+    if (!ctx) return PANACHE_EINVAL;
+    ctx->st = stream ? (cudaStream_t)stream : ctx->own;
+    return PANACHE_OK;
+}
+
+int panache_pmp(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min, int32_t m_max,
+                int32_t k, int32_t excl, panache_motif *out, int64_t out_cap, int64_t *out_len) {
+    if (!ctx || !out_len) return PANACHE_EINVAL;
+    std::vector<SeriesIn> in{SeriesIn{series, dtype, n, m_min, m_max, k, excl}};
+    std::vector<std::vector<panache_motif>> res;
+    PN_TRY(run_request(ctx, in, res));
+    return copy_out(res[0], out, out_cap, out_len);
+}
+
+int panache_pmp_batch(panache_ctx *ctx, const panache_request *reqs, int32_t nreq, panache_motif *out,
+                      int64_t out_cap_per_req, int64_t *out_len) {
+    if (!ctx || !reqs || nreq <= 0 || !out_len || out_cap_per_req < 0) return PANACHE_EINVAL;
+    std::vector<SeriesIn> in;
+    for (int32_t r = 0; r < nreq; ++r)
+        in.push_back(SeriesIn{reqs[r].series, reqs[r].dtype, reqs[r].n, reqs[r].m_min, reqs[r].m_max, reqs[r].k,
+                              reqs[r].excl});
+    std::vector<std::vector<panache_motif>> res;
+    PN_TRY(run_request(ctx, in, res));
+    int rc = PANACHE_OK;
+    for (int32_t r = 0; r < nreq; ++r) {
+        int e = copy_out(res[r], out ? out + (int64_t)r * out_cap_per_req : nullptr, out_cap_per_req, &out_len[r]);
+        if (e != PANACHE_OK) rc = e;
+    }
+    return rc;
+}
+
+int panache_stream_open(panache_ctx *ctx, int32_t m_min, int32_t m_max, int32_t k, int32_t excl,
+                        panache_stream **out) {
+    if (!ctx || !out) return PANACHE_EINVAL;
+    *out = nullptr;
+    SeriesIn probe{nullptr, PANACHE_F64, 0, m_min, m_max, k, excl};
+    PN_TRY(check_series(probe));
+    panache_stream *h = new (std::nothrow) panache_stream();
+    if (!h) return PANACHE_ENOMEM;
+    h->ctx = ctx;
+    h->m_min = m_min;
+    h->m_max = m_max;
+    h->k = k;
+    h->excl = excl;
+    *out = h;
+    return PANACHE_OK;
+}
+
+int panache_append(panache_stream *h, const void *chunk, int32_t dtype, int64_t len) {
+    if (!h || len < 0 || (len > 0 && !chunk)) return PANACHE_EINVAL;
+    const int dt = dtype & 0xFF;
+    if ((dt != PANACHE_F32 && dt != PANACHE_F64) || (dtype & ~0x1FF)) return PANACHE_EINVAL;
+    if (len == 0) return PANACHE_OK;
+    if (h->len + len > PN_MAX_SERIES_LEN) return PANACHE_EINVAL;
+    cudaStream_t st = h->ctx->st;
+    if (h->len + len > h->cap) {
+        int64_t nc = std::max<int64_t>(h->cap * 2, h->len + len);
+        nc = std::max<int64_t>(nc, 4096);
+        double *nd = nullptr;
+        PN_CU(cudaMalloc((void **)&nd, sizeof(double) * nc));
+        if (h->len) PN_CU(cudaMemcpyAsync(nd, h->dev, sizeof(double) * h->len, cudaMemcpyDeviceToDevice, st));
+        PN_CU(cudaStreamSynchronize(st));
+        cudaFree(h->dev);
+        h->dev = nd;
+        h->cap = nc;
+    }
+    std::vector<double> tmp;
+    const void *src = chunk;
+    if (dt == PANACHE_F32 || (dtype & PANACHE_DEVICE)) {
+        // widen on the host (host chunks) or copy back and widen (device chunks)
+        std::vector<float> f;
+        tmp.resize(len);
+        if (dt == PANACHE_F32) {
+            f.resize(len);
+            if (dtype & PANACHE_DEVICE)
+                PN_CU(cudaMemcpy(f.data(), chunk, 4 * len, cudaMemcpyDeviceToHost));
+            else
+                memcpy(f.data(), chunk, 4 * len);
+            for (int64_t t = 0; t < len; ++t) tmp[t] = f[t];
+        } else {
+            PN_CU(cudaMemcpy(tmp.data(), chunk, 8 * len, cudaMemcpyDeviceToHost));
+        }
+        src = tmp.data();
+    }
+    PN_CU(cudaMemcpyAsync(h->dev + h->len, src, sizeof(double) * len, cudaMemcpyHostToDevice, st));
+    PN_CU(cudaStreamSynchronize(st));
+    h->len += len;
+    return PANACHE_OK;
+}
+
+int panache_stream_topk(panache_stream *h, panache_motif *out, int64_t out_cap, int64_t *out_len) {
+    if (!h || !out_len) return PANACHE_EINVAL;
+    std::vector<SeriesIn> in{SeriesIn{h->dev, PANACHE_F64 | PANACHE_DEVICE, h->len, h->m_min, h->m_max, h->k, h->excl}};
+    if (h->len == 0) {
+        *out_len = 0;
+        return PANACHE_OK;
+    }
+    std::vector<std::vector<panache_motif>> res;
+    PN_TRY(run_request(h->ctx, in, res));
+    return copy_out(res[0], out, out_cap, out_len);
+}
+
+int64_t panache_stream_length(const panache_stream *h) { return h ? h->len : -1; }
+
+void panache_stream_close(panache_stream *h) {
+    if (!h) return;
+    if (h->dev) {
+        cudaStreamSynchronize(h->ctx->st);
+        cudaFree(h->dev);
+    }
+    delete h;
+}
+
+int panache_last_stats(const panache_ctx *ctx, panache_stats *out) {
+    if (!ctx || !out) return PANACHE_EINVAL;
+    *out = ctx->stats;
+    return PANACHE_OK;
+}
+
+int panache_profile_rows(const panache_ctx *ctx, int32_t series_index, uint64_t *keys, int64_t cap) {
+    if (!ctx || !keys) return PANACHE_EINVAL;
+    if (!ctx->last) return PANACHE_ESTATE;
+    const PnRequest &R = *ctx->last;
+    if (series_index < 0 || series_index >= (int32_t)R.ser.size()) return PANACHE_EINVAL;
+    const PnSeries &S = R.ser[series_index];
+    const int64_t cells = (int64_t)(S.m_max - S.m_min + 1) * S.n;
+    if (cap < cells) return PANACHE_ETRUNC;
+    PN_CU(cudaMemcpy(keys, R.prof + S.row_off, 8 * cells, cudaMemcpyDeviceToHost));
+    return PANACHE_OK;
+}
+
+int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *a_out,
+                         float *features, uint32_t *keys, int64_t cap_windows) {
+    if (!ctx) return PANACHE_EINVAL;
+    if (!ctx->last) return PANACHE_ESTATE;
+    const PnRequest &R = *ctx->last;
+    if (series_index < 0 || series_index >= (int32_t)R.ser.size()) return PANACHE_EINVAL;
+    const PnSeries &S = R.ser[series_index];
+    if (anchor_index < 0 || anchor_index >= S.anchor_count) return PANACHE_EINVAL;
+    const PnAnchor &A = R.anc[S.anchor_begin + anchor_index];
+    if (a_out) *a_out = A.a;
+    if ((features || keys) && cap_windows < A.nw) return PANACHE_ETRUNC;
+    const int C = (int)ctx->cfg.chunk;
+    if (features) {
+        std::vector<float> blk((size_t)A.nchunk * C * PN_FEAT);
+        PN_CU(cudaMemcpy(blk.data(), R.F + A.row_off * PN_FEAT, 4 * blk.size(), cudaMemcpyDeviceToHost));
+        for (int64_t q = 0; q < A.nw; ++q)
+            memcpy(features + q * PN_FEAT, blk.data() + pn_row(q, C, A.nchunk) * PN_FEAT, 4 * PN_FEAT);
+    }
+    if (keys) PN_CU(cudaMemcpy(keys, R.sig + A.win_off, 4 * A.nw, cudaMemcpyDeviceToHost));
+    return PANACHE_OK;
+}
+
+int panache_projections(const panache_config *cfg, int32_t a, float *g, int64_t cap) {
+    if (!g || a < 1) return PANACHE_EINVAL;
+    panache_config c;
+    if (cfg) c = *cfg; else memset(&c, 0, sizeof(c));
+    fill_defaults(c);
+    PN_TRY(check_config(c));
+    const int64_t need = (int64_t)(c.B + 1) * PN_FEAT;
+    if (cap < need) return PANACHE_ETRUNC;
+    pn::projections(a, c.seed, (int)c.B, (int)c.K, g);
+    return PANACHE_OK;
+}
+
+const char *panache_strerror(int code) {
+    switch (code) {
+        case PANACHE_OK: return "ok";
+        case PANACHE_EINVAL: return "invalid argument";
+        case PANACHE_ENOMEM: return "out of memory";
+        case PANACHE_EBUDGET: return "request exceeds the HBM budget (admission refused)";
+        case PANACHE_ECUDA: return "CUDA error";
+        case PANACHE_ETRUNC: return "output buffer too small";
+        case PANACHE_ESTATE: return "invalid state for this call";
+        case PANACHE_EPOOL: return "top-k selection pool overflow";
+        case PANACHE_ENODEV: return "no sm_103 CUDA device";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Shared device helpers of the Panache CUDA path (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define PN_WARP 32
+#define PN_FEAT 32            // floats per feature row: 2(K-1) <= 30 used, padded to 32 (128 B)
+#define PN_MAXB 24            // signature bits
+#define PN_MAXK 16            // spectral width K (bins 1..K-1 kept)
+
+// ---------------------------------------------------------------------------
+// Profile cells.  A cell (m, i) holds one 64-bit key: the non-negative
+// distance's IEEE-754 double bit pattern with its low PN_IDX_BITS bits
+// replaced by the partner's start index.  For non-negative doubles the bit
+// pattern is monotone in the value, so an unsigned atomicMin keeps the
+// smallest distance and, among equal (truncated) distances, the lowest
+// partner index -- the tie rule of the exact profile (Sec. 2).  The stored
+// distance is the true one truncated to 64 - PN_IDX_BITS bits (relative
+// resolution 2^-26); reported distances are recomputed in FP64.
+// ---------------------------------------------------------------------------
+#define PN_IDX_BITS 26
+#define PN_IDX_MASK ((1ull << PN_IDX_BITS) - 1ull)
+#define PN_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+#define PN_MAX_SERIES_LEN ((int64_t)PN_IDX_MASK)   // partner index 2^26-1 is reserved
+
+__host__ __device__ __forceinline__ uint64_t pn_pack(double d, uint32_t idx) {
+#ifdef __CUDA_ARCH__
+    uint64_t b = (uint64_t)__double_as_longlong(d);
+#else
+    uint64_t b;
+    __builtin_memcpy(&b, &d, 8);
+#endif
+    return (b & ~PN_IDX_MASK) | (uint64_t)idx;
+}
+
+__host__ __device__ __forceinline__ double pn_key_dist(uint64_t key) {
+    uint64_t b = key & ~PN_IDX_MASK;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double d;
+    __builtin_memcpy(&d, &b, 8);
+    return d;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint32_t pn_key_idx(uint64_t key) { return (uint32_t)(key & PN_IDX_MASK); }
+
+__device__ __forceinline__ float pn_warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double pn_warp_sumd(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Orderable unsigned image of a float (ascending float order -> ascending uint order).
+__device__ __forceinline__ uint32_t pn_float_order(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Number of retained non-DC bins at length m: K' = min(K-1, ceil(m/2)-1) (Sec. 3.2).
+__host__ __device__ __forceinline__ int pn_kprime(int m, int K) {
+    int c = (m + 1) / 2 - 1;
+    int k = K - 1 < c ? K - 1 : c;
+    return k < 0 ? 0 : k;
+}
+
+// Global depth after P insertions: smallest d >= 0 with P <= alpha 2^d, capped at B (Sec. 3.4).
+__host__ __device__ __forceinline__ int pn_depth(int64_t P, int alpha, int B) {
+    int d = 0;
+    while (d < B && P > ((int64_t)alpha << d)) ++d;
+    return d;
+}

@@ -1,0 +1,517 @@
+// Emit stage (Sec. 3.6, Algorithm 2): hot-class sieve, local completion and
+// the zero-snapped top-k selection with FP64 re-verification.
+#include "distance.cuh"
+#include "emit.cuh"
+#include "prims.cuh"
+
+namespace pn {
+namespace {
+
+inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// ---------------------------------------------------------------------------
+// Hot classes: buckets of an anchor's final directory (depth(N)) that hold
+// more than R entries -- classes no budgeted scan covered (Sec. 3.6).
+// ---------------------------------------------------------------------------
+__global__ void k_hot_flags(PnView v, const int64_t *slot_off, int64_t total, uint32_t *flag, uint32_t *size) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int ai = pn_find(slot_off, v.nanchors, t, [](int64_t o) { return o; });
+    const PnAnchor &A = v.anchors[ai];
+    uint32_t N = v.cnt[A.win_off + A.nw - 1];
+    int D = pn_depth(N, v.alpha, v.B);
+    int64_t b = t - slot_off[ai];
+    uint32_t f = 0, sz = 0;
+    if (b < ((int64_t)1 << D)) {
+        const PnLevel &L = v.levels[A.level_begin + D];
+        int64_t gb = L.bucket_base + b;
+        uint32_t c = v.bstart[gb + 1] - v.bstart[gb];
+        if ((int)c > v.R) {
+            f = 1;
+            sz = c;
+        }
+    }
+    flag[t] = f;
+    size[t] = sz;
+}
+
+__global__ void k_hot_compact(PnView v, const int64_t *slot_off, int64_t total, const uint32_t *flag,
+                              const uint32_t *cid, const uint32_t *moff, PnClass *cls) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total || !flag[t]) return;
+    int ai = pn_find(slot_off, v.nanchors, t, [](int64_t o) { return o; });
+    const PnAnchor &A = v.anchors[ai];
+    uint32_t N = v.cnt[A.win_off + A.nw - 1];
+    int D = pn_depth(N, v.alpha, v.B);
+    const PnLevel &L = v.levels[A.level_begin + D];
+    int64_t gb = L.bucket_base + (t - slot_off[ai]);
+    PnClass c;
+    c.anchor = ai;
+    c.lo = v.bstart[gb];
+    c.size = v.bstart[gb + 1] - v.bstart[gb];
+    c.moff = moff[t];
+    cls[cid[t]] = c;
+}
+
+// Sort key of a member: its projection on the sieve direction g_{a,B+1}.
+__global__ void k_sieve_keys(PnView v, const PnClass *cls, int32_t ncls, int64_t total, uint32_t *keys,
+                             uint32_t *vals) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int ci = pn_find(cls, ncls, t, [](const PnClass &c) { return (int64_t)c.moff; });
+    const PnClass &c = cls[ci];
+    const PnAnchor &A = v.anchors[c.anchor];
+    uint32_t x = v.dir_vals[c.lo + (t - c.moff)];
+    const float *f = v.F + (A.row_off + pn_row(x, v.C, A.nchunk)) * PN_FEAT;
+    const float *g = v.g + ((int64_t)c.anchor * (v.B + 1) + v.B) * PN_FEAT;
+    keys[t] = pn_float_order(pn_margin(g, f, 2 * (v.K - 1)));
+    vals[t] = (uint32_t)t;
+}
+
+// After the projection sort: re-key by class (second stable sort) and carry the start.
+__global__ void k_sieve_rekey(PnView v, const PnClass *cls, int32_t ncls, int64_t total, uint32_t *keys,
+                              uint32_t *vals) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    uint32_t t = vals[p];
+    int ci = pn_find(cls, ncls, (int64_t)t, [](const PnClass &c) { return (int64_t)c.moff; });
+    const PnClass &c = cls[ci];
+    keys[p] = (uint32_t)ci;
+    vals[p] = v.dir_vals[c.lo + (t - c.moff)];
+}
+
+// One warp per sorted member u: pairs (u, v) with u < v <= u + w (or every
+// v > u in the exhaustive variant), valid pairs only, bound-filtered, exact.
+__global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_t total, const uint32_t *members,
+                              int w, int exhaustive) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float shrink = 1.0f - v.lam;
+    unsigned long long n_ex = 0;
+    for (int64_t p = wid; p < total; p += nw) {
+        const int ci = pn_find(cls, ncls, p, [](const PnClass &c) { return (int64_t)c.moff; });
+        const PnClass &c = cls[ci];
+        const PnAnchor &A = v.anchors[c.anchor];
+        const int s = A.series;
+        const PnSeries &S = v.series[s];
+        const int a = A.a;
+        const int64_t u = p - c.moff;
+        const int64_t vend = exhaustive ? (int64_t)c.size : min((int64_t)c.size, u + 1 + w);
+        const uint32_t xu = members[p];
+        const float *Fa = v.F + A.row_off * PN_FEAT;
+        const float fu = Fa[pn_row(xu, v.C, A.nchunk) * PN_FEAT + lane];
+        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
+        const PnWin wu = pn_window(v, s, xu, a);
+        for (int64_t v0 = u + 1; v0 < vend; v0 += 32) {
+            const int64_t vi = v0 + lane;
+            uint32_t xv = 0;
+            const float *fv = nullptr;
+            if (vi < vend) {
+                xv = members[c.moff + vi];
+                if (llabs((int64_t)xv - (int64_t)xu) >= S.excl) fv = Fa + pn_row(xv, v.C, A.nchunk) * PN_FEAT;
+            }
+            float acc = 0.0f;
+            for (int t = 0; t < PN_FEAT; ++t) {
+                const float ut = __shfl_sync(0xffffffffu, fu, t);
+                if (fv) {
+                    const float dfe = ut - fv[t];
+                    acc = fmaf(dfe, dfe, acc);
+                }
+            }
+            bool surv = false;
+            if (fv) {
+                const float lb = sqrtf(2.0f / (float)a * acc);
+                const double thr = fmax(pn_cell_dist(__ldcg(&prow[xu])), pn_cell_dist(__ldcg(&prow[xv])));
+                surv = (double)(shrink * lb) < thr;
+            }
+            uint32_t sm = __ballot_sync(0xffffffffu, surv);
+            while (sm) {
+                const int src = __ffs(sm) - 1;
+                sm &= sm - 1;
+                const uint32_t xx = __shfl_sync(0xffffffffu, xv, src);
+                const PnWin wx = pn_window(v, s, xx, a);
+                const double dd = pn_dist_warp(v, S.x_off, a, xu, wu, xx, wx, lane);
+                n_ex += 1;
+                if (lane == 0 && dd < __longlong_as_double(0x7ff0000000000000ll)) {
+                    atomicMin(&prow[xu], pn_pack(dd, xx));
+                    atomicMin(&prow[xx], pn_pack(dd, xu));
+                }
+            }
+        }
+    }
+    if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);
+}
+
+// ---------------------------------------------------------------------------
+// Local completion (Sec. 3.6): for each seed (m0, i0, j0) every admissible
+// (m, i, j) with |m-m0| <= dm, |i-i0| <= dp, |j-j0| <= dp, |i-j| >= excl is
+// evaluated exactly; both cells take the distance, and the partner written
+// is the hint later rounds re-cut from.  One block (8 warps) per seed.
+// ---------------------------------------------------------------------------
+__global__ void k_complete(PnView v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    unsigned long long n_ex = 0;
+    int imp = 0;
+    for (int sd = blockIdx.x; sd < nseeds; sd += gridDim.x) {
+        const PnSeed sdv = seeds[sd];
+        const int s = sdv.series;
+        const PnSeries &S = v.series[s];
+        const int side = 2 * dp + 1;
+        const int ntrip = (2 * dm + 1) * side * side;
+        for (int t = warp; t < ntrip; t += nwarps) {
+            const int tm = t / (side * side);
+            const int rem = t - tm * side * side;
+            const int m = sdv.m + tm - dm;
+            const int64_t i = sdv.i + rem / side - dp;
+            const int64_t j = sdv.j + rem % side - dp;
+            if (m < S.m_min || m > S.m_max) continue;
+            if (i < 0 || j < 0 || i > S.n - m || j > S.n - m) continue;
+            if (llabs(i - j) < S.excl) continue;
+            if (v.runlen[S.x_off + i] >= m || v.runlen[S.x_off + j] >= m) continue;
+            const PnWin wi = pn_window(v, s, i, m);
+            const PnWin wj = pn_window(v, s, j, m);
+            const double dd = pn_dist_warp(v, S.x_off, m, i, wi, j, wj, lane);
+            n_ex += 1;
+            if (lane == 0 && dd < __longlong_as_double(0x7ff0000000000000ll)) {
+                unsigned long long *row = v.prof + S.row_off + (int64_t)(m - S.m_min) * S.n;
+                const unsigned long long ki = pn_pack(dd, (uint32_t)j), kj = pn_pack(dd, (uint32_t)i);
+                if (atomicMin(&row[i], ki) > ki) imp = 1;
+                if (atomicMin(&row[j], kj) > kj) imp = 1;
+            }
+        }
+    }
+    if (lane == 0) {
+        if (imp) atomicExch(improved, 1);
+        if (v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_COMPLETION], n_ex);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Top-k selection (Sec. 2, Algorithm 2 last step).
+//
+// A selection group is one series (global mode) or one length row of a
+// series (per-length mode).  Each accepted cell suppresses at most m+1 cells
+// of its length, so the first k accepted cells lie among the k(m_max+1)
+// smallest cells: a two-level radix select on the key bits picks a
+// threshold covering that many cells (plus one bin of slack for the
+// in-stream rounding), the cells under it are pooled, their distances are
+// recomputed in FP64 from two-pass moments, snapped to 0 below eps0, sorted
+// by (d, m, i) and scanned greedily under the m/2 rule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sel_bits(unsigned long long key, double eps0, int level) {
+    double d = pn_key_dist(key);
+    unsigned long long b = d < eps0 ? 0ull : (key & ~PN_IDX_MASK);
+    return level == 0 ? (uint32_t)(b >> 51) & 0xFFFu : (uint32_t)(b >> 39) & 0xFFFu;
+}
+
+__device__ __forceinline__ int group_of(const PnView &v, const PnSelGroup *grp, int32_t ngrp, int64_t cell) {
+    return pn_find(grp, ngrp, cell, [](const PnSelGroup &g) { return g.cell_off; });
+}
+
+__global__ void k_sel_hist(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_t total, double eps0, int level,
+                           const uint32_t *b1, uint32_t *hist) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = t < total;
+    unsigned long long key = ok ? v.prof[t] : PN_EMPTY_KEY;
+    int gi = 0;
+    uint32_t bin = 0;
+    if (ok) {
+        gi = group_of(v, grp, ngrp, t);
+        ok = key != PN_EMPTY_KEY && t < grp[gi].cell_off + grp[gi].ncell;
+    }
+    if (ok && level == 1) ok = sel_bits(key, eps0, 0) == b1[gi];
+    if (ok) bin = sel_bits(key, eps0, level);
+    unsigned long long tag = ok ? (((unsigned long long)gi << 12) | bin) : (0xFFFFFFFF00000000ull | threadIdx.x);
+    unsigned peers = __match_any_sync(0xffffffffu, tag);
+    if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[(int64_t)gi * 4096 + bin], (uint32_t)__popc(peers));
+}
+
+// One thread per group: first bin whose cumulative count reaches `need`.
+__global__ void k_sel_pick(const PnSelGroup *grp, int32_t ngrp, const uint32_t *hist, const uint32_t *carry_in,
+                           uint32_t *bin_out, uint32_t *carry_out) {
+    int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ngrp) return;
+    uint32_t need = grp[gi].need;
+    uint32_t run = carry_in ? carry_in[gi] : 0u;
+    uint32_t b = 4095;
+    for (int t = 0; t < 4096; ++t) {
+        uint32_t c = hist[(int64_t)gi * 4096 + t];
+        if (run + c >= need) {
+            b = t;
+            break;
+        }
+        run += c;
+    }
+    bin_out[gi] = b;
+    if (carry_out) carry_out[gi] = run;
+}
+
+__global__ void k_sel_pool(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_t total, double eps0,
+                           const uint32_t *b1, const uint32_t *b2, PnPoolEntry *pool, uint32_t *pool_cnt,
+                           int32_t cap, int *overflow) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    unsigned long long key = v.prof[t];
+    if (key == PN_EMPTY_KEY) return;
+    int gi = group_of(v, grp, ngrp, t);
+    if (t >= grp[gi].cell_off + grp[gi].ncell) return;
+    uint32_t h = (sel_bits(key, eps0, 0) << 12) | sel_bits(key, eps0, 1);
+    uint32_t thr = (b1[gi] << 12) | b2[gi];
+    if (h > thr + 1u) return;
+    uint32_t slot = atomicAdd(&pool_cnt[gi], 1u);
+    if ((int32_t)slot >= cap) {
+        atomicExch(overflow, 1);
+        return;
+    }
+    PnPoolEntry e;
+    e.cell = (uint32_t)(t - grp[gi].cell_off);
+    e.j = pn_key_idx(key);
+    e.d = pn_key_dist(key);
+    pool[(int64_t)gi * cap + slot] = e;
+}
+
+// FP64 two-pass distance of every pooled cell (one warp per entry).
+__global__ void k_sel_verify(PnView v, const PnSelGroup *grp, int32_t ngrp, PnPoolEntry *pool,
+                             const uint32_t *pool_cnt, int32_t cap, double eps0) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = (int64_t)ngrp * cap;
+    for (int64_t e = wid; e < total; e += nwp) {
+        const int gi = (int)(e / cap);
+        const int slot = (int)(e - (int64_t)gi * cap);
+        if (slot >= (int)min(pool_cnt[gi], (uint32_t)cap)) continue;
+        const PnSelGroup &G = grp[gi];
+        const PnSeries &S = v.series[G.series];
+        PnPoolEntry &pe = pool[e];
+        const int64_t cell = (int64_t)pe.cell + (G.cell_off - S.row_off);
+        const int m = S.m_min + (int)(cell / S.n);
+        const int64_t i = cell % S.n, j = pe.j;
+        const double *xi = v.x + S.x_off + i, *xj = v.x + S.x_off + j;
+        double si = 0, sj = 0;
+        for (int r = lane; r < m; r += 32) {
+            si += xi[r];
+            sj += xj[r];
+        }
+        const double mi = pn_warp_sumd(si) / m, mj = pn_warp_sumd(sj) / m;
+        double qi = 0, qj = 0;
+        for (int r = lane; r < m; r += 32) {
+            qi += (xi[r] - mi) * (xi[r] - mi);
+            qj += (xj[r] - mj) * (xj[r] - mj);
+        }
+        const double ii = 1.0 / sqrt(pn_warp_sumd(qi) / m), ij = 1.0 / sqrt(pn_warp_sumd(qj) / m);
+        double acc = 0;
+        for (int r = lane; r < m; r += 32) {
+            const double dz = (xi[r] - mi) * ii - (xj[r] - mj) * ij;
+            acc += dz * dz;
+        }
+        const double d = sqrt(pn_warp_sumd(acc));
+        if (lane == 0) pe.d = d < eps0 ? 0.0 : d;
+    }
+}
+
+__device__ __forceinline__ bool pool_less(const PnPoolEntry &a, const PnPoolEntry &b) {
+    return a.d < b.d || (a.d == b.d && a.cell < b.cell);
+}
+
+// One block per group: bitonic sort of the pool in shared memory, then a
+// greedy scan by warp 0 under the m/2 rule.
+__global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry *pool, const uint32_t *pool_cnt,
+                             int32_t cap, int32_t npow2, PnPick *out, int32_t *out_cnt, int32_t kmax) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    PnPoolEntry *e = reinterpret_cast<PnPoolEntry *>(smem);
+    int32_t *acc_m = reinterpret_cast<int32_t *>(e + npow2);
+    int64_t *acc_i = reinterpret_cast<int64_t *>(acc_m + kmax + (kmax & 1));
+    const int gi = blockIdx.x;
+    const PnSelGroup G = grp[gi];
+    const PnSeries &S = v.series[G.series];
+    const int cnt = (int)min(pool_cnt[gi], (uint32_t)cap);
+    for (int t = threadIdx.x; t < npow2; t += blockDim.x) {
+        if (t < cnt) {
+            e[t] = pool[(int64_t)gi * cap + t];
+        } else {
+            e[t].d = __longlong_as_double(0x7ff0000000000000ll);
+            e[t].cell = 0xFFFFFFFFu;
+            e[t].j = 0;
+        }
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= npow2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = threadIdx.x; t < npow2; t += blockDim.x) {
+                int p = t ^ jj;
+                if (p > t) {
+                    bool up = (t & kk) == 0;
+                    PnPoolEntry A = e[t], Bv = e[p];
+                    if (pool_less(Bv, A) == up) {
+                        e[t] = Bv;
+                        e[p] = A;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int nacc = 0;
+        const int k = min(G.k, kmax);
+        const int64_t base = G.cell_off - S.row_off;
+        for (int t = 0; t < cnt && nacc < k; ++t) {
+            const int64_t cell = base + e[t].cell;
+            const int m = S.m_min + (int)(cell / S.n);
+            const int64_t i = cell % S.n;
+            bool clash = false;
+            for (int u = lane; u < nacc; u += 32)
+                if (acc_m[u] == m && 2 * llabs(i - acc_i[u]) <= m) clash = true;
+            clash = __any_sync(0xffffffffu, clash);
+            if (!clash) {
+                if (lane == 0) {
+                    acc_m[nacc] = m;
+                    acc_i[nacc] = i;
+                    PnPick pk;
+                    pk.series = G.series;
+                    pk.m = m;
+                    pk.i = i;
+                    pk.j = e[t].j;
+                    pk.d = e[t].d;
+                    out[(int64_t)gi * kmax + nacc] = pk;
+                }
+                ++nacc;
+                __syncwarp();
+            }
+        }
+        if (lane == 0) out_cnt[gi] = nacc;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t total_slots, int w, int exhaustive,
+                         int grid_blocks, cudaStream_t st, int32_t *n_classes_out) {
+    *n_classes_out = 0;
+    if (total_slots <= 0) return cudaSuccess;
+    uint32_t *flag = nullptr, *size = nullptr, *cid = nullptr, *moff = nullptr, *tot = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&flag, 4 * total_slots, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&size, 4 * total_slots, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&cid, 4 * total_slots, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&moff, 4 * total_slots, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot, 8, st);
+    if (e == cudaSuccess) {
+        k_hot_flags<<<grid_for(total_slots, 256), 256, 0, st>>>(v, slot_off_dev, total_slots, flag, size);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = excl_scan_u32(flag, cid, total_slots, tot, st);
+    if (e == cudaSuccess) e = excl_scan_u32(size, moff, total_slots, tot + 1, st);
+    uint32_t h_tot[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_tot, tot, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const int32_t ncls = (int32_t)h_tot[0];
+    const int64_t nmem = (int64_t)h_tot[1];
+    PnClass *cls = nullptr;
+    uint32_t *keys = nullptr, *vals = nullptr;
+    if (e == cudaSuccess && ncls > 0) {
+        e = cudaMallocAsync((void **)&cls, sizeof(PnClass) * ncls, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&keys, 4 * nmem, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&vals, 4 * nmem, st);
+        if (e == cudaSuccess) {
+            k_hot_compact<<<grid_for(total_slots, 256), 256, 0, st>>>(v, slot_off_dev, total_slots, flag, cid, moff,
+                                                                      cls);
+            k_sieve_keys<<<grid_for(nmem, 256), 256, 0, st>>>(v, cls, ncls, nmem, keys, vals);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, nmem, 32, st);
+        if (e == cudaSuccess) {
+            k_sieve_rekey<<<grid_for(nmem, 256), 256, 0, st>>>(v, cls, ncls, nmem, keys, vals);
+            e = cudaGetLastError();
+        }
+        int cbits = 1;
+        while (cbits < 32 && ((int64_t)1 << cbits) <= ncls) ++cbits;
+        if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, nmem, cbits, st);
+        if (e == cudaSuccess) {
+            int64_t warps_needed = nmem;
+            int64_t blocks = (warps_needed + 7) / 8;
+            if (blocks > grid_blocks) blocks = grid_blocks;
+            k_sieve_pairs<<<(unsigned)blocks, 256, 0, st>>>(v, cls, ncls, nmem, vals, w, exhaustive);
+            e = cudaGetLastError();
+        }
+    }
+    *n_classes_out = ncls;
+    if (cls) cudaFreeAsync(cls, st);
+    if (keys) cudaFreeAsync(keys, st);
+    if (vals) cudaFreeAsync(vals, st);
+    cudaFreeAsync(flag, st);
+    cudaFreeAsync(size, st);
+    cudaFreeAsync(cid, st);
+    cudaFreeAsync(moff, st);
+    cudaFreeAsync(tot, st);
+    return e;
+}
+
+cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved,
+                            int grid_blocks, cudaStream_t st) {
+    if (nseeds <= 0) return cudaSuccess;
+    int g = nseeds < grid_blocks ? nseeds : grid_blocks;
+    k_complete<<<g, 256, 0, st>>>(v, seeds, nseeds, dm, dp, improved);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ngrp, int64_t cell_begin,
+                          int64_t cell_end, int32_t cap, double eps0, int32_t kmax, PnPick *out, int32_t *out_cnt,
+                          int *overflow, int grid_blocks, cudaStream_t st) {
+    if (ngrp <= 0) return cudaSuccess;
+    (void)cell_begin;
+    const int64_t total = cell_end;
+    uint32_t *hist = nullptr, *b1 = nullptr, *b2 = nullptr, *carry = nullptr, *pcnt = nullptr;
+    PnPoolEntry *pool = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&hist, sizeof(uint32_t) * 4096 * ngrp, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&b1, 4 * ngrp, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&b2, 4 * ngrp, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&carry, 4 * ngrp, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&pcnt, 4 * ngrp, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&pool, sizeof(PnPoolEntry) * (int64_t)cap * ngrp, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4096 * ngrp, st);
+    if (e == cudaSuccess) {
+        k_sel_hist<<<grid_for(total, 256), 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, 0, nullptr, hist);
+        k_sel_pick<<<grid_for(ngrp, 128), 128, 0, st>>>(grp_dev, ngrp, hist, nullptr, b1, carry);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4096 * ngrp, st);
+    if (e == cudaSuccess) {
+        k_sel_hist<<<grid_for(total, 256), 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, 1, b1, hist);
+        k_sel_pick<<<grid_for(ngrp, 128), 128, 0, st>>>(grp_dev, ngrp, hist, carry, b2, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(pcnt, 0, 4 * ngrp, st);
+    if (e == cudaSuccess) {
+        k_sel_pool<<<grid_for(total, 256), 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, b1, b2, pool, pcnt, cap,
+                                                          overflow);
+        int64_t vw = (int64_t)ngrp * cap;
+        int64_t vb = (vw + 7) / 8;
+        if (vb > grid_blocks) vb = grid_blocks;
+        k_sel_verify<<<(unsigned)vb, 256, 0, st>>>(v, grp_dev, ngrp, pool, pcnt, cap, eps0);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        int npow2 = 1;
+        while (npow2 < cap) npow2 <<= 1;
+        size_t sm = sizeof(PnPoolEntry) * npow2 + sizeof(int32_t) * (kmax + 1) + sizeof(int64_t) * kmax + 16;
+        e = cudaFuncSetAttribute(k_sel_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess) {
+            k_sel_greedy<<<ngrp, 1024, sm, st>>>(v, grp_dev, pool, pcnt, cap, npow2, out, out_cnt, kmax);
+            e = cudaGetLastError();
+        }
+    }
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(b1, st);
+    cudaFreeAsync(b2, st);
+    cudaFreeAsync(carry, st);
+    cudaFreeAsync(pcnt, st);
+    cudaFreeAsync(pool, st);
+    return e;
+}
+
+}  // namespace pn

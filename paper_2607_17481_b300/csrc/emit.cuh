@@ -1,0 +1,50 @@
+// Emit-stage records and launch wrappers (Sec. 3.6, Algorithm 2).
+#pragma once
+#include "kernels.cuh"
+
+struct PnClass {          // one hot class: a final-depth bucket larger than R
+    int32_t anchor;
+    uint32_t lo;          // first sorted directory item of the bucket
+    uint32_t size;        // members
+    uint32_t moff;        // first member in the flat member space
+};
+
+struct PnSeed {           // a completion seed: cell (m, i) of a series and its neighbour j
+    int32_t series;
+    int32_t m;
+    int64_t i;
+    int64_t j;
+};
+
+struct PnSelGroup {       // one top-k selection group
+    int64_t cell_off;     // first profile cell of the group
+    int64_t ncell;        // cells in the group
+    int32_t series;
+    int32_t k;            // motifs wanted
+    uint32_t need;        // pool size that must be covered: k (m_max + 1)
+    int32_t _pad;
+};
+
+struct PnPoolEntry {
+    double d;             // in-stream distance, then the FP64 verified and zero-snapped one
+    uint32_t cell;        // cell offset inside the group ((m - m_min) n + i for a series group)
+    uint32_t j;           // neighbour
+};
+
+struct PnPick {           // one selected motif
+    int32_t series;
+    int32_t m;
+    int64_t i;
+    int64_t j;
+    double d;
+};
+
+namespace pn {
+cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t total_slots, int w, int exhaustive,
+                         int grid_blocks, cudaStream_t st, int32_t *n_classes_out);
+cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved,
+                            int grid_blocks, cudaStream_t st);
+cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ngrp, int64_t cell_begin,
+                          int64_t cell_end, int32_t cap, double eps0, int32_t kmax, PnPick *out, int32_t *out_cnt,
+                          int *overflow, int grid_blocks, cudaStream_t st);
+}  // namespace pn

@@ -1,0 +1,106 @@
+// Kernel-side view of one request and the launch wrappers of every step.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "plan.h"
+
+// Everything a kernel needs to know about a request, passed by value.
+struct PnView {
+    // tables
+    const PnSeries *series;
+    const PnAnchor *anchors;
+    const PnLevel *levels;
+    int32_t nseries, nanchors, nlevels;
+    int32_t B;            // signature bits
+    int32_t K;            // spectral width
+    int32_t C;            // chunk length of the feature kernel (slides per direct-DFT anchor)
+    int32_t alpha;        // occupancy target
+    int32_t R;            // verification budget gamma * alpha
+    int32_t d0;           // probe reference depth
+    int32_t probe_cap;    // implementation cap on Hamming-1 probes
+    int32_t beta;         // batch length (samples) of the streaming schedule
+    float lam;            // bound shrink lambda
+    int32_t precision;    // 0 plain FP64, 1 mixed
+    // samples
+    const double *x;      // samples widened to FP64, concatenated over series
+    const float2 *xs;     // samples as (hi, lo) float pairs: hi + lo == x to ~2^-48
+    const double2 *sq;    // per series n+1 prefix sums (sum, sum of squares) of x - shift
+    const double *shift;  // per series shift subtracted before the prefix sums
+    const int32_t *runlen;// equal-value run length from each sample, capped at the series' m_max
+    // per-window arrays (indexed by anchor.win_off + q)
+    float *F;             // feature rows, anchor.row_off + row(q), PN_FEAT floats each
+    uint32_t *sig;        // B-bit SimHash keys
+    uint32_t *cnt;        // inclusive count of non-constant windows with start <= q
+    uint32_t *nclist;     // start of the r-th non-constant window
+    const float *g;       // projections [nanchors][B+1][PN_FEAT]
+    // directory
+    uint32_t *dir_keys;   // global bucket id of every item (sorted)
+    uint32_t *dir_vals;   // window start of every item (sorted by (bucket, start))
+    uint32_t *bstart;     // first sorted item of every global bucket (+1 sentinel)
+    // profile rows, PN_EMPTY_KEY when unset
+    unsigned long long *prof;
+    // counters (device)
+    unsigned long long *stats;
+};
+
+enum PnStat {
+    PN_ST_QUERIES = 0,
+    PN_ST_CANDIDATES,
+    PN_ST_LB_PASSED,
+    PN_ST_EXACT_SIEVE,
+    PN_ST_EXACT_COMPLETION,
+    PN_ST_HOT_CLASSES,
+    PN_ST_IMPROVED,
+    PN_ST_COUNT
+};
+
+// Window row inside an anchor's feature block: windows are interleaved by
+// chunk, row(q) = (q mod C) * nchunk + q / C, so that the chunks advanced in
+// lock-step by one warp write one contiguous run of rows.
+__host__ __device__ __forceinline__ int64_t pn_row(int64_t q, int32_t C, int64_t nchunk) {
+    return (q % C) * nchunk + q / C;
+}
+
+// <g_l, F> in a fixed order of fused multiply-adds; the feature kernel and
+// the query kernel both call this, so their margins agree bit for bit.
+__device__ __forceinline__ float pn_margin(const float *g, const float *f, int dims) {
+    float acc = 0.0f;
+    for (int t = 0; t < dims; ++t) acc = fmaf(g[t], f[t], acc);
+    return acc;
+}
+
+// Binary search: index of the last table entry whose `off` is <= key.
+template <class T, class F>
+__device__ __forceinline__ int pn_find(const T *tab, int count, int64_t key, F off) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off(tab[mid]) <= key) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Window moments from the FP64 prefix sums (Sec. 3.2: mu = S/m, sigma^2 = Q/m - mu^2),
+// of the shifted samples; returns mu of the unshifted window.
+__device__ __forceinline__ void pn_moments(const PnView &v, int s, int64_t i, int m, double &mu, double &var) {
+    const PnSeries &se = v.series[s];
+    const double2 *p = v.sq + se.x_off + s;
+    double2 a = p[i], b = p[i + m];
+    double ms = (b.x - a.x) / m;
+    var = (b.y - a.y) / m - ms * ms;
+    mu = ms + v.shift[s];
+}
+
+namespace pn {
+cudaError_t launch_runlen(const PnView &v, int64_t total, cudaStream_t st);
+cudaError_t launch_moments(const PnView &v, int64_t total, double2 *sq_out, cudaStream_t st);
+size_t features_smem(int a_max, int B);
+cudaError_t launch_features(const PnView &v, const int32_t *blk_anchor, const int32_t *blk_chunk0,
+                            int32_t nblocks, int a_max, cudaStream_t st);
+cudaError_t launch_ranks(const PnView &v, int64_t total_windows, cudaStream_t st);
+cudaError_t launch_directory(const PnView &v, int64_t total_items, int64_t total_buckets, cudaStream_t st);
+int search_max_budget();
+cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, cudaStream_t st);
+}  // namespace pn

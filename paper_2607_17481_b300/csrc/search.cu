@@ -1,0 +1,191 @@
+// Streaming candidate search at the anchor lengths (Sec. 3.4-3.5,
+// Algorithm 1 phase B), one warp per query window.
+//
+// For query q of anchor a the directory population is the number of
+// non-constant windows inserted by the end of q's batch (batches of beta
+// samples of stream time), which fixes the global depth d and so the level
+// to probe.  Probes: the exact d-bit prefix bucket, then 1 + max(0, d - d0)
+// Hamming-1 buckets (capped by d and the probe cap) in increasing
+// |<g_{a,l}, F_q>|.  Candidates are earlier windows c <= q - excl; a bucket
+// with more valid entries than the remaining budget r gives ceil(r/2) of its
+// most recent entries and floor(r/2) evenly spaced ones.  A candidate is
+// evaluated exactly iff (1 - lambda) LB < max(best_q, P[c]) (Lemma 2, the
+// threshold of Algorithm 1), where best_q also takes the live value of the
+// query's own cell; both cells receive the distance by packed atomicMin.
+//
+// The final profile does not depend on the schedule: a pair is skipped only
+// when its distance exceeds, by the factor 1/(1 - lambda), the current value
+// of both cells it could lower, and cells only decrease, so every pair whose
+// key would win a cell is evaluated.
+#include "distance.cuh"
+
+namespace pn {
+namespace {
+
+constexpr int SR_WARPS = 8;
+constexpr int SR_THREADS = SR_WARPS * 32;
+constexpr int SR_MAXR = 512;   // largest supported budget R
+constexpr int SR_MAXPROBE = 9; // exact bucket + up to 8 Hamming-1 buckets
+
+__global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total) {
+    __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
+    __shared__ uint32_t scand[SR_WARPS][SR_MAXR];
+    __shared__ unsigned long long s_stat[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 3) s_stat[threadIdx.x] = 0ull;
+    __syncthreads();
+    unsigned long long n_q = 0, n_c = 0, n_lb = 0;
+    const int dims = 2 * (v.K - 1);
+    const float shrink = 1.0f - v.lam;
+
+    for (int64_t w = (int64_t)blockIdx.x * SR_WARPS + warp; w < total; w += (int64_t)gridDim.x * SR_WARPS) {
+        const int ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
+        const PnAnchor &A = v.anchors[ai];
+        const int s = A.series;
+        const PnSeries &S = v.series[s];
+        const int64_t q = w - A.win_off;
+        const int a = A.a;
+        if (v.runlen[S.x_off + q] >= a) continue;          // constant window
+        if (q < S.excl) continue;                          // no valid earlier window
+        // population seen by q: everything inserted by the end of its batch
+        const int beta = (v.beta > 0 && v.beta < S.excl) ? v.beta : S.excl;
+        const int64_t tau = q + a - 1;
+        const int64_t tend = min(S.n - 1, (tau / beta + 1) * beta - 1);
+        const int64_t last = tend - a + 1;
+        const uint32_t P = v.cnt[A.win_off + last];
+        const int d = pn_depth(P, v.alpha, v.B);
+        const PnLevel &L = v.levels[A.level_begin + d];
+
+        const float *Fa = v.F + A.row_off * PN_FEAT;
+        sF[warp][lane] = Fa[pn_row(q, v.C, A.nchunk) * PN_FEAT + lane];
+        __syncwarp();
+        float mg = __int_as_float(0x7f800000);
+        if (lane < d) {
+            mg = fabsf(pn_margin(v.g + ((int64_t)ai * (v.B + 1) + lane) * PN_FEAT, sF[warp], dims));
+            if (!(mg <= 3.0e38f)) mg = 3.0e38f;            // non-finite input: still a bit below d
+        }
+        const uint32_t sgq = v.sig[A.win_off + q];
+        const uint32_t pre = d > 0 ? (sgq >> (v.B - d)) : 0u;
+        int h = d <= 0 ? 0 : min(d, min(v.probe_cap, 1 + max(0, d - v.d0)));
+        uint32_t probes[SR_MAXPROBE];
+        probes[0] = pre;
+        for (int j = 0; j < h; ++j) {
+            float bm = mg;
+            int bl = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                float om = __shfl_xor_sync(0xffffffffu, bm, o);
+                int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                if (om < bm || (om == bm && ol < bl)) {
+                    bm = om;
+                    bl = ol;
+                }
+            }
+            probes[1 + j] = pre ^ (1u << (d - 1 - bl));
+            if (lane == bl) mg = __int_as_float(0x7f800000);
+        }
+
+        // budgeted candidate list, in probe order
+        const int R = v.R;
+        const int64_t qmax = q - S.excl;
+        int taken = 0;
+        for (int j = 0; j <= h && taken < R; ++j) {
+            const uint32_t gb = (uint32_t)(L.bucket_base + probes[j]);
+            const uint32_t lo = v.bstart[gb], hi = v.bstart[gb + 1];
+            uint32_t sv = 0;
+            if (lane == 0) {
+                uint32_t l = lo, r = hi;     // first entry with start > qmax
+                while (l < r) {
+                    uint32_t mid = (l + r) >> 1;
+                    if ((int64_t)v.dir_vals[mid] <= qmax) l = mid + 1; else r = mid;
+                }
+                sv = l - lo;
+            }
+            const int sz = (int)__shfl_sync(0xffffffffu, sv, 0);
+            const int rem = R - taken;
+            const int cnt = min(sz, rem);
+            for (int t = lane; t < cnt; t += 32) {
+                int pos;
+                if (sz <= rem) {
+                    pos = t;
+                } else {
+                    const int h1 = (rem + 1) / 2, h2 = rem / 2;
+                    pos = t < h2 ? (int)(((int64_t)t * (sz - h1)) / h2) : (sz - h1 + (t - h2));
+                }
+                scand[warp][taken + t] = v.dir_vals[lo + pos];
+            }
+            taken += cnt;
+        }
+        __syncwarp();
+        n_q += 1;
+        n_c += taken;
+        if (taken == 0) continue;
+
+        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
+        const PnWin wq = pn_window(v, s, q, a);
+        const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
+        unsigned long long bestkey = PN_EMPTY_KEY;
+        const float lbscale = 2.0f / (float)a;
+        for (int base = 0; base < taken; base += 4) {
+            const int slot = base + (lane >> 3);
+            const bool has = slot < taken;
+            const uint32_t c = has ? scand[warp][slot] : 0u;
+            float part = 0.0f;
+            if (has) {
+                const float4 fc = reinterpret_cast<const float4 *>(Fa + pn_row(c, v.C, A.nchunk) * PN_FEAT)[lane & 7];
+                float dx = fq.x - fc.x, dy = fq.y - fc.y, dz = fq.z - fc.z, dw = fq.w - fc.w;
+                part = dx * dx + dy * dy + dz * dz + dw * dw;
+            }
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            part += __shfl_xor_sync(0xffffffffu, part, 4);
+            bool surv = false;
+            if (has && (lane & 7) == 0) {
+                const float lb = sqrtf(lbscale * part);
+                const double tq = fmin(pn_cell_dist(bestkey), pn_cell_dist(__ldcg(&prow[q])));
+                const double tc = pn_cell_dist(__ldcg(&prow[c]));
+                surv = (double)(shrink * lb) < fmax(tq, tc);
+            }
+            uint32_t sm = __ballot_sync(0xffffffffu, surv);
+            while (sm) {
+                const int src = __ffs(sm) - 1;
+                sm &= sm - 1;
+                const uint32_t cc = __shfl_sync(0xffffffffu, c, src);
+                const PnWin wc = pn_window(v, s, cc, a);
+                const double dd = pn_dist_warp(v, S.x_off, a, q, wq, cc, wc, lane);
+                n_lb += 1;
+                if (dd < __longlong_as_double(0x7ff0000000000000ll)) {
+                    const unsigned long long kq = pn_pack(dd, cc);
+                    if (kq < bestkey) bestkey = kq;
+                    if (lane == 0) atomicMin(&prow[cc], pn_pack(dd, (uint32_t)q));
+                }
+            }
+        }
+        if (lane == 0 && bestkey != PN_EMPTY_KEY) atomicMin(&prow[q], bestkey);
+    }
+    if (lane == 0) {
+        atomicAdd(&s_stat[0], n_q);
+        atomicAdd(&s_stat[1], n_c);
+        atomicAdd(&s_stat[2], n_lb);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && v.stats) {
+        atomicAdd(&v.stats[PN_ST_QUERIES], s_stat[0]);
+        atomicAdd(&v.stats[PN_ST_CANDIDATES], s_stat[1]);
+        atomicAdd(&v.stats[PN_ST_LB_PASSED], s_stat[2]);
+    }
+}
+
+}  // namespace
+
+int search_max_budget() { return SR_MAXR; }
+
+cudaError_t launch_search(const PnView &v, int64_t total, int grid_blocks, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
+    unsigned g = (unsigned)(need < grid_blocks ? need : grid_blocks);
+    k_search<<<g, SR_THREADS, 0, st>>>(v, total);
+    return cudaGetLastError();
+}
+
+}  // namespace pn

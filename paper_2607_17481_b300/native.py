@@ -1,0 +1,269 @@
+"""ctypes binding of libpanache.so: argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; this module only
+converts Python arguments to the C ABI of ``include/panache.h``.  It raises
+``ImportError`` when the compiled library is missing -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpanache.so")
+
+OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETRUNC, ESTATE, EPOOL, ENODEV = 0, -1, -2, -3, -4, -5, -6, -7, -8
+F32, F64, DEVICE = 1, 2, 0x100
+PLAIN_FP64, MIXED = 0, 1
+TOPK_GLOBAL, TOPK_PER_LENGTH = 0, 1
+FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION = 0x1, 0x2, 0x4
+
+EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
+            "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
+            "panache_stream_length", "panache_stream_close", "panache_last_stats", "panache_profile_rows",
+            "panache_anchor_state", "panache_projections", "panache_strerror")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_uint32), ("gamma", ctypes.c_uint32), ("stride", ctypes.c_uint32),
+                ("K", ctypes.c_uint32), ("B", ctypes.c_uint32), ("d0", ctypes.c_uint32),
+                ("probe_cap", ctypes.c_uint32), ("sieve_w", ctypes.c_uint32), ("dm", ctypes.c_uint32),
+                ("dp", ctypes.c_uint32), ("rounds", ctypes.c_uint32), ("precision", ctypes.c_uint32),
+                ("topk_mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("beta", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("lambda_", ctypes.c_double), ("eps0", ctypes.c_double)]
+
+
+class Motif(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("_pad", ctypes.c_int32), ("i", ctypes.c_int64), ("j", ctypes.c_int64),
+                ("d", ctypes.c_double)]
+
+
+MOTIF_DTYPE = np.dtype([("m", np.int32), ("_pad", np.int32), ("i", np.int64), ("j", np.int64), ("d", np.float64)])
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("series", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("_pad", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("m_min", ctypes.c_int32), ("m_max", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("excl", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "queries", "candidates", "exact_stream", "exact_sieve", "exact_completion", "hot_classes",
+        "completion_rounds", "device_bytes", "kernel_launches")]
+
+
+_lib = None
+
+
+def lib():
+    """Loads the compiled library; raises ImportError when it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2607_17481_b300.build` "
+                              "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32)
+        L.panache_default_config.argtypes = [ctypes.POINTER(Config)]
+        L.panache_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+        L.panache_destroy.argtypes = [vp]
+        L.panache_destroy.restype = None
+        L.panache_set_stream.argtypes = [vp, vp]
+        L.panache_pmp.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32, vp, i64, ctypes.POINTER(i64)]
+        L.panache_pmp_batch.argtypes = [vp, vp, i32, vp, i64, vp]
+        L.panache_stream_open.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(vp)]
+        L.panache_append.argtypes = [vp, vp, i32, i64]
+        L.panache_stream_topk.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
+        L.panache_stream_length.argtypes = [vp]
+        L.panache_stream_length.restype = i64
+        L.panache_stream_close.argtypes = [vp]
+        L.panache_stream_close.restype = None
+        L.panache_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.panache_profile_rows.argtypes = [vp, i32, vp, i64]
+        L.panache_anchor_state.argtypes = [vp, i32, i32, ctypes.POINTER(i32), vp, vp, i64]
+        L.panache_projections.argtypes = [ctypes.POINTER(Config), i32, vp, i64]
+        L.panache_strerror.argtypes = [ctypes.c_int]
+        L.panache_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+class PanacheError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {lib().panache_strerror(code).decode()} ({code})")
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise PanacheError(rc, what)
+
+
+def default_config(**over) -> Config:
+    c = Config()
+    _check(lib().panache_default_config(ctypes.byref(c)), "default_config")
+    for k, v in over.items():
+        setattr(c, "lambda_" if k == "lam" else k, v)
+    return c
+
+
+def _series_arg(x):
+    """(pointer, dtype flag, n, keepalive) for a numpy array or a CUDA tensor."""
+    if hasattr(x, "is_cuda") and x.is_cuda:
+        import torch
+        if x.dtype not in (torch.float32, torch.float64) or not x.is_contiguous():
+            raise ValueError("series tensor must be contiguous float32/float64")
+        return ctypes.c_void_p(x.data_ptr()), (F32 if x.dtype == torch.float32 else F64) | DEVICE, x.numel(), x
+    a = np.asarray(x)
+    if a.dtype not in (np.float32, np.float64):
+        a = a.astype(np.float64)
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data_as(ctypes.c_void_p), F32 if a.dtype == np.float32 else F64, a.shape[0], a
+
+
+def projections(a: int, config: Config | None = None) -> np.ndarray:
+    """The FP32 projections [B+1][32] a context with `config` draws for anchor length a."""
+    cfg = config if config is not None else default_config()
+    g = np.empty((cfg.B + 1, 32), dtype=np.float32)
+    _check(lib().panache_projections(ctypes.byref(cfg), a, g.ctypes.data_as(ctypes.c_void_p), g.size),
+           "projections")
+    return g
+
+
+class Context:
+    """One engine context on the current CUDA device."""
+
+    def __init__(self, config: Config | None = None, **over):
+        cfg = config if config is not None else default_config(**over)
+        self._h = ctypes.c_void_p()
+        _check(lib().panache_create(ctypes.byref(cfg), ctypes.byref(self._h)), "create")
+        self.config = cfg
+
+    def close(self):
+        if self._h:
+            lib().panache_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr: int | None):
+        _check(lib().panache_set_stream(self._h, ctypes.c_void_p(stream_ptr or 0)), "set_stream")
+
+    def pmp(self, x, m_min: int, m_max: int, k: int, excl: int, out_cap: int | None = None) -> np.ndarray:
+        ptr, dt, n, keep = _series_arg(x)
+        L = m_max - m_min + 1
+        cap = out_cap if out_cap is not None else k * L
+        out = np.zeros(cap, dtype=MOTIF_DTYPE)
+        ln = ctypes.c_int64()
+        rc = lib().panache_pmp(self._h, ptr, dt, n, m_min, m_max, k, excl,
+                               out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(ln))
+        _check(rc, "pmp")
+        del keep
+        return out[:ln.value]
+
+    def pmp_batch(self, series: list, params: list[tuple[int, int, int, int]], out_cap_per_req: int | None = None):
+        reqs = (Request * len(series))()
+        keep = []
+        cap = out_cap_per_req or max(k * (mx - mn + 1) for (mn, mx, k, _) in params)
+        for r, (x, (mn, mx, k, ex)) in enumerate(zip(series, params)):
+            ptr, dt, n, kp = _series_arg(x)
+            keep.append(kp)
+            reqs[r].series, reqs[r].dtype, reqs[r].n = ptr, dt, n
+            reqs[r].m_min, reqs[r].m_max, reqs[r].k, reqs[r].excl = mn, mx, k, ex
+        out = np.zeros(cap * len(series), dtype=MOTIF_DTYPE)
+        lens = np.zeros(len(series), dtype=np.int64)
+        rc = lib().panache_pmp_batch(self._h, ctypes.cast(reqs, ctypes.c_void_p), len(series),
+                                     out.ctypes.data_as(ctypes.c_void_p), cap,
+                                     lens.ctypes.data_as(ctypes.c_void_p))
+        _check(rc, "pmp_batch")
+        return [out[r * cap: r * cap + lens[r]] for r in range(len(series))]
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().panache_last_stats(self._h, ctypes.byref(s)), "last_stats")
+        return {name: int(getattr(s, name)) for name, _ in Stats._fields_}
+
+    def profile_rows(self, series_index: int, n: int, L: int) -> np.ndarray:
+        keys = np.empty(n * L, dtype=np.uint64)
+        _check(lib().panache_profile_rows(self._h, series_index, keys.ctypes.data_as(ctypes.c_void_p), keys.size),
+               "profile_rows")
+        return keys.reshape(L, n)
+
+    def anchor_state(self, series_index: int, anchor_index: int, nw: int):
+        a = ctypes.c_int32()
+        F = np.empty((nw, 32), dtype=np.float32)
+        sig = np.empty(nw, dtype=np.uint32)
+        _check(lib().panache_anchor_state(self._h, series_index, anchor_index, ctypes.byref(a),
+                                          F.ctypes.data_as(ctypes.c_void_p), sig.ctypes.data_as(ctypes.c_void_p),
+                                          nw), "anchor_state")
+        return a.value, F, sig
+
+    def projections(self, a: int) -> np.ndarray:
+        return projections(a, self.config)
+
+    def stream(self, m_min: int, m_max: int, k: int, excl: int) -> "Stream":
+        return Stream(self, m_min, m_max, k, excl)
+
+
+class Stream:
+    """A live series: appends of any size, top-k on request."""
+
+    def __init__(self, ctx: Context, m_min: int, m_max: int, k: int, excl: int):
+        self.ctx = ctx
+        self.L, self.k = m_max - m_min + 1, k
+        self._h = ctypes.c_void_p()
+        _check(lib().panache_stream_open(ctx._h, m_min, m_max, k, excl, ctypes.byref(self._h)), "stream_open")
+
+    def append(self, chunk):
+        ptr, dt, n, keep = _series_arg(chunk)
+        _check(lib().panache_append(self._h, ptr, dt, n), "append")
+        del keep
+
+    def __len__(self):
+        return int(lib().panache_stream_length(self._h))
+
+    def topk(self) -> np.ndarray:
+        cap = self.k * self.L
+        out = np.zeros(cap, dtype=MOTIF_DTYPE)
+        ln = ctypes.c_int64()
+        _check(lib().panache_stream_topk(self._h, out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(ln)),
+               "stream_topk")
+        return out[:ln.value]
+
+    def close(self):
+        if self._h:
+            lib().panache_stream_close(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unpack_keys(keys: np.ndarray):
+    """(distance, neighbour) arrays from packed profile keys; empty cells give (inf, -1)."""
+    keys = np.asarray(keys, dtype=np.uint64)
+    empty = keys == np.uint64(0xFFFFFFFFFFFFFFFF)
+    mask = np.uint64((1 << 26) - 1)
+    d = (keys & ~mask).view(np.float64).copy()
+    j = (keys & mask).astype(np.int64)
+    d[empty] = np.inf
+    j[empty] = -1
+    return d, j

@@ -1,0 +1,186 @@
+"""GPU parity of the CUDA path against the CPU oracle, step by step and end to end.
+
+Tolerances (derived in the design notes):
+* features: FP32 rows of FP64 sliding-DFT state (plain) differ from the
+  oracle's direct FP64 DFT by FP32 rounding, |dF| <= 2^-22 (|F| + 1); the
+  mixed form's FP32 recurrence adds at most ~sqrt(C) eps |X| / sigma, bounded
+  here by 2e-4 (|F| + 1).
+* signature bits: equal wherever the oracle's margin exceeds the feature
+  error times the projection norm (the decision is taken in FP32 on the GPU).
+* in-stream distances: 1e-9 relative (plain, FP64) or 2e-5 relative + 2e-5
+  absolute (mixed, FP32 sums of float-float centred samples).
+* reported motifs: the oracle's top-k (m, i, j) exactly, distances within
+  1e-6 relative (FP64 recomputation of the reported cells).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import exact, spectral, topk
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pn():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2607_17481_b300 as pkg
+    from paper_2607_17481_b300 import build
+    build.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def small():
+    return workloads.planted_random_walk()
+
+
+@pytest.fixture(scope="module")
+def small_exact(small):
+    return exact.pmp(small.x, small.m_min, small.m_max, small.excl, tier="diag")
+
+
+def run(pn, s, **cfg):
+    ctx = pn.Context(**cfg)
+    mot = ctx.pmp(s.x, s.m_min, s.m_max, s.k, s.excl)
+    return ctx, mot
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_features_and_signatures(pn, small, precision):
+    s = small
+    ctx, _ = run(pn, s, precision=precision, topk_mode=1)
+    for ai in (0, 5, 16):
+        a = spectral.anchors(s.m_min, s.m_max)[ai]
+        nw = s.x.shape[0] - a + 1
+        a_got, F, sig = ctx.anchor_state(0, ai, nw)
+        assert a_got == a
+        ref = spectral.dft_features(s.x, a)
+        err = np.abs(F[:, :30].astype(np.float64) - ref)
+        tol = (2.0 ** -22 if precision == 0 else 2e-4) * (np.abs(ref) + 1.0)
+        assert np.all(err <= tol), (a, float(err.max()))
+        assert np.all(F[:, 30:] == 0.0)
+        g = ctx.projections(a).astype(np.float64)[:, :30]
+        marg = ref @ g[:24].T
+        bits = ((sig[:, None] >> np.arange(23, -1, -1)[None, :]) & 1).astype(bool)
+        decided = np.abs(marg) > 1e-3 * (np.linalg.norm(ref, axis=1, keepdims=True) + 1.0)
+        assert np.array_equal(bits[decided], (marg >= 0)[decided])
+        assert decided.mean() > 0.99
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_profile_rows_are_sound(pn, small, small_exact, precision):
+    """Every finite cell is the exact distance of a valid neighbour and never below the exact profile (Prop. 1)."""
+    s = small
+    P, I = small_exact
+    ctx, _ = run(pn, s, precision=precision, topk_mode=1)
+    L = s.m_max - s.m_min + 1
+    d, j = pn.unpack_keys(ctx.profile_rows(0, s.x.shape[0], L))
+    rtol, atol = (1e-9, 1e-9) if precision == 0 else (2e-5, 2e-5)
+    fin = np.isfinite(d)
+    assert fin[::2].mean() > 0.9           # anchor rows are filled by the streaming pass
+    ms, iis = np.nonzero(fin)
+    assert np.all(np.abs(iis - j[ms, iis]) >= s.excl)
+    rng = np.random.default_rng(0)
+    pick = rng.choice(ms.shape[0], size=min(3000, ms.shape[0]), replace=False)
+    for t in pick:
+        m = s.m_min + ms[t]
+        ref = exact.dist(s.x, m, iis[t], j[ms[t], iis[t]])
+        assert abs(d[ms[t], iis[t]] - ref) <= rtol * ref + atol, (m, iis[t])
+    assert np.all(d[fin] >= P[fin] * (1 - rtol) - atol)
+
+
+def _recall(got, ref):
+    gs = {(int(r["m"]), int(r["i"]), int(r["j"])) for r in got}
+    hits = [(m, i, j) in gs for (m, i, j, _) in ref]
+    return float(np.mean(hits)) if hits else 1.0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_topk_matches_oracle(pn, small, small_exact, mode, precision):
+    s = small
+    P, I = small_exact
+    ref = topk.select(P, I, s.m_min, s.k, mode)
+    _, got = run(pn, s, precision=precision, topk_mode=mode)
+    assert len(got) == len(ref)
+    rec = _recall(got, ref)
+    assert rec == 1.0, f"recall {rec}"
+    gd = {(int(r["m"]), int(r["i"]), int(r["j"])): float(r["d"]) for r in got}
+    for (m, i, j, dref) in ref:
+        assert abs(gd[(m, i, j)] - dref) <= 1e-6 * dref + 1e-12
+
+
+def test_deterministic(pn, small):
+    s = small
+    ctx, a = run(pn, s, topk_mode=1, precision=1)
+    rows_a = ctx.profile_rows(0, s.x.shape[0], s.m_max - s.m_min + 1)
+    ctx2, b = run(pn, s, topk_mode=1, precision=1)
+    rows_b = ctx2.profile_rows(0, s.x.shape[0], s.m_max - s.m_min + 1)
+    assert np.array_equal(a, b)
+    assert np.array_equal(rows_a, rows_b)
+
+
+def test_batch_equals_single(pn):
+    series = workloads.batched_workload(5, seed=3, n_hi=12000)
+    ctx = pn.Context(precision=1)
+    params = [(q.m_min, q.m_max, q.k, q.excl) for q in series]
+    batch = ctx.pmp_batch([q.x for q in series], params)
+    for q, got in zip(series, batch):
+        one = ctx.pmp(q.x, q.m_min, q.m_max, q.k, q.excl)
+        assert np.array_equal(one, got)
+
+
+def test_stream_equals_offline(pn, small):
+    s = small
+    ctx = pn.Context(topk_mode=1)
+    st = ctx.stream(s.m_min, s.m_max, s.k, s.excl)
+    rng = np.random.default_rng(1)
+    pos = 0
+    while pos < s.x.shape[0]:
+        step = int(rng.integers(1, 3000))
+        st.append(s.x[pos:pos + step])
+        pos += step
+    assert len(st) == s.x.shape[0]
+    got = st.topk()
+    ref = ctx.pmp(s.x, s.m_min, s.m_max, s.k, s.excl)
+    assert np.array_equal(got, ref)
+
+
+def test_device_input_equals_host(pn, small):
+    s = small
+    ctx = pn.Context(topk_mode=0)
+    host = ctx.pmp(s.x, s.m_min, s.m_max, s.k, s.excl)
+    dev = ctx.pmp(torch.from_numpy(s.x).cuda(), s.m_min, s.m_max, s.k, s.excl)
+    assert np.array_equal(host, dev)
+
+
+def test_edge_cases(pn):
+    ctx = pn.Context(topk_mode=0)
+    rng = np.random.default_rng(4)
+    x = np.cumsum(rng.standard_normal(700))
+    # series shorter than every length: no windows, no motifs
+    assert len(ctx.pmp(x[:20], 32, 40, 5, 8)) == 0
+    # windows exist but no valid pair (n < m + excl)
+    assert len(ctx.pmp(x[:60], 32, 40, 5, 40)) == 0
+    # a single length, ragged chunk tail, planted exactly constant run
+    y = x.copy()
+    y[300:360] = 1.5
+    got = ctx.pmp(y, 16, 16, 4, 16)
+    P, I = exact.pmp(y, 16, 16, 16, tier="direct")
+    ref = topk.select(P, I, 16, 4, topk.GLOBAL)
+    assert [(int(r["m"]), int(r["i"]), int(r["j"])) for r in got] == [(m, i, j) for (m, i, j, _) in ref]
+    # constant windows never appear as cells or neighbours
+    L = 1
+    d, j = pn.unpack_keys(ctx.profile_rows(0, y.shape[0], L))
+    const = [i for i in range(700 - 16 + 1) if y[i:i + 16].max() == y[i:i + 16].min()]
+    assert np.all(np.isinf(d[0, const]))
+    assert not set(const) & set(j[0][j[0] >= 0].tolist())
+    # invalid arguments are rejected
+    with pytest.raises(pn.PanacheError):
+        ctx.pmp(x, 2, 10, 5, 8)
+    with pytest.raises(pn.PanacheError):
+        ctx.pmp(x, 20, 10, 5, 8)
