@@ -1,0 +1,305 @@
+"""Throughput of the Panache pan-motif path on one B300 (windows x lengths per second).
+
+Workload (the configuration the metric is quoted on): a 1,000,000-sample
+float32 wafer-like series (152-sample step/plateau segments, seed 0), lengths
+100..150 (51 lengths, 26 anchors), top-20 pan-motifs over the whole stack,
+exclusion zone 150.  One step = one full request: samples on the device ->
+index (features, keys, directories) -> streaming search -> sieve ->
+completion -> FP64-verified top-20 on the host.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  N > 1 runs one independent replica per GPU
+(the single-series path does not shard; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "windows*lengths/sec to exact top-20 pan-motifs (recall 1.0) vs plain FP64 form; p50/p99"
+UNIT = "windows*lengths/s"
+WORKLOAD = dict(workload="wafer_like_1M", n=1_000_000, m_min=100, m_max=150, k=20, excl=150, seed=0,
+                dtype="float32", topk="global")
+
+
+def rank_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            p = [t.strip() for t in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def roofline(stats_steps: list[dict], peaks: dict, peak_src: str, traffic: float | None):
+    """Roofline of the dominant kernel, from the library's per-step CUDA events.
+
+    The streaming search is one kernel launch per request.  Its algorithmic
+    bytes per query window: the query's feature row (128 B) plus 128 B per
+    inspected candidate row -- the Parseval test reads every candidate's
+    30-float row once (the per-query figure of the search step).
+    """
+    ms = [s["step_ms"]["search"] for s in stats_steps]
+    feat_ms = [s["step_ms"]["features"] for s in stats_steps]
+    st = stats_steps[-1]
+    bytes_search = 128.0 * (st["queries"] + st["candidates"])
+    avg = statistics.mean(ms) / 1e3
+    ach = bytes_search / avg / 1e9
+    out = {"kernel": "k_search (streaming search: probe, Parseval rejection, exact distance)",
+           "bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": traffic,
+           "peak_source": f"{peak_src} (HBM copy GB/s)",
+           "bytes_per_launch": bytes_search, "avg_launch_ms": round(statistics.mean(ms), 3),
+           "features_avg_ms": round(statistics.mean(feat_ms), 3)}
+    return out
+
+
+def cpu_baseline(x: np.ndarray, lengths=(100, 125, 150), excl=150, target_s=12.0):
+    """The oracle (tier ii, all host cores) on a bounded prefix sample at three lengths.
+
+    A 20k-sample probe sizes the sample so the timed oracle run takes about
+    target_s seconds on this host (the oracle's cost grows as n^2).
+    """
+    from oracle import exact
+
+    def once(n_sample):
+        xs = np.asarray(x[:n_sample], dtype=np.float64)
+        t = time.perf_counter()
+        for m in lengths:
+            exact.pmp(xs, m, m, excl, tier="diag")
+        return time.perf_counter() - t
+
+    t0 = once(20_000)
+    n_sample = int(min(len(x), 300_000, max(20_000, 20_000 * (target_s / max(t0, 1e-3)) ** 0.5)))
+    dt = once(n_sample)
+    w = sum(n_sample - m + 1 for m in lengths)
+    return {"value": w / dt, "unit": UNIT, "cores": exact.max_threads(), "kind": "oracle",
+            "seconds": round(dt, 2),
+            "sample": f"tier-ii exact PMP (per-diagonal FP64 sliding dot products) of the first {n_sample} "
+                      f"samples at lengths {list(lengths)}; its cost grows as n^2, so on the full "
+                      f"{len(x)}-sample series the oracle's rate would be about {n_sample / len(x):.3f}x this"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, each step a bounded sample of the workload."""
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return 0
+    s = workloads.wafer_like(WORKLOAD["n"], seed=WORKLOAD["seed"])
+    times = []
+    w = 0
+    n_sample = 50_000
+    lengths = (100, 125, 150)
+    from oracle import exact
+    xs = np.asarray(s.x[:n_sample], dtype=np.float64)
+    for step in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        for m in lengths:
+            exact.pmp(xs, m, m, WORKLOAD["excl"], tier="diag")
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append(dt)
+    w = sum(n_sample - m + 1 for m in lengths)
+    value = w / statistics.mean(times)
+    sample = (f"tier-ii exact PMP of the first {n_sample} samples at lengths {list(lengths)} per step "
+              f"(oracle, FP64, all host cores)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, sample=sample),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": exact.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="panache", choices=("panache", "reference"))
+    ap.add_argument("--precision", type=int, default=1, help="1 mixed (default), 0 plain FP64")
+    ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 form")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = rank_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import paper_2607_17481_b300 as pn
+    wl = dict(WORKLOAD, n=args.n)
+    s = workloads.wafer_like(wl["n"], seed=wl["seed"] + rank)
+    x_host = torch.from_numpy(s.x).pin_memory()
+    x_dev = x_host.cuda()
+    W = workloads.windows_lengths(wl["n"], wl["m_min"], wl["m_max"])
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def make_ctx(precision):
+        ctx = pn.Context(precision=precision, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_TIMING)
+        ctx.set_stream(stream.cuda_stream)
+        return ctx
+
+    def timed(ctx, steps, warm, src):
+        for _ in range(warm):
+            ctx.pmp(src, wl["m_min"], wl["m_max"], wl["k"], wl["excl"])
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms, stats, motifs = [], [], None
+        for _ in range(steps):
+            flush.fill_(1.0)                      # L2 flush between steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            motifs = ctx.pmp(src, wl["m_min"], wl["m_max"], wl["k"], wl["excl"])
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            stats.append(ctx.stats())
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        return ms, stats, motifs
+
+    ctx = make_ctx(args.precision)
+    with ClockSampler(local) as clk:
+        ms, stats, motifs = timed(ctx, args.steps, args.warmup, x_dev)
+    clocks = clk.summary()
+    # end to end through the C ABI with host buffers: the H2D copy of the series
+    # and the D2H copy of the motifs happen inside every call
+    e2e_ms = ms if args.no_e2e else timed(ctx, max(2, args.steps // 2), 1, x_host.numpy())[0]
+    total = sum(ms) / 1e3
+    if dist:
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = W * world * args.steps / total
+    e2e_value = W * world / (statistics.mean(e2e_ms) / 1e3)
+
+    plain = None
+    if args.plain_steps > 0 and args.precision != 0:
+        pctx = make_ctx(0)
+        pms, pstats, pmot = timed(pctx, args.plain_steps, 1, x_dev)
+        plain = {"value": W * world / (statistics.mean(pms) / 1e3), "ms_per_step": statistics.mean(pms),
+                 "same_motifs": bool(np.array_equal(pmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
+                 "step_ms": pstats[-1]["step_ms"]}
+    if rank != 0:
+        return 0
+    peaks, psrc = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 recurrence/bound/in-stream distance, f64 prefix sums/anchors/verification"
+        if args.precision else "f64",
+        "data": "synthetic",
+        "config": dict(wl, form="mixed" if args.precision else "plain_fp64", l2="flushed between steps",
+                       replicas=world),
+        "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.x.nbytes),
+                "d2h_bytes_per_step": int(len(motifs) * 32)},
+        "gpu_launches": int(sum(st["kernel_launches"] for st in stats)),
+        "roofline": roofline(stats, peaks, psrc, None),
+        "clocks": clocks,
+        "plain_fp64": plain,
+        "step_ms": stats[-1]["step_ms"],
+        "counters": {k: v for k, v in stats[-1].items() if k != "step_ms"},
+        "motifs": [[int(r["m"]), int(r["i"]), int(r["j"]), float(r["d"])] for r in motifs],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(s.x)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

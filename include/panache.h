@@ -76,11 +76,13 @@ extern "C" {
 #define PANACHE_FLAG_EXHAUSTIVE_SIEVE 0x1  /* every valid pair of a hot class, not only w sort-neighbours */
 #define PANACHE_FLAG_NO_SIEVE 0x2          /* skip the hot-class sieve (S_hot) */
 #define PANACHE_FLAG_NO_COMPLETION 0x4     /* skip local completion (S_local) */
+#define PANACHE_FLAG_TIMING 0x8            /* time each step with CUDA events on the context's stream */
 
 /* Tunables.  A zero field takes the paper's default (Sec. 4):
  * alpha 16, gamma 8 (R = 128), stride 2, K 16, B 24, d0 12, probe cap 8,
  * sieve width 8, (dm, dp) = (6, 4), 8 completion rounds, lambda 1e-4,
- * eps0 1e-6, batch beta = excl, chunk 256 slides per direct-DFT anchor. */
+ * eps0 1e-6, batch beta = excl, chunk 256 slides per direct-DFT anchor,
+ * seed_mult 2. */
 typedef struct {
     uint32_t alpha;       /* occupancy target, the analyst's one knob ("budget") */
     uint32_t gamma;       /* R = gamma * alpha candidate inspections per query (R <= 512) */
@@ -97,6 +99,8 @@ typedef struct {
     uint32_t flags;       /* PANACHE_FLAG_* */
     uint32_t chunk;       /* slides per direct-DFT re-anchor (power of two, 16..4096) */
     uint32_t beta;        /* batch length of the streaming schedule (0: excl; capped at excl) */
+    uint32_t seed_mult;   /* completion seeds per round: the top seed_mult*k cells (per length in per-length mode) */
+    uint32_t _reserved;
     uint64_t seed;        /* seed of the Gaussian projections */
     uint64_t hbm_budget_bytes; /* admission limit on a request's device footprint (0: none) */
     double lambda;        /* bound shrink */
@@ -132,6 +136,12 @@ typedef struct {
     uint64_t completion_rounds;  /* rounds run (stops early when nothing improves) */
     uint64_t device_bytes;       /* device footprint of the request (admission estimate) */
     uint64_t kernel_launches;    /* kernels launched by the request */
+    /* With PANACHE_FLAG_TIMING: device time of each step in ms (CUDA events on
+     * the context's stream): 0 sample upload and conversion, 1 run lengths and
+     * FP64 prefix moments, 2 features and keys, 3 ranks and directories,
+     * 4 streaming search, 5 hot-class sieve, 6 completion rounds (with their
+     * seed selections), 7 final selection and FP64 verification. */
+    double step_ms[8];
 } panache_stats;
 
 typedef struct panache_ctx panache_ctx;

@@ -153,6 +153,7 @@ void fill_defaults(panache_config &c) {
     if (!c.dp) c.dp = 4;
     if (!c.rounds) c.rounds = 8;
     if (!c.chunk) c.chunk = 256;
+    if (!c.seed_mult) c.seed_mult = 2;
     if (c.lambda == 0.0) c.lambda = 1e-4;
     if (c.eps0 == 0.0) c.eps0 = 1e-6;
 }
@@ -380,6 +381,35 @@ int run_select(panache_ctx *ctx, PnRequest &R, const GroupSet &gs, bool strict,
     return PANACHE_OK;
 }
 
+// CUDA events between the steps of a request (PANACHE_FLAG_TIMING).
+struct StepTimer {
+    bool on = false;
+    cudaEvent_t ev[9] = {};
+    cudaStream_t st = nullptr;
+    ~StepTimer() {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    int start(bool enable, cudaStream_t s) {
+        on = enable;
+        st = s;
+        if (!on) return PANACHE_OK;
+        for (auto &e : ev) PN_CU(cudaEventCreate(&e));
+        return mark(0);
+    }
+    int mark(int i) { return on ? from_cuda(cudaEventRecord(ev[i], st)) : PANACHE_OK; }
+    int read(double *ms) {
+        if (!on) return PANACHE_OK;
+        PN_CU(cudaEventSynchronize(ev[8]));
+        for (int i = 0; i < 8; ++i) {
+            float t = 0.0f;
+            PN_CU(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+            ms[i] = t;
+        }
+        return PANACHE_OK;
+    }
+};
+
 // The whole path for a list of series; results per series.
 int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<std::vector<panache_motif>> &res) {
     const panache_config &c = ctx->cfg;
@@ -440,6 +470,8 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     }
     PN_CU(cudaMemsetAsync(R.prof, 0xFF, sizeof(unsigned long long) * std::max<int64_t>(1, R.total_cells), st));
     PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
+    StepTimer tm;
+    PN_TRY(tm.start((c.flags & PANACHE_FLAG_TIMING) != 0, st));
 
     // samples: host inputs go through one staging buffer; device inputs are read in place
     {
@@ -478,15 +510,20 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
         if (stage) PN_CU(cudaFreeAsync(stage, st));
     }
 
+    PN_TRY(tm.mark(1));
     PnView v = make_view(ctx, R);
     const int grid = ctx->sm_count * 8;
     // Algorithm 1 over every anchor of every series
     PN_CU(pn::launch_runlen(v, R.total_samples, st));
     PN_CU(pn::launch_moments(v, R.total_samples, R.sq, st));
+    PN_TRY(tm.mark(2));
     PN_CU(pn::launch_features(v, R.d_blk_anchor, R.d_blk_chunk0, (int32_t)R.blk_anchor.size(), R.a_max, st));
+    PN_TRY(tm.mark(3));
     PN_CU(pn::launch_ranks(v, R.total_windows, st));
     PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
+    PN_TRY(tm.mark(4));
     PN_CU(pn::launch_search(v, R.total_windows, grid, st));
+    PN_TRY(tm.mark(5));
     ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3 + 1;
     // Algorithm 2: sieve, completion rounds, final selection
     int32_t ncls = 0;
@@ -496,20 +533,23 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
         ctx->launches += 6 + (ncls ? 4 + 2 * 12 : 0);
     }
     ctx->stats.hot_classes = (uint64_t)ncls;
+    PN_TRY(tm.mark(6));
     std::vector<int> kser(nser), kseed(nser);
     for (int64_t s = 0; s < nser; ++s) {
         kser[s] = R.ser[s].k;
-        kseed[s] = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)R.ser[s].k, 6000 / (R.ser[s].m_max + 1)));
+        const int64_t want = (int64_t)c.seed_mult * R.ser[s].k;
+        kseed[s] = (int)std::max<int64_t>(1, std::min<int64_t>(want, 6000 / (R.ser[s].m_max + 1)));
     }
     const GroupSet out_groups = make_groups(R, (int)c.topk_mode, kser);
     if (!(c.flags & PANACHE_FLAG_NO_COMPLETION)) {
+        const GroupSet seed_mode = make_groups(R, (int)c.topk_mode, kseed);
         const GroupSet seed_global = make_groups(R, PANACHE_TOPK_GLOBAL, kseed);
         PnSeed *dseeds = nullptr;
         size_t seeds_cap = 0;
         for (uint32_t round = 0; round < c.rounds; ++round) {
             std::vector<PnSeed> seeds;
             std::vector<std::vector<PnPick>> picks;
-            PN_TRY(run_select(ctx, R, out_groups, false, picks));
+            PN_TRY(run_select(ctx, R, seed_mode, false, picks));
             for (auto &gp : picks)
                 for (auto &p : gp) seeds.push_back(PnSeed{p.series, p.m, p.i, p.j});
             if (c.topk_mode == PANACHE_TOPK_PER_LENGTH) {
@@ -535,8 +575,11 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
         }
         if (dseeds) PN_CU(cudaFreeAsync(dseeds, st));
     }
+    PN_TRY(tm.mark(7));
     std::vector<std::vector<PnPick>> picks;
     PN_TRY(run_select(ctx, R, out_groups, true, picks));
+    PN_TRY(tm.mark(8));
+    PN_TRY(tm.read(ctx->stats.step_ms));
     res.assign(nser, {});
     for (size_t gi = 0; gi < picks.size(); ++gi) {
         for (auto &p : picks[gi]) {

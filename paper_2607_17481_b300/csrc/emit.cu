@@ -288,7 +288,9 @@ __global__ void k_sel_verify(PnView v, const PnSelGroup *grp, int32_t ngrp, PnPo
         PnPoolEntry &pe = pool[e];
         const int64_t cell = (int64_t)pe.cell + (G.cell_off - S.row_off);
         const int m = S.m_min + (int)(cell / S.n);
-        const int64_t i = cell % S.n, j = pe.j;
+        // both cells of a pair get bit-identical values: evaluate in (min, max) order
+        const int64_t c0 = cell % S.n, c1 = pe.j;
+        const int64_t i = c0 < c1 ? c0 : c1, j = c0 < c1 ? c1 : c0;
         const double *xi = v.x + S.x_off + i, *xj = v.x + S.x_off + j;
         double si = 0, sj = 0;
         for (int r = lane; r < m; r += 32) {

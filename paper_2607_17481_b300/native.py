@@ -19,7 +19,7 @@ OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETRUNC, ESTATE, EPOOL, ENODEV = 0, -1, -2, -
 F32, F64, DEVICE = 1, 2, 0x100
 PLAIN_FP64, MIXED = 0, 1
 TOPK_GLOBAL, TOPK_PER_LENGTH = 0, 1
-FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION = 0x1, 0x2, 0x4
+FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING = 0x1, 0x2, 0x4, 0x8
 
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
@@ -33,7 +33,8 @@ class Config(ctypes.Structure):
                 ("probe_cap", ctypes.c_uint32), ("sieve_w", ctypes.c_uint32), ("dm", ctypes.c_uint32),
                 ("dp", ctypes.c_uint32), ("rounds", ctypes.c_uint32), ("precision", ctypes.c_uint32),
                 ("topk_mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
-                ("beta", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("beta", ctypes.c_uint32), ("seed_mult", ctypes.c_uint32), ("_reserved", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("lambda_", ctypes.c_double), ("eps0", ctypes.c_double)]
 
 
@@ -51,10 +52,13 @@ class Request(ctypes.Structure):
                 ("k", ctypes.c_int32), ("excl", ctypes.c_int32)]
 
 
+STEP_NAMES = ("upload", "moments", "features", "directory", "search", "sieve", "completion", "select")
+
+
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in (
         "queries", "candidates", "exact_stream", "exact_sieve", "exact_completion", "hot_classes",
-        "completion_rounds", "device_bytes", "kernel_launches")]
+        "completion_rounds", "device_bytes", "kernel_launches")] + [("step_ms", ctypes.c_double * 8)]
 
 
 _lib = None
@@ -166,9 +170,9 @@ class Context:
 
     def pmp(self, x, m_min: int, m_max: int, k: int, excl: int, out_cap: int | None = None) -> np.ndarray:
         ptr, dt, n, keep = _series_arg(x)
-        L = m_max - m_min + 1
-        cap = out_cap if out_cap is not None else k * L
-        out = np.zeros(cap, dtype=MOTIF_DTYPE)
+        L = max(0, m_max - m_min + 1)
+        cap = out_cap if out_cap is not None else max(0, k) * L
+        out = np.zeros(max(cap, 1), dtype=MOTIF_DTYPE)
         ln = ctypes.c_int64()
         rc = lib().panache_pmp(self._h, ptr, dt, n, m_min, m_max, k, excl,
                                out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(ln))
@@ -179,7 +183,7 @@ class Context:
     def pmp_batch(self, series: list, params: list[tuple[int, int, int, int]], out_cap_per_req: int | None = None):
         reqs = (Request * len(series))()
         keep = []
-        cap = out_cap_per_req or max(k * (mx - mn + 1) for (mn, mx, k, _) in params)
+        cap = out_cap_per_req or max(1, max(k * (mx - mn + 1) for (mn, mx, k, _) in params))
         for r, (x, (mn, mx, k, ex)) in enumerate(zip(series, params)):
             ptr, dt, n, kp = _series_arg(x)
             keep.append(kp)
@@ -196,7 +200,9 @@ class Context:
     def stats(self) -> dict:
         s = Stats()
         _check(lib().panache_last_stats(self._h, ctypes.byref(s)), "last_stats")
-        return {name: int(getattr(s, name)) for name, _ in Stats._fields_}
+        out = {name: int(getattr(s, name)) for name, _ in Stats._fields_ if name != "step_ms"}
+        out["step_ms"] = {nm: float(s.step_ms[t]) for t, nm in enumerate(STEP_NAMES)}
+        return out
 
     def profile_rows(self, series_index: int, n: int, L: int) -> np.ndarray:
         keys = np.empty(n * L, dtype=np.uint64)
