@@ -91,7 +91,9 @@ struct PnRequest {
     double *shift = nullptr;
     int32_t *runlen = nullptr;
     float *F = nullptr;
-    uint32_t *sig = nullptr, *cnt = nullptr, *nclist = nullptr;
+    uint32_t *sig = nullptr, *cnt = nullptr, *nclist = nullptr, *qorder = nullptr;
+    float4 *wmf = nullptr;
+    double2 *wmd = nullptr;
     float *g = nullptr;
     uint32_t *dir_keys = nullptr, *dir_vals = nullptr, *bstart = nullptr;
     unsigned long long *prof = nullptr, *stats = nullptr;
@@ -250,7 +252,7 @@ int plan(panache_ctx *ctx, const std::vector<SeriesIn> &in, PnRequest &R) {
     size_t b = 0;
     b += (size_t)R.total_samples * (8 + 8 + 16 + 4 + 8);   // x, xs, sq, runlen, staging
     b += (size_t)R.total_rows * PN_FEAT * 4;                // features
-    b += (size_t)R.total_windows * 12;                      // sig, cnt, nclist
+    b += (size_t)R.total_windows * (16 + 16);               // sig, cnt, nclist, qorder, moments
     b += (size_t)R.total_items * 8 * 2;                     // directory + sort scratch
     b += (size_t)R.total_buckets * 4 + (size_t)R.total_items / 4096 * 1024;
     b += (size_t)R.total_cells * 8;                         // profile rows
@@ -289,6 +291,9 @@ PnView make_view(panache_ctx *ctx, PnRequest &R) {
     v.sig = R.sig;
     v.cnt = R.cnt;
     v.nclist = R.nclist;
+    v.qorder = R.qorder;
+    v.wmf = R.wmf;
+    v.wmd = R.wmd;
     v.g = R.g;
     v.dir_keys = R.dir_keys;
     v.dir_vals = R.dir_vals;
@@ -443,6 +448,9 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PN_CU(R.alloc(R.sig, R.total_windows));
     PN_CU(R.alloc(R.cnt, R.total_windows));
     PN_CU(R.alloc(R.nclist, R.total_windows));
+    PN_CU(R.alloc(R.qorder, R.total_windows));
+    if (c.precision == PANACHE_PLAIN_FP64) PN_CU(R.alloc(R.wmd, R.total_windows));
+    else PN_CU(R.alloc(R.wmf, R.total_windows));
     PN_CU(R.alloc(R.g, nanc * (c.B + 1) * PN_FEAT));
     PN_CU(R.alloc(R.dir_keys, R.total_items));
     PN_CU(R.alloc(R.dir_vals, R.total_items));
@@ -521,15 +529,16 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PN_TRY(tm.mark(3));
     PN_CU(pn::launch_ranks(v, R.total_windows, st));
     PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
+    PN_CU(pn::launch_query_order(v, R.total_windows, R.total_buckets, st));
     PN_TRY(tm.mark(4));
-    PN_CU(pn::launch_search(v, R.total_windows, grid, st));
+    PN_CU(pn::launch_search(v, R.total_windows, grid, R.a_max, st));
     PN_TRY(tm.mark(5));
-    ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3 + 1;
+    ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3 + 1 + 1 + 4 * 3;
     // Algorithm 2: sieve, completion rounds, final selection
     int32_t ncls = 0;
     if (!(c.flags & PANACHE_FLAG_NO_SIEVE)) {
         PN_CU(pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w,
-                               (c.flags & PANACHE_FLAG_EXHAUSTIVE_SIEVE) ? 1 : 0, grid, st, &ncls));
+                               (c.flags & PANACHE_FLAG_EXHAUSTIVE_SIEVE) ? 1 : 0, grid, R.a_max, st, &ncls));
         ctx->launches += 6 + (ncls ? 4 + 2 * 12 : 0);
     }
     ctx->stats.hot_classes = (uint64_t)ncls;

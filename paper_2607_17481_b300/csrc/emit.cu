@@ -2,6 +2,7 @@
 // the zero-snapped top-k selection with FP64 re-verification.
 #include "distance.cuh"
 #include "emit.cuh"
+#include "zops.cuh"
 #include "prims.cuh"
 
 namespace pn {
@@ -82,9 +83,13 @@ __global__ void k_sieve_rekey(PnView v, const PnClass *cls, int32_t ncls, int64_
 
 // One warp per sorted member u: pairs (u, v) with u < v <= u + w (or every
 // v > u in the exhaustive variant), valid pairs only, bound-filtered, exact.
+// u's z-normalised window is staged in shared memory once.
+template <typename ZT>
 __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_t total, const uint32_t *members,
-                              int w, int exhaustive) {
+                              int w, int exhaustive, int zcap) {
+    extern __shared__ __align__(16) unsigned char zsm[];
     const int lane = threadIdx.x & 31;
+    ZT *zu = reinterpret_cast<ZT *>(zsm) + (threadIdx.x >> 5) * zcap;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float shrink = 1.0f - v.lam;
@@ -93,8 +98,7 @@ __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_
         const int ci = pn_find(cls, ncls, p, [](const PnClass &c) { return (int64_t)c.moff; });
         const PnClass &c = cls[ci];
         const PnAnchor &A = v.anchors[c.anchor];
-        const int s = A.series;
-        const PnSeries &S = v.series[s];
+        const PnSeries &S = v.series[A.series];
         const int a = A.a;
         const int64_t u = p - c.moff;
         const int64_t vend = exhaustive ? (int64_t)c.size : min((int64_t)c.size, u + 1 + w);
@@ -102,7 +106,13 @@ __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_
         const float *Fa = v.F + A.row_off * PN_FEAT;
         const float fu = Fa[pn_row(xu, v.C, A.nchunk) * PN_FEAT + lane];
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
-        const PnWin wu = pn_window(v, s, xu, a);
+        const auto mu_ = ZOps<ZT>::load(v, A.win_off + xu);
+        if (ZOps<ZT>::degenerate(mu_)) continue;
+        {
+            const auto *xs = ZOps<ZT>::samples(v, S.x_off + xu);
+            for (int r = lane; r < a; r += 32) zu[r] = ZOps<ZT>::z(mu_, xs[r]);
+        }
+        __syncwarp();
         for (int64_t v0 = u + 1; v0 < vend; v0 += 32) {
             const int64_t vi = v0 + lane;
             uint32_t xv = 0;
@@ -123,22 +133,29 @@ __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_
             if (fv) {
                 const float lb = sqrtf(2.0f / (float)a * acc);
                 const double thr = fmax(pn_cell_dist(__ldcg(&prow[xu])), pn_cell_dist(__ldcg(&prow[xv])));
-                surv = (double)(shrink * lb) < thr;
+                surv = (double)(shrink * lb) < thr && !ZOps<ZT>::degenerate(ZOps<ZT>::load(v, A.win_off + xv));
             }
             uint32_t sm = __ballot_sync(0xffffffffu, surv);
             while (sm) {
                 const int src = __ffs(sm) - 1;
                 sm &= sm - 1;
                 const uint32_t xx = __shfl_sync(0xffffffffu, xv, src);
-                const PnWin wx = pn_window(v, s, xx, a);
-                const double dd = pn_dist_warp(v, S.x_off, a, xu, wu, xx, wx, lane);
+                const auto mx = ZOps<ZT>::load(v, A.win_off + xx);
+                const auto *xs = ZOps<ZT>::samples(v, S.x_off + xx);
+                ZT dacc = 0;
+                for (int r = lane; r < a; r += 32) {
+                    const ZT dz = zu[r] - ZOps<ZT>::z(mx, xs[r]);
+                    dacc = fma(dz, dz, dacc);
+                }
+                const double dd = ZOps<ZT>::finish(dacc);
                 n_ex += 1;
-                if (lane == 0 && dd < __longlong_as_double(0x7ff0000000000000ll)) {
+                if (lane == 0) {
                     atomicMin(&prow[xu], pn_pack(dd, xx));
                     atomicMin(&prow[xx], pn_pack(dd, xu));
                 }
             }
         }
+        __syncwarp();
     }
     if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);
 }
@@ -393,7 +410,7 @@ __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry 
 
 // ---------------------------------------------------------------------------
 cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t total_slots, int w, int exhaustive,
-                         int grid_blocks, cudaStream_t st, int32_t *n_classes_out) {
+                         int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out) {
     *n_classes_out = 0;
     if (total_slots <= 0) return cudaSuccess;
     uint32_t *flag = nullptr, *size = nullptr, *cid = nullptr, *moff = nullptr, *tot = nullptr;
@@ -437,8 +454,19 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             int64_t warps_needed = nmem;
             int64_t blocks = (warps_needed + 7) / 8;
             if (blocks > grid_blocks) blocks = grid_blocks;
-            k_sieve_pairs<<<(unsigned)blocks, 256, 0, st>>>(v, cls, ncls, nmem, vals, w, exhaustive);
-            e = cudaGetLastError();
+            const int zcap = (a_max + 3) & ~3;
+            if (v.precision == 0) {
+                const size_t sm = sizeof(double) * zcap * 8;
+                e = cudaFuncSetAttribute(k_sieve_pairs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (e == cudaSuccess)
+                    k_sieve_pairs<double><<<(unsigned)blocks, 256, sm, st>>>(v, cls, ncls, nmem, vals, w, exhaustive, zcap);
+            } else {
+                const size_t sm = sizeof(float) * zcap * 8;
+                e = cudaFuncSetAttribute(k_sieve_pairs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (e == cudaSuccess)
+                    k_sieve_pairs<float><<<(unsigned)blocks, 256, sm, st>>>(v, cls, ncls, nmem, vals, w, exhaustive, zcap);
+            }
+            if (e == cudaSuccess) e = cudaGetLastError();
         }
     }
     *n_classes_out = ncls;

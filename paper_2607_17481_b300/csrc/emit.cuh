@@ -41,7 +41,7 @@ struct PnPick {           // one selected motif
 
 namespace pn {
 cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t total_slots, int w, int exhaustive,
-                         int grid_blocks, cudaStream_t st, int32_t *n_classes_out);
+                         int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out);
 cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved,
                             int grid_blocks, cudaStream_t st);
 cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ngrp, int64_t cell_begin,

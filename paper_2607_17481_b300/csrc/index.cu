@@ -142,8 +142,14 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
             double mu, var;
             pn_moments(v, A.series, q, a, mu, var);
             const bool nonconst = rl[q] < a;
-            if (nonconst && var > 0.0) {
-                const double inv = 1.0 / sqrt(var);
+            const double inv = (nonconst && var > 0.0) ? 1.0 / sqrt(var) : 0.0;
+            if (v.precision == 0) {
+                v.wmd[A.win_off + q] = make_double2(mu, inv);
+            } else {
+                const float mh = (float)mu;
+                v.wmf[A.win_off + q] = make_float4(mh, (float)(mu - (double)mh), (float)inv, 0.0f);
+            }
+            if (inv != 0.0) {
 #pragma unroll
                 for (int k = 0; k < PN_MAXK - 1; ++k) {
                     if (k < kp) {
@@ -245,6 +251,31 @@ __global__ void k_dir_items(PnView v, int64_t total, uint32_t *hist) {
     v.dir_vals[t] = val;
 }
 
+// Search order: every query is keyed by the global bucket it probes first
+// (its level's d-bit prefix), so warps running close together read the
+// same candidate rows.  Constant windows and windows without an earlier
+// valid partner sort last with key 0xFFFFFFFF.
+__global__ void k_query_keys(PnView v, int64_t total, uint32_t *keys) {
+    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= total) return;
+    int ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
+    const PnAnchor &A = v.anchors[ai];
+    const PnSeries &S = v.series[A.series];
+    const int64_t q = w - A.win_off;
+    uint32_t key = 0xFFFFFFFFu;
+    if (v.runlen[S.x_off + q] < A.a && q >= S.excl) {
+        const int beta = (v.beta > 0 && v.beta < S.excl) ? v.beta : S.excl;
+        const int64_t tau = q + A.a - 1;
+        const int64_t tend = min(S.n - 1, (tau / beta + 1) * beta - 1);
+        const uint32_t P = v.cnt[A.win_off + tend - A.a + 1];
+        const int d = pn_depth(P, v.alpha, v.B);
+        const uint32_t sg = v.sig[w];
+        key = (uint32_t)(v.levels[A.level_begin + d].bucket_base + (d > 0 ? (sg >> (v.B - d)) : 0u));
+    }
+    keys[w] = key;
+    v.qorder[w] = (uint32_t)w;
+}
+
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
@@ -325,6 +356,20 @@ cudaError_t launch_directory(const PnView &v, int64_t total_items, int64_t total
     while (bits < 32 && ((int64_t)1 << bits) <= total_buckets) ++bits;
     if (e == cudaSuccess) e = radix_sort_pairs(v.dir_keys, v.dir_vals, total_items, bits, st);
     if (e == cudaSuccess) e = excl_scan_u32(v.bstart, v.bstart, total_buckets + 1, nullptr, st);
+    return e;
+}
+
+cudaError_t launch_query_order(const PnView &v, int64_t total, int64_t total_buckets, cudaStream_t st) {
+    if (total <= 0) return cudaSuccess;
+    uint32_t *keys = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&keys, sizeof(uint32_t) * total, st);
+    if (e != cudaSuccess) return e;
+    k_query_keys<<<grid_for(total, 256), 256, 0, st>>>(v, total, keys);
+    e = cudaGetLastError();
+    int bits = 1;
+    while (bits < 32 && ((int64_t)1 << bits) <= total_buckets) ++bits;
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, v.qorder, total, bits, st);
+    cudaFreeAsync(keys, st);
     return e;
 }
 

@@ -34,6 +34,9 @@ struct PnView {
     uint32_t *sig;        // B-bit SimHash keys
     uint32_t *cnt;        // inclusive count of non-constant windows with start <= q
     uint32_t *nclist;     // start of the r-th non-constant window
+    float4 *wmf;          // mixed form: per-window (mu_hi, mu_lo, 1/sigma, 0); 1/sigma = 0 if degenerate
+    double2 *wmd;         // plain form: per-window (mu, 1/sigma)
+    uint32_t *qorder;     // search order of the flat query space (grouped by probe bucket)
     const float *g;       // projections [nanchors][B+1][PN_FEAT]
     // directory
     uint32_t *dir_keys;   // global bucket id of every item (sorted)
@@ -101,6 +104,7 @@ cudaError_t launch_features(const PnView &v, const int32_t *blk_anchor, const in
                             int32_t nblocks, int a_max, cudaStream_t st);
 cudaError_t launch_ranks(const PnView &v, int64_t total_windows, cudaStream_t st);
 cudaError_t launch_directory(const PnView &v, int64_t total_items, int64_t total_buckets, cudaStream_t st);
+cudaError_t launch_query_order(const PnView &v, int64_t total_windows, int64_t total_buckets, cudaStream_t st);
 int search_max_budget();
-cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, cudaStream_t st);
+cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, int a_max, cudaStream_t st);
 }  // namespace pn

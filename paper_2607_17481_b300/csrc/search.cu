@@ -17,7 +17,13 @@
 // when its distance exceeds, by the factor 1/(1 - lambda), the current value
 // of both cells it could lower, and cells only decrease, so every pair whose
 // key would win a cell is evaluated.
+//
+// Queries run in the order of the bucket they probe first (qorder), so warps
+// active at the same time share candidate rows in L2.  The query's
+// z-normalised window is staged once in shared memory; each surviving
+// candidate streams its own window against it.
 #include "distance.cuh"
+#include "zops.cuh"
 
 namespace pn {
 namespace {
@@ -27,18 +33,22 @@ constexpr int SR_THREADS = SR_WARPS * 32;
 constexpr int SR_MAXR = 512;   // largest supported budget R
 constexpr int SR_MAXPROBE = 9; // exact bucket + up to 8 Hamming-1 buckets
 
-__global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total) {
+template <typename ZT>
+__global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, int zcap) {
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
     __shared__ uint32_t scand[SR_WARPS][SR_MAXR];
     __shared__ unsigned long long s_stat[3];
+    extern __shared__ __align__(16) unsigned char zsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ZT *zq = reinterpret_cast<ZT *>(zsm) + warp * zcap;
     if (threadIdx.x < 3) s_stat[threadIdx.x] = 0ull;
     __syncthreads();
     unsigned long long n_q = 0, n_c = 0, n_lb = 0;
     const int dims = 2 * (v.K - 1);
     const float shrink = 1.0f - v.lam;
 
-    for (int64_t w = (int64_t)blockIdx.x * SR_WARPS + warp; w < total; w += (int64_t)gridDim.x * SR_WARPS) {
+    for (int64_t it = (int64_t)blockIdx.x * SR_WARPS + warp; it < total; it += (int64_t)gridDim.x * SR_WARPS) {
+        const int64_t w = v.qorder[it];
         const int ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
         const PnAnchor &A = v.anchors[ai];
         const int s = A.series;
@@ -64,9 +74,9 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total) 
             mg = fabsf(pn_margin(v.g + ((int64_t)ai * (v.B + 1) + lane) * PN_FEAT, sF[warp], dims));
             if (!(mg <= 3.0e38f)) mg = 3.0e38f;            // non-finite input: still a bit below d
         }
-        const uint32_t sgq = v.sig[A.win_off + q];
+        const uint32_t sgq = v.sig[w];
         const uint32_t pre = d > 0 ? (sgq >> (v.B - d)) : 0u;
-        int h = d <= 0 ? 0 : min(d, min(v.probe_cap, 1 + max(0, d - v.d0)));
+        const int h = d <= 0 ? 0 : min(d, min(v.probe_cap, 1 + max(0, d - v.d0)));
         uint32_t probes[SR_MAXPROBE];
         probes[0] = pre;
         for (int j = 0; j < h; ++j) {
@@ -121,8 +131,14 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total) 
         n_c += taken;
         if (taken == 0) continue;
 
+        // z-normalised query window, staged once
+        {
+            const auto mq = ZOps<ZT>::load(v, w);
+            const auto *xq = ZOps<ZT>::samples(v, S.x_off + q);
+            for (int r = lane; r < a; r += 32) zq[r] = ZOps<ZT>::z(mq, xq[r]);
+        }
+        __syncwarp();
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
-        const PnWin wq = pn_window(v, s, q, a);
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
         unsigned long long bestkey = PN_EMPTY_KEY;
         const float lbscale = 2.0f / (float)a;
@@ -144,24 +160,29 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total) 
                 const float lb = sqrtf(lbscale * part);
                 const double tq = fmin(pn_cell_dist(bestkey), pn_cell_dist(__ldcg(&prow[q])));
                 const double tc = pn_cell_dist(__ldcg(&prow[c]));
-                surv = (double)(shrink * lb) < fmax(tq, tc);
+                surv = (double)(shrink * lb) < fmax(tq, tc) && !ZOps<ZT>::degenerate(ZOps<ZT>::load(v, A.win_off + c));
             }
             uint32_t sm = __ballot_sync(0xffffffffu, surv);
             while (sm) {
                 const int src = __ffs(sm) - 1;
                 sm &= sm - 1;
                 const uint32_t cc = __shfl_sync(0xffffffffu, c, src);
-                const PnWin wc = pn_window(v, s, cc, a);
-                const double dd = pn_dist_warp(v, S.x_off, a, q, wq, cc, wc, lane);
-                n_lb += 1;
-                if (dd < __longlong_as_double(0x7ff0000000000000ll)) {
-                    const unsigned long long kq = pn_pack(dd, cc);
-                    if (kq < bestkey) bestkey = kq;
-                    if (lane == 0) atomicMin(&prow[cc], pn_pack(dd, (uint32_t)q));
+                const auto mc = ZOps<ZT>::load(v, A.win_off + cc);
+                const auto *xc = ZOps<ZT>::samples(v, S.x_off + cc);
+                ZT acc = 0;
+                for (int r = lane; r < a; r += 32) {
+                    const ZT dz = zq[r] - ZOps<ZT>::z(mc, xc[r]);
+                    acc = fma(dz, dz, acc);
                 }
+                const double dd = ZOps<ZT>::finish(acc);
+                n_lb += 1;
+                const unsigned long long kq = pn_pack(dd, cc);
+                if (kq < bestkey) bestkey = kq;
+                if (lane == 0) atomicMin(&prow[cc], pn_pack(dd, (uint32_t)q));
             }
         }
         if (lane == 0 && bestkey != PN_EMPTY_KEY) atomicMin(&prow[q], bestkey);
+        __syncwarp();
     }
     if (lane == 0) {
         atomicAdd(&s_stat[0], n_q);
@@ -176,16 +197,26 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total) 
     }
 }
 
+template <typename ZT>
+cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
+    const int zcap = (a_max + 3) & ~3;
+    const size_t sm = sizeof(ZT) * (size_t)zcap * SR_WARPS;
+    cudaError_t e = cudaFuncSetAttribute(k_search<ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
+    unsigned g = (unsigned)(need < grid_blocks ? need : grid_blocks);
+    k_search<ZT><<<g, SR_THREADS, sm, st>>>(v, total, zcap);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int search_max_budget() { return SR_MAXR; }
 
-cudaError_t launch_search(const PnView &v, int64_t total, int grid_blocks, cudaStream_t st) {
+cudaError_t launch_search(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
-    unsigned g = (unsigned)(need < grid_blocks ? need : grid_blocks);
-    k_search<<<g, SR_THREADS, 0, st>>>(v, total);
-    return cudaGetLastError();
+    return v.precision == 0 ? launch_t<double>(v, total, grid_blocks, a_max, st)
+                            : launch_t<float>(v, total, grid_blocks, a_max, st);
 }
 
 }  // namespace pn
