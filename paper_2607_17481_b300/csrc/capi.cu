@@ -50,7 +50,7 @@ struct PnConv {
     int32_t _pad;
 };
 
-__global__ void k_convert(const PnConv *cv, int32_t ncv, int64_t total, double *x, float2 *xs) {
+__global__ void k_convert(const PnConv *cv, int32_t ncv, int64_t total, double *x, float2 *xs, float *x1) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
     int c = pn_find(cv, ncv, t, [](const PnConv &e) { return e.x_off; });
@@ -60,6 +60,7 @@ __global__ void k_convert(const PnConv *cv, int32_t ncv, int64_t total, double *
     float hi = (float)v;
     x[t] = v;
     xs[t] = make_float2(hi, (float)(v - (double)hi));
+    if (x1) x1[t] = hi;
 }
 
 }  // namespace
@@ -87,6 +88,7 @@ struct PnRequest {
     int64_t *d_slot_off = nullptr;
     double *x = nullptr;
     float2 *xs = nullptr;
+    float *x1 = nullptr;
     double2 *sq = nullptr;
     double *shift = nullptr;
     int32_t *runlen = nullptr;
@@ -284,6 +286,7 @@ PnView make_view(panache_ctx *ctx, PnRequest &R) {
     v.precision = (int32_t)c.precision;
     v.x = R.x;
     v.xs = R.xs;
+    v.x1 = R.x1;
     v.sq = R.sq;
     v.shift = R.shift;
     v.runlen = R.runlen;
@@ -441,6 +444,9 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PN_CU(R.alloc(R.d_slot_off, nanc));
     PN_CU(R.alloc(R.x, R.total_samples));
     PN_CU(R.alloc(R.xs, R.total_samples));
+    bool all_f32 = true;
+    for (auto &si : in) all_f32 = all_f32 && (si.dtype & 0xFF) == PANACHE_F32;
+    if (all_f32 && c.precision == PANACHE_MIXED) PN_CU(R.alloc(R.x1, R.total_samples));
     PN_CU(R.alloc(R.sq, R.total_samples + nser));
     PN_CU(R.alloc(R.shift, nser));
     PN_CU(R.alloc(R.runlen, R.total_samples));
@@ -510,7 +516,7 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
         PN_CU(cudaMemcpyAsync(dcv, cv.data(), sizeof(PnConv) * nser, cudaMemcpyHostToDevice, st));
         if (R.total_samples > 0) {
             k_convert<<<(unsigned)((R.total_samples + 255) / 256), 256, 0, st>>>(dcv, (int32_t)nser, R.total_samples,
-                                                                                R.x, R.xs);
+                                                                                R.x, R.xs, R.x1);
             PN_CU(cudaGetLastError());
             ctx->launches += 1;
         }

@@ -46,6 +46,30 @@ __host__ __device__ __forceinline__ double pn_key_dist(uint64_t key) {
 
 __host__ __device__ __forceinline__ uint32_t pn_key_idx(uint64_t key) { return (uint32_t)(key & PN_IDX_MASK); }
 
+// Key of a non-negative float distance, built with integer operations only:
+// the float's 23 mantissa bits land above the 26-bit index field, so the
+// result equals pn_pack((double)d, idx) exactly.
+__device__ __forceinline__ uint64_t pn_pack_f(float d, uint32_t idx) {
+    const uint32_t fb = __float_as_uint(d);
+    const uint32_t e = fb >> 23;
+    uint64_t db;
+    if (e == 0) db = 0ull;                                  // zero (subnormals flush to zero)
+    else if (e >= 0xFF) db = 0x7FF0000000000000ull;         // +inf
+    else db = ((uint64_t)(e - 127 + 1023) << 52) | ((uint64_t)(fb & 0x7FFFFFu) << 29);
+    return (db & ~PN_IDX_MASK) | (uint64_t)idx;
+}
+
+// Distance of a key as a float, truncated toward zero (integer operations
+// only); an empty cell reads as +inf.
+__device__ __forceinline__ float pn_key_distf(uint64_t key) {
+    if (key == PN_EMPTY_KEY) return __int_as_float(0x7f800000);
+    const uint32_t e = (uint32_t)(key >> 52) & 0x7FFu;
+    const int ef = (int)e - 1023 + 127;
+    if (e == 0 || ef <= 0) return 0.0f;
+    if (ef >= 0xFF) return __int_as_float(0x7f800000);
+    return __uint_as_float(((uint32_t)ef << 23) | ((uint32_t)(key >> 29) & 0x7FFFFFu));
+}
+
 __device__ __forceinline__ float pn_warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -84,9 +84,10 @@ __global__ void k_sieve_rekey(PnView v, const PnClass *cls, int32_t ncls, int64_
 // One warp per sorted member u: pairs (u, v) with u < v <= u + w (or every
 // v > u in the exhaustive variant), valid pairs only, bound-filtered, exact.
 // u's z-normalised window is staged in shared memory once.
-template <typename ZT>
+template <class Z>
 __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_t total, const uint32_t *members,
                               int w, int exhaustive, int zcap) {
+    using ZT = typename Z::T;
     extern __shared__ __align__(16) unsigned char zsm[];
     const int lane = threadIdx.x & 31;
     ZT *zu = reinterpret_cast<ZT *>(zsm) + (threadIdx.x >> 5) * zcap;
@@ -106,11 +107,11 @@ __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_
         const float *Fa = v.F + A.row_off * PN_FEAT;
         const float fu = Fa[pn_row(xu, v.C, A.nchunk) * PN_FEAT + lane];
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
-        const auto mu_ = ZOps<ZT>::load(v, A.win_off + xu);
-        if (ZOps<ZT>::degenerate(mu_)) continue;
+        const auto mu_ = Z::load(v, A.win_off + xu);
+        if (Z::degenerate(mu_)) continue;
         {
-            const auto *xs = ZOps<ZT>::samples(v, S.x_off + xu);
-            for (int r = lane; r < a; r += 32) zu[r] = ZOps<ZT>::z(mu_, xs[r]);
+            const auto *xs = Z::samples(v, S.x_off + xu);
+            for (int r = lane; r < a; r += 32) zu[r] = Z::z(mu_, xs[r]);
         }
         __syncwarp();
         for (int64_t v0 = u + 1; v0 < vend; v0 += 32) {
@@ -132,26 +133,26 @@ __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_
             bool surv = false;
             if (fv) {
                 const float lb = sqrtf(2.0f / (float)a * acc);
-                const double thr = fmax(pn_cell_dist(__ldcg(&prow[xu])), pn_cell_dist(__ldcg(&prow[xv])));
-                surv = (double)(shrink * lb) < thr && !ZOps<ZT>::degenerate(ZOps<ZT>::load(v, A.win_off + xv));
+                const ZT thr = Z::fmx(Z::cell(__ldcg(&prow[xu])), Z::cell(__ldcg(&prow[xv])));
+                surv = (ZT)(shrink * lb) < thr && !Z::degenerate(Z::load(v, A.win_off + xv));
             }
             uint32_t sm = __ballot_sync(0xffffffffu, surv);
             while (sm) {
                 const int src = __ffs(sm) - 1;
                 sm &= sm - 1;
                 const uint32_t xx = __shfl_sync(0xffffffffu, xv, src);
-                const auto mx = ZOps<ZT>::load(v, A.win_off + xx);
-                const auto *xs = ZOps<ZT>::samples(v, S.x_off + xx);
+                const auto mx = Z::load(v, A.win_off + xx);
+                const auto *xs = Z::samples(v, S.x_off + xx);
                 ZT dacc = 0;
                 for (int r = lane; r < a; r += 32) {
-                    const ZT dz = zu[r] - ZOps<ZT>::z(mx, xs[r]);
+                    const ZT dz = zu[r] - Z::z(mx, xs[r]);
                     dacc = fma(dz, dz, dacc);
                 }
-                const double dd = ZOps<ZT>::finish(dacc);
+                const ZT dd = Z::finish(dacc);
                 n_ex += 1;
                 if (lane == 0) {
-                    atomicMin(&prow[xu], pn_pack(dd, xx));
-                    atomicMin(&prow[xx], pn_pack(dd, xu));
+                    atomicMin(&prow[xu], Z::pack(dd, xx));
+                    atomicMin(&prow[xx], Z::pack(dd, xu));
                 }
             }
         }
@@ -406,6 +407,16 @@ __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry 
     }
 }
 
+template <class Z>
+cudaError_t sieve_t(const PnView &v, const PnClass *cls, int32_t ncls, int64_t nmem, const uint32_t *vals, int w,
+                    int exhaustive, int zcap, int64_t blocks, cudaStream_t st) {
+    const size_t sm = sizeof(typename Z::T) * zcap * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_sieve_pairs<Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sieve_pairs<Z><<<(unsigned)blocks, 256, sm, st>>>(v, cls, ncls, nmem, vals, w, exhaustive, zcap);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -455,17 +466,9 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             int64_t blocks = (warps_needed + 7) / 8;
             if (blocks > grid_blocks) blocks = grid_blocks;
             const int zcap = (a_max + 3) & ~3;
-            if (v.precision == 0) {
-                const size_t sm = sizeof(double) * zcap * 8;
-                e = cudaFuncSetAttribute(k_sieve_pairs<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                if (e == cudaSuccess)
-                    k_sieve_pairs<double><<<(unsigned)blocks, 256, sm, st>>>(v, cls, ncls, nmem, vals, w, exhaustive, zcap);
-            } else {
-                const size_t sm = sizeof(float) * zcap * 8;
-                e = cudaFuncSetAttribute(k_sieve_pairs<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                if (e == cudaSuccess)
-                    k_sieve_pairs<float><<<(unsigned)blocks, 256, sm, st>>>(v, cls, ncls, nmem, vals, w, exhaustive, zcap);
-            }
+            if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, ncls, nmem, vals, w, exhaustive, zcap, blocks, st);
+            else if (v.x1) e = sieve_t<ZMix1>(v, cls, ncls, nmem, vals, w, exhaustive, zcap, blocks, st);
+            else e = sieve_t<ZMix2>(v, cls, ncls, nmem, vals, w, exhaustive, zcap, blocks, st);
             if (e == cudaSuccess) e = cudaGetLastError();
         }
     }

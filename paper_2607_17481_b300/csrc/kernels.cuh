@@ -26,6 +26,7 @@ struct PnView {
     // samples
     const double *x;      // samples widened to FP64, concatenated over series
     const float2 *xs;     // samples as (hi, lo) float pairs: hi + lo == x to ~2^-48
+    const float *x1;      // samples as floats (null unless every series was given as float32)
     const double2 *sq;    // per series n+1 prefix sums (sum, sum of squares) of x - shift
     const double *shift;  // per series shift subtracted before the prefix sums
     const int32_t *runlen;// equal-value run length from each sample, capped at the series' m_max

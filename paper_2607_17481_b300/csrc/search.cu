@@ -33,8 +33,9 @@ constexpr int SR_THREADS = SR_WARPS * 32;
 constexpr int SR_MAXR = 512;   // largest supported budget R
 constexpr int SR_MAXPROBE = 9; // exact bucket + up to 8 Hamming-1 buckets
 
-template <typename ZT>
+template <class Z>
 __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, int zcap) {
+    using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
     __shared__ uint32_t scand[SR_WARPS][SR_MAXR];
     __shared__ unsigned long long s_stat[3];
@@ -133,9 +134,9 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
 
         // z-normalised query window, staged once
         {
-            const auto mq = ZOps<ZT>::load(v, w);
-            const auto *xq = ZOps<ZT>::samples(v, S.x_off + q);
-            for (int r = lane; r < a; r += 32) zq[r] = ZOps<ZT>::z(mq, xq[r]);
+            const auto mq = Z::load(v, w);
+            const auto *xq = Z::samples(v, S.x_off + q);
+            for (int r = lane; r < a; r += 32) zq[r] = Z::z(mq, xq[r]);
         }
         __syncwarp();
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
@@ -158,27 +159,27 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
             bool surv = false;
             if (has && (lane & 7) == 0) {
                 const float lb = sqrtf(lbscale * part);
-                const double tq = fmin(pn_cell_dist(bestkey), pn_cell_dist(__ldcg(&prow[q])));
-                const double tc = pn_cell_dist(__ldcg(&prow[c]));
-                surv = (double)(shrink * lb) < fmax(tq, tc) && !ZOps<ZT>::degenerate(ZOps<ZT>::load(v, A.win_off + c));
+                const ZT tq = Z::fmn(Z::cell(bestkey), Z::cell(__ldcg(&prow[q])));
+                const ZT tc = Z::cell(__ldcg(&prow[c]));
+                surv = (ZT)(shrink * lb) < Z::fmx(tq, tc) && !Z::degenerate(Z::load(v, A.win_off + c));
             }
             uint32_t sm = __ballot_sync(0xffffffffu, surv);
             while (sm) {
                 const int src = __ffs(sm) - 1;
                 sm &= sm - 1;
                 const uint32_t cc = __shfl_sync(0xffffffffu, c, src);
-                const auto mc = ZOps<ZT>::load(v, A.win_off + cc);
-                const auto *xc = ZOps<ZT>::samples(v, S.x_off + cc);
+                const auto mc = Z::load(v, A.win_off + cc);
+                const auto *xc = Z::samples(v, S.x_off + cc);
                 ZT acc = 0;
                 for (int r = lane; r < a; r += 32) {
-                    const ZT dz = zq[r] - ZOps<ZT>::z(mc, xc[r]);
+                    const ZT dz = zq[r] - Z::z(mc, xc[r]);
                     acc = fma(dz, dz, acc);
                 }
-                const double dd = ZOps<ZT>::finish(acc);
+                const ZT dd = Z::finish(acc);
                 n_lb += 1;
-                const unsigned long long kq = pn_pack(dd, cc);
+                const unsigned long long kq = Z::pack(dd, cc);
                 if (kq < bestkey) bestkey = kq;
-                if (lane == 0) atomicMin(&prow[cc], pn_pack(dd, (uint32_t)q));
+                if (lane == 0) atomicMin(&prow[cc], Z::pack(dd, (uint32_t)q));
             }
         }
         if (lane == 0 && bestkey != PN_EMPTY_KEY) atomicMin(&prow[q], bestkey);
@@ -197,15 +198,15 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
     }
 }
 
-template <typename ZT>
+template <class Z>
 cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     const int zcap = (a_max + 3) & ~3;
-    const size_t sm = sizeof(ZT) * (size_t)zcap * SR_WARPS;
-    cudaError_t e = cudaFuncSetAttribute(k_search<ZT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = sizeof(typename Z::T) * (size_t)zcap * SR_WARPS;
+    cudaError_t e = cudaFuncSetAttribute(k_search<Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
     unsigned g = (unsigned)(need < grid_blocks ? need : grid_blocks);
-    k_search<ZT><<<g, SR_THREADS, sm, st>>>(v, total, zcap);
+    k_search<Z><<<g, SR_THREADS, sm, st>>>(v, total, zcap);
     return cudaGetLastError();
 }
 
@@ -215,8 +216,8 @@ int search_max_budget() { return SR_MAXR; }
 
 cudaError_t launch_search(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    return v.precision == 0 ? launch_t<double>(v, total, grid_blocks, a_max, st)
-                            : launch_t<float>(v, total, grid_blocks, a_max, st);
+    if (v.precision == 0) return launch_t<ZPlain>(v, total, grid_blocks, a_max, st);
+    return v.x1 ? launch_t<ZMix1>(v, total, grid_blocks, a_max, st) : launch_t<ZMix2>(v, total, grid_blocks, a_max, st);
 }
 
 }  // namespace pn
