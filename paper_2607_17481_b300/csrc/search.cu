@@ -33,15 +33,61 @@ constexpr int SR_THREADS = SR_WARPS * 32;
 constexpr int SR_MAXR = 512;   // largest supported budget R
 constexpr int SR_MAXPROBE = 9; // exact bucket + up to 8 Hamming-1 buckets
 
+// Exact distances of up to four queued survivors at once (warp-cooperative
+// over samples, four independent accumulators), then the packed-key updates:
+// the query's running best in registers, the candidate's cell by atomicMin
+// only when the new key is below the snapshot read for the bound test (cells
+// only decrease, so a key at or above the snapshot cannot change the cell).
 template <class Z>
-__global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, int zcap) {
+__device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T *zq, const uint32_t *sc,
+                                           const unsigned long long *sk, int nb, int64_t x_off, int64_t win_off,
+                                           int a, uint32_t q, unsigned long long *prow,
+                                           unsigned long long &bestkey, int lane) {
+    using ZT = typename Z::T;
+    const uint32_t c0 = sc[0], c1 = sc[nb > 1 ? 1 : 0], c2 = sc[nb > 2 ? 2 : 0], c3 = sc[nb > 3 ? 3 : 0];
+    const auto m0 = Z::load(v, win_off + c0), m1 = Z::load(v, win_off + c1);
+    const auto m2 = Z::load(v, win_off + c2), m3 = Z::load(v, win_off + c3);
+    const auto *x0 = Z::samples(v, x_off + c0), *x1 = Z::samples(v, x_off + c1);
+    const auto *x2 = Z::samples(v, x_off + c2), *x3 = Z::samples(v, x_off + c3);
+    ZT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int r = lane; r < a; r += 32) {
+        const ZT zr = zq[r];
+        const ZT d0 = zr - Z::z(m0, x0[r]);
+        const ZT d1 = zr - Z::z(m1, x1[r]);
+        const ZT d2 = zr - Z::z(m2, x2[r]);
+        const ZT d3 = zr - Z::z(m3, x3[r]);
+        a0 = fma(d0, d0, a0);
+        a1 = fma(d1, d1, a1);
+        a2 = fma(d2, d2, a2);
+        a3 = fma(d3, d3, a3);
+    }
+    const ZT dd[4] = {Z::finish(a0), Z::finish(a1), Z::finish(a2), Z::finish(a3)};
+    const uint32_t cc[4] = {c0, c1, c2, c3};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k < nb) {
+            const unsigned long long kq = Z::pack(dd[k], cc[k]);
+            if (kq < bestkey) bestkey = kq;
+            if (lane == k) {
+                const unsigned long long kc = Z::pack(dd[k], q);
+                if (kc < sk[k]) atomicMin(&prow[cc[k]], kc);
+            }
+        }
+    }
+}
+
+template <class Z>
+__global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {
     using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
-    __shared__ uint32_t scand[SR_WARPS][SR_MAXR];
     __shared__ unsigned long long s_stat[3];
-    extern __shared__ __align__(16) unsigned char zsm[];
+    extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    ZT *zq = reinterpret_cast<ZT *>(zsm) + warp * zcap;
+    const int R = v.R;
+    unsigned long long *snap = reinterpret_cast<unsigned long long *>(dsm) + warp * R;
+    ZT *zq = reinterpret_cast<ZT *>(reinterpret_cast<unsigned long long *>(dsm) + SR_WARPS * R) + warp * zcap;
+    uint32_t *scand = reinterpret_cast<uint32_t *>(reinterpret_cast<ZT *>(reinterpret_cast<unsigned long long *>(dsm) +
+                                                                        SR_WARPS * R) + SR_WARPS * zcap) + warp * R;
     if (threadIdx.x < 3) s_stat[threadIdx.x] = 0ull;
     __syncthreads();
     unsigned long long n_q = 0, n_c = 0, n_lb = 0;
@@ -78,8 +124,9 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
         const uint32_t sgq = v.sig[w];
         const uint32_t pre = d > 0 ? (sgq >> (v.B - d)) : 0u;
         const int h = d <= 0 ? 0 : min(d, min(v.probe_cap, 1 + max(0, d - v.d0)));
-        uint32_t probes[SR_MAXPROBE];
-        probes[0] = pre;
+        // lane j (0 <= j <= h) owns probe j: the exact prefix, then Hamming-1
+        // buckets in increasing margin (ties to the lower bit)
+        uint32_t my_probe = pre;
         for (int j = 0; j < h; ++j) {
             float bm = mg;
             int bl = lane;
@@ -92,27 +139,28 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
                     bl = ol;
                 }
             }
-            probes[1 + j] = pre ^ (1u << (d - 1 - bl));
+            if (lane == j + 1) my_probe = pre ^ (1u << (d - 1 - bl));
             if (lane == bl) mg = __int_as_float(0x7f800000);
         }
-
-        // budgeted candidate list, in probe order
-        const int R = v.R;
+        // every probe's bucket range and valid prefix (start <= q - excl), in parallel
         const int64_t qmax = q - S.excl;
+        uint32_t my_lo = 0, my_sz = 0;
+        if (lane <= h) {
+            const uint32_t gb = (uint32_t)(L.bucket_base + my_probe);
+            const uint32_t lo = v.bstart[gb], hi = v.bstart[gb + 1];
+            uint32_t l = lo, r = hi;                       // first entry with start > qmax
+            while (l < r) {
+                const uint32_t mid = (l + r) >> 1;
+                if ((int64_t)v.dir_vals[mid] <= qmax) l = mid + 1; else r = mid;
+            }
+            my_lo = lo;
+            my_sz = l - lo;
+        }
+        // budgeted candidate list, in probe order
         int taken = 0;
         for (int j = 0; j <= h && taken < R; ++j) {
-            const uint32_t gb = (uint32_t)(L.bucket_base + probes[j]);
-            const uint32_t lo = v.bstart[gb], hi = v.bstart[gb + 1];
-            uint32_t sv = 0;
-            if (lane == 0) {
-                uint32_t l = lo, r = hi;     // first entry with start > qmax
-                while (l < r) {
-                    uint32_t mid = (l + r) >> 1;
-                    if ((int64_t)v.dir_vals[mid] <= qmax) l = mid + 1; else r = mid;
-                }
-                sv = l - lo;
-            }
-            const int sz = (int)__shfl_sync(0xffffffffu, sv, 0);
+            const uint32_t lo = __shfl_sync(0xffffffffu, my_lo, j);
+            const int sz = (int)__shfl_sync(0xffffffffu, my_sz, j);
             const int rem = R - taken;
             const int cnt = min(sz, rem);
             for (int t = lane; t < cnt; t += 32) {
@@ -123,7 +171,7 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
                     const int h1 = (rem + 1) / 2, h2 = rem / 2;
                     pos = t < h2 ? (int)(((int64_t)t * (sz - h1)) / h2) : (sz - h1 + (t - h2));
                 }
-                scand[warp][taken + t] = v.dir_vals[lo + pos];
+                scand[taken + t] = v.dir_vals[lo + pos];
             }
             taken += cnt;
         }
@@ -143,10 +191,13 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
         unsigned long long bestkey = PN_EMPTY_KEY;
         const float lbscale = 2.0f / (float)a;
+        // survivors are compacted in place at the front of scand (never past
+        // the candidates already read) with their cell snapshots in snap
+        int nsurv = 0, head = 0;
         for (int base = 0; base < taken; base += 4) {
             const int slot = base + (lane >> 3);
             const bool has = slot < taken;
-            const uint32_t c = has ? scand[warp][slot] : 0u;
+            const uint32_t c = has ? scand[slot] : 0u;
             float part = 0.0f;
             if (has) {
                 const float4 fc = reinterpret_cast<const float4 *>(Fa + pn_row(c, v.C, A.nchunk) * PN_FEAT)[lane & 7];
@@ -157,31 +208,32 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
             part += __shfl_xor_sync(0xffffffffu, part, 2);
             part += __shfl_xor_sync(0xffffffffu, part, 4);
             bool surv = false;
+            unsigned long long kc = 0;
             if (has && (lane & 7) == 0) {
                 const float lb = sqrtf(lbscale * part);
+                kc = __ldcg(&prow[c]);
                 const ZT tq = Z::fmn(Z::cell(bestkey), Z::cell(__ldcg(&prow[q])));
-                const ZT tc = Z::cell(__ldcg(&prow[c]));
-                surv = (ZT)(shrink * lb) < Z::fmx(tq, tc) && !Z::degenerate(Z::load(v, A.win_off + c));
+                surv = (ZT)(shrink * lb) < Z::fmx(tq, Z::cell(kc)) && !Z::degenerate(Z::load(v, A.win_off + c));
             }
-            uint32_t sm = __ballot_sync(0xffffffffu, surv);
-            while (sm) {
-                const int src = __ffs(sm) - 1;
-                sm &= sm - 1;
-                const uint32_t cc = __shfl_sync(0xffffffffu, c, src);
-                const auto mc = Z::load(v, A.win_off + cc);
-                const auto *xc = Z::samples(v, S.x_off + cc);
-                ZT acc = 0;
-                for (int r = lane; r < a; r += 32) {
-                    const ZT dz = zq[r] - Z::z(mc, xc[r]);
-                    acc = fma(dz, dz, acc);
-                }
-                const ZT dd = Z::finish(acc);
-                n_lb += 1;
-                const unsigned long long kq = Z::pack(dd, cc);
-                if (kq < bestkey) bestkey = kq;
-                if (lane == 0) atomicMin(&prow[cc], Z::pack(dd, (uint32_t)q));
+            const uint32_t sm = __ballot_sync(0xffffffffu, surv);
+            __syncwarp();
+            if (surv) {
+                const int rank = __popc(sm & ((1u << lane) - 1u));
+                scand[nsurv + rank] = c;
+                snap[nsurv + rank] = kc;
+            }
+            nsurv += __popc(sm);
+            __syncwarp();
+            while (nsurv - head >= 4) {
+                eval_batch<Z>(v, zq, scand + head, snap + head, 4, S.x_off, A.win_off, a, (uint32_t)q, prow,
+                              bestkey, lane);
+                head += 4;
             }
         }
+        if (nsurv > head)
+            eval_batch<Z>(v, zq, scand + head, snap + head, nsurv - head, S.x_off, A.win_off, a, (uint32_t)q, prow,
+                          bestkey, lane);
+        n_lb += nsurv;
         if (lane == 0 && bestkey != PN_EMPTY_KEY) atomicMin(&prow[q], bestkey);
         __syncwarp();
     }
@@ -201,7 +253,8 @@ __global__ void __launch_bounds__(SR_THREADS) k_search(PnView v, int64_t total, 
 template <class Z>
 cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     const int zcap = (a_max + 3) & ~3;
-    const size_t sm = sizeof(typename Z::T) * (size_t)zcap * SR_WARPS;
+    const size_t sm = (sizeof(unsigned long long) + sizeof(uint32_t)) * (size_t)v.R * SR_WARPS +
+                      sizeof(typename Z::T) * (size_t)zcap * SR_WARPS;
     cudaError_t e = cudaFuncSetAttribute(k_search<Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
