@@ -277,6 +277,8 @@ PnView make_view(panache_ctx *ctx, PnRequest &R) {
     v.B = (int32_t)c.B;
     v.K = (int32_t)c.K;
     v.C = (int32_t)c.chunk;
+    v.cshift = 0;
+    while ((1 << v.cshift) < v.C) ++v.cshift;
     v.alpha = (int32_t)c.alpha;
     v.R = (int32_t)(c.gamma * c.alpha);
     v.d0 = (int32_t)c.d0;

@@ -105,7 +105,8 @@ __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_
         const int64_t vend = exhaustive ? (int64_t)c.size : min((int64_t)c.size, u + 1 + w);
         const uint32_t xu = members[p];
         const float *Fa = v.F + A.row_off * PN_FEAT;
-        const float fu = Fa[pn_row(xu, v.C, A.nchunk) * PN_FEAT + lane];
+        const uint32_t nch = (uint32_t)A.nchunk;
+        const float fu = Fa[(size_t)pn_row32(xu, v.cshift, nch) * PN_FEAT + lane];
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
         const auto mu_ = Z::load(v, A.win_off + xu);
         if (Z::degenerate(mu_)) continue;
@@ -120,7 +121,7 @@ __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_
             const float *fv = nullptr;
             if (vi < vend) {
                 xv = members[c.moff + vi];
-                if (llabs((int64_t)xv - (int64_t)xu) >= S.excl) fv = Fa + pn_row(xv, v.C, A.nchunk) * PN_FEAT;
+                if (llabs((int64_t)xv - (int64_t)xu) >= S.excl) fv = Fa + (size_t)pn_row32(xv, v.cshift, nch) * PN_FEAT;
             }
             float acc = 0.0f;
             for (int t = 0; t < PN_FEAT; ++t) {

@@ -15,7 +15,8 @@ struct PnView {
     int32_t nseries, nanchors, nlevels;
     int32_t B;            // signature bits
     int32_t K;            // spectral width
-    int32_t C;            // chunk length of the feature kernel (slides per direct-DFT anchor)
+    int32_t C;            // chunk length of the feature kernel (slides per direct-DFT anchor), a power of two
+    int32_t cshift;       // log2(C)
     int32_t alpha;        // occupancy target
     int32_t R;            // verification budget gamma * alpha
     int32_t d0;           // probe reference depth
@@ -65,6 +66,11 @@ enum PnStat {
 // lock-step by one warp write one contiguous run of rows.
 __host__ __device__ __forceinline__ int64_t pn_row(int64_t q, int32_t C, int64_t nchunk) {
     return (q % C) * nchunk + q / C;
+}
+
+// The same row with C = 2^cshift and 32-bit window indices (kernels' hot loops).
+__device__ __forceinline__ uint32_t pn_row32(uint32_t q, int cshift, uint32_t nchunk) {
+    return (q & ((1u << cshift) - 1u)) * nchunk + (q >> cshift);
 }
 
 // <g_l, F> in a fixed order of fused multiply-adds; the feature kernel and

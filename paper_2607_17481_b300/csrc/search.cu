@@ -63,9 +63,10 @@ __device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T 
     }
     const ZT dd[4] = {Z::finish(a0), Z::finish(a1), Z::finish(a2), Z::finish(a3)};
     const uint32_t cc[4] = {c0, c1, c2, c3};
+    const bool dg[4] = {Z::degenerate(m0), Z::degenerate(m1), Z::degenerate(m2), Z::degenerate(m3)};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (k < nb) {
+        if (k < nb && !dg[k]) {
             const unsigned long long kq = Z::pack(dd[k], cc[k]);
             if (kq < bestkey) bestkey = kq;
             if (lane == k) {
@@ -114,7 +115,8 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         const PnLevel &L = v.levels[A.level_begin + d];
 
         const float *Fa = v.F + A.row_off * PN_FEAT;
-        sF[warp][lane] = Fa[pn_row(q, v.C, A.nchunk) * PN_FEAT + lane];
+        const uint32_t nch = (uint32_t)A.nchunk;
+        sF[warp][lane] = Fa[(size_t)pn_row32((uint32_t)q, v.cshift, nch) * PN_FEAT + lane];
         __syncwarp();
         float mg = __int_as_float(0x7f800000);
         if (lane < d) {
@@ -163,14 +165,15 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
             const int sz = (int)__shfl_sync(0xffffffffu, my_sz, j);
             const int rem = R - taken;
             const int cnt = min(sz, rem);
+            // even-interval positions floor(t (sz - h1) / h2), with rest = sz - h1
+            // split as rest = qh h2 + rh so only t rh (< 2^18) is divided
+            const int h1 = (rem + 1) / 2, h2 = rem / 2, h2d = max(1, h2);
+            const int rest = sz - h1;
+            const int qh = rest / h2d, rh = rest - qh * h2d;
             for (int t = lane; t < cnt; t += 32) {
                 int pos;
-                if (sz <= rem) {
-                    pos = t;
-                } else {
-                    const int h1 = (rem + 1) / 2, h2 = rem / 2;
-                    pos = t < h2 ? (int)(((int64_t)t * (sz - h1)) / h2) : (sz - h1 + (t - h2));
-                }
+                if (sz <= rem) pos = t;
+                else pos = t < h2 ? t * qh + (t * rh) / h2d : (rest + (t - h2));
                 scand[taken + t] = v.dir_vals[lo + pos];
             }
             taken += cnt;
@@ -200,7 +203,8 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
             const uint32_t c = has ? scand[slot] : 0u;
             float part = 0.0f;
             if (has) {
-                const float4 fc = reinterpret_cast<const float4 *>(Fa + pn_row(c, v.C, A.nchunk) * PN_FEAT)[lane & 7];
+                const float4 fc =
+                    reinterpret_cast<const float4 *>(Fa + (size_t)pn_row32(c, v.cshift, nch) * PN_FEAT)[lane & 7];
                 float dx = fq.x - fc.x, dy = fq.y - fc.y, dz = fq.z - fc.z, dw = fq.w - fc.w;
                 part = dx * dx + dy * dy + dz * dz + dw * dw;
             }
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
                 const float lb = sqrtf(lbscale * part);
                 kc = __ldcg(&prow[c]);
                 const ZT tq = Z::fmn(Z::cell(bestkey), Z::cell(__ldcg(&prow[q])));
-                surv = (ZT)(shrink * lb) < Z::fmx(tq, Z::cell(kc)) && !Z::degenerate(Z::load(v, A.win_off + c));
+                surv = (ZT)(shrink * lb) < Z::fmx(tq, Z::cell(kc));
             }
             const uint32_t sm = __ballot_sync(0xffffffffu, surv);
             __syncwarp();
