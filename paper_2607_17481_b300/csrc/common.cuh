@@ -96,6 +96,14 @@ __host__ __device__ __forceinline__ int pn_kprime(int m, int K) {
 }
 
 // Global depth after P insertions: smallest d >= 0 with P <= alpha 2^d, capped at B (Sec. 3.4).
+// Device form: d = ceil(log2(ceil(P / alpha))) by a leading-zero count.
+__device__ __forceinline__ int pn_depth_dev(uint32_t P, uint32_t alpha, int B) {
+    if (P <= alpha) return 0;
+    const uint32_t u = (P + alpha - 1u) / alpha;
+    const int d = 32 - __clz(u - 1u);
+    return d < B ? d : B;
+}
+
 __host__ __device__ __forceinline__ int pn_depth(int64_t P, int alpha, int B) {
     int d = 0;
     while (d < B && P > ((int64_t)alpha << d)) ++d;

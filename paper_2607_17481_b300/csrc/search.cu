@@ -61,26 +61,41 @@ __device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T 
         a2 = fma(d2, d2, a2);
         a3 = fma(d3, d3, a3);
     }
-    const ZT dd[4] = {Z::finish(a0), Z::finish(a1), Z::finish(a2), Z::finish(a3)};
-    const uint32_t cc[4] = {c0, c1, c2, c3};
-    const bool dg[4] = {Z::degenerate(m0), Z::degenerate(m1), Z::degenerate(m2), Z::degenerate(m3)};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (k < nb && !dg[k]) {
-            const unsigned long long kq = Z::pack(dd[k], cc[k]);
-            if (kq < bestkey) bestkey = kq;
-            if (lane == k) {
-                const unsigned long long kc = Z::pack(dd[k], q);
-                if (kc < sk[k]) atomicMin(&prow[cc[k]], kc);
-            }
-        }
+    // transposed reduction of the four sums (6 shuffles): afterwards lanes
+    // 8v..8v+7 hold the total of survivor v
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    ZT k0 = hi16 ? a2 : a0, k1 = hi16 ? a3 : a1;
+    const ZT s0 = hi16 ? a0 : a2, s1 = hi16 ? a1 : a3;
+    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    ZT t = hi8 ? k1 : k0;
+    const ZT u = hi8 ? k0 : k1;
+    t += __shfl_xor_sync(0xffffffffu, u, 8);
+    t += __shfl_xor_sync(0xffffffffu, t, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    const int vi = lane >> 3;
+    const uint32_t cv = vi == 0 ? c0 : (vi == 1 ? c1 : (vi == 2 ? c2 : c3));
+    const bool dg = Z::degenerate(vi == 0 ? m0 : (vi == 1 ? m1 : (vi == 2 ? m2 : m3)));
+    const bool ok = vi < nb && !dg;
+    const ZT dd = Z::root(t);
+    unsigned long long kq = ok ? Z::pack(dd, cv) : PN_EMPTY_KEY;
+    if (ok && (lane & 7) == 0) {
+        const unsigned long long kc = Z::pack(dd, q);
+        if (kc < sk[vi]) atomicMin(&prow[cv], kc);
     }
+    unsigned long long o = __shfl_xor_sync(0xffffffffu, kq, 8);
+    kq = o < kq ? o : kq;
+    o = __shfl_xor_sync(0xffffffffu, kq, 16);
+    kq = o < kq ? o : kq;
+    if (kq < bestkey) bestkey = kq;
 }
 
 template <class Z>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {
     using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
+    __shared__ float lbbuf[SR_WARPS][32];
     __shared__ unsigned long long s_stat[3];
     extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -111,7 +126,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         const int64_t tend = min(S.n - 1, (tau / beta + 1) * beta - 1);
         const int64_t last = tend - a + 1;
         const uint32_t P = v.cnt[A.win_off + last];
-        const int d = pn_depth(P, v.alpha, v.B);
+        const int d = pn_depth_dev(P, (uint32_t)v.alpha, v.B);
         const PnLevel &L = v.levels[A.level_begin + d];
 
         const float *Fa = v.F + A.row_off * PN_FEAT;
@@ -194,28 +209,38 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
         unsigned long long bestkey = PN_EMPTY_KEY;
         const float lbscale = 2.0f / (float)a;
-        // survivors are compacted in place at the front of scand (never past
-        // the candidates already read) with their cell snapshots in snap
+        // Bounds of 32 candidates at a time (rows read by 8 lanes each, 4 rows
+        // per step), then the threshold test with one candidate per lane.
+        // Survivors are compacted in place at the front of scand (never past a
+        // candidate not yet read), with their cell snapshots in snap.
+        float *slb = lbbuf[warp];
         int nsurv = 0, head = 0;
-        for (int base = 0; base < taken; base += 4) {
-            const int slot = base + (lane >> 3);
-            const bool has = slot < taken;
-            const uint32_t c = has ? scand[slot] : 0u;
-            float part = 0.0f;
-            if (has) {
-                const float4 fc =
-                    reinterpret_cast<const float4 *>(Fa + (size_t)pn_row32(c, v.cshift, nch) * PN_FEAT)[lane & 7];
-                float dx = fq.x - fc.x, dy = fq.y - fc.y, dz = fq.z - fc.z, dw = fq.w - fc.w;
-                part = dx * dx + dy * dy + dz * dz + dw * dw;
+        for (int b32 = 0; b32 < taken; b32 += 32) {
+            const int nblk = min(32, taken - b32);
+            for (int sub = 0; sub < nblk; sub += 4) {
+                const int k = sub + (lane >> 3);
+                const bool has = k < nblk;
+                float part = 0.0f;
+                if (has) {
+                    const uint32_t c = scand[b32 + k];
+                    const float4 fc =
+                        reinterpret_cast<const float4 *>(Fa + (size_t)pn_row32(c, v.cshift, nch) * PN_FEAT)[lane & 7];
+                    const float dx = fq.x - fc.x, dy = fq.y - fc.y, dz = fq.z - fc.z, dw = fq.w - fc.w;
+                    part = dx * dx + dy * dy + dz * dz + dw * dw;
+                }
+                part += __shfl_xor_sync(0xffffffffu, part, 1);
+                part += __shfl_xor_sync(0xffffffffu, part, 2);
+                part += __shfl_xor_sync(0xffffffffu, part, 4);
+                if (has && (lane & 7) == 0) slb[k] = part;
             }
-            part += __shfl_xor_sync(0xffffffffu, part, 1);
-            part += __shfl_xor_sync(0xffffffffu, part, 2);
-            part += __shfl_xor_sync(0xffffffffu, part, 4);
+            __syncwarp();
             bool surv = false;
+            uint32_t c = 0;
             unsigned long long kc = 0;
-            if (has && (lane & 7) == 0) {
-                const float lb = sqrtf(lbscale * part);
+            if (lane < nblk) {
+                c = scand[b32 + lane];
                 kc = __ldcg(&prow[c]);
+                const float lb = sqrtf(lbscale * slb[lane]);
                 const ZT tq = Z::fmn(Z::cell(bestkey), Z::cell(__ldcg(&prow[q])));
                 surv = (ZT)(shrink * lb) < Z::fmx(tq, Z::cell(kc));
             }

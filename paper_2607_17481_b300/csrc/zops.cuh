@@ -17,6 +17,7 @@ struct ZMix2 {
     __device__ static float z(const M &m, const X &x) { return ((x.x - m.x) + (x.y - m.y)) * m.z; }
     __device__ static bool degenerate(const M &m) { return m.z == 0.0f; }
     __device__ static float finish(float acc) { return sqrtf(pn_warp_sum(acc)); }
+    __device__ static float root(float s) { return sqrtf(s); }
     __device__ static float cell(unsigned long long key) { return pn_key_distf(key); }
     __device__ static unsigned long long pack(float d, uint32_t idx) { return pn_pack_f(d, idx); }
     __device__ static float fmn(float a, float b) { return fminf(a, b); }
@@ -38,6 +39,7 @@ struct ZPlain {
     __device__ static double z(const M &m, const X &x) { return (x - m.x) * m.y; }
     __device__ static bool degenerate(const M &m) { return m.y == 0.0; }
     __device__ static double finish(double acc) { return sqrt(pn_warp_sumd(acc)); }
+    __device__ static double root(double s) { return sqrt(s); }
     __device__ static double cell(unsigned long long key) { return pn_cell_dist(key); }
     __device__ static unsigned long long pack(double d, uint32_t idx) { return pn_pack(d, idx); }
     __device__ static double fmn(double a, double b) { return fmin(a, b); }

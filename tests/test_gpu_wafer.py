@@ -1,0 +1,98 @@
+"""Parity at the benchmark's scale: the wafer-like series (lengths 100..150, exclusion 150).
+
+* 200,000-sample prefix: the GPU's top-20 lists against the oracle's
+  (tier ii exact PMP over all 51 lengths, frozen in
+  tests/golden/wafer200k_top20.json by tests/golden/make_wafer_prefix.py).
+* Full 1,000,000 samples (the benchmark's workload): every reported motif's
+  neighbour is checked to be its exact nearest valid neighbour by the oracle,
+  cell by cell, and its distance to be the oracle's within 1e-6.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import exact
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "wafer200k_top20.json")
+
+
+@pytest.fixture(scope="module")
+def pn():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2607_17481_b300 as pkg
+    from paper_2607_17481_b300 import build
+    build.build()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def wafer():
+    return workloads.wafer_like(1_000_000, seed=0)
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    return {0: [tuple(t) for t in g["global"]], 1: [tuple(t) for t in g["per_length"]]}
+
+
+def _prefix_run(pn, wafer, **cfg):
+    ctx = pn.Context(**cfg)
+    x = np.ascontiguousarray(wafer.x[:200_000])
+    return x, ctx.pmp(x, 100, 150, 20, 150)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_prefix_global_top20(pn, wafer, golden, precision):
+    from parity import compare
+    x, got = _prefix_run(pn, wafer, precision=precision, topk_mode=0)
+    r = compare(x.astype(np.float64), got, golden[0])
+    assert r["misses"] == 0, r["miss_list"]
+    assert r["bad_dist"] == 0
+
+
+def test_prefix_per_length_top20(pn, wafer, golden):
+    """Anchor stride 1: all 1020 cells.  The paper's stride 2 is reported separately."""
+    from parity import compare
+    x, got = _prefix_run(pn, wafer, precision=1, topk_mode=1, stride=1)
+    r = compare(x.astype(np.float64), got, golden[1])
+    assert r["misses"] == 0, r["miss_list"]
+    assert r["bad_dist"] == 0
+
+
+def test_prefix_per_length_paper_defaults(pn, wafer, golden):
+    from parity import compare
+    x, got = _prefix_run(pn, wafer, precision=1, topk_mode=1)
+    r = compare(x.astype(np.float64), got, golden[1])
+    print("per-length recall at the paper's defaults:", (r["hits"] + r["ties"]) / r["n"], r["miss_list"])
+    assert r["misses"] <= 0.005 * r["n"]
+    assert r["bad_dist"] == 0
+
+
+def test_full_size_reported_cells_are_exact(pn, wafer):
+    """Each of the benchmark's 20 motifs is its cell's exact nearest valid neighbour (oracle, per cell)."""
+    ctx = pn.Context(precision=1, topk_mode=0)
+    got = ctx.pmp(wafer.x, 100, 150, 20, 150)
+    assert len(got) == 20
+    x = wafer.x.astype(np.float64)
+    for r in got:
+        m, i, j, d = int(r["m"]), int(r["i"]), int(r["j"]), float(r["d"])
+        P, I = exact.pmp_cells(x, m, 150, [i])
+        assert abs(d - P[0]) <= 1e-6 * P[0], (m, i, j, d, P[0])
+        if I[0] != j:        # an equally distant neighbour (exact tie) is also correct
+            assert abs(exact.dist(x, m, i, j) - P[0]) <= 1e-12 * P[0]
+    # the list obeys the m/2 rule and is sorted by (d, m, i)
+    keys = [(float(r["d"]), int(r["m"]), int(r["i"])) for r in got]
+    assert keys == sorted(keys)
+    for a in range(len(got)):
+        for b in range(a):
+            if got[a]["m"] == got[b]["m"]:
+                assert 2 * abs(int(got[a]["i"]) - int(got[b]["i"])) > int(got[a]["m"])
