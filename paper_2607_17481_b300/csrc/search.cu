@@ -91,6 +91,30 @@ __device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T 
     if (kq < bestkey) bestkey = kq;
 }
 
+// Exact distance of one candidate (warp-cooperative), same updates as eval_batch.
+template <class Z>
+__device__ __forceinline__ void eval_one(const PnView &v, const typename Z::T *zq, uint32_t c,
+                                         unsigned long long snapkey, int64_t x_off, int64_t win_off, int a,
+                                         uint32_t q, unsigned long long *prow, unsigned long long &bestkey,
+                                         int lane) {
+    using ZT = typename Z::T;
+    const auto m = Z::load(v, win_off + c);
+    if (Z::degenerate(m)) return;
+    const auto *x = Z::samples(v, x_off + c);
+    ZT acc = 0;
+    for (int r = lane; r < a; r += 32) {
+        const ZT dz = zq[r] - Z::z(m, x[r]);
+        acc = fma(dz, dz, acc);
+    }
+    const ZT dd = Z::finish(acc);
+    const unsigned long long kq = Z::pack(dd, c);
+    if (kq < bestkey) bestkey = kq;
+    if (lane == 0) {
+        const unsigned long long kc = Z::pack(dd, q);
+        if (kc < snapkey) atomicMin(&prow[c], kc);
+    }
+}
+
 template <class Z>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {
     using ZT = typename Z::T;
@@ -234,16 +258,39 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
                 if (has && (lane & 7) == 0) slb[k] = part;
             }
             __syncwarp();
-            bool surv = false;
             uint32_t c = 0;
             unsigned long long kc = 0;
+            float lbs = __int_as_float(0x7f800000);
             if (lane < nblk) {
                 c = scand[b32 + lane];
                 kc = __ldcg(&prow[c]);
-                const float lb = sqrtf(lbscale * slb[lane]);
-                const ZT tq = Z::fmn(Z::cell(bestkey), Z::cell(__ldcg(&prow[q])));
-                surv = (ZT)(shrink * lb) < Z::fmx(tq, Z::cell(kc));
+                lbs = shrink * sqrtf(lbscale * slb[lane]);
             }
+            const ZT cq = Z::cell(__ldcg(&prow[q]));
+            // best-first: the block's smallest bound is evaluated before the
+            // others are tested, so the query's threshold is tight early
+            {
+                float bm = lbs;
+                int bl = lane;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float om = __shfl_xor_sync(0xffffffffu, bm, o);
+                    const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                    if (om < bm || (om == bm && ol < bl)) {
+                        bm = om;
+                        bl = ol;
+                    }
+                }
+                const uint32_t cb = __shfl_sync(0xffffffffu, c, bl);
+                const unsigned long long kb = __shfl_sync(0xffffffffu, kc, bl);
+                if (bl < nblk && (ZT)bm < Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kb))) {
+                    eval_one<Z>(v, zq, cb, kb, S.x_off, A.win_off, a, (uint32_t)q, prow, bestkey, lane);
+                    n_lb += 1;
+                }
+                if (lane == bl) lbs = __int_as_float(0x7f800000);   // done: not retested
+            }
+            bool surv = false;
+            if (lane < nblk) surv = (ZT)lbs < Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kc));
             const uint32_t sm = __ballot_sync(0xffffffffu, surv);
             __syncwarp();
             if (surv) {
