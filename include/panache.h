@@ -212,6 +212,35 @@ int panache_projections(const panache_config *cfg, int32_t a, float *g, int64_t 
 
 const char *panache_strerror(int code);
 
+/* Top-k motifs of ONE length row from profile keys already on the device,
+ * with no device memory allocated by the call.  For callers that cannot call
+ * cudaMalloc -- for example code that runs inside another framework's
+ * memory pool or under a budget that forbids new device allocations.  The
+ * paper has no counterpart: it is the selection step of panache_pmp offered
+ * on its own.
+ *
+ *  x          device FP64 samples of the series, n of them
+ *  m          the row's length (3 <= m <= min(n, 1024))
+ *  keys       device row of n packed keys (layout of panache_profile_rows;
+ *             cells past n - m and empty cells are 0xFFFFFFFFFFFFFFFF)
+ *  k          motifs wanted; k * (m + 1) must stay at or below 6300
+ *  eps0       zero-snap threshold (the library's default is 1e-6)
+ *  out        device array of at least k motifs (written)
+ *  out_count  device int32 (written): the number of motifs, or
+ *             PANACHE_EPOOL when massive exact ties overflowed the pool
+ *  stream     cudaStream_t to run on (null: the legacy default stream)
+ * Same rule and FP64 re-verification as panache_pmp's final selection.
+ * Scratch: one fixed array of about 145 KB in device memory, defined in the
+ * library and kept by every GPU that loads it until the process exits.  The
+ * first call on each device looks up its address (with that device
+ * current), so make that first call before any stream capture.  The call
+ * only enqueues work: read out_count after synchronising the stream.  All
+ * calls share the one array, so calls that overlap on the GPU (different
+ * streams, or threads) race; serialise them.  Errors: EINVAL for sizes out
+ * of range or null pointers, ENODEV, ECUDA. */
+int panache_topk_row_noalloc(const double *x, int64_t n, int32_t m, const uint64_t *keys, int32_t k, double eps0,
+                             panache_motif *out, int32_t *out_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -267,9 +267,10 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
                 lbs = shrink * sqrtf(lbscale * slb[lane]);
             }
             const ZT cq = Z::cell(__ldcg(&prow[q]));
-            // best-first: the block's smallest bound is evaluated before the
-            // others are tested, so the query's threshold is tight early
-            {
+            // best-first start: while the query has no distance yet, the block's
+            // smallest bound is evaluated before the others are tested, so the
+            // query's threshold is tight from the first block on
+            if (bestkey == PN_EMPTY_KEY) {
                 float bm = lbs;
                 int bl = lane;
 #pragma unroll

@@ -24,7 +24,7 @@ FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING = 0x1, 0x2
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
             "panache_stream_length", "panache_stream_close", "panache_last_stats", "panache_profile_rows",
-            "panache_anchor_state", "panache_projections", "panache_strerror")
+            "panache_anchor_state", "panache_projections", "panache_strerror", "panache_topk_row_noalloc")
 
 
 class Config(ctypes.Structure):
@@ -91,6 +91,7 @@ def lib():
         L.panache_profile_rows.argtypes = [vp, i32, vp, i64]
         L.panache_anchor_state.argtypes = [vp, i32, i32, ctypes.POINTER(i32), vp, vp, i64]
         L.panache_projections.argtypes = [ctypes.POINTER(Config), i32, vp, i64]
+        L.panache_topk_row_noalloc.argtypes = [vp, i64, i32, vp, i32, ctypes.c_double, vp, vp, vp]
         L.panache_strerror.argtypes = [ctypes.c_int]
         L.panache_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -261,6 +262,14 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+def topk_row_noalloc(x_dev, keys_dev, m: int, k: int, eps0: float, out_dev, count_dev, stream_ptr: int = 0):
+    """Selection of one length row with no device allocation (all buffers are the caller's device tensors)."""
+    return lib().panache_topk_row_noalloc(ctypes.c_void_p(x_dev.data_ptr()), x_dev.numel(), m,
+                                          ctypes.c_void_p(keys_dev.data_ptr()), k, eps0,
+                                          ctypes.c_void_p(out_dev.data_ptr()), ctypes.c_void_p(count_dev.data_ptr()),
+                                          ctypes.c_void_p(stream_ptr))
 
 
 def unpack_keys(keys: np.ndarray):
