@@ -104,6 +104,24 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
+def measured_traffic(queries: int):
+    """DRAM bytes per search launch from the committed ncu capture, scaled by queries.
+
+    Null when the kernel's sources changed since the capture (hashes differ).
+    """
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)["k_search"]
+    except (OSError, KeyError, ValueError):
+        return None
+    for path, want in t["sources_sha256_16"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != want:
+                return None
+    return t["dram_bytes_per_query"] * queries
+
+
 def roofline(stats_steps: list[dict], peaks: dict, peak_src: str, traffic: float | None):
     """Roofline of the dominant kernel, from the library's per-step CUDA events.
 
@@ -286,7 +304,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.x.nbytes),
                 "d2h_bytes_per_step": int(len(motifs) * 32)},
         "gpu_launches": int(sum(st["kernel_launches"] for st in stats)),
-        "roofline": roofline(stats, peaks, psrc, None),
+        "roofline": roofline(stats, peaks, psrc, measured_traffic(stats[-1]["queries"])),
         "clocks": clocks,
         "plain_fp64": plain,
         "step_ms": stats[-1]["step_ms"],
