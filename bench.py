@@ -171,6 +171,50 @@ def cpu_baseline(x: np.ndarray, lengths=(100, 125, 150), excl=150, target_s=12.0
                       f"{len(x)}-sample series the oracle's rate would be about {n_sample / len(x):.3f}x this"}
 
 
+def run_batched(pn, stream, n_series: int, n_loop: int):
+    """The batched form: the first n_series series of the batched workload
+    (4096 log-uniform lengths in [2000, 200000], per-series length intervals,
+    top-10, exclusion m_max) in one pmp_batch call (waves under the HBM
+    budget), against n_loop of them run one pmp call at a time."""
+    import torch
+    series = workloads.batched_workload(4096, seed=0, indices=range(n_series))
+    params = [(q.m_min, q.m_max, q.k, q.excl) for q in series]
+    xs = [torch.from_numpy(q.x).cuda() for q in series]
+    W = sum(workloads.windows_lengths(len(q.x), q.m_min, q.m_max) for q in series)
+    ctx = pn.Context(precision=1, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_TIMING)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.pmp_batch(xs, params)                      # warm-up
+    times = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.pmp_batch(xs, params)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st = ctx.stats()
+    out = {"series": n_series, "samples": int(sum(len(q.x) for q in series)), "windows_lengths": W,
+           "value": W / (statistics.mean(times) / 1e3), "unit": UNIT, "ms_per_batch": statistics.mean(times),
+           "waves": st["waves"], "kernel_launches": st["kernel_launches"], "step_ms": st["step_ms"],
+           "workload": "batched_workload(4096, seed=0)[:n]: random walk / ECG-like / sine mix, 0-5 planted "
+                       "motifs, lengths m_min~U{16..128} with 20-64 lengths, top-10, excl=m_max"}
+    if n_loop > 0:
+        sub = list(range(min(n_loop, n_series)))
+        Wl = sum(workloads.windows_lengths(len(series[i].x), series[i].m_min, series[i].m_max) for i in sub)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in sub:
+            ctx.pmp(xs[i], *params[i])
+        e1.record(stream)
+        e1.synchronize()
+        out["one_at_a_time"] = {"series": len(sub), "value": Wl / (e0.elapsed_time(e1) / 1e3), "unit": UNIT}
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, each step a bounded sample of the workload."""
     rank, world, _ = rank_env()
@@ -215,6 +259,10 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--batched", type=int, default=256,
+                    help="series of the batched workload timed as one pmp_batch (0: skip)")
+    ap.add_argument("--batched-loop", type=int, default=64,
+                    help="series of the same batch timed one pmp call at a time (0: skip)")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
     args = ap.parse_args()
     if args.warmup < 3:
@@ -288,6 +336,7 @@ def main():
         plain = {"value": W * world / (statistics.mean(pms) / 1e3), "ms_per_step": statistics.mean(pms),
                  "same_motifs": bool(np.array_equal(pmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                  "step_ms": pstats[-1]["step_ms"]}
+    batched = run_batched(pn, stream, args.batched, args.batched_loop) if args.batched > 0 else None
     if rank != 0:
         return 0
     peaks, psrc = measured_peaks()
@@ -307,6 +356,7 @@ def main():
         "roofline": roofline(stats, peaks, psrc, measured_traffic(stats[-1]["queries"])),
         "clocks": clocks,
         "plain_fp64": plain,
+        "batched": batched,
         "step_ms": stats[-1]["step_ms"],
         "counters": {k: v for k, v in stats[-1].items() if k != "step_ms"},
         "motifs": [[int(r["m"]), int(r["i"]), int(r["j"]), float(r["d"])] for r in motifs],

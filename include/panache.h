@@ -136,6 +136,7 @@ typedef struct {
     uint64_t completion_rounds;  /* rounds run (stops early when nothing improves) */
     uint64_t device_bytes;       /* device footprint of the request (admission estimate) */
     uint64_t kernel_launches;    /* kernels launched by the request */
+    uint64_t waves;              /* waves a batch was split into to fit the HBM budget */
     /* With PANACHE_FLAG_TIMING: device time of each step in ms (CUDA events on
      * the context's stream): 0 sample upload and conversion, 1 run lengths and
      * FP64 prefix moments, 2 features and keys, 3 ranks and directories,
@@ -171,8 +172,10 @@ int panache_pmp(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, 
 
 /* Many independent series in one set of launches (the batched form).  The
  * motifs of request r go to out[r * out_cap_per_req ...], their count to
- * out_len[r].  Errors as panache_pmp; EBUDGET when the whole batch exceeds
- * the budget (split it and retry). */
+ * out_len[r].  The batch runs in waves of consecutive series whose device
+ * footprint fits hbm_budget_bytes (when unset: 60% of the free device
+ * memory); each series' result does not depend on the split.  Errors as
+ * panache_pmp; EBUDGET when a single series exceeds the budget. */
 int panache_pmp_batch(panache_ctx *ctx, const panache_request *reqs, int32_t nreq, panache_motif *out,
                       int64_t out_cap_per_req, int64_t *out_len);
 

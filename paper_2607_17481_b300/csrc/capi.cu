@@ -618,6 +618,7 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     ctx->stats.exact_sieve = hs[PN_ST_EXACT_SIEVE];
     ctx->stats.exact_completion = hs[PN_ST_EXACT_COMPLETION];
     ctx->stats.kernel_launches = ctx->launches;
+    ctx->stats.waves = 1;
     return PANACHE_OK;
 }
 
@@ -699,16 +700,74 @@ int panache_pmp_batch(panache_ctx *ctx, const panache_request *reqs, int32_t nre
                       int64_t out_cap_per_req, int64_t *out_len) {
     if (!ctx || !reqs || nreq <= 0 || !out_len || out_cap_per_req < 0) return PANACHE_EINVAL;
     std::vector<SeriesIn> in;
-    for (int32_t r = 0; r < nreq; ++r)
+    for (int32_t r = 0; r < nreq; ++r) {
         in.push_back(SeriesIn{reqs[r].series, reqs[r].dtype, reqs[r].n, reqs[r].m_min, reqs[r].m_max, reqs[r].k,
                               reqs[r].excl});
-    std::vector<std::vector<panache_motif>> res;
-    PN_TRY(run_request(ctx, in, res));
-    int rc = PANACHE_OK;
-    for (int32_t r = 0; r < nreq; ++r) {
-        int e = copy_out(res[r], out ? out + (int64_t)r * out_cap_per_req : nullptr, out_cap_per_req, &out_len[r]);
-        if (e != PANACHE_OK) rc = e;
+        PN_TRY(check_series(in.back()));
     }
+    // Waves: consecutive series whose summed footprint fits the budget (the
+    // configured one, else 60% of the free device memory) and the 32-bit
+    // index spaces of one request.
+    size_t budget = ctx->cfg.hbm_budget_bytes;
+    if (!budget) {
+        size_t fr = 0, tot = 0;
+        PN_CU(cudaMemGetInfo(&fr, &tot));
+        budget = (size_t)(0.6 * (double)fr);
+    }
+    std::vector<std::pair<int32_t, int32_t>> waves;
+    {
+        int32_t w0 = 0;
+        size_t acc = 0;
+        int64_t items = 0, buckets = 0, wins = 0;
+        for (int32_t r = 0; r < nreq; ++r) {
+            PnRequest one;
+            const panache_config saved = ctx->cfg;
+            ctx->cfg.hbm_budget_bytes = 0;
+            const int prc = plan(ctx, std::vector<SeriesIn>{in[r]}, one);
+            ctx->cfg = saved;
+            PN_TRY(prc);
+            if (one.footprint > budget) return PANACHE_EBUDGET;
+            const bool full = acc + one.footprint > budget || items + one.total_items >= 0xFFFFFFFFll ||
+                              buckets + one.total_buckets >= 0xFFFFFFFEll || wins + one.total_windows >= 0xFFFFFFFFll;
+            if (r > w0 && full) {
+                waves.push_back({w0, r});
+                w0 = r;
+                acc = 0;
+                items = buckets = wins = 0;
+            }
+            acc += one.footprint;
+            items += one.total_items;
+            buckets += one.total_buckets;
+            wins += one.total_windows;
+        }
+        waves.push_back({w0, nreq});
+    }
+    panache_stats total;
+    memset(&total, 0, sizeof(total));
+    int rc = PANACHE_OK;
+    for (auto &wv : waves) {
+        std::vector<SeriesIn> part(in.begin() + wv.first, in.begin() + wv.second);
+        std::vector<std::vector<panache_motif>> res;
+        PN_TRY(run_request(ctx, part, res));
+        const panache_stats &st = ctx->stats;
+        total.queries += st.queries;
+        total.candidates += st.candidates;
+        total.exact_stream += st.exact_stream;
+        total.exact_sieve += st.exact_sieve;
+        total.exact_completion += st.exact_completion;
+        total.hot_classes += st.hot_classes;
+        total.completion_rounds = std::max(total.completion_rounds, st.completion_rounds);
+        total.device_bytes = std::max(total.device_bytes, st.device_bytes);
+        total.kernel_launches += st.kernel_launches;
+        for (int t = 0; t < 8; ++t) total.step_ms[t] += st.step_ms[t];
+        for (int32_t r = wv.first; r < wv.second; ++r) {
+            int e = copy_out(res[r - wv.first], out ? out + (int64_t)r * out_cap_per_req : nullptr, out_cap_per_req,
+                             &out_len[r]);
+            if (e != PANACHE_OK) rc = e;
+        }
+    }
+    total.waves = waves.size();
+    ctx->stats = total;
     return rc;
 }
 

@@ -58,7 +58,7 @@ STEP_NAMES = ("upload", "moments", "features", "directory", "search", "sieve", "
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in (
         "queries", "candidates", "exact_stream", "exact_sieve", "exact_completion", "hot_classes",
-        "completion_rounds", "device_bytes", "kernel_launches")] + [("step_ms", ctypes.c_double * 8)]
+        "completion_rounds", "device_bytes", "kernel_launches", "waves")] + [("step_ms", ctypes.c_double * 8)]
 
 
 _lib = None

@@ -150,6 +150,33 @@ def test_batch_equals_single(pn):
         assert np.array_equal(one, got)
 
 
+def test_batched_series_match_oracle(pn):
+    """Batched form: every series' top-10 equals the oracle's (seeded subset of the batched workload)."""
+    from parity import compare
+    series = workloads.batched_workload(6, seed=5, n_hi=6000)
+    ctx = pn.Context(precision=1, topk_mode=0)
+    got = ctx.pmp_batch([q.x for q in series], [(q.m_min, q.m_max, q.k, q.excl) for q in series])
+    for q, g in zip(series, got):
+        P, I = exact.pmp(q.x, q.m_min, q.m_max, q.excl, tier="diag")
+        ref = topk.select(P, I, q.m_min, q.k, topk.GLOBAL)
+        r = compare(q.x.astype(np.float64), g, ref)
+        assert r["misses"] == 0 and r["bad_dist"] == 0, (q.kind, len(q.x), r["miss_list"])
+
+
+def test_batch_waves_do_not_change_results(pn):
+    """A small HBM budget splits the batch into several waves; results are unchanged."""
+    series = workloads.batched_workload(8, seed=2, n_hi=20000)
+    params = [(q.m_min, q.m_max, q.k, q.excl) for q in series]
+    ctx = pn.Context(precision=1)
+    one = ctx.pmp_batch([q.x for q in series], params)
+    assert ctx.stats()["waves"] == 1
+    small = pn.Context(precision=1, hbm_budget_bytes=max(ctx.stats()["device_bytes"] // 3, 200_000_000))
+    many = small.pmp_batch([q.x for q in series], params)
+    assert small.stats()["waves"] > 1
+    for a, b in zip(one, many):
+        assert np.array_equal(a, b)
+
+
 def test_stream_equals_offline(pn, small):
     s = small
     ctx = pn.Context(topk_mode=1)
