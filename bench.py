@@ -215,6 +215,68 @@ def run_batched(pn, stream, n_series: int, n_loop: int):
     return out
 
 
+def run_served(pn, args):
+    """The served form: Poisson arrivals of batched-workload series plus live
+    streams (random walk or ECG-like, starting at 50,000 samples, lengths
+    64..128, top-20, exclusion 128) receiving 1,024-sample appends at 50 Hz,
+    each stream asked for its top-20 once a second; one request server with
+    4 slots under a 120 GB budget.  Latency: submission to motifs on the host."""
+    import numpy as np
+    rng = np.random.default_rng(99)
+    n_req = int(args.served_rate * args.served_seconds * 1.3) + 8
+    reqs = workloads.batched_workload(n_req, seed=5)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.served_rate, size=n_req))
+    arrivals = arrivals[arrivals < args.served_seconds]
+    live = []
+    for sidx in range(args.served_streams):
+        g = np.random.default_rng([123, sidx])
+        kind = "random_walk" if sidx % 2 == 0 else "ecg_like"
+        total = 50_000 + 1024 * int(50 * args.served_seconds + 2)
+        x = workloads.random_walk(g, total) if kind == "random_walk" else workloads.ecg_like(g, total)
+        live.append(x.astype(np.float32))
+    sv = pn.Server(slots=4, hbm_budget_bytes=120 * 10 ** 9, precision=1, topk_mode=pn.TOPK_GLOBAL)
+    sids = []
+    for x in live:
+        sid = sv.stream_open(64, 128, 20, 128)
+        sv.append(sid, x[:50_000])
+        sids.append(sid)
+    tickets = []
+    t0 = time.perf_counter()
+    next_req, tick = 0, 0
+    fed = [50_000] * len(live)
+    while True:
+        now = time.perf_counter() - t0
+        if now >= args.served_seconds:
+            break
+        while next_req < len(arrivals) and arrivals[next_req] <= now:
+            q = reqs[next_req]
+            tickets.append(sv.submit(q.x, q.m_min, q.m_max, q.k, q.excl))
+            next_req += 1
+        if now >= tick * 0.02:                     # 50 Hz append round
+            for i, sid in enumerate(sids):
+                sv.append(sid, live[i][fed[i]:fed[i] + 1024])
+                fed[i] += 1024
+            if tick % 50 == 49:                    # once a second: top-20 of every live stream
+                tickets.extend(sv.stream_topk(sid) for sid in sids)
+            tick += 1
+        time.sleep(0.0005)
+    tickets.extend(sv.stream_topk(sid) for sid in sids)
+    for t in tickets:
+        sv.wait(t)
+    st = sv.stats()
+    sv.close()
+    return {"requests": int(next_req), "stream_topk_requests": int(len(tickets) - next_req),
+            "live_streams": len(live), "appended_samples": int(sum(f - 50_000 for f in fed)),
+            "arrival_rate_per_s": args.served_rate, "window_s": args.served_seconds,
+            "completed": int(st["completed"]), "failed": int(st["failed"]),
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "windows_lengths": int(st["windows_lengths"]),
+            "sustained_value": st["windows_lengths"] / (st["span_ms"] / 1e3) if st["span_ms"] else None,
+            "unit": UNIT, "batches": int(st["batches"]), "max_concurrent_batches": int(st["max_concurrent_batches"]),
+            "peak_reserved_bytes": int(st["peak_reserved_bytes"]), "budget_bytes": int(st["budget_bytes"]),
+            "note": "stream top-k requests process each stream's samples received so far"}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, each step a bounded sample of the workload."""
     rank, world, _ = rank_env()
@@ -261,6 +323,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batched", type=int, default=256,
                     help="series of the batched workload timed as one pmp_batch (0: skip)")
+    ap.add_argument("--served-seconds", type=float, default=2.0, help="arrival window of the served leg (0: skip)")
+    ap.add_argument("--served-rate", type=float, default=200.0, help="Poisson request arrivals per second")
+    ap.add_argument("--served-streams", type=int, default=32, help="live streams (the workload names 256)")
     ap.add_argument("--batched-loop", type=int, default=64,
                     help="series of the same batch timed one pmp call at a time (0: skip)")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
@@ -337,6 +402,7 @@ def main():
                  "same_motifs": bool(np.array_equal(pmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                  "step_ms": pstats[-1]["step_ms"]}
     batched = run_batched(pn, stream, args.batched, args.batched_loop) if args.batched > 0 else None
+    served = run_served(pn, args) if args.served_seconds > 0 and rank == 0 else None
     if rank != 0:
         return 0
     peaks, psrc = measured_peaks()
@@ -357,6 +423,7 @@ def main():
         "clocks": clocks,
         "plain_fp64": plain,
         "batched": batched,
+        "served": served,
         "step_ms": stats[-1]["step_ms"],
         "counters": {k: v for k, v in stats[-1].items() if k != "step_ms"},
         "motifs": [[int(r["m"]), int(r["i"]), int(r["j"]), float(r["d"])] for r in motifs],

@@ -58,6 +58,7 @@ extern "C" {
 #define PANACHE_ESTATE (-6)   /* call not valid in the handle's current state */
 #define PANACHE_EPOOL (-7)    /* top-k pool overflow (massive exact ties); results withheld */
 #define PANACHE_ENODEV (-8)   /* no CUDA device, or the device is not sm_103 */
+#define PANACHE_ETIMEOUT (-9) /* a wait ran out of time before the result was ready */
 
 /* ---- sample types (low byte) and pointer location flag ---- */
 #define PANACHE_F32 1
@@ -214,6 +215,52 @@ int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t a
 int panache_projections(const panache_config *cfg, int32_t a, float *g, int64_t cap);
 
 const char *panache_strerror(int code);
+
+/* ---- request server (continuous batching under an HBM budget) ----
+ *
+ * A server runs `slots` worker threads, each with its own context and CUDA
+ * stream, so requests of different slots overlap on the GPU.  A request
+ * reserves its device footprint (the planner's estimate) from the budget
+ * before it runs and releases it when its motifs are on the host; one larger
+ * than the whole budget is refused at submission (EBUDGET).  A free slot
+ * takes, in arrival order, every queued request that fits the free budget
+ * and the slot's share of it (budget / slots) and runs them as one batch.
+ * Results do not depend on which requests share a batch or run alongside.
+ * Latency is measured from submission to the motifs being on the host.
+ * The server's contexts use cfg (the paper's defaults when null) and the
+ * device current at creation.  All calls are thread-safe. */
+typedef struct panache_server panache_server;
+
+typedef struct {
+    uint64_t submitted, completed, failed, queued, batches;
+    uint64_t windows_lengths;      /* sum over completed requests */
+    uint64_t budget_bytes, peak_reserved_bytes;
+    uint32_t max_concurrent_batches, _pad;
+    double span_ms;                /* first submission to last completion */
+    double p50_ms, p99_ms, mean_ms;   /* request latency of completed requests */
+} panache_server_stats;
+
+/* hbm_budget_bytes 0: 60% of the free device memory.  1 <= slots <= 64. */
+int panache_server_create(const panache_config *cfg, int32_t slots, uint64_t hbm_budget_bytes,
+                          panache_server **out);
+/* Drains the queue, stops the workers and frees everything. */
+void panache_server_destroy(panache_server *sv);
+/* Queues a host series (copied before returning); *ticket names the request. */
+int panache_server_submit(panache_server *sv, const void *series, int32_t dtype, int64_t n, int32_t m_min,
+                          int32_t m_max, int32_t k, int32_t excl, uint64_t *ticket);
+/* Waits up to timeout_ms (negative: forever, 0: poll) for a request; on
+ * success copies its motifs and latency and forgets the ticket.  ETIMEOUT
+ * when not ready; the request's own error code when it failed. */
+int panache_server_wait(panache_server *sv, uint64_t ticket, int32_t timeout_ms, panache_motif *out, int64_t cap,
+                        int64_t *out_len, double *latency_ms);
+/* Live streams: samples appended in chunks of any size stay on the device;
+ * panache_server_stream_topk queues a request over the samples received so
+ * far (a snapshot: later appends do not affect it). */
+int panache_server_stream_open(panache_server *sv, int32_t m_min, int32_t m_max, int32_t k, int32_t excl,
+                               uint64_t *stream_id);
+int panache_server_append(panache_server *sv, uint64_t stream_id, const void *chunk, int32_t dtype, int64_t len);
+int panache_server_stream_topk(panache_server *sv, uint64_t stream_id, uint64_t *ticket);
+int panache_server_get_stats(panache_server *sv, panache_server_stats *out);
 
 /* Top-k motifs of ONE length row from profile keys already on the device,
  * with no device memory allocated by the call.  For callers that cannot call

@@ -7,5 +7,5 @@ that needs it does, and fails loudly if it has not been built.
 """
 from .native import (DEVICE, F32, F64, FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_COMPLETION, FLAG_NO_SIEVE,  # noqa: F401
                      FLAG_TIMING, STEP_NAMES,
-                     MIXED, PLAIN_FP64, TOPK_GLOBAL, TOPK_PER_LENGTH, Context, PanacheError, Stream,
+                     MIXED, PLAIN_FP64, TOPK_GLOBAL, TOPK_PER_LENGTH, Context, PanacheError, Server, Stream,
                      default_config, unpack_keys)

@@ -12,15 +12,11 @@
 #include "panache.h"
 #include "philox.h"
 #include "prims.cuh"
+#include "runtime.h"
 
 namespace {
 
-struct SeriesIn {
-    const void *ptr;
-    int32_t dtype;
-    int64_t n;
-    int32_t m_min, m_max, k, excl;
-};
+using SeriesIn = PnSeriesIn;
 
 int from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return PANACHE_OK;
@@ -101,15 +97,18 @@ struct PnRequest {
     unsigned long long *prof = nullptr, *stats = nullptr;
     int *flagbuf = nullptr;
 
+    // Buffers come from the stream-ordered pool of the request's stream and
+    // go back to it in stream order, so requests on different streams never
+    // synchronise the device through allocation.
     ~PnRequest() {
-        for (void *p : allocs) cudaFree(p);
+        for (void *p : allocs) cudaFreeAsync(p, st);
     }
 
     template <class T>
     cudaError_t alloc(T *&p, int64_t count) {
         p = nullptr;
         if (count <= 0) count = 1;
-        cudaError_t e = cudaMalloc((void **)&p, sizeof(T) * (size_t)count);
+        cudaError_t e = cudaMallocAsync((void **)&p, sizeof(T) * (size_t)count, st);
         if (e == cudaSuccess) allocs.push_back(p);
         return e;
     }
@@ -182,8 +181,7 @@ int check_series(const SeriesIn &s) {
 }
 
 // Builds every table of a request and its device footprint.
-int plan(panache_ctx *ctx, const std::vector<SeriesIn> &in, PnRequest &R) {
-    const panache_config &c = ctx->cfg;
+int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R) {
     const int C = (int)c.chunk;
     int64_t x_off = 0, row_off = 0;
     for (size_t s = 0; s < in.size(); ++s) {
@@ -432,10 +430,10 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     if (!Rp) return PANACHE_ENOMEM;
     ctx->last = Rp;
     PnRequest &R = *Rp;
-    PN_TRY(plan(ctx, in, R));
-    ctx->stats.device_bytes = R.footprint;
     cudaStream_t st = ctx->st;
     R.st = st;
+    PN_TRY(plan(ctx->cfg, in, R));
+    ctx->stats.device_bytes = R.footprint;
     const int64_t nser = (int64_t)R.ser.size(), nanc = (int64_t)R.anc.size();
 
     PN_CU(R.alloc(R.d_ser, nser));
@@ -634,6 +632,22 @@ int copy_out(const std::vector<panache_motif> &m, panache_motif *out, int64_t ca
 
 }  // namespace
 
+namespace pn_rt {
+int run(panache_ctx *ctx, const std::vector<PnSeriesIn> &in, std::vector<std::vector<panache_motif>> &res) {
+    return run_request(ctx, in, res);
+}
+
+int footprint(panache_ctx *ctx, const PnSeriesIn &s, uint64_t *bytes) {
+    PN_TRY(check_series(s));
+    PnRequest one;
+    panache_config unbounded = ctx->cfg;      // read only: safe while ctx runs a request
+    unbounded.hbm_budget_bytes = 0;
+    PN_TRY(plan(unbounded, std::vector<SeriesIn>{s}, one));
+    *bytes = one.footprint;
+    return PANACHE_OK;
+}
+}  // namespace pn_rt
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -721,11 +735,9 @@ int panache_pmp_batch(panache_ctx *ctx, const panache_request *reqs, int32_t nre
         int64_t items = 0, buckets = 0, wins = 0;
         for (int32_t r = 0; r < nreq; ++r) {
             PnRequest one;
-            const panache_config saved = ctx->cfg;
-            ctx->cfg.hbm_budget_bytes = 0;
-            const int prc = plan(ctx, std::vector<SeriesIn>{in[r]}, one);
-            ctx->cfg = saved;
-            PN_TRY(prc);
+            panache_config unbounded = ctx->cfg;
+            unbounded.hbm_budget_bytes = 0;
+            PN_TRY(plan(unbounded, std::vector<SeriesIn>{in[r]}, one));
             if (one.footprint > budget) return PANACHE_EBUDGET;
             const bool full = acc + one.footprint > budget || items + one.total_items >= 0xFFFFFFFFll ||
                               buckets + one.total_buckets >= 0xFFFFFFFEll || wins + one.total_windows >= 0xFFFFFFFFll;

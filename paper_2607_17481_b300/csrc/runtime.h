@@ -1,0 +1,22 @@
+// Internal interface between the C ABI's request runner (capi.cu) and the
+// request server (server.cu).
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "panache.h"
+
+struct PnSeriesIn {          // one series of a request, as the caller gave it
+    const void *ptr;
+    int32_t dtype;           // PANACHE_F32 / PANACHE_F64, optionally | PANACHE_DEVICE
+    int64_t n;
+    int32_t m_min, m_max, k, excl;
+};
+
+namespace pn_rt {
+// Runs the whole path for a list of series on ctx's stream; results per series.
+int run(panache_ctx *ctx, const std::vector<PnSeriesIn> &in, std::vector<std::vector<panache_motif>> &res);
+// Device footprint of one series under ctx's configuration (admission estimate).
+int footprint(panache_ctx *ctx, const PnSeriesIn &s, uint64_t *bytes);
+}  // namespace pn_rt

@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpanache.so")
 
-OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETRUNC, ESTATE, EPOOL, ENODEV = 0, -1, -2, -3, -4, -5, -6, -7, -8
+OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETRUNC, ESTATE, EPOOL, ENODEV, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 F32, F64, DEVICE = 1, 2, 0x100
 PLAIN_FP64, MIXED = 0, 1
 TOPK_GLOBAL, TOPK_PER_LENGTH = 0, 1
@@ -24,7 +24,10 @@ FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING = 0x1, 0x2
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
             "panache_stream_length", "panache_stream_close", "panache_last_stats", "panache_profile_rows",
-            "panache_anchor_state", "panache_projections", "panache_strerror", "panache_topk_row_noalloc")
+            "panache_anchor_state", "panache_projections", "panache_strerror", "panache_topk_row_noalloc",
+            "panache_server_create", "panache_server_destroy", "panache_server_submit", "panache_server_wait",
+            "panache_server_stream_open", "panache_server_append", "panache_server_stream_topk",
+            "panache_server_get_stats")
 
 
 class Config(ctypes.Structure):
@@ -61,6 +64,13 @@ class Stats(ctypes.Structure):
         "completion_rounds", "device_bytes", "kernel_launches", "waves")] + [("step_ms", ctypes.c_double * 8)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "submitted", "completed", "failed", "queued", "batches", "windows_lengths", "budget_bytes",
+        "peak_reserved_bytes")] + [("max_concurrent_batches", ctypes.c_uint32), ("_pad", ctypes.c_uint32)] + \
+        [(name, ctypes.c_double) for name in ("span_ms", "p50_ms", "p99_ms", "mean_ms")]
+
+
 _lib = None
 
 
@@ -92,6 +102,17 @@ def lib():
         L.panache_anchor_state.argtypes = [vp, i32, i32, ctypes.POINTER(i32), vp, vp, i64]
         L.panache_projections.argtypes = [ctypes.POINTER(Config), i32, vp, i64]
         L.panache_topk_row_noalloc.argtypes = [vp, i64, i32, vp, i32, ctypes.c_double, vp, vp, vp]
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.panache_server_create.argtypes = [ctypes.POINTER(Config), i32, ctypes.c_uint64, ctypes.POINTER(vp)]
+        L.panache_server_destroy.argtypes = [vp]
+        L.panache_server_destroy.restype = None
+        L.panache_server_submit.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32, u64p]
+        L.panache_server_wait.argtypes = [vp, ctypes.c_uint64, i32, vp, i64, ctypes.POINTER(i64),
+                                          ctypes.POINTER(ctypes.c_double)]
+        L.panache_server_stream_open.argtypes = [vp, i32, i32, i32, i32, u64p]
+        L.panache_server_append.argtypes = [vp, ctypes.c_uint64, vp, i32, i64]
+        L.panache_server_stream_topk.argtypes = [vp, ctypes.c_uint64, u64p]
+        L.panache_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         L.panache_strerror.argtypes = [ctypes.c_int]
         L.panache_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -255,6 +276,74 @@ class Stream:
     def close(self):
         if self._h:
             lib().panache_stream_close(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request server: continuous batching over `slots` concurrent streams under an HBM budget."""
+
+    def __init__(self, slots: int = 4, hbm_budget_bytes: int = 0, config: Config | None = None, **over):
+        cfg = config if config is not None else default_config(**over)
+        self._h = ctypes.c_void_p()
+        _check(lib().panache_server_create(ctypes.byref(cfg), slots, hbm_budget_bytes, ctypes.byref(self._h)),
+               "server_create")
+        self.config = cfg
+        self._caps: dict[int, int] = {}
+
+    def submit(self, x, m_min: int, m_max: int, k: int, excl: int) -> int:
+        a = np.ascontiguousarray(np.asarray(x))
+        if a.dtype not in (np.float32, np.float64):
+            a = a.astype(np.float64)
+        t = ctypes.c_uint64()
+        _check(lib().panache_server_submit(self._h, a.ctypes.data_as(ctypes.c_void_p), F32 if a.dtype == np.float32
+                                           else F64, a.shape[0], m_min, m_max, k, excl, ctypes.byref(t)), "submit")
+        self._caps[t.value] = k * (m_max - m_min + 1)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(motifs, latency_ms); raises PanacheError (ETIMEOUT when not ready in time)."""
+        cap = max(1, self._caps.get(ticket, 4096))
+        out = np.zeros(cap, dtype=MOTIF_DTYPE)
+        ln = ctypes.c_int64()
+        lat = ctypes.c_double()
+        _check(lib().panache_server_wait(self._h, ticket, timeout_ms, out.ctypes.data_as(ctypes.c_void_p), cap,
+                                         ctypes.byref(ln), ctypes.byref(lat)), "wait")
+        self._caps.pop(ticket, None)
+        return out[:ln.value], lat.value
+
+    def stream_open(self, m_min: int, m_max: int, k: int, excl: int) -> int:
+        sid = ctypes.c_uint64()
+        _check(lib().panache_server_stream_open(self._h, m_min, m_max, k, excl, ctypes.byref(sid)), "stream_open")
+        self._caps[("s", sid.value)] = k * (m_max - m_min + 1)
+        return sid.value
+
+    def append(self, sid: int, chunk):
+        a = np.ascontiguousarray(np.asarray(chunk))
+        if a.dtype not in (np.float32, np.float64):
+            a = a.astype(np.float64)
+        _check(lib().panache_server_append(self._h, sid, a.ctypes.data_as(ctypes.c_void_p),
+                                           F32 if a.dtype == np.float32 else F64, a.shape[0]), "append")
+
+    def stream_topk(self, sid: int) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().panache_server_stream_topk(self._h, sid, ctypes.byref(t)), "stream_topk")
+        self._caps[t.value] = self._caps.get(("s", sid), 4096)
+        return t.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().panache_server_get_stats(self._h, ctypes.byref(s)), "server_stats")
+        return {name: getattr(s, name) for name, _ in ServerStats._fields_ if name != "_pad"}
+
+    def close(self):
+        if self._h:
+            lib().panache_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

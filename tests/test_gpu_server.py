@@ -1,0 +1,109 @@
+"""The request server: continuous batching, admission by HBM footprint, live streams.
+
+Results must not depend on which requests share a batch or run alongside
+(the north star's "same alone and in the mix"); the parity tolerance here is
+zero: motifs are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pn():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2607_17481_b300 as pkg
+    from paper_2607_17481_b300 import build
+    build.build()
+    return pkg
+
+
+def _series(count, seed, n_hi=30000):
+    return workloads.batched_workload(count, seed=seed, n_hi=n_hi)
+
+
+def test_alone_equals_mix(pn):
+    reqs = _series(12, seed=11)
+    alone = []
+    with_one = pn.Server(slots=1)
+    for q in reqs:
+        t = with_one.submit(q.x, q.m_min, q.m_max, q.k, q.excl)
+        alone.append(with_one.wait(t)[0])
+    with_one.close()
+    mix = pn.Server(slots=3)
+    noise = _series(20, seed=12)
+    tickets = []
+    for a, b in zip(noise[:12], reqs):               # interleave with unrelated requests
+        mix.submit(a.x, a.m_min, a.m_max, a.k, a.excl)
+        tickets.append(mix.submit(b.x, b.m_min, b.m_max, b.k, b.excl))
+    for t, ref in zip(tickets, alone):
+        got, lat = mix.wait(t)
+        assert np.array_equal(got, ref)
+        assert lat > 0
+    st = mix.stats()
+    assert st["completed"] >= 24 and st["failed"] == 0
+    mix.close()
+
+
+def test_server_matches_context(pn):
+    q = _series(1, seed=3)[0]
+    ctx = pn.Context()
+    ref = ctx.pmp(q.x, q.m_min, q.m_max, q.k, q.excl)
+    sv = pn.Server(slots=2)
+    got, _ = sv.wait(sv.submit(q.x, q.m_min, q.m_max, q.k, q.excl))
+    assert np.array_equal(got, ref)
+    sv.close()
+
+
+def test_admission_budget(pn):
+    reqs = _series(6, seed=21, n_hi=20000)
+    ctx = pn.Context()
+    ctx.pmp(reqs[0].x, reqs[0].m_min, reqs[0].m_max, reqs[0].k, reqs[0].excl)
+    one = ctx.stats()["device_bytes"]
+    # a budget below one request refuses it at submission
+    tiny = pn.Server(slots=2, hbm_budget_bytes=max(1, one // 4))
+    with pytest.raises(pn.PanacheError) as e:
+        tiny.submit(reqs[0].x, reqs[0].m_min, reqs[0].m_max, reqs[0].k, reqs[0].excl)
+    assert e.value.code == -3
+    tiny.close()
+    # a budget that fits about one request at a time serialises the slots; nothing is lost
+    big = max(one, max(_footprint(pn, q) for q in reqs))
+    tight = pn.Server(slots=4, hbm_budget_bytes=int(big * 1.3))
+    ts = [tight.submit(q.x, q.m_min, q.m_max, q.k, q.excl) for q in reqs]
+    for t in ts:
+        tight.wait(t)
+    st = tight.stats()
+    assert st["completed"] == 6 and st["peak_reserved_bytes"] <= st["budget_bytes"]
+    tight.close()
+
+
+def _footprint(pn, q):
+    ctx = pn.Context()
+    ctx.pmp(q.x, q.m_min, q.m_max, q.k, q.excl)
+    return ctx.stats()["device_bytes"]
+
+
+def test_live_stream_topk_equals_offline(pn):
+    s = workloads.planted_random_walk()
+    sv = pn.Server(slots=2, topk_mode=1)
+    sid = sv.stream_open(s.m_min, s.m_max, s.k, s.excl)
+    rng = np.random.default_rng(7)
+    pos = 0
+    mid_ticket = None
+    while pos < s.x.shape[0]:
+        step = int(rng.integers(1, 2500))
+        sv.append(sid, s.x[pos:pos + step])
+        pos += step
+        if mid_ticket is None and pos > 4000:
+            mid_ticket, mid_len = sv.stream_topk(sid), pos   # snapshot while appends continue
+    final, _ = sv.wait(sv.stream_topk(sid))
+    ctx = pn.Context(topk_mode=1)
+    assert np.array_equal(final, ctx.pmp(s.x, s.m_min, s.m_max, s.k, s.excl))
+    snap, _ = sv.wait(mid_ticket)
+    assert np.array_equal(snap, ctx.pmp(s.x[:mid_len], s.m_min, s.m_max, s.k, s.excl))
+    sv.close()
