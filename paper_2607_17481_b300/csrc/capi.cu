@@ -637,7 +637,9 @@ int run(panache_ctx *ctx, const std::vector<PnSeriesIn> &in, std::vector<std::ve
     return run_request(ctx, in, res);
 }
 
-int footprint(panache_ctx *ctx, const PnSeriesIn &s, uint64_t *bytes) {
+int footprint(panache_ctx *ctx, const PnSeriesIn &s_in, uint64_t *bytes) {
+    PnSeriesIn s = s_in;
+    if (!s.ptr) s.ptr = bytes;          // planning reads sizes only, never the samples
     PN_TRY(check_series(s));
     PnRequest one;
     panache_config unbounded = ctx->cfg;      // read only: safe while ctx runs a request
