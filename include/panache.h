@@ -78,12 +78,13 @@ extern "C" {
 #define PANACHE_FLAG_NO_SIEVE 0x2          /* skip the hot-class sieve (S_hot) */
 #define PANACHE_FLAG_NO_COMPLETION 0x4     /* skip local completion (S_local) */
 #define PANACHE_FLAG_TIMING 0x8            /* time each step with CUDA events on the context's stream */
+#define PANACHE_FLAG_INDEX_ONLY 0x10       /* build features, keys and directories, then stop (no motifs) */
 
 /* Tunables.  A zero field takes the paper's default (Sec. 4):
  * alpha 16, gamma 8 (R = 128), stride 2, K 16, B 24, d0 12, probe cap 8,
  * sieve width 8, (dm, dp) = (6, 4), 8 completion rounds, lambda 1e-4,
  * eps0 1e-6, batch beta = excl, chunk 256 slides per direct-DFT anchor,
- * seed_mult 2. */
+ * seed_mult 2, grid_mult 8. */
 typedef struct {
     uint32_t alpha;       /* occupancy target, the analyst's one knob ("budget") */
     uint32_t gamma;       /* R = gamma * alpha candidate inspections per query (R <= 512) */
@@ -101,7 +102,7 @@ typedef struct {
     uint32_t chunk;       /* slides per direct-DFT re-anchor (power of two, 16..4096) */
     uint32_t beta;        /* batch length of the streaming schedule (0: excl; capped at excl) */
     uint32_t seed_mult;   /* completion seeds per round: the top seed_mult*k cells (per length in per-length mode) */
-    uint32_t _reserved;
+    uint32_t grid_mult;   /* resident-block multiple of the search and sieve grids (blocks = SMs * grid_mult) */
     uint64_t seed;        /* seed of the Gaussian projections */
     uint64_t hbm_budget_bytes; /* admission limit on a request's device footprint (0: none) */
     double lambda;        /* bound shrink */

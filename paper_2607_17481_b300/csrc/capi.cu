@@ -157,6 +157,7 @@ void fill_defaults(panache_config &c) {
     if (!c.rounds) c.rounds = 8;
     if (!c.chunk) c.chunk = 256;
     if (!c.seed_mult) c.seed_mult = 2;
+    if (!c.grid_mult) c.grid_mult = 8;
     if (c.lambda == 0.0) c.lambda = 1e-4;
     if (c.eps0 == 0.0) c.eps0 = 1e-6;
 }
@@ -166,6 +167,7 @@ int check_config(const panache_config &c) {
     if ((int)(c.gamma * c.alpha) > pn::search_max_budget() || c.alpha > (1u << 20)) return PANACHE_EINVAL;
     if (c.probe_cap < 1 || c.probe_cap > 8 || c.precision > 1 || c.topk_mode > 1) return PANACHE_EINVAL;
     if (c.chunk < 16 || c.chunk > 4096 || (c.chunk & (c.chunk - 1))) return PANACHE_EINVAL;
+    if (c.grid_mult > 64) return PANACHE_EINVAL;
     if (!(c.lambda > 0.0 && c.lambda < 1.0) || !(c.eps0 >= 0.0)) return PANACHE_EINVAL;
     return PANACHE_OK;
 }
@@ -526,7 +528,7 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
 
     PN_TRY(tm.mark(1));
     PnView v = make_view(ctx, R);
-    const int grid = ctx->sm_count * 8;
+    const int grid = ctx->sm_count * (int)c.grid_mult;
     // Algorithm 1 over every anchor of every series
     PN_CU(pn::launch_runlen(v, R.total_samples, st));
     PN_CU(pn::launch_moments(v, R.total_samples, R.sq, st));
@@ -537,6 +539,15 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
     PN_CU(pn::launch_query_order(v, R.total_windows, R.total_buckets, st));
     PN_TRY(tm.mark(4));
+    if (c.flags & PANACHE_FLAG_INDEX_ONLY) {
+        for (int t = 5; t <= 8; ++t) PN_TRY(tm.mark(t));
+        PN_TRY(tm.read(ctx->stats.step_ms));
+        PN_CU(cudaStreamSynchronize(st));
+        res.assign(nser, {});
+        ctx->stats.kernel_launches = ctx->launches;
+        ctx->stats.waves = 1;
+        return PANACHE_OK;
+    }
     PN_CU(pn::launch_search(v, R.total_windows, grid, R.a_max, st));
     PN_TRY(tm.mark(5));
     ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3 + 1 + 1 + 4 * 3;

@@ -93,6 +93,8 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
     const double *xs = v.x + S.x_off;
     const double shift = v.shift[A.series];
     const int32_t *rl = v.runlen + S.x_off;
+    const double2 *sqp = v.sq + S.x_off + A.series;
+    const double inv_a = 1.0 / (double)a;
 
     ST Xr[PN_MAXK - 1], Xi[PN_MAXK - 1];
 #pragma unroll
@@ -139,22 +141,36 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
 #pragma unroll
         for (int t = 0; t < PN_FEAT; ++t) f[t] = 0.0f;
         if (act) {
-            double mu, var;
-            pn_moments(v, A.series, q, a, mu, var);
+            // moments from the FP64 prefix sums; the mixed form normalises in FP32
+            const double2 pa = sqp[q], pb = sqp[q + a];
+            const double ms = (pb.x - pa.x) * inv_a;
+            const double var = (pb.y - pa.y) * inv_a - ms * ms;
+            const double mu = ms + shift;
             const bool nonconst = rl[q] < a;
-            const double inv = (nonconst && var > 0.0) ? 1.0 / sqrt(var) : 0.0;
+            const bool ok = nonconst && var > 0.0;
             if (v.precision == 0) {
+                const double inv = ok ? 1.0 / sqrt(var) : 0.0;
                 v.wmd[A.win_off + q] = make_double2(mu, inv);
-            } else {
-                const float mh = (float)mu;
-                v.wmf[A.win_off + q] = make_float4(mh, (float)(mu - (double)mh), (float)inv, 0.0f);
-            }
-            if (inv != 0.0) {
+                if (ok) {
 #pragma unroll
-                for (int k = 0; k < PN_MAXK - 1; ++k) {
-                    if (k < kp) {
-                        f[2 * k] = (float)((double)Xr[k] * inv);
-                        f[2 * k + 1] = (float)((double)Xi[k] * inv);
+                    for (int k = 0; k < PN_MAXK - 1; ++k) {
+                        if (k < kp) {
+                            f[2 * k] = (float)((double)Xr[k] * inv);
+                            f[2 * k + 1] = (float)((double)Xi[k] * inv);
+                        }
+                    }
+                }
+            } else {
+                const float invf = ok ? rsqrtf((float)var) : 0.0f;
+                const float mh = (float)mu;
+                v.wmf[A.win_off + q] = make_float4(mh, (float)(mu - (double)mh), invf, 0.0f);
+                if (ok) {
+#pragma unroll
+                    for (int k = 0; k < PN_MAXK - 1; ++k) {
+                        if (k < kp) {
+                            f[2 * k] = (float)Xr[k] * invf;
+                            f[2 * k + 1] = (float)Xi[k] * invf;
+                        }
                     }
                 }
             }
@@ -192,11 +208,19 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
             for (int k = 0; k < PN_MAXK - 1; ++k) {
                 if (k < kp) {
                     const double2 w = tw[k + 1];
-                    const ST cr_ = (ST)w.x, sr_ = (ST)w.y;
                     const ST re = Xr[k] + delta;
                     const ST im = Xi[k];
-                    Xr[k] = re * cr_ - im * sr_;
-                    Xi[k] = re * sr_ + im * cr_;
+                    if constexpr (sizeof(ST) == 8) {
+                        Xr[k] = re * (ST)w.x - im * (ST)w.y;
+                        Xi[k] = re * (ST)w.y + im * (ST)w.x;
+                    } else {
+                        // FP32 state: the rotation factor as a float-float pair, so its
+                        // rounding does not compound into a phase drift over the chunk
+                        const float ch = (float)w.x, sh = (float)w.y;
+                        const float cl = (float)(w.x - (double)ch), sl = (float)(w.y - (double)sh);
+                        Xr[k] = fmaf(re, ch, fmaf(-im, sh, fmaf(re, cl, -im * sl)));
+                        Xi[k] = fmaf(re, sh, fmaf(im, ch, fmaf(re, sl, im * cl)));
+                    }
                 }
             }
         }

@@ -19,7 +19,7 @@ OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETRUNC, ESTATE, EPOOL, ENODEV, ETIMEOUT = 0,
 F32, F64, DEVICE = 1, 2, 0x100
 PLAIN_FP64, MIXED = 0, 1
 TOPK_GLOBAL, TOPK_PER_LENGTH = 0, 1
-FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING = 0x1, 0x2, 0x4, 0x8
+FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING, FLAG_INDEX_ONLY = 0x1, 0x2, 0x4, 0x8, 0x10
 
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
                 ("probe_cap", ctypes.c_uint32), ("sieve_w", ctypes.c_uint32), ("dm", ctypes.c_uint32),
                 ("dp", ctypes.c_uint32), ("rounds", ctypes.c_uint32), ("precision", ctypes.c_uint32),
                 ("topk_mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
-                ("beta", ctypes.c_uint32), ("seed_mult", ctypes.c_uint32), ("_reserved", ctypes.c_uint32),
+                ("beta", ctypes.c_uint32), ("seed_mult", ctypes.c_uint32), ("grid_mult", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("lambda_", ctypes.c_double), ("eps0", ctypes.c_double)]
 

@@ -227,3 +227,26 @@ def test_edge_cases(pn):
         ctx.pmp(x, 2, 10, 5, 8)
     with pytest.raises(pn.PanacheError):
         ctx.pmp(x, 20, 10, 5, 8)
+
+
+def test_mixed_drift_within_lambda_over_ten(pn):
+    """Mixed form: FP32 sliding state from FP64 anchors drifts at most lambda/10 at the default chunk.
+
+    This keeps Lemma 5's (1 - lambda) shrink valid at the paper's margin.
+    Measured on the planted walk (large offsets) and the wafer-like series.
+    """
+    from paper_2607_17481_b300 import autotune
+    for x, (m1, m2) in ((workloads.planted_random_walk().x, (32, 64)),
+                        (workloads.wafer_like(100_000, seed=0).x, (100, 150))):
+        for a in (m1, m2):
+            d, curve = autotune.feature_drift(x, a, 256)
+            assert d <= 1e-5, (a, d)
+            assert curve[0] <= 1e-6            # windows at an anchor carry FP32 rounding only
+
+
+def test_autotune_picks_a_valid_chunk(pn):
+    from paper_2607_17481_b300 import autotune
+    x = workloads.wafer_like(60_000, seed=1).x
+    r = autotune.tune(x, 100, 150, sample=60_000, grid_mults=(4, 8))
+    assert r["drift"][r["chunk"]] <= 1e-5
+    assert r["grid_mult"] in (4, 8)
