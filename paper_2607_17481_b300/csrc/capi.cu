@@ -90,7 +90,7 @@ struct PnRequest {
     int32_t *runlen = nullptr;
     float *F = nullptr;
     uint32_t *sig = nullptr, *cnt = nullptr, *nclist = nullptr, *qorder = nullptr;
-    float4 *wmf = nullptr;
+    float2 *wmf = nullptr;
     double2 *wmd = nullptr;
     float *g = nullptr;
     uint32_t *dir_keys = nullptr, *dir_vals = nullptr, *bstart = nullptr;

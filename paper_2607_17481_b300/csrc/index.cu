@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
             const bool ok = nonconst && var > 0.0;
             if (v.precision == 0) {
                 const double inv = ok ? 1.0 / sqrt(var) : 0.0;
-                v.wmd[A.win_off + q] = make_double2(mu, inv);
+                v.wmd[A.win_off + q] = make_double2(inv, -mu * inv);
                 if (ok) {
 #pragma unroll
                     for (int k = 0; k < PN_MAXK - 1; ++k) {
@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
                 }
             } else {
                 const float invf = ok ? rsqrtf((float)var) : 0.0f;
-                const float mh = (float)mu;
-                v.wmf[A.win_off + q] = make_float4(mh, (float)(mu - (double)mh), invf, 0.0f);
+                // z = fma(x, 1/sigma, -mu/sigma): one rounding, no cancellation for |mu| >> sigma
+                v.wmf[A.win_off + q] = make_float2(invf, (float)(-mu * (double)invf));
                 if (ok) {
 #pragma unroll
                     for (int k = 0; k < PN_MAXK - 1; ++k) {

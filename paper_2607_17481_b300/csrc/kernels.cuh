@@ -36,8 +36,8 @@ struct PnView {
     uint32_t *sig;        // B-bit SimHash keys
     uint32_t *cnt;        // inclusive count of non-constant windows with start <= q
     uint32_t *nclist;     // start of the r-th non-constant window
-    float4 *wmf;          // mixed form: per-window (mu_hi, mu_lo, 1/sigma, 0); 1/sigma = 0 if degenerate
-    double2 *wmd;         // plain form: per-window (mu, 1/sigma)
+    float2 *wmf;          // mixed form: per-window (1/sigma, -mu/sigma) as floats; 1/sigma = 0 if degenerate
+    double2 *wmd;         // plain form: per-window (1/sigma, -mu/sigma)
     uint32_t *qorder;     // search order of the flat query space (grouped by probe bucket)
     const float *g;       // projections [nanchors][B+1][PN_FEAT]
     // directory
