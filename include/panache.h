@@ -67,7 +67,7 @@ extern "C" {
 
 /* ---- precision forms ---- */
 #define PANACHE_PLAIN_FP64 0  /* FP64 sliding-DFT state and FP64 in-stream distances */
-#define PANACHE_MIXED 1       /* FP32 recurrence from FP64 anchors, FP32 in-stream distances */
+#define PANACHE_MIXED 1       /* FP32 recurrence from tensor-core anchors, FP32 in-stream distances */
 
 /* ---- top-k modes ---- */
 #define PANACHE_TOPK_GLOBAL 0      /* k cells over the whole stack */
@@ -79,6 +79,8 @@ extern "C" {
 #define PANACHE_FLAG_NO_COMPLETION 0x4     /* skip local completion (S_local) */
 #define PANACHE_FLAG_TIMING 0x8            /* time each step with CUDA events on the context's stream */
 #define PANACHE_FLAG_INDEX_ONLY 0x10       /* build features, keys and directories, then stop (no motifs) */
+#define PANACHE_FLAG_FP64_ANCHORS 0x20     /* mixed form: chunk anchors by FP64 direct DFT instead of the
+                                              tensor cores (3xTF32 tcgen05 contraction, the default) */
 
 /* Tunables.  A zero field takes the paper's default (Sec. 4):
  * alpha 16, gamma 8 (R = 128), stride 2, K 16, B 24, d0 12, probe cap 8,

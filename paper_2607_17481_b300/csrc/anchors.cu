@@ -1,0 +1,224 @@
+// Chunk anchors of the mixed form on the tensor cores (tcgen05, kind::tf32).
+//
+// The sliding DFT of each chunk starts from the direct DFT of its first
+// window (Sec. 3.2, the periodic recompute):
+//   X_k(q0) = sum_{r<a} (t_{q0+r} - mu_{q0}) e^{-2 pi i k r / a},  k = 1..K'.
+// (Centring by the window mean leaves every k >= 1 bin unchanged and keeps
+// the operands near sigma in magnitude.)  For one anchor length this is a
+// dense contraction D[chunks x 32] = A[chunks x a] B[32 x a]^T with
+// A[c][r] = t_{cC + r} - mu_c and B[2k-2][r] = cos(2 pi k r / a),
+// B[2k-1][r] = -sin(2 pi k r / a).  Each CTA computes a 128-row tile:
+// operands are staged in shared memory in the K-major no-swizzle canonical
+// layout (8-row x 16-byte core matrices), split into TF32 hi + lo parts, and
+// one thread issues three tcgen05.mma per 8-wide K step (hi*hi + hi*lo +
+// lo*hi, FP32 accumulation in tensor memory), which carries about 21 bits of
+// each product.  The accumulator is read back with tcgen05.ld (each warp its
+// 32 lanes) and written as FP32 (re, im) pairs per chunk.
+//
+// Every wait is bounded: on timeout the kernel records an error word, waits
+// once more (bounded), frees its tensor memory and returns.
+#include "kernels.cuh"
+
+namespace pn {
+namespace {
+
+constexpr int AT_ROWS = 128;      // chunks per CTA (MMA M)
+constexpr int AT_N = 32;          // accumulator columns (2 K' <= 30, padded)
+constexpr int AT_KS = 64;         // samples per K slice staged at a time
+constexpr int AT_THREADS = 128;
+constexpr int AT_SPIN = 1 << 22;  // try_wait iterations before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory matrix descriptor: start, leading (K-direction) and
+// stride (M/N-direction) byte offsets of the core matrices, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor: D F32, A and B TF32, both K-major, M x N.
+__device__ __forceinline__ uint32_t umma_idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Element (row, k) of a K-major canonical layout with kg = KS/4 core matrices along K.
+__device__ __forceinline__ int kmaj(int row, int k, int kg) {
+    return ((row >> 3) * kg + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    uint32_t done = 0;
+    for (int it = 0; it < AT_SPIN && !done; ++it) {
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(phase)
+                     : "memory");
+    }
+    return done != 0;
+}
+
+__global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_t *tile_anchor, const int32_t *tile_row0) {
+    extern __shared__ __align__(128) float sm[];
+    float *Ahi = sm;                                  // [128 x KS] canonical
+    float *Alo = Ahi + AT_ROWS * AT_KS;
+    float *Bhi = Alo + AT_ROWS * AT_KS;               // [32 x KS] canonical
+    float *Blo = Bhi + AT_N * AT_KS;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t taddr_s;
+    __shared__ double mu_s[AT_ROWS];
+    __shared__ int fail_s;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ai = tile_anchor[blockIdx.x];
+    const PnAnchor A = v.anchors[ai];
+    const PnSeries S = v.series[A.series];
+    const int a = A.a, kp = A.kp, C = v.C;
+    const int64_t c0 = tile_row0[blockIdx.x];
+    const int kg = AT_KS / 4;
+
+    // window means of the tile's chunk starts (FP64 prefix sums)
+    for (int m = tid; m < AT_ROWS; m += AT_THREADS) {
+        const int64_t c = c0 + m;
+        double mu = 0.0;
+        if (c < A.nchunk) {
+            double var;
+            pn_moments(v, A.series, c * C, a, mu, var);
+        }
+        mu_s[m] = mu;
+    }
+    if (tid == 0) {
+        fail_s = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                     "r"(AT_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = taddr_s;
+    const double *xs = v.x + S.x_off;
+    const uint32_t idesc = umma_idesc_tf32(AT_ROWS, AT_N);
+
+    uint32_t phase = 0;
+    bool ok = true;
+    const int nslice = (a + AT_KS - 1) / AT_KS;
+    for (int sl = 0; sl < nslice && ok; ++sl) {
+        const int r0 = sl * AT_KS;
+        // A slice: centred samples of every chunk start, split into TF32 hi + lo
+        for (int t = tid; t < AT_ROWS * AT_KS; t += AT_THREADS) {
+            const int m = t / AT_KS, k = t - m * AT_KS, r = r0 + k;
+            const int64_t c = c0 + m;
+            float val = 0.0f;
+            if (c < A.nchunk && r < a) val = (float)(xs[c * C + r] - mu_s[m]);
+            const float hi = tf32_hi(val);
+            Ahi[kmaj(m, k, kg)] = hi;
+            Alo[kmaj(m, k, kg)] = val - hi;
+        }
+        // B slice: twiddles of bins 1..K' (rows 2k-2: cos, 2k-1: -sin)
+        for (int t = tid; t < AT_N * AT_KS; t += AT_THREADS) {
+            const int n = t / AT_KS, k = t - n * AT_KS, r = r0 + k;
+            const int bin = (n >> 1) + 1;
+            float val = 0.0f;
+            if (bin <= kp && r < a) {
+                const int ph = (int)(((int64_t)bin * r) % a);
+                double sn, cs;
+                sincospi(2.0 * (double)ph / (double)a, &sn, &cs);
+                val = (n & 1) ? (float)(-sn) : (float)cs;
+            }
+            const float hi = tf32_hi(val);
+            Bhi[kmaj(n, k, kg)] = hi;
+            Blo[kmaj(n, k, kg)] = val - hi;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t lbo = 128, sbo = kg * 128;
+            for (int s = 0; s < AT_KS / 8; ++s) {
+                const uint32_t off = (uint32_t)(s * 2 * 32 * sizeof(float));
+                const uint64_t ah = umma_desc(smem_u32(Ahi) + off, lbo, sbo);
+                const uint64_t al = umma_desc(smem_u32(Alo) + off, lbo, sbo);
+                const uint64_t bh = umma_desc(smem_u32(Bhi) + off, lbo, sbo);
+                const uint64_t bl = umma_desc(smem_u32(Blo) + off, lbo, sbo);
+                const uint32_t acc0 = (sl > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }"
+                             ::"r"(taddr), "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(taddr), "l"(ah), "l"(bl),
+                             "r"(idesc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(taddr), "l"(al), "l"(bh),
+                             "r"(idesc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&mbar))
+                         : "memory");
+        }
+        // the next slice overwrites the operands: wait until the MMAs have read them
+        if (!mbar_wait(smem_u32(&mbar), phase)) {
+            if (lane == 0) atomicExch(&fail_s, 1);
+        }
+        phase ^= 1u;
+        __syncthreads();
+        ok = fail_s == 0;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        uint32_t r[32];
+        const uint32_t ta = taddr + ((uint32_t)(warp * 32) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+            "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int64_t c = c0 + warp * 32 + lane;
+        if (c < A.nchunk) {
+            float4 *dst = reinterpret_cast<float4 *>(v.anc + (A.chunk_off + c) * PN_FEAT);
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                dst[t] = make_float4(__uint_as_float(r[4 * t]), __uint_as_float(r[4 * t + 1]),
+                                     __uint_as_float(r[4 * t + 2]), __uint_as_float(r[4 * t + 3]));
+        }
+    } else if (tid == 0) {
+        atomicExch(v.err, PN_ERR_TC_TIMEOUT);
+        mbar_wait(smem_u32(&mbar), phase ^ 1u);     // let any MMA still in flight finish (bounded)
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(AT_N));
+}
+
+}  // namespace
+
+size_t anchor_tc_smem() { return sizeof(float) * (2 * AT_ROWS * AT_KS + 2 * AT_N * AT_KS); }
+
+cudaError_t launch_anchor_tc(const PnView &v, const int32_t *tile_anchor, const int32_t *tile_row0, int32_t ntiles,
+                             cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    const size_t sm = anchor_tc_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_anchor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_anchor_tc<<<ntiles, AT_THREADS, sm, st>>>(v, tile_anchor, tile_row0);
+    return cudaGetLastError();
+}
+
+}  // namespace pn

@@ -69,6 +69,8 @@ struct PnRequest {
     std::vector<PnAnchor> anc;
     std::vector<PnLevel> lev;
     std::vector<int32_t> blk_anchor, blk_chunk0;
+    std::vector<int32_t> tile_anchor, tile_row0;   // tensor-core anchor tiles (128 chunks each)
+    int64_t total_chunks = 0;
     std::vector<int64_t> slot_off;
     int64_t total_samples = 0, total_windows = 0, total_rows = 0, total_items = 0, total_buckets = 0;
     int64_t total_cells = 0, total_slots = 0;
@@ -81,6 +83,9 @@ struct PnRequest {
     PnAnchor *d_anc = nullptr;
     PnLevel *d_lev = nullptr;
     int32_t *d_blk_anchor = nullptr, *d_blk_chunk0 = nullptr;
+    int32_t *d_tile_anchor = nullptr, *d_tile_row0 = nullptr;
+    float *tca = nullptr;      // tensor-core chunk anchors
+    int *err = nullptr;
     int64_t *d_slot_off = nullptr;
     double *x = nullptr;
     float2 *xs = nullptr;
@@ -214,6 +219,7 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R)
             A.dmax = pn_depth(nw, (int)c.alpha, (int)c.B);
             A.win_off = R.total_windows;
             A.nchunk = (nw + C - 1) / C;
+            A.chunk_off = R.total_chunks;
             A.row_off = R.total_rows;
             A.item_off = R.total_items;
             A.bucket_base = R.total_buckets;
@@ -233,7 +239,10 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R)
             for (int64_t b = 0; b < A.nchunk; b += 128) {
                 R.blk_anchor.push_back((int32_t)R.anc.size());
                 R.blk_chunk0.push_back((int32_t)b);
+                R.tile_anchor.push_back((int32_t)R.anc.size());
+                R.tile_row0.push_back((int32_t)b);
             }
+            R.total_chunks += A.nchunk;
             R.slot_off.push_back(R.total_slots);
             R.total_slots += (int64_t)1 << A.dmax;
             R.total_windows += nw;
@@ -259,6 +268,7 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R)
     b += (size_t)R.total_buckets * 4 + (size_t)R.total_items / 4096 * 1024;
     b += (size_t)R.total_cells * 8;                         // profile rows
     b += (size_t)R.anc.size() * (c.B + 1) * PN_FEAT * 4;
+    b += (size_t)R.total_chunks * PN_FEAT * 4;               // tensor-core anchors
     R.footprint = b;
     if (c.hbm_budget_bytes && b > c.hbm_budget_bytes) return PANACHE_EBUDGET;
     return PANACHE_OK;
@@ -300,6 +310,8 @@ PnView make_view(panache_ctx *ctx, PnRequest &R) {
     v.wmf = R.wmf;
     v.wmd = R.wmd;
     v.g = R.g;
+    v.anc = R.tca;
+    v.err = R.err;
     v.dir_keys = R.dir_keys;
     v.dir_vals = R.dir_vals;
     v.bstart = R.bstart;
@@ -466,6 +478,13 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PN_CU(R.alloc(R.prof, R.total_cells));
     PN_CU(R.alloc(R.stats, PN_ST_COUNT));
     PN_CU(R.alloc(R.flagbuf, 4));
+    PN_CU(R.alloc(R.err, 1));
+    const bool tc_anchors = c.precision == PANACHE_MIXED && !(c.flags & PANACHE_FLAG_FP64_ANCHORS);
+    if (tc_anchors) {
+        PN_CU(R.alloc(R.tca, R.total_chunks * PN_FEAT));
+        PN_CU(R.alloc(R.d_tile_anchor, (int64_t)R.tile_anchor.size()));
+        PN_CU(R.alloc(R.d_tile_row0, (int64_t)R.tile_row0.size()));
+    }
 
     // tables and projections
     std::vector<float> hg((size_t)nanc * (c.B + 1) * PN_FEAT);
@@ -482,10 +501,17 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
         PN_CU(cudaMemcpyAsync(R.d_blk_chunk0, R.blk_chunk0.data(), 4 * R.blk_chunk0.size(), cudaMemcpyHostToDevice,
                               st));
         PN_CU(cudaMemcpyAsync(R.d_slot_off, R.slot_off.data(), 8 * nanc, cudaMemcpyHostToDevice, st));
+        if (R.tca) {
+            PN_CU(cudaMemcpyAsync(R.d_tile_anchor, R.tile_anchor.data(), 4 * R.tile_anchor.size(),
+                                  cudaMemcpyHostToDevice, st));
+            PN_CU(cudaMemcpyAsync(R.d_tile_row0, R.tile_row0.data(), 4 * R.tile_row0.size(), cudaMemcpyHostToDevice,
+                                  st));
+        }
         PN_CU(cudaMemcpyAsync(R.g, hg.data(), 4 * hg.size(), cudaMemcpyHostToDevice, st));
     }
     PN_CU(cudaMemsetAsync(R.prof, 0xFF, sizeof(unsigned long long) * std::max<int64_t>(1, R.total_cells), st));
     PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
+    PN_CU(cudaMemsetAsync(R.err, 0, sizeof(int), st));
     StepTimer tm;
     PN_TRY(tm.start((c.flags & PANACHE_FLAG_TIMING) != 0, st));
 
@@ -533,6 +559,10 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PN_CU(pn::launch_runlen(v, R.total_samples, st));
     PN_CU(pn::launch_moments(v, R.total_samples, R.sq, st));
     PN_TRY(tm.mark(2));
+    if (R.tca) {
+        PN_CU(pn::launch_anchor_tc(v, R.d_tile_anchor, R.d_tile_row0, (int32_t)R.tile_anchor.size(), st));
+        ctx->launches += 1;
+    }
     PN_CU(pn::launch_features(v, R.d_blk_anchor, R.d_blk_chunk0, (int32_t)R.blk_anchor.size(), R.a_max, st));
     PN_TRY(tm.mark(3));
     PN_CU(pn::launch_ranks(v, R.total_windows, st));
@@ -542,7 +572,10 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     if (c.flags & PANACHE_FLAG_INDEX_ONLY) {
         for (int t = 5; t <= 8; ++t) PN_TRY(tm.mark(t));
         PN_TRY(tm.read(ctx->stats.step_ms));
+        int herr = 0;
+        PN_CU(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         PN_CU(cudaStreamSynchronize(st));
+        if (herr) return PANACHE_ETIMEOUT;
         res.assign(nser, {});
         ctx->stats.kernel_launches = ctx->launches;
         ctx->stats.waves = 1;
@@ -619,8 +652,11 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
         }
     }
     unsigned long long hs[PN_ST_COUNT];
+    int herr = 0;
     PN_CU(cudaMemcpyAsync(hs, R.stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    PN_CU(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     PN_CU(cudaStreamSynchronize(st));
+    if (herr) return PANACHE_ETIMEOUT;
     ctx->stats.queries = hs[PN_ST_QUERIES];
     ctx->stats.candidates = hs[PN_ST_CANDIDATES];
     ctx->stats.exact_stream = hs[PN_ST_LB_PASSED];

@@ -102,7 +102,17 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
         Xr[k] = 0;
         Xi[k] = 0;
     }
-    if (q0 < qend) {
+    if constexpr (sizeof(ST) == 4) {
+        if (q0 < qend && v.anc) {      // mixed form: chunk anchor from the tensor-core kernel
+            const float *an = v.anc + (A.chunk_off + c) * PN_FEAT;
+#pragma unroll
+            for (int k = 0; k < PN_MAXK - 1; ++k) {
+                Xr[k] = an[2 * k];
+                Xi[k] = an[2 * k + 1];
+            }
+        }
+    }
+    if (q0 < qend && !(sizeof(ST) == 4 && v.anc)) {
         double dr[PN_MAXK - 1], di[PN_MAXK - 1];
         int idx[PN_MAXK - 1];
 #pragma unroll

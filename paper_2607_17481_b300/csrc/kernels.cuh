@@ -40,6 +40,8 @@ struct PnView {
     double2 *wmd;         // plain form: per-window (1/sigma, -mu/sigma)
     uint32_t *qorder;     // search order of the flat query space (grouped by probe bucket)
     const float *g;       // projections [nanchors][B+1][PN_FEAT]
+    float *anc;           // mixed form: tensor-core chunk anchors, [flat chunk][PN_FEAT] (null: FP64 direct DFT)
+    int *err;             // device error word (PN_ERR_*), 0 when every bounded wait succeeded
     // directory
     uint32_t *dir_keys;   // global bucket id of every item (sorted)
     uint32_t *dir_vals;   // window start of every item (sorted by (bucket, start))
@@ -49,6 +51,8 @@ struct PnView {
     // counters (device)
     unsigned long long *stats;
 };
+
+#define PN_ERR_TC_TIMEOUT 1   // a tensor-core anchor tile's bounded wait ran out
 
 enum PnStat {
     PN_ST_QUERIES = 0,
@@ -111,6 +115,9 @@ cudaError_t launch_features(const PnView &v, const int32_t *blk_anchor, const in
                             int32_t nblocks, int a_max, cudaStream_t st);
 cudaError_t launch_ranks(const PnView &v, int64_t total_windows, cudaStream_t st);
 cudaError_t launch_directory(const PnView &v, int64_t total_items, int64_t total_buckets, cudaStream_t st);
+size_t anchor_tc_smem();
+cudaError_t launch_anchor_tc(const PnView &v, const int32_t *tile_anchor, const int32_t *tile_row0, int32_t ntiles,
+                             cudaStream_t st);
 cudaError_t launch_query_order(const PnView &v, int64_t total_windows, int64_t total_buckets, cudaStream_t st);
 int search_max_budget();
 cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, int a_max, cudaStream_t st);

@@ -29,6 +29,7 @@ struct PnAnchor {
     int64_t win_off;      // first window in the per-window arrays (keys, counts, lists)
     int64_t row_off;      // first feature row of this anchor (nchunk * C rows)
     int64_t nchunk;       // chunks of C windows: ceil(nw / C)
+    int64_t chunk_off;    // first chunk of this anchor in the flat chunk space (tensor-core anchors)
     int64_t item_off;     // first directory item (all levels of this anchor)
     int64_t bucket_base;  // first global bucket id of level 0
     int32_t level_begin;  // first level in the level table
