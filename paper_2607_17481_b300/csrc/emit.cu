@@ -3,6 +3,7 @@
 #include "distance.cuh"
 #include "emit.cuh"
 #include "zops.cuh"
+#include "evalbatch.cuh"
 #include "prims.cuh"
 
 namespace pn {
@@ -82,20 +83,27 @@ __global__ void k_sieve_rekey(PnView v, const PnClass *cls, int32_t ncls, int64_
 }
 
 // One warp per sorted member u: pairs (u, v) with u < v <= u + w (or every
-// v > u in the exhaustive variant), valid pairs only, bound-filtered, exact.
-// u's z-normalised window is staged in shared memory once.
+// v > u in the exhaustive variant), valid pairs only (|x_u - x_v| >= excl),
+// bound-filtered, exact.  The same machinery as the streaming search: u's
+// z-normalised window staged once, bounds of up to 32 neighbours with each
+// row read by 8 lanes, threshold tests lane-parallel, survivors evaluated
+// four at a time against the staged window, both cells updated.
 template <class Z>
-__global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_t total, const uint32_t *members,
-                              int w, int exhaustive, int zcap) {
+__global__ void __launch_bounds__(256) k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_t total,
+                                                     const uint32_t *members, int w, int exhaustive, int zcap) {
     using ZT = typename Z::T;
     extern __shared__ __align__(16) unsigned char zsm[];
-    const int lane = threadIdx.x & 31;
-    ZT *zu = reinterpret_cast<ZT *>(zsm) + (threadIdx.x >> 5) * zcap;
+    __shared__ __align__(16) float sF[8][PN_FEAT];
+    __shared__ float lbbuf[8][32];
+    __shared__ uint32_t scand[8][32];
+    __shared__ unsigned long long snap[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ZT *zu = reinterpret_cast<ZT *>(zsm) + warp * zcap;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nwp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float shrink = 1.0f - v.lam;
     unsigned long long n_ex = 0;
-    for (int64_t p = wid; p < total; p += nw) {
+    for (int64_t p = wid; p < total; p += nwp) {
         const int ci = pn_find(cls, ncls, p, [](const PnClass &c) { return (int64_t)c.moff; });
         const PnClass &c = cls[ci];
         const PnAnchor &A = v.anchors[c.anchor];
@@ -103,60 +111,67 @@ __global__ void k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_
         const int a = A.a;
         const int64_t u = p - c.moff;
         const int64_t vend = exhaustive ? (int64_t)c.size : min((int64_t)c.size, u + 1 + w);
+        if (u + 1 >= vend) continue;
         const uint32_t xu = members[p];
-        const float *Fa = v.F + A.row_off * PN_FEAT;
-        const uint32_t nch = (uint32_t)A.nchunk;
-        const float fu = Fa[(size_t)pn_row32(xu, v.cshift, nch) * PN_FEAT + lane];
-        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
         const auto mu_ = Z::load(v, A.win_off + xu);
         if (Z::degenerate(mu_)) continue;
+        const float *Fa = v.F + A.row_off * PN_FEAT;
+        const uint32_t nch = (uint32_t)A.nchunk;
+        sF[warp][lane] = Fa[(size_t)pn_row32(xu, v.cshift, nch) * PN_FEAT + lane];
         {
             const auto *xs = Z::samples(v, S.x_off + xu);
             for (int r = lane; r < a; r += 32) zu[r] = Z::z(mu_, xs[r]);
         }
         __syncwarp();
-        for (int64_t v0 = u + 1; v0 < vend; v0 += 32) {
-            const int64_t vi = v0 + lane;
-            uint32_t xv = 0;
-            const float *fv = nullptr;
-            if (vi < vend) {
-                xv = members[c.moff + vi];
-                if (llabs((int64_t)xv - (int64_t)xu) >= S.excl) fv = Fa + (size_t)pn_row32(xv, v.cshift, nch) * PN_FEAT;
-            }
-            float acc = 0.0f;
-            for (int t = 0; t < PN_FEAT; ++t) {
-                const float ut = __shfl_sync(0xffffffffu, fu, t);
-                if (fv) {
-                    const float dfe = ut - fv[t];
-                    acc = fmaf(dfe, dfe, acc);
+        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
+        const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
+        const float lbscale = 2.0f / (float)a;
+        unsigned long long bestkey = PN_EMPTY_KEY;
+        for (int64_t b0 = u + 1; b0 < vend; b0 += 32) {
+            const int nblk = (int)min((int64_t)32, vend - b0);
+            for (int sub = 0; sub < nblk; sub += 4) {
+                const int k = sub + (lane >> 3);
+                float part = 0.0f;
+                if (k < nblk) {
+                    const uint32_t xv = members[c.moff + b0 + k];
+                    const float4 fc =
+                        reinterpret_cast<const float4 *>(Fa + (size_t)pn_row32(xv, v.cshift, nch) * PN_FEAT)[lane & 7];
+                    const float dx = fq.x - fc.x, dy = fq.y - fc.y, dz = fq.z - fc.z, dw = fq.w - fc.w;
+                    part = dx * dx + dy * dy + dz * dz + dw * dw;
                 }
+                part += __shfl_xor_sync(0xffffffffu, part, 1);
+                part += __shfl_xor_sync(0xffffffffu, part, 2);
+                part += __shfl_xor_sync(0xffffffffu, part, 4);
+                if (k < nblk && (lane & 7) == 0) lbbuf[warp][k] = part;
             }
+            __syncwarp();
             bool surv = false;
-            if (fv) {
-                const float lb = sqrtf(2.0f / (float)a * acc);
-                const ZT thr = Z::fmx(Z::cell(__ldcg(&prow[xu])), Z::cell(__ldcg(&prow[xv])));
-                surv = (ZT)(shrink * lb) < thr && !Z::degenerate(Z::load(v, A.win_off + xv));
-            }
-            uint32_t sm = __ballot_sync(0xffffffffu, surv);
-            while (sm) {
-                const int src = __ffs(sm) - 1;
-                sm &= sm - 1;
-                const uint32_t xx = __shfl_sync(0xffffffffu, xv, src);
-                const auto mx = Z::load(v, A.win_off + xx);
-                const auto *xs = Z::samples(v, S.x_off + xx);
-                ZT dacc = 0;
-                for (int r = lane; r < a; r += 32) {
-                    const ZT dz = zu[r] - Z::z(mx, xs[r]);
-                    dacc = fma(dz, dz, dacc);
-                }
-                const ZT dd = Z::finish(dacc);
-                n_ex += 1;
-                if (lane == 0) {
-                    atomicMin(&prow[xu], Z::pack(dd, xx));
-                    atomicMin(&prow[xx], Z::pack(dd, xu));
+            uint32_t xv = 0;
+            unsigned long long kc = 0;
+            if (lane < nblk) {
+                xv = members[c.moff + b0 + lane];
+                if (llabs((int64_t)xv - (int64_t)xu) >= S.excl) {
+                    kc = __ldcg(&prow[xv]);
+                    const float lbs = shrink * sqrtf(lbscale * lbbuf[warp][lane]);
+                    const ZT tu = Z::fmn(Z::cell(bestkey), Z::cell(__ldcg(&prow[xu])));
+                    surv = (ZT)lbs < Z::fmx(tu, Z::cell(kc));
                 }
             }
+            const uint32_t sm = __ballot_sync(0xffffffffu, surv);
+            if (surv) {
+                const int rank = __popc(sm & ((1u << lane) - 1u));
+                scand[warp][rank] = xv;
+                snap[warp][rank] = kc;
+            }
+            __syncwarp();
+            const int ns = __popc(sm);
+            for (int h = 0; h < ns; h += 4)
+                eval_batch<Z>(v, zu, scand[warp] + h, snap[warp] + h, min(4, ns - h), S.x_off, A.win_off, a, xu,
+                              prow, bestkey, lane);
+            n_ex += ns;
+            __syncwarp();
         }
+        if (lane == 0 && bestkey != PN_EMPTY_KEY) atomicMin(&prow[xu], bestkey);
         __syncwarp();
     }
     if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);

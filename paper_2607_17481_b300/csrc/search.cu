@@ -24,6 +24,7 @@
 // candidate streams its own window against it.
 #include "distance.cuh"
 #include "zops.cuh"
+#include "evalbatch.cuh"
 
 namespace pn {
 namespace {
@@ -32,88 +33,6 @@ constexpr int SR_WARPS = 8;
 constexpr int SR_THREADS = SR_WARPS * 32;
 constexpr int SR_MAXR = 512;   // largest supported budget R
 constexpr int SR_MAXPROBE = 9; // exact bucket + up to 8 Hamming-1 buckets
-
-// Exact distances of up to four queued survivors at once (warp-cooperative
-// over samples, four independent accumulators), then the packed-key updates:
-// the query's running best in registers, the candidate's cell by atomicMin
-// only when the new key is below the snapshot read for the bound test (cells
-// only decrease, so a key at or above the snapshot cannot change the cell).
-template <class Z>
-__device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T *zq, const uint32_t *sc,
-                                           const unsigned long long *sk, int nb, int64_t x_off, int64_t win_off,
-                                           int a, uint32_t q, unsigned long long *prow,
-                                           unsigned long long &bestkey, int lane) {
-    using ZT = typename Z::T;
-    const uint32_t c0 = sc[0], c1 = sc[nb > 1 ? 1 : 0], c2 = sc[nb > 2 ? 2 : 0], c3 = sc[nb > 3 ? 3 : 0];
-    const auto m0 = Z::load(v, win_off + c0), m1 = Z::load(v, win_off + c1);
-    const auto m2 = Z::load(v, win_off + c2), m3 = Z::load(v, win_off + c3);
-    const auto *x0 = Z::samples(v, x_off + c0), *x1 = Z::samples(v, x_off + c1);
-    const auto *x2 = Z::samples(v, x_off + c2), *x3 = Z::samples(v, x_off + c3);
-    ZT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int r = lane; r < a; r += 32) {
-        const ZT zr = zq[r];
-        const ZT d0 = zr - Z::z(m0, x0[r]);
-        const ZT d1 = zr - Z::z(m1, x1[r]);
-        const ZT d2 = zr - Z::z(m2, x2[r]);
-        const ZT d3 = zr - Z::z(m3, x3[r]);
-        a0 = fma(d0, d0, a0);
-        a1 = fma(d1, d1, a1);
-        a2 = fma(d2, d2, a2);
-        a3 = fma(d3, d3, a3);
-    }
-    // transposed reduction of the four sums (6 shuffles): afterwards lanes
-    // 8v..8v+7 hold the total of survivor v
-    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
-    ZT k0 = hi16 ? a2 : a0, k1 = hi16 ? a3 : a1;
-    const ZT s0 = hi16 ? a0 : a2, s1 = hi16 ? a1 : a3;
-    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-    ZT t = hi8 ? k1 : k0;
-    const ZT u = hi8 ? k0 : k1;
-    t += __shfl_xor_sync(0xffffffffu, u, 8);
-    t += __shfl_xor_sync(0xffffffffu, t, 4);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
-    const int vi = lane >> 3;
-    const uint32_t cv = vi == 0 ? c0 : (vi == 1 ? c1 : (vi == 2 ? c2 : c3));
-    const bool dg = Z::degenerate(vi == 0 ? m0 : (vi == 1 ? m1 : (vi == 2 ? m2 : m3)));
-    const bool ok = vi < nb && !dg;
-    const ZT dd = Z::root(t);
-    unsigned long long kq = ok ? Z::pack(dd, cv) : PN_EMPTY_KEY;
-    if (ok && (lane & 7) == 0) {
-        const unsigned long long kc = Z::pack(dd, q);
-        if (kc < sk[vi]) atomicMin(&prow[cv], kc);
-    }
-    unsigned long long o = __shfl_xor_sync(0xffffffffu, kq, 8);
-    kq = o < kq ? o : kq;
-    o = __shfl_xor_sync(0xffffffffu, kq, 16);
-    kq = o < kq ? o : kq;
-    if (kq < bestkey) bestkey = kq;
-}
-
-// Exact distance of one candidate (warp-cooperative), same updates as eval_batch.
-template <class Z>
-__device__ __forceinline__ void eval_one(const PnView &v, const typename Z::T *zq, uint32_t c,
-                                         unsigned long long snapkey, int64_t x_off, int64_t win_off, int a,
-                                         uint32_t q, unsigned long long *prow, unsigned long long &bestkey,
-                                         int lane) {
-    using ZT = typename Z::T;
-    const auto m = Z::load(v, win_off + c);
-    if (Z::degenerate(m)) return;
-    const auto *x = Z::samples(v, x_off + c);
-    ZT acc = 0;
-    for (int r = lane; r < a; r += 32) {
-        const ZT dz = zq[r] - Z::z(m, x[r]);
-        acc = fma(dz, dz, acc);
-    }
-    const ZT dd = Z::finish(acc);
-    const unsigned long long kq = Z::pack(dd, c);
-    if (kq < bestkey) bestkey = kq;
-    if (lane == 0) {
-        const unsigned long long kc = Z::pack(dd, q);
-        if (kc < snapkey) atomicMin(&prow[c], kc);
-    }
-}
 
 template <class Z>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {

@@ -241,7 +241,9 @@ def test_mixed_drift_within_lambda_over_ten(pn):
         for a in (m1, m2):
             d, curve = autotune.feature_drift(x, a, 256)
             assert d <= 1e-5, (a, d)
-            assert curve[0] <= 1e-6            # windows at an anchor carry FP32 rounding only
+            # windows at an anchor carry the anchor's own error only: 3xTF32
+            # tensor-core products (about 2^-21 relative) plus FP32 rounding
+            assert curve[0] <= 2e-6
 
 
 def test_autotune_picks_a_valid_chunk(pn):
