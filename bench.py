@@ -220,6 +220,35 @@ def run_batched(pn, stream, n_series: int, n_loop: int):
         e1.record(stream)
         e1.synchronize()
         out["one_at_a_time"] = {"series": len(sub), "value": Wl / (e0.elapsed_time(e1) / 1e3), "unit": UNIT}
+    # the same batch with the index and search steps replayed from a captured CUDA graph
+    ctx_g = pn.Context(precision=1, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_GRAPH)
+    ctx_g.set_stream(stream.cuda_stream)
+    shard.run_sharded(xs, params, lambda s_, p_: ctx_g.pmp_batch(s_, p_))      # capture
+    gt = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        shard.run_sharded(xs, params, lambda s_, p_: ctx_g.pmp_batch(s_, p_))
+        torch.cuda.synchronize()
+        gt.append(1e3 * (time.perf_counter() - t0))
+    out["graph"] = {"value": W / (statistics.mean(gt) / 1e3), "unit": UNIT, "ms_per_batch": statistics.mean(gt)}
+    # many small series of one shape, one call each: eager launches vs graph replay
+    fleet = [workloads.random_walk(np.random.default_rng([77, i]), 8192) for i in range(64)]
+    fl = [torch.from_numpy(f).cuda() for f in fleet]
+    Wf = len(fl) * workloads.windows_lengths(8192, 32, 64)
+    res = {}
+    for name, flags in (("eager", 0), ("graph", pn.FLAG_GRAPH)):
+        c = pn.Context(precision=1, topk_mode=pn.TOPK_GLOBAL, flags=flags)
+        c.set_stream(stream.cuda_stream)
+        c.pmp(fl[0], 32, 64, 20, 64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for f in fl:
+            c.pmp(f, 32, 64, 20, 64)
+        torch.cuda.synchronize()
+        res[name] = Wf / (time.perf_counter() - t0)
+    out["fleet_8192"] = {"series": len(fl), "n": 8192, "lengths": "32..64", "unit": UNIT,
+                         "eager_value": res["eager"], "graph_value": res["graph"]}
     return out
 
 

@@ -81,6 +81,11 @@ extern "C" {
 #define PANACHE_FLAG_INDEX_ONLY 0x10       /* build features, keys and directories, then stop (no motifs) */
 #define PANACHE_FLAG_FP64_ANCHORS 0x20     /* mixed form: chunk anchors by FP64 direct DFT instead of the
                                               tensor cores (3xTF32 tcgen05 contraction, the default) */
+#define PANACHE_FLAG_GRAPH 0x40           /* capture the index and search steps of a request into a CUDA
+                                              graph and replay it while requests keep the same shape
+                                              (series lengths, dtypes, length intervals, k, excl): the
+                                              context keeps that request's buffers, copies each new
+                                              request's samples into them and launches the graph once */
 
 /* Tunables.  A zero field takes the paper's default (Sec. 4):
  * alpha 16, gamma 8 (R = 128), stride 2, K 16, B 24, d0 12, probe cap 8,
@@ -184,15 +189,35 @@ int panache_pmp_batch(panache_ctx *ctx, const panache_request *reqs, int32_t nre
                       int64_t out_cap_per_req, int64_t *out_len);
 
 /* Streaming handles (Sec. 3.1): samples arrive by panache_append in chunks
- * of any size; windows complete when their last sample arrives; the emit
- * stage runs when panache_stream_topk is called.  A stream's samples and
- * index stay resident on the device until panache_stream_close. */
+ * of any size (host memory, or device memory with PANACHE_DEVICE; FP32 or
+ * FP64; the call copies them).  The whole index stays resident on the
+ * device until panache_stream_close: samples, FP64 prefix sums, features
+ * and keys, directory levels and profile rows, laid out for a capacity that
+ * grows to max(2 cap, 1.5 n) when an append outgrows it (the state is then
+ * rebuilt from the samples).  An append computes the features of the new windows and
+ * searches every query whose batch of beta samples it completes
+ * (Algorithm 1: such a query's population, level and candidates are final).
+ * panache_stream_topk searches the still-pending queries and runs the emit
+ * stage (Algorithm 2) on a copy of the profile rows, so its result equals
+ * panache_pmp on the samples received so far and the resident state does
+ * not depend on when snapshots were taken.  Both calls run on the
+ * context's stream and return when the work is done.  Errors as
+ * panache_pmp; ETIMEOUT when a bounded device wait ran out.  Destroying the
+ * context frees the device state of its open streams; their handles then
+ * fail with ESTATE until panache_stream_close releases them. */
 int panache_stream_open(panache_ctx *ctx, int32_t m_min, int32_t m_max, int32_t k, int32_t excl,
                         panache_stream **out);
 int panache_append(panache_stream *h, const void *chunk, int32_t dtype, int64_t len);
 int panache_stream_topk(panache_stream *h, panache_motif *out, int64_t out_cap, int64_t *out_len);
 int64_t panache_stream_length(const panache_stream *h);
 void panache_stream_close(panache_stream *h);
+/* Checkpoint of a stream: its samples as FP64 (out[0..cap), *out_len set to
+ * the length; ETRUNC when cap is smaller).  Every part of a stream's state
+ * is a function of its samples and the context's configuration, so opening
+ * a stream with the same parameters and appending the checkpoint (in one
+ * chunk or any others) resumes it: later snapshots equal those of the
+ * uninterrupted stream. */
+int panache_stream_checkpoint(const panache_stream *h, double *out, int64_t cap, int64_t *out_len);
 
 /* Counters of the context's last request. */
 int panache_last_stats(const panache_ctx *ctx, panache_stats *out);
@@ -256,13 +281,22 @@ int panache_server_submit(panache_server *sv, const void *series, int32_t dtype,
  * when not ready; the request's own error code when it failed. */
 int panache_server_wait(panache_server *sv, uint64_t ticket, int32_t timeout_ms, panache_motif *out, int64_t cap,
                         int64_t *out_len, double *latency_ms);
-/* Live streams: samples appended in chunks of any size stay on the device;
- * panache_server_stream_topk queues a request over the samples received so
- * far (a snapshot: later appends do not affect it). */
+/* Live streams: each is a resident stream (panache_stream_open) on a
+ * context and CUDA stream of its own, so its appends and snapshots overlap
+ * the slots' batches on the GPU.  Appends (host chunks, FP32 or FP64) and
+ * snapshots run in the calling thread; calls on one stream are serialised.
+ * The resident state plus the row copy a snapshot uses are reserved from
+ * the budget; an append that would grow them past it fails with EBUDGET
+ * (the stream keeps its samples).  panache_server_stream_topk computes the
+ * top-k over the samples received so far and files the result under a
+ * ticket for panache_server_wait (latency: the snapshot's own time).
+ * ESTATE when the stream has no samples.  panache_server_stream_close
+ * frees the stream and its reservation. */
 int panache_server_stream_open(panache_server *sv, int32_t m_min, int32_t m_max, int32_t k, int32_t excl,
                                uint64_t *stream_id);
 int panache_server_append(panache_server *sv, uint64_t stream_id, const void *chunk, int32_t dtype, int64_t len);
 int panache_server_stream_topk(panache_server *sv, uint64_t stream_id, uint64_t *ticket);
+int panache_server_stream_close(panache_server *sv, uint64_t stream_id);
 int panache_server_get_stats(panache_server *sv, panache_server_stats *out);
 
 /* Top-k motifs of ONE length row from profile keys already on the device,

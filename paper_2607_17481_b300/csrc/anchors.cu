@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
     for (int m = tid; m < AT_ROWS; m += AT_THREADS) {
         const int64_t c = c0 + m;
         double mu = 0.0;
-        if (c < A.nchunk) {
+        if (c * C < A.nw) {
             double var;
             pn_moments(v, A.series, c * C, a, mu, var);
         }
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
             const int m = t / AT_KS, k = t - m * AT_KS, r = r0 + k;
             const int64_t c = c0 + m;
             float val = 0.0f;
-            if (c < A.nchunk && r < a) val = (float)(xs[c * C + r] - mu_s[m]);
+            if (c * C < A.nw && r < a) val = (float)(xs[c * C + r] - mu_s[m]);
             const float hi = tf32_hi(val);
             Ahi[kmaj(m, k, kg)] = hi;
             Alo[kmaj(m, k, kg)] = val - hi;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
             : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int64_t c = c0 + warp * 32 + lane;
-        if (c < A.nchunk) {
+        if (c * C < A.nw) {
             float4 *dst = reinterpret_cast<float4 *>(v.anc + (A.chunk_off + c) * PN_FEAT);
 #pragma unroll
             for (int t = 0; t < 8; ++t)

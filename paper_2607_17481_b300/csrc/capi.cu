@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <set>
 #include <new>
 #include <vector>
 
@@ -57,6 +58,17 @@ __global__ void k_convert(const PnConv *cv, int32_t ncv, int64_t total, double *
     x[t] = v;
     xs[t] = make_float2(hi, (float)(v - (double)hi));
     if (x1) x1[t] = hi;
+}
+
+// Stream samples: n values (FP32 or FP64) written at offset `off` as FP64 and
+// as (hi, lo) float pairs.
+__global__ void k_put(const void *src, int32_t dtype, int64_t n, int64_t off, double *x, float2 *xs) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double v = (dtype & 0xFF) == PANACHE_F32 ? (double)((const float *)src)[t] : ((const double *)src)[t];
+    float hi = (float)v;
+    x[off + t] = v;
+    xs[off + t] = make_float2(hi, (float)(v - (double)hi));
 }
 
 }  // namespace
@@ -128,7 +140,23 @@ struct panache_ctx {
     PnRequest *last = nullptr;
     panache_stats stats;
     std::map<int, std::vector<float>> gcache;
+    std::set<panache_stream *> streams;   // open streams: their state is freed with the context
     uint64_t launches = 0;
+    // PANACHE_FLAG_GRAPH: the captured index + search steps of `last`, the
+    // request shape they were captured for, and the persistent input staging
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<PnSeriesIn> gshape;
+    unsigned char *gstage = nullptr;
+    std::vector<int64_t> gstage_off;
+    uint64_t glaunches = 0;
+
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        gshape.clear();
+        gstage = nullptr;            // owned by `last` (allocated through it)
+        gstage_off.clear();
+    }
 
     const std::vector<float> &proj(int a) {
         auto it = gcache.find(a);
@@ -139,11 +167,20 @@ struct panache_ctx {
     }
 };
 
+// A live series whose whole index stays resident (Sec. 3.1): samples, prefix
+// sums, features and keys, ranks, directory levels and profile rows, all laid
+// out for `cap` samples.  Appends search only the queries whose batch the new
+// samples complete; a snapshot searches the pending tail and runs Algorithm 2
+// on a copy of the rows, so the resident state never depends on when
+// snapshots were taken.
 struct panache_stream {
     panache_ctx *ctx;
     int32_t m_min, m_max, k, excl;
-    double *dev = nullptr;  // resident samples (FP64)
+    PnRequest *R = nullptr;
     int64_t len = 0, cap = 0;
+    std::vector<int64_t> q_done;   // per anchor: queries [0, q_done) searched into the resident rows
+    std::vector<int64_t> nw_feat;  // per anchor: windows whose features and keys are written
+    ~panache_stream() { delete R; }
 };
 
 namespace {
@@ -187,17 +224,23 @@ int check_series(const SeriesIn &s) {
     return PANACHE_OK;
 }
 
-// Builds every table of a request and its device footprint.
-int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R) {
+// Builds every table of a request and its device footprint.  With `caps`,
+// series s is laid out for caps[s] >= n samples (a resident stream): every
+// per-window array, feature block, directory level and profile row is sized
+// for the capacity, while n, nw and the launches cover the samples present.
+int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R,
+         const std::vector<int64_t> *caps = nullptr) {
     const int C = (int)c.chunk;
     int64_t x_off = 0, row_off = 0;
     for (size_t s = 0; s < in.size(); ++s) {
         const SeriesIn &si = in[s];
+        const int64_t ncap = caps ? (*caps)[s] : si.n;
         PnSeries S;
         memset(&S, 0, sizeof(S));
         S.x_off = x_off;
         S.n = si.n;
         S.row_off = row_off;
+        S.ld = ncap;
         S.m_min = si.m_min;
         S.m_max = si.m_max;
         S.excl = si.excl;
@@ -208,17 +251,17 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R)
         for (int a = si.m_min; a <= si.m_max; a += (int)c.stride) al.push_back(a);
         if (al.back() != si.m_max) al.push_back(si.m_max);
         for (int a : al) {
-            const int64_t nw = si.n - a + 1;
-            if (nw <= 0) continue;
+            const int64_t nwc = ncap - a + 1;             // windows at capacity
+            if (nwc <= 0) continue;
             PnAnchor A;
             memset(&A, 0, sizeof(A));
             A.series = (int32_t)s;
             A.a = a;
             A.kp = pn_kprime(a, (int)c.K);
-            A.nw = nw;
-            A.dmax = pn_depth(nw, (int)c.alpha, (int)c.B);
+            A.nw = std::max<int64_t>(0, si.n - a + 1);
+            A.dmax = pn_depth(nwc, (int)c.alpha, (int)c.B);
             A.win_off = R.total_windows;
-            A.nchunk = (nw + C - 1) / C;
+            A.nchunk = (nwc + C - 1) / C;
             A.chunk_off = R.total_chunks;
             A.row_off = R.total_rows;
             A.item_off = R.total_items;
@@ -229,7 +272,7 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R)
                 PnLevel L;
                 L.anchor = (int32_t)R.anc.size();
                 L.d = d;
-                L.cap = std::min<int64_t>(nw, (int64_t)c.alpha << d);
+                L.cap = std::min<int64_t>(nwc, (int64_t)c.alpha << d);
                 L.item_off = R.total_items;
                 L.bucket_base = R.total_buckets;
                 R.total_items += L.cap;
@@ -245,15 +288,15 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R)
             R.total_chunks += A.nchunk;
             R.slot_off.push_back(R.total_slots);
             R.total_slots += (int64_t)1 << A.dmax;
-            R.total_windows += nw;
+            R.total_windows += nwc;
             R.total_rows += A.nchunk * C;
             R.a_max = std::max(R.a_max, a);
             R.anc.push_back(A);
         }
         S.anchor_count = (int32_t)R.anc.size() - S.anchor_begin;
         R.ser.push_back(S);
-        x_off += si.n;
-        row_off += (int64_t)(si.m_max - si.m_min + 1) * si.n;
+        x_off += ncap;
+        row_off += (int64_t)(si.m_max - si.m_min + 1) * ncap;
     }
     R.total_samples = x_off;
     R.total_cells = row_off;
@@ -334,7 +377,7 @@ GroupSet make_groups(const PnRequest &R, int mode, const std::vector<int> &k_of_
             PnSelGroup G;
             memset(&G, 0, sizeof(G));
             G.cell_off = S.row_off;
-            G.ncell = (int64_t)L * S.n;
+            G.ncell = (int64_t)L * S.ld;
             G.series = (int32_t)s;
             G.k = k_of_series[s];
             G.need = (uint32_t)((int64_t)G.k * (S.m_max + 1));
@@ -344,8 +387,8 @@ GroupSet make_groups(const PnRequest &R, int mode, const std::vector<int> &k_of_
             for (int r = 0; r < L; ++r) {
                 PnSelGroup G;
                 memset(&G, 0, sizeof(G));
-                G.cell_off = S.row_off + (int64_t)r * S.n;
-                G.ncell = S.n;
+                G.cell_off = S.row_off + (int64_t)r * S.ld;
+                G.ncell = S.ld;
                 G.series = (int32_t)s;
                 G.k = k_of_series[s];
                 G.need = (uint32_t)((int64_t)G.k * (S.m_min + r + 1));
@@ -358,7 +401,7 @@ GroupSet make_groups(const PnRequest &R, int mode, const std::vector<int> &k_of_
 }
 
 // Runs the selection of `gs` and returns the picks per group on the host.
-int run_select(panache_ctx *ctx, PnRequest &R, const GroupSet &gs, bool strict,
+int run_select(panache_ctx *ctx, PnRequest &R, const PnView &v, const GroupSet &gs, bool strict,
                std::vector<std::vector<PnPick>> &picks) {
     picks.assign(gs.g.size(), {});
     if (gs.g.empty()) return PANACHE_OK;
@@ -383,7 +426,6 @@ int run_select(panache_ctx *ctx, PnRequest &R, const GroupSet &gs, bool strict,
     PN_CU(cudaMallocAsync((void **)&dcnt, sizeof(int32_t) * ng, st));
     PN_CU(cudaMemcpyAsync(dg, gs.g.data(), sizeof(PnSelGroup) * ng, cudaMemcpyHostToDevice, st));
     PN_CU(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
-    PnView v = make_view(ctx, R);
     PN_CU(pn::launch_select(v, dg, ng, 0, R.total_cells, (int32_t)cap, ctx->cfg.eps0, kmax, dout, dcnt, R.flagbuf,
                             ctx->sm_count * 8, st));
     ctx->launches += 10;
@@ -432,35 +474,19 @@ struct StepTimer {
     }
 };
 
-// The whole path for a list of series; results per series.
-int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<std::vector<panache_motif>> &res) {
+// Device buffers of a planned request (or of a resident stream), its tables,
+// projections and initial state: profile rows unset, counters and error word zero.
+int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) {
     const panache_config &c = ctx->cfg;
-    for (auto &s : in) PN_TRY(check_series(s));
-    delete ctx->last;
-    ctx->last = nullptr;
-    memset(&ctx->stats, 0, sizeof(ctx->stats));
-    ctx->launches = 0;
-    PnRequest *Rp = new (std::nothrow) PnRequest();
-    if (!Rp) return PANACHE_ENOMEM;
-    ctx->last = Rp;
-    PnRequest &R = *Rp;
-    cudaStream_t st = ctx->st;
-    R.st = st;
-    PN_TRY(plan(ctx->cfg, in, R));
-    ctx->stats.device_bytes = R.footprint;
+    cudaStream_t st = R.st;
     const int64_t nser = (int64_t)R.ser.size(), nanc = (int64_t)R.anc.size();
-
     PN_CU(R.alloc(R.d_ser, nser));
     PN_CU(R.alloc(R.d_anc, nanc));
     PN_CU(R.alloc(R.d_lev, (int64_t)R.lev.size()));
-    PN_CU(R.alloc(R.d_blk_anchor, (int64_t)R.blk_anchor.size()));
-    PN_CU(R.alloc(R.d_blk_chunk0, (int64_t)R.blk_chunk0.size()));
     PN_CU(R.alloc(R.d_slot_off, nanc));
     PN_CU(R.alloc(R.x, R.total_samples));
     PN_CU(R.alloc(R.xs, R.total_samples));
-    bool all_f32 = true;
-    for (auto &si : in) all_f32 = all_f32 && (si.dtype & 0xFF) == PANACHE_F32;
-    if (all_f32 && c.precision == PANACHE_MIXED) PN_CU(R.alloc(R.x1, R.total_samples));
+    if (want_x1) PN_CU(R.alloc(R.x1, R.total_samples));
     PN_CU(R.alloc(R.sq, R.total_samples + nser));
     PN_CU(R.alloc(R.shift, nser));
     PN_CU(R.alloc(R.runlen, R.total_samples));
@@ -480,13 +506,15 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PN_CU(R.alloc(R.flagbuf, 4));
     PN_CU(R.alloc(R.err, 1));
     const bool tc_anchors = c.precision == PANACHE_MIXED && !(c.flags & PANACHE_FLAG_FP64_ANCHORS);
-    if (tc_anchors) {
-        PN_CU(R.alloc(R.tca, R.total_chunks * PN_FEAT));
-        PN_CU(R.alloc(R.d_tile_anchor, (int64_t)R.tile_anchor.size()));
-        PN_CU(R.alloc(R.d_tile_row0, (int64_t)R.tile_row0.size()));
+    if (tc_anchors) PN_CU(R.alloc(R.tca, R.total_chunks * PN_FEAT));
+    if (full_tables) {
+        PN_CU(R.alloc(R.d_blk_anchor, (int64_t)R.blk_anchor.size()));
+        PN_CU(R.alloc(R.d_blk_chunk0, (int64_t)R.blk_chunk0.size()));
+        if (tc_anchors) {
+            PN_CU(R.alloc(R.d_tile_anchor, (int64_t)R.tile_anchor.size()));
+            PN_CU(R.alloc(R.d_tile_row0, (int64_t)R.tile_row0.size()));
+        }
     }
-
-    // tables and projections
     std::vector<float> hg((size_t)nanc * (c.B + 1) * PN_FEAT);
     for (int64_t a = 0; a < nanc; ++a) {
         const std::vector<float> &g = ctx->proj(R.anc[a].a);
@@ -496,95 +524,35 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     if (nanc) {
         PN_CU(cudaMemcpyAsync(R.d_anc, R.anc.data(), sizeof(PnAnchor) * nanc, cudaMemcpyHostToDevice, st));
         PN_CU(cudaMemcpyAsync(R.d_lev, R.lev.data(), sizeof(PnLevel) * R.lev.size(), cudaMemcpyHostToDevice, st));
-        PN_CU(cudaMemcpyAsync(R.d_blk_anchor, R.blk_anchor.data(), 4 * R.blk_anchor.size(), cudaMemcpyHostToDevice,
-                              st));
-        PN_CU(cudaMemcpyAsync(R.d_blk_chunk0, R.blk_chunk0.data(), 4 * R.blk_chunk0.size(), cudaMemcpyHostToDevice,
-                              st));
         PN_CU(cudaMemcpyAsync(R.d_slot_off, R.slot_off.data(), 8 * nanc, cudaMemcpyHostToDevice, st));
-        if (R.tca) {
-            PN_CU(cudaMemcpyAsync(R.d_tile_anchor, R.tile_anchor.data(), 4 * R.tile_anchor.size(),
+        if (full_tables) {
+            PN_CU(cudaMemcpyAsync(R.d_blk_anchor, R.blk_anchor.data(), 4 * R.blk_anchor.size(),
                                   cudaMemcpyHostToDevice, st));
-            PN_CU(cudaMemcpyAsync(R.d_tile_row0, R.tile_row0.data(), 4 * R.tile_row0.size(), cudaMemcpyHostToDevice,
-                                  st));
+            PN_CU(cudaMemcpyAsync(R.d_blk_chunk0, R.blk_chunk0.data(), 4 * R.blk_chunk0.size(),
+                                  cudaMemcpyHostToDevice, st));
+            if (tc_anchors) {
+                PN_CU(cudaMemcpyAsync(R.d_tile_anchor, R.tile_anchor.data(), 4 * R.tile_anchor.size(),
+                                      cudaMemcpyHostToDevice, st));
+                PN_CU(cudaMemcpyAsync(R.d_tile_row0, R.tile_row0.data(), 4 * R.tile_row0.size(),
+                                      cudaMemcpyHostToDevice, st));
+            }
         }
         PN_CU(cudaMemcpyAsync(R.g, hg.data(), 4 * hg.size(), cudaMemcpyHostToDevice, st));
     }
     PN_CU(cudaMemsetAsync(R.prof, 0xFF, sizeof(unsigned long long) * std::max<int64_t>(1, R.total_cells), st));
     PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
     PN_CU(cudaMemsetAsync(R.err, 0, sizeof(int), st));
-    StepTimer tm;
-    PN_TRY(tm.start((c.flags & PANACHE_FLAG_TIMING) != 0, st));
+    return PANACHE_OK;
+}
 
-    // samples: host inputs go through one staging buffer; device inputs are read in place
-    {
-        std::vector<PnConv> cv(nser);
-        int64_t stage_bytes = 0;
-        for (int64_t s = 0; s < nser; ++s) {
-            const int es = (in[s].dtype & 0xFF) == PANACHE_F32 ? 4 : 8;
-            if (!(in[s].dtype & PANACHE_DEVICE)) stage_bytes += ((in[s].n * es + 15) / 16) * 16;
-        }
-        unsigned char *stage = nullptr;
-        if (stage_bytes) PN_CU(cudaMallocAsync((void **)&stage, stage_bytes, st));
-        int64_t off = 0;
-        for (int64_t s = 0; s < nser; ++s) {
-            const int es = (in[s].dtype & 0xFF) == PANACHE_F32 ? 4 : 8;
-            cv[s].n = in[s].n;
-            cv[s].x_off = R.ser[s].x_off;
-            cv[s].dtype = in[s].dtype;
-            if (in[s].dtype & PANACHE_DEVICE) {
-                cv[s].src = in[s].ptr;
-            } else {
-                cv[s].src = stage + off;
-                if (in[s].n) PN_CU(cudaMemcpyAsync(stage + off, in[s].ptr, in[s].n * es, cudaMemcpyHostToDevice, st));
-                off += ((in[s].n * es + 15) / 16) * 16;
-            }
-        }
-        PnConv *dcv = nullptr;
-        PN_CU(cudaMallocAsync((void **)&dcv, sizeof(PnConv) * std::max<int64_t>(1, nser), st));
-        PN_CU(cudaMemcpyAsync(dcv, cv.data(), sizeof(PnConv) * nser, cudaMemcpyHostToDevice, st));
-        if (R.total_samples > 0) {
-            k_convert<<<(unsigned)((R.total_samples + 255) / 256), 256, 0, st>>>(dcv, (int32_t)nser, R.total_samples,
-                                                                                R.x, R.xs, R.x1);
-            PN_CU(cudaGetLastError());
-            ctx->launches += 1;
-        }
-        PN_CU(cudaFreeAsync(dcv, st));
-        if (stage) PN_CU(cudaFreeAsync(stage, st));
-    }
-
-    PN_TRY(tm.mark(1));
-    PnView v = make_view(ctx, R);
+// Algorithm 2 on the profile rows `v.prof`: hot-class sieve, completion
+// rounds and the final selection; then the counters and the error word.
+int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
+             std::vector<std::vector<panache_motif>> &res) {
+    const panache_config &c = ctx->cfg;
+    cudaStream_t st = R.st;
+    const int64_t nser = (int64_t)R.ser.size();
     const int grid = ctx->sm_count * (int)c.grid_mult;
-    // Algorithm 1 over every anchor of every series
-    PN_CU(pn::launch_runlen(v, R.total_samples, st));
-    PN_CU(pn::launch_moments(v, R.total_samples, R.sq, st));
-    PN_TRY(tm.mark(2));
-    if (R.tca) {
-        PN_CU(pn::launch_anchor_tc(v, R.d_tile_anchor, R.d_tile_row0, (int32_t)R.tile_anchor.size(), st));
-        ctx->launches += 1;
-    }
-    PN_CU(pn::launch_features(v, R.d_blk_anchor, R.d_blk_chunk0, (int32_t)R.blk_anchor.size(), R.a_max, st));
-    PN_TRY(tm.mark(3));
-    PN_CU(pn::launch_ranks(v, R.total_windows, st));
-    PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
-    PN_CU(pn::launch_query_order(v, R.total_windows, R.total_buckets, st));
-    PN_TRY(tm.mark(4));
-    if (c.flags & PANACHE_FLAG_INDEX_ONLY) {
-        for (int t = 5; t <= 8; ++t) PN_TRY(tm.mark(t));
-        PN_TRY(tm.read(ctx->stats.step_ms));
-        int herr = 0;
-        PN_CU(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        PN_CU(cudaStreamSynchronize(st));
-        if (herr) return PANACHE_ETIMEOUT;
-        res.assign(nser, {});
-        ctx->stats.kernel_launches = ctx->launches;
-        ctx->stats.waves = 1;
-        return PANACHE_OK;
-    }
-    PN_CU(pn::launch_search(v, R.total_windows, grid, R.a_max, st));
-    PN_TRY(tm.mark(5));
-    ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3 + 1 + 1 + 4 * 3;
-    // Algorithm 2: sieve, completion rounds, final selection
     int32_t ncls = 0;
     if (!(c.flags & PANACHE_FLAG_NO_SIEVE)) {
         PN_CU(pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w,
@@ -608,11 +576,11 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
         for (uint32_t round = 0; round < c.rounds; ++round) {
             std::vector<PnSeed> seeds;
             std::vector<std::vector<PnPick>> picks;
-            PN_TRY(run_select(ctx, R, seed_mode, false, picks));
+            PN_TRY(run_select(ctx, R, v, seed_mode, false, picks));
             for (auto &gp : picks)
                 for (auto &p : gp) seeds.push_back(PnSeed{p.series, p.m, p.i, p.j});
             if (c.topk_mode == PANACHE_TOPK_PER_LENGTH) {
-                PN_TRY(run_select(ctx, R, seed_global, false, picks));
+                PN_TRY(run_select(ctx, R, v, seed_global, false, picks));
                 for (auto &gp : picks)
                     for (auto &p : gp) seeds.push_back(PnSeed{p.series, p.m, p.i, p.j});
             }
@@ -636,7 +604,7 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     }
     PN_TRY(tm.mark(7));
     std::vector<std::vector<PnPick>> picks;
-    PN_TRY(run_select(ctx, R, out_groups, true, picks));
+    PN_TRY(run_select(ctx, R, v, out_groups, true, picks));
     PN_TRY(tm.mark(8));
     PN_TRY(tm.read(ctx->stats.step_ms));
     res.assign(nser, {});
@@ -667,6 +635,313 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     return PANACHE_OK;
 }
 
+bool same_shape(const std::vector<SeriesIn> &a, const std::vector<SeriesIn> &b) {
+    if (a.size() != b.size()) return false;
+    for (size_t s = 0; s < a.size(); ++s) {
+        if (a[s].n != b[s].n || (a[s].dtype & 0xFF) != (b[s].dtype & 0xFF) || a[s].m_min != b[s].m_min ||
+            a[s].m_max != b[s].m_max || a[s].k != b[s].k || a[s].excl != b[s].excl)
+            return false;
+    }
+    return true;
+}
+
+// Copies every series of `in` into the persistent staging buffer of the
+// captured graph (host or device sources; the graph reads fixed addresses).
+int stage_inputs(panache_ctx *ctx, const std::vector<SeriesIn> &in) {
+    for (size_t s = 0; s < in.size(); ++s) {
+        const size_t es = (in[s].dtype & 0xFF) == PANACHE_F32 ? 4 : 8;
+        if (!in[s].n) continue;
+        const cudaMemcpyKind kind = (in[s].dtype & PANACHE_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        PN_CU(cudaMemcpyAsync(ctx->gstage + ctx->gstage_off[s], in[s].ptr, (size_t)in[s].n * es, kind, ctx->st));
+    }
+    return PANACHE_OK;
+}
+
+// Algorithm 1 over every anchor of every series (conversion of the staged
+// samples, moments, anchors, features and keys, ranks, directory, query
+// order) and the streaming search: the part of a request whose launches
+// depend only on its shape.
+int index_and_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const PnConv *dcv, int32_t ncv,
+                     StepTimer &tm, bool search) {
+    const panache_config &c = ctx->cfg;
+    cudaStream_t st = R.st;
+    if (R.total_samples > 0) {
+        k_convert<<<(unsigned)((R.total_samples + 255) / 256), 256, 0, st>>>(dcv, ncv, R.total_samples, R.x, R.xs,
+                                                                            R.x1);
+        PN_CU(cudaGetLastError());
+        ctx->launches += 1;
+    }
+    PN_TRY(tm.mark(1));
+    PN_CU(pn::launch_runlen(v, R.total_samples, st));
+    PN_CU(pn::launch_moments(v, R.total_samples, R.sq, st));
+    PN_TRY(tm.mark(2));
+    if (R.tca) {
+        PN_CU(pn::launch_anchor_tc(v, R.d_tile_anchor, R.d_tile_row0, (int32_t)R.tile_anchor.size(), st));
+        ctx->launches += 1;
+    }
+    PN_CU(pn::launch_features(v, R.d_blk_anchor, R.d_blk_chunk0, (int32_t)R.blk_anchor.size(), R.a_max, st));
+    PN_TRY(tm.mark(3));
+    PN_CU(pn::launch_ranks(v, R.total_windows, st));
+    PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
+    PN_CU(pn::launch_query_order(v, R.total_windows, R.total_buckets, st));
+    PN_TRY(tm.mark(4));
+    ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3;
+    if (!search) return PANACHE_OK;
+    PN_CU(pn::launch_search(v, R.total_windows, ctx->sm_count * (int)c.grid_mult, R.a_max, st));
+    ctx->launches += 1;
+    return PANACHE_OK;
+}
+
+// The whole path for a list of series; results per series.
+int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<std::vector<panache_motif>> &res) {
+    const panache_config &c = ctx->cfg;
+    for (auto &s : in) PN_TRY(check_series(s));
+    const bool graph = (c.flags & PANACHE_FLAG_GRAPH) && !(c.flags & (PANACHE_FLAG_INDEX_ONLY | PANACHE_FLAG_TIMING));
+    if (graph && ctx->gexec && ctx->last && same_shape(ctx->gshape, in)) {
+        // replay: new samples into the kept buffers, one graph launch, then Algorithm 2
+        memset(&ctx->stats, 0, sizeof(ctx->stats));
+        ctx->launches = ctx->glaunches;
+        PnRequest &R = *ctx->last;
+        ctx->stats.device_bytes = R.footprint;
+        PN_TRY(stage_inputs(ctx, in));
+        PN_CU(cudaGraphLaunch(ctx->gexec, R.st));
+        StepTimer tm;
+        PN_TRY(tm.start(false, R.st));
+        return run_emit(ctx, R, make_view(ctx, R), tm, res);
+    }
+    ctx->drop_graph();
+    delete ctx->last;
+    ctx->last = nullptr;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->launches = 0;
+    PnRequest *Rp = new (std::nothrow) PnRequest();
+    if (!Rp) return PANACHE_ENOMEM;
+    ctx->last = Rp;
+    PnRequest &R = *Rp;
+    cudaStream_t st = ctx->st;
+    R.st = st;
+    PN_TRY(plan(ctx->cfg, in, R));
+    ctx->stats.device_bytes = R.footprint;
+    const int64_t nser = (int64_t)R.ser.size();
+    bool all_f32 = true;
+    for (auto &si : in) all_f32 = all_f32 && (si.dtype & 0xFF) == PANACHE_F32;
+    PN_TRY(alloc_state(ctx, R, all_f32 && c.precision == PANACHE_MIXED, true));
+    StepTimer tm;
+    PN_TRY(tm.start((c.flags & PANACHE_FLAG_TIMING) != 0, st));
+
+    // samples: host inputs go through one staging buffer; device inputs are
+    // read in place (with the graph, every input is staged at a fixed address)
+    std::vector<PnConv> cv(nser);
+    int64_t stage_bytes = 0;
+    std::vector<int64_t> stage_off(nser, -1);
+    for (int64_t s = 0; s < nser; ++s) {
+        const int es = (in[s].dtype & 0xFF) == PANACHE_F32 ? 4 : 8;
+        if (graph || !(in[s].dtype & PANACHE_DEVICE)) {
+            stage_off[s] = stage_bytes;
+            stage_bytes += ((in[s].n * es + 15) / 16) * 16;
+        }
+    }
+    unsigned char *stage = nullptr;
+    if (stage_bytes) {
+        if (graph) PN_CU(R.alloc(stage, stage_bytes));
+        else PN_CU(cudaMallocAsync((void **)&stage, stage_bytes, st));
+    }
+    for (int64_t s = 0; s < nser; ++s) {
+        const int es = (in[s].dtype & 0xFF) == PANACHE_F32 ? 4 : 8;
+        cv[s].n = in[s].n;
+        cv[s].x_off = R.ser[s].x_off;
+        cv[s].dtype = in[s].dtype & 0xFF;
+        if (stage_off[s] < 0) {
+            cv[s].src = in[s].ptr;
+        } else {
+            cv[s].src = stage + stage_off[s];
+            if (in[s].n) {
+                const cudaMemcpyKind kind =
+                    (in[s].dtype & PANACHE_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+                PN_CU(cudaMemcpyAsync(stage + stage_off[s], in[s].ptr, in[s].n * es, kind, st));
+            }
+        }
+    }
+    PnConv *dcv = nullptr;
+    PN_CU(R.alloc(dcv, std::max<int64_t>(1, nser)));
+    PN_CU(cudaMemcpyAsync(dcv, cv.data(), sizeof(PnConv) * nser, cudaMemcpyHostToDevice, st));
+    PnView v = make_view(ctx, R);
+    const bool search = !(c.flags & PANACHE_FLAG_INDEX_ONLY);
+    if (graph) {
+        // capture once; this and every later request of the same shape launch it
+        cudaGraph_t g = nullptr;
+        PN_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = from_cuda(cudaMemsetAsync(R.prof, 0xFF, sizeof(unsigned long long) *
+                                                               std::max<int64_t>(1, R.total_cells), st));
+        if (rc == PANACHE_OK) rc = from_cuda(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
+        if (rc == PANACHE_OK) rc = from_cuda(cudaMemsetAsync(R.err, 0, sizeof(int), st));
+        StepTimer off;
+        if (rc == PANACHE_OK) rc = index_and_search(ctx, R, v, dcv, (int32_t)nser, off, true);
+        const cudaError_t ec = cudaStreamEndCapture(st, &g);
+        if (rc == PANACHE_OK) rc = from_cuda(ec);
+        if (rc == PANACHE_OK) rc = from_cuda(cudaGraphInstantiate(&ctx->gexec, g, 0));
+        if (g) cudaGraphDestroy(g);
+        if (rc != PANACHE_OK) {
+            ctx->drop_graph();
+            return rc;
+        }
+        ctx->gshape = in;
+        ctx->gstage = stage;
+        ctx->gstage_off = stage_off;
+        ctx->glaunches = ctx->launches;
+        PN_CU(cudaGraphLaunch(ctx->gexec, st));
+    } else {
+        int rc = index_and_search(ctx, R, v, dcv, (int32_t)nser, tm, search);
+        if (stage) cudaFreeAsync(stage, st);
+        PN_TRY(rc);
+    }
+    if (!search) {
+        for (int t = 5; t <= 8; ++t) PN_TRY(tm.mark(t));
+        PN_TRY(tm.read(ctx->stats.step_ms));
+        int herr = 0;
+        PN_CU(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        PN_CU(cudaStreamSynchronize(st));
+        if (herr) return PANACHE_ETIMEOUT;
+        res.assign(nser, {});
+        ctx->stats.kernel_launches = ctx->launches;
+        ctx->stats.waves = 1;
+        return PANACHE_OK;
+    }
+    PN_TRY(tm.mark(5));
+    return run_emit(ctx, R, v, tm, res);
+}
+
+// ---------------------------------------------------------------------------
+// Resident streams
+// ---------------------------------------------------------------------------
+
+// Fresh resident state for `cap` samples (none present yet).
+int stream_alloc(panache_stream *h, int64_t cap, PnRequest *&out) {
+    out = nullptr;
+    panache_ctx *ctx = h->ctx;
+    PnRequest *R = new (std::nothrow) PnRequest();
+    if (!R) return PANACHE_ENOMEM;
+    R->st = ctx->st;
+    static const double none = 0.0;
+    std::vector<SeriesIn> in{SeriesIn{&none, PANACHE_F64 | PANACHE_DEVICE, 0, h->m_min, h->m_max, h->k, h->excl}};
+    std::vector<int64_t> caps{cap};
+    int rc = plan(ctx->cfg, in, *R, &caps);
+    if (rc == PANACHE_OK) rc = alloc_state(ctx, *R, false, false);
+    if (rc != PANACHE_OK) {
+        delete R;
+        return rc;
+    }
+    out = R;
+    return PANACHE_OK;
+}
+
+// Copies a host table into a stream-ordered temporary of the request's stream.
+template <class T>
+int upload_tmp(cudaStream_t st, const std::vector<T> &h, T *&d) {
+    d = nullptr;
+    if (h.empty()) return PANACHE_OK;
+    PN_CU(cudaMallocAsync((void **)&d, sizeof(T) * h.size(), st));
+    PN_CU(cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+    return PANACHE_OK;
+}
+
+// Searches queries [q_lo[a], q_hi[a]) of every anchor into `v.prof`.
+int stream_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const std::vector<int64_t> &q_lo,
+                  const std::vector<int64_t> &q_hi) {
+    std::vector<PnQRange> rng;
+    int64_t total = 0;
+    for (size_t ai = 0; ai < R.anc.size(); ++ai) {
+        if (q_hi[ai] <= q_lo[ai]) continue;
+        rng.push_back(PnQRange{total, q_lo[ai], (int32_t)ai, 0});
+        total += q_hi[ai] - q_lo[ai];
+    }
+    if (!total) return PANACHE_OK;
+    PnQRange *drng = nullptr;
+    PN_TRY(upload_tmp(R.st, rng, drng));
+    PN_CU(pn::launch_query_order(v, total, R.total_buckets, R.st, drng, (int32_t)rng.size()));
+    PN_CU(pn::launch_search(v, total, ctx->sm_count * (int)ctx->cfg.grid_mult, R.a_max, R.st));
+    PN_CU(cudaFreeAsync(drng, R.st));
+    ctx->launches += 2 + 4 * 3;
+    return PANACHE_OK;
+}
+
+// Brings the resident index up to the samples present: moments, features of
+// the chunks that gained windows, ranks, directory, and the search of every
+// query whose batch of beta samples is now complete (its population, and so
+// its level and candidates, can no longer change).
+int stream_advance(panache_stream *h) {
+    panache_ctx *ctx = h->ctx;
+    const panache_config &c = ctx->cfg;
+    PnRequest &R = *h->R;
+    cudaStream_t st = R.st;
+    const int64_t n = h->len;
+    const int C = (int)c.chunk;
+    R.ser[0].n = n;
+    for (auto &A : R.anc) A.nw = std::max<int64_t>(0, n - A.a + 1);
+    PN_CU(cudaMemcpyAsync(R.d_ser, R.ser.data(), sizeof(PnSeries), cudaMemcpyHostToDevice, st));
+    PN_CU(cudaMemcpyAsync(R.d_anc, R.anc.data(), sizeof(PnAnchor) * R.anc.size(), cudaMemcpyHostToDevice, st));
+    PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
+    PnView v = make_view(ctx, R);
+    PN_CU(pn::launch_runlen(v, n, st));
+    PN_CU(pn::launch_moments(v, n, R.sq, st));
+    std::vector<int32_t> ba, bc, ta, tc;
+    for (size_t ai = 0; ai < R.anc.size(); ++ai) {
+        const PnAnchor &A = R.anc[ai];
+        const int64_t c_lo = h->nw_feat[ai] / C, c_hi = (A.nw + C - 1) / C;
+        for (int64_t b = c_lo; b < c_hi; b += 128) {
+            ba.push_back((int32_t)ai);
+            bc.push_back((int32_t)b);
+        }
+        // tensor-core tiles keep the request's 128-chunk alignment
+        for (int64_t b = c_lo / 128 * 128; b < c_hi; b += 128) {
+            ta.push_back((int32_t)ai);
+            tc.push_back((int32_t)b);
+        }
+    }
+    if (!ba.empty()) {
+        int32_t *dba = nullptr, *dbc = nullptr, *dta = nullptr, *dtc = nullptr;
+        PN_TRY(upload_tmp(st, ba, dba));
+        PN_TRY(upload_tmp(st, bc, dbc));
+        if (R.tca) {
+            PN_TRY(upload_tmp(st, ta, dta));
+            PN_TRY(upload_tmp(st, tc, dtc));
+            PN_CU(pn::launch_anchor_tc(v, dta, dtc, (int32_t)ta.size(), st));
+            PN_CU(cudaFreeAsync(dta, st));
+            PN_CU(cudaFreeAsync(dtc, st));
+            ctx->launches += 1;
+        }
+        PN_CU(pn::launch_features(v, dba, dbc, (int32_t)ba.size(), R.a_max, st));
+        PN_CU(cudaFreeAsync(dba, st));
+        PN_CU(cudaFreeAsync(dbc, st));
+    }
+    for (size_t ai = 0; ai < R.anc.size(); ++ai) h->nw_feat[ai] = R.anc[ai].nw;
+    PN_CU(pn::launch_ranks(v, R.total_windows, st));
+    PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
+    ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3;
+    const int beta = (c.beta > 0 && (int)c.beta < h->excl) ? (int)c.beta : h->excl;
+    const int64_t nb = n / beta * beta;                // samples of complete batches
+    std::vector<int64_t> q_ready(R.anc.size());
+    for (size_t ai = 0; ai < R.anc.size(); ++ai) {
+        const PnAnchor &A = R.anc[ai];
+        q_ready[ai] = std::max(h->q_done[ai], std::min<int64_t>(A.nw, std::max<int64_t>(0, nb - A.a + 1)));
+    }
+    PN_TRY(stream_search(ctx, R, v, h->q_done, q_ready));
+    h->q_done = q_ready;
+    unsigned long long hs[PN_ST_COUNT];
+    int herr = 0;
+    PN_CU(cudaMemcpyAsync(hs, R.stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    PN_CU(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PN_CU(cudaStreamSynchronize(st));
+    // counters of this append: the queries it searched and their candidates
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.queries = hs[PN_ST_QUERIES];
+    ctx->stats.candidates = hs[PN_ST_CANDIDATES];
+    ctx->stats.exact_stream = hs[PN_ST_LB_PASSED];
+    ctx->stats.device_bytes = R.footprint;
+    ctx->stats.kernel_launches = ctx->launches;
+    return herr ? PANACHE_ETIMEOUT : PANACHE_OK;
+}
+
 int copy_out(const std::vector<panache_motif> &m, panache_motif *out, int64_t cap, int64_t *out_len) {
     if (out_len) *out_len = (int64_t)m.size();
     if ((int64_t)m.size() > cap) return PANACHE_ETRUNC;
@@ -680,6 +955,13 @@ int copy_out(const std::vector<panache_motif> &m, panache_motif *out, int64_t ca
 }  // namespace
 
 namespace pn_rt {
+int64_t stream_capacity(const panache_stream *h) { return h ? h->cap : 0; }
+
+int64_t grow_capacity(int64_t cap, int64_t need) {
+    if (need <= cap) return cap;
+    return std::min<int64_t>(PN_MAX_SERIES_LEN, std::max<int64_t>(std::max<int64_t>(cap * 2, need + need / 2), 4096));
+}
+
 int run(panache_ctx *ctx, const std::vector<PnSeriesIn> &in, std::vector<std::vector<panache_motif>> &res) {
     return run_request(ctx, in, res);
 }
@@ -739,6 +1021,15 @@ int panache_create(const panache_config *cfg, panache_ctx **out) {
 void panache_destroy(panache_ctx *ctx) {
     if (!ctx) return;
     if (ctx->st) cudaStreamSynchronize(ctx->st);
+    // streams still open lose their device state; their handles stay valid
+    // for panache_stream_close (and fail with ESTATE otherwise)
+    for (panache_stream *h : ctx->streams) {
+        delete h->R;
+        h->R = nullptr;
+        h->ctx = nullptr;
+    }
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    ctx->drop_graph();
     delete ctx->last;
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
@@ -845,6 +1136,7 @@ int panache_stream_open(panache_ctx *ctx, int32_t m_min, int32_t m_max, int32_t 
     h->m_max = m_max;
     h->k = k;
     h->excl = excl;
+    ctx->streams.insert(h);
     *out = h;
     return PANACHE_OK;
 }
@@ -855,61 +1147,95 @@ int panache_append(panache_stream *h, const void *chunk, int32_t dtype, int64_t 
     if ((dt != PANACHE_F32 && dt != PANACHE_F64) || (dtype & ~0x1FF)) return PANACHE_EINVAL;
     if (len == 0) return PANACHE_OK;
     if (h->len + len > PN_MAX_SERIES_LEN) return PANACHE_EINVAL;
-    cudaStream_t st = h->ctx->st;
+    panache_ctx *ctx = h->ctx;
+    if (!ctx) return PANACHE_ESTATE;
+    cudaStream_t st = ctx->st;
+    ctx->launches = 0;
     if (h->len + len > h->cap) {
-        int64_t nc = std::max<int64_t>(h->cap * 2, h->len + len);
-        nc = std::max<int64_t>(nc, 4096);
-        double *nd = nullptr;
-        PN_CU(cudaMalloc((void **)&nd, sizeof(double) * nc));
-        if (h->len) PN_CU(cudaMemcpyAsync(nd, h->dev, sizeof(double) * h->len, cudaMemcpyDeviceToDevice, st));
-        PN_CU(cudaStreamSynchronize(st));
-        cudaFree(h->dev);
-        h->dev = nd;
-        h->cap = nc;
-    }
-    std::vector<double> tmp;
-    const void *src = chunk;
-    if (dt == PANACHE_F32 || (dtype & PANACHE_DEVICE)) {
-        // widen on the host (host chunks) or copy back and widen (device chunks)
-        std::vector<float> f;
-        tmp.resize(len);
-        if (dt == PANACHE_F32) {
-            f.resize(len);
-            if (dtype & PANACHE_DEVICE)
-                PN_CU(cudaMemcpy(f.data(), chunk, 4 * len, cudaMemcpyDeviceToHost));
-            else
-                memcpy(f.data(), chunk, 4 * len);
-            for (int64_t t = 0; t < len; ++t) tmp[t] = f[t];
-        } else {
-            PN_CU(cudaMemcpy(tmp.data(), chunk, 8 * len, cudaMemcpyDeviceToHost));
+        // grow: a fresh state at twice the capacity, rebuilt from the samples
+        // (every step is a function of the samples, so the rebuilt state
+        // equals the one the appends would have produced)
+        const int64_t nc = pn_rt::grow_capacity(h->cap, h->len + len);
+        PnRequest *R2 = nullptr;
+        PN_TRY(stream_alloc(h, nc, R2));
+        if (h->len) {
+            k_put<<<(unsigned)((h->len + 255) / 256), 256, 0, st>>>(h->R->x, PANACHE_F64, h->len, 0, R2->x, R2->xs);
+            PN_CU(cudaGetLastError());
         }
-        src = tmp.data();
+        delete h->R;
+        h->R = R2;
+        h->cap = nc;
+        h->q_done.assign(R2->anc.size(), 0);
+        h->nw_feat.assign(R2->anc.size(), 0);
     }
-    PN_CU(cudaMemcpyAsync(h->dev + h->len, src, sizeof(double) * len, cudaMemcpyHostToDevice, st));
-    PN_CU(cudaStreamSynchronize(st));
+    PnRequest &R = *h->R;
+    const int es = dt == PANACHE_F32 ? 4 : 8;
+    const void *src = chunk;
+    void *stage = nullptr;
+    if (!(dtype & PANACHE_DEVICE)) {
+        PN_CU(cudaMallocAsync(&stage, (size_t)len * es, st));
+        PN_CU(cudaMemcpyAsync(stage, chunk, (size_t)len * es, cudaMemcpyHostToDevice, st));
+        src = stage;
+    }
+    k_put<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(src, dtype, len, h->len, R.x, R.xs);
+    PN_CU(cudaGetLastError());
+    if (stage) PN_CU(cudaFreeAsync(stage, st));
     h->len += len;
-    return PANACHE_OK;
+    return stream_advance(h);
 }
 
 int panache_stream_topk(panache_stream *h, panache_motif *out, int64_t out_cap, int64_t *out_len) {
     if (!h || !out_len) return PANACHE_EINVAL;
-    std::vector<SeriesIn> in{SeriesIn{h->dev, PANACHE_F64 | PANACHE_DEVICE, h->len, h->m_min, h->m_max, h->k, h->excl}};
-    if (h->len == 0) {
+    if (!h->ctx) return PANACHE_ESTATE;
+    if (h->len == 0 || !h->R) {
         *out_len = 0;
         return PANACHE_OK;
     }
+    panache_ctx *ctx = h->ctx;
+    PnRequest &R = *h->R;
+    cudaStream_t st = R.st;
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->launches = 0;
+    ctx->stats.device_bytes = R.footprint;
+    PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
+    // Algorithm 2 and the pending tail run on a copy of the rows
+    unsigned long long *rows = nullptr;
+    const size_t bytes = sizeof(unsigned long long) * (size_t)std::max<int64_t>(1, R.total_cells);
+    PN_CU(cudaMallocAsync((void **)&rows, bytes, st));
+    PN_CU(cudaMemcpyAsync(rows, R.prof, bytes, cudaMemcpyDeviceToDevice, st));
+    PnView v = make_view(ctx, R);
+    v.prof = rows;
+    std::vector<int64_t> q_end(R.anc.size());
+    for (size_t ai = 0; ai < R.anc.size(); ++ai) q_end[ai] = R.anc[ai].nw;
+    int rc = stream_search(ctx, R, v, h->q_done, q_end);
     std::vector<std::vector<panache_motif>> res;
-    PN_TRY(run_request(h->ctx, in, res));
+    StepTimer tm;
+    if (rc == PANACHE_OK) rc = tm.start(false, st);
+    if (rc == PANACHE_OK) rc = run_emit(ctx, R, v, tm, res);
+    cudaFreeAsync(rows, st);
+    if (rc != PANACHE_OK) return rc;
     return copy_out(res[0], out, out_cap, out_len);
 }
 
 int64_t panache_stream_length(const panache_stream *h) { return h ? h->len : -1; }
 
+int panache_stream_checkpoint(const panache_stream *h, double *out, int64_t cap, int64_t *out_len) {
+    if (!h || !out_len) return PANACHE_EINVAL;
+    *out_len = h->len;
+    if (cap < h->len) return PANACHE_ETRUNC;
+    if (!h->len) return PANACHE_OK;
+    if (!out) return PANACHE_EINVAL;
+    if (!h->ctx || !h->R) return PANACHE_ESTATE;
+    PN_CU(cudaMemcpyAsync(out, h->R->x, sizeof(double) * h->len, cudaMemcpyDeviceToHost, h->R->st));
+    PN_CU(cudaStreamSynchronize(h->R->st));
+    return PANACHE_OK;
+}
+
 void panache_stream_close(panache_stream *h) {
     if (!h) return;
-    if (h->dev) {
-        cudaStreamSynchronize(h->ctx->st);
-        cudaFree(h->dev);
+    if (h->ctx) {
+        if (h->ctx->st) cudaStreamSynchronize(h->ctx->st);
+        h->ctx->streams.erase(h);
     }
     delete h;
 }

@@ -20,7 +20,7 @@ __global__ void k_hot_flags(PnView v, const int64_t *slot_off, int64_t total, ui
     if (t >= total) return;
     int ai = pn_find(slot_off, v.nanchors, t, [](int64_t o) { return o; });
     const PnAnchor &A = v.anchors[ai];
-    uint32_t N = v.cnt[A.win_off + A.nw - 1];
+    uint32_t N = A.nw > 0 ? v.cnt[A.win_off + A.nw - 1] : 0u;
     int D = pn_depth(N, v.alpha, v.B);
     int64_t b = t - slot_off[ai];
     uint32_t f = 0, sz = 0;
@@ -43,7 +43,7 @@ __global__ void k_hot_compact(PnView v, const int64_t *slot_off, int64_t total, 
     if (t >= total || !flag[t]) return;
     int ai = pn_find(slot_off, v.nanchors, t, [](int64_t o) { return o; });
     const PnAnchor &A = v.anchors[ai];
-    uint32_t N = v.cnt[A.win_off + A.nw - 1];
+    uint32_t N = A.nw > 0 ? v.cnt[A.win_off + A.nw - 1] : 0u;
     int D = pn_depth(N, v.alpha, v.B);
     const PnLevel &L = v.levels[A.level_begin + D];
     int64_t gb = L.bucket_base + (t - slot_off[ai]);
@@ -89,12 +89,12 @@ __global__ void k_sieve_rekey(PnView v, const PnClass *cls, int32_t ncls, int64_
 // row read by 8 lanes, threshold tests lane-parallel, survivors evaluated
 // four at a time against the staged window, both cells updated.
 template <class Z>
-__global__ void __launch_bounds__(256) k_sieve_pairs(PnView v, const PnClass *cls, int32_t ncls, int64_t total,
-                                                     const uint32_t *members, int w, int exhaustive, int zcap) {
+__global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass *cls, int64_t total,
+                                                        const uint32_t *member_class, const uint32_t *members, int w,
+                                                        int exhaustive, int zcap) {
     using ZT = typename Z::T;
     extern __shared__ __align__(16) unsigned char zsm[];
     __shared__ __align__(16) float sF[8][PN_FEAT];
-    __shared__ float lbbuf[8][32];
     __shared__ uint32_t scand[8][32];
     __shared__ unsigned long long snap[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -104,8 +104,7 @@ __global__ void __launch_bounds__(256) k_sieve_pairs(PnView v, const PnClass *cl
     const float shrink = 1.0f - v.lam;
     unsigned long long n_ex = 0;
     for (int64_t p = wid; p < total; p += nwp) {
-        const int ci = pn_find(cls, ncls, p, [](const PnClass &c) { return (int64_t)c.moff; });
-        const PnClass &c = cls[ci];
+        const PnClass &c = cls[member_class[p]];
         const PnAnchor &A = v.anchors[c.anchor];
         const PnSeries &S = v.series[A.series];
         const int a = A.a;
@@ -123,36 +122,53 @@ __global__ void __launch_bounds__(256) k_sieve_pairs(PnView v, const PnClass *cl
             for (int r = lane; r < a; r += 32) zu[r] = Z::z(mu_, xs[r]);
         }
         __syncwarp();
-        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
+        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
         const float lbscale = 2.0f / (float)a;
         unsigned long long bestkey = PN_EMPTY_KEY;
         for (int64_t b0 = u + 1; b0 < vend; b0 += 32) {
             const int nblk = (int)min((int64_t)32, vend - b0);
-            for (int sub = 0; sub < nblk; sub += 4) {
-                const int k = sub + (lane >> 3);
-                float part = 0.0f;
-                if (k < nblk) {
-                    const uint32_t xv = members[c.moff + b0 + k];
-                    const float4 fc =
-                        reinterpret_cast<const float4 *>(Fa + (size_t)pn_row32(xv, v.cshift, nch) * PN_FEAT)[lane & 7];
-                    const float dx = fq.x - fc.x, dy = fq.y - fc.y, dz = fq.z - fc.z, dw = fq.w - fc.w;
-                    part = dx * dx + dy * dy + dz * dz + dw * dw;
-                }
-                part += __shfl_xor_sync(0xffffffffu, part, 1);
-                part += __shfl_xor_sync(0xffffffffu, part, 2);
-                part += __shfl_xor_sync(0xffffffffu, part, 4);
-                if (k < nblk && (lane & 7) == 0) lbbuf[warp][k] = part;
-            }
-            __syncwarp();
-            bool surv = false;
-            uint32_t xv = 0;
-            unsigned long long kc = 0;
+            // lane l owns neighbour l of the block; rows read by 8-lane groups,
+            // partial sums reduced by a transposed butterfly (as in the search)
+            uint32_t xv = 0, roff = 0;
             if (lane < nblk) {
                 xv = members[c.moff + b0 + lane];
+                roff = pn_row32(xv, v.cshift, nch);
+            }
+            float4 fc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = 4 * j + (lane >> 3);
+                const uint32_t ro = __shfl_sync(0xffffffffu, roff, k);
+                fc[j] = k < nblk ? reinterpret_cast<const float4 *>(Fa + (size_t)ro * PN_FEAT)[lane & 7] : fq;
+            }
+            float acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float dx = fq.x - fc[j].x, dy = fq.y - fc[j].y, dz = fq.z - fc[j].z, dw = fq.w - fc[j].w;
+                acc[j] = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, dw * dw)));
+            }
+            const bool b2 = (lane & 4) != 0, b1 = (lane & 2) != 0, b0l = (lane & 1) != 0;
+            float r4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float send = b2 ? acc[i] : acc[i + 4];
+                r4[i] = (b2 ? acc[i + 4] : acc[i]) + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            float r2[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float send = b1 ? r4[i] : r4[i + 2];
+                r2[i] = (b1 ? r4[i + 2] : r4[i]) + __shfl_xor_sync(0xffffffffu, send, 2);
+            }
+            const float tot = (b0l ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, b0l ? r2[0] : r2[1], 1);
+            const float lbsq = __shfl_sync(0xffffffffu, tot, ((lane & 3) << 3) | (lane >> 2));
+            bool surv = false;
+            unsigned long long kc = 0;
+            if (lane < nblk) {
                 if (llabs((int64_t)xv - (int64_t)xu) >= S.excl) {
                     kc = __ldcg(&prow[xv]);
-                    const float lbs = shrink * sqrtf(lbscale * lbbuf[warp][lane]);
+                    const float lbs = shrink * sqrtf(lbscale * lbsq);
                     const ZT tu = Z::fmn(Z::cell(bestkey), Z::cell(__ldcg(&prow[xu])));
                     surv = (ZT)lbs < Z::fmx(tu, Z::cell(kc));
                 }
@@ -209,7 +225,7 @@ __global__ void k_complete(PnView v, const PnSeed *seeds, int32_t nseeds, int dm
             const double dd = pn_dist_warp(v, S.x_off, m, i, wi, j, wj, lane);
             n_ex += 1;
             if (lane == 0 && dd < __longlong_as_double(0x7ff0000000000000ll)) {
-                unsigned long long *row = v.prof + S.row_off + (int64_t)(m - S.m_min) * S.n;
+                unsigned long long *row = v.prof + S.row_off + (int64_t)(m - S.m_min) * S.ld;
                 const unsigned long long ki = pn_pack(dd, (uint32_t)j), kj = pn_pack(dd, (uint32_t)i);
                 if (atomicMin(&row[i], ki) > ki) imp = 1;
                 if (atomicMin(&row[j], kj) > kj) imp = 1;
@@ -321,9 +337,9 @@ __global__ void k_sel_verify(PnView v, const PnSelGroup *grp, int32_t ngrp, PnPo
         const PnSeries &S = v.series[G.series];
         PnPoolEntry &pe = pool[e];
         const int64_t cell = (int64_t)pe.cell + (G.cell_off - S.row_off);
-        const int m = S.m_min + (int)(cell / S.n);
+        const int m = S.m_min + (int)(cell / S.ld);
         // both cells of a pair get bit-identical values: evaluate in (min, max) order
-        const int64_t c0 = cell % S.n, c1 = pe.j;
+        const int64_t c0 = cell % S.ld, c1 = pe.j;
         const int64_t i = c0 < c1 ? c0 : c1, j = c0 < c1 ? c1 : c0;
         const double *xi = v.x + S.x_off + i, *xj = v.x + S.x_off + j;
         double si = 0, sj = 0;
@@ -397,8 +413,8 @@ __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry 
         const int64_t base = G.cell_off - S.row_off;
         for (int t = 0; t < cnt && nacc < k; ++t) {
             const int64_t cell = base + e[t].cell;
-            const int m = S.m_min + (int)(cell / S.n);
-            const int64_t i = cell % S.n;
+            const int m = S.m_min + (int)(cell / S.ld);
+            const int64_t i = cell % S.ld;
             bool clash = false;
             for (int u = lane; u < nacc; u += 32)
                 if (acc_m[u] == m && 2 * llabs(i - acc_i[u]) <= m) clash = true;
@@ -424,12 +440,12 @@ __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry 
 }
 
 template <class Z>
-cudaError_t sieve_t(const PnView &v, const PnClass *cls, int32_t ncls, int64_t nmem, const uint32_t *vals, int w,
-                    int exhaustive, int zcap, int64_t blocks, cudaStream_t st) {
+cudaError_t sieve_t(const PnView &v, const PnClass *cls, int64_t nmem, const uint32_t *keys, const uint32_t *vals,
+                    int w, int exhaustive, int zcap, int64_t blocks, cudaStream_t st) {
     const size_t sm = sizeof(typename Z::T) * zcap * 8;
     cudaError_t e = cudaFuncSetAttribute(k_sieve_pairs<Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_sieve_pairs<Z><<<(unsigned)blocks, 256, sm, st>>>(v, cls, ncls, nmem, vals, w, exhaustive, zcap);
+    k_sieve_pairs<Z><<<(unsigned)blocks, 256, sm, st>>>(v, cls, nmem, keys, vals, w, exhaustive, zcap);
     return cudaGetLastError();
 }
 
@@ -482,9 +498,10 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             int64_t blocks = (warps_needed + 7) / 8;
             if (blocks > grid_blocks) blocks = grid_blocks;
             const int zcap = (a_max + 3) & ~3;
-            if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, ncls, nmem, vals, w, exhaustive, zcap, blocks, st);
-            else if (v.x1) e = sieve_t<ZMix1>(v, cls, ncls, nmem, vals, w, exhaustive, zcap, blocks, st);
-            else e = sieve_t<ZMix2>(v, cls, ncls, nmem, vals, w, exhaustive, zcap, blocks, st);
+            // after the class sort, keys[p] is the class of member p
+            if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
+            else if (v.x1) e = sieve_t<ZMix1>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
+            else e = sieve_t<ZMix2>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             if (e == cudaSuccess) e = cudaGetLastError();
         }
     }

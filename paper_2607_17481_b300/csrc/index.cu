@@ -244,7 +244,7 @@ __global__ void k_nonconst(PnView v, int64_t total, uint32_t *flag, uint8_t *hea
     int ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
     const PnAnchor &A = v.anchors[ai];
     int64_t q = w - A.win_off;
-    flag[w] = (uint32_t)(v.runlen[v.series[A.series].x_off + q] < A.a);
+    flag[w] = q < A.nw ? (uint32_t)(v.runlen[v.series[A.series].x_off + q] < A.a) : 0u;
     head[w] = (uint8_t)(q == 0);
 }
 
@@ -271,7 +271,7 @@ __global__ void k_dir_items(PnView v, int64_t total, uint32_t *hist) {
     const PnLevel &L = v.levels[li];
     const PnAnchor &A = v.anchors[L.anchor];
     int64_t r = t - L.item_off;
-    uint32_t N = v.cnt[A.win_off + A.nw - 1];
+    uint32_t N = A.nw > 0 ? v.cnt[A.win_off + A.nw - 1] : 0u;
     uint32_t key = 0xFFFFFFFFu, val = 0xFFFFFFFFu;
     if (r < (int64_t)N) {
         uint32_t q = v.nclist[A.win_off + r];
@@ -288,11 +288,22 @@ __global__ void k_dir_items(PnView v, int64_t total, uint32_t *hist) {
 // Search order: every query is keyed by the global bucket it probes first
 // (its level's d-bit prefix), so warps running close together read the
 // same candidate rows.  Constant windows and windows without an earlier
-// valid partner sort last with key 0xFFFFFFFF.
-__global__ void k_query_keys(PnView v, int64_t total, uint32_t *keys) {
-    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= total) return;
-    int ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
+// valid partner sort last with key 0xFFFFFFFF.  Without a range table the
+// query space is every window; with one, entry t is the window its range
+// places there.
+__global__ void k_query_keys(PnView v, int64_t total, uint32_t *keys, const PnQRange *rng, int32_t nrng) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int ai;
+    int64_t w;
+    if (rng) {
+        const int ri = pn_find(rng, nrng, t, [](const PnQRange &r) { return r.off; });
+        ai = rng[ri].anchor;
+        w = v.anchors[ai].win_off + rng[ri].q_lo + (t - rng[ri].off);
+    } else {
+        w = t;
+        ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
+    }
     const PnAnchor &A = v.anchors[ai];
     const PnSeries &S = v.series[A.series];
     const int64_t q = w - A.win_off;
@@ -306,8 +317,8 @@ __global__ void k_query_keys(PnView v, int64_t total, uint32_t *keys) {
         const uint32_t sg = v.sig[w];
         key = (uint32_t)(v.levels[A.level_begin + d].bucket_base + (d > 0 ? (sg >> (v.B - d)) : 0u));
     }
-    keys[w] = key;
-    v.qorder[w] = (uint32_t)w;
+    keys[t] = key;
+    v.qorder[t] = (uint32_t)w;
 }
 
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -393,12 +404,13 @@ cudaError_t launch_directory(const PnView &v, int64_t total_items, int64_t total
     return e;
 }
 
-cudaError_t launch_query_order(const PnView &v, int64_t total, int64_t total_buckets, cudaStream_t st) {
+cudaError_t launch_query_order(const PnView &v, int64_t total, int64_t total_buckets, cudaStream_t st,
+                               const PnQRange *rng, int32_t nrng) {
     if (total <= 0) return cudaSuccess;
     uint32_t *keys = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&keys, sizeof(uint32_t) * total, st);
     if (e != cudaSuccess) return e;
-    k_query_keys<<<grid_for(total, 256), 256, 0, st>>>(v, total, keys);
+    k_query_keys<<<grid_for(total, 256), 256, 0, st>>>(v, total, keys, rng, nrng);
     e = cudaGetLastError();
     int bits = 1;
     while (bits < 32 && ((int64_t)1 << bits) <= total_buckets) ++bits;

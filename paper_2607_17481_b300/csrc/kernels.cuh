@@ -118,7 +118,8 @@ cudaError_t launch_directory(const PnView &v, int64_t total_items, int64_t total
 size_t anchor_tc_smem();
 cudaError_t launch_anchor_tc(const PnView &v, const int32_t *tile_anchor, const int32_t *tile_row0, int32_t ntiles,
                              cudaStream_t st);
-cudaError_t launch_query_order(const PnView &v, int64_t total_windows, int64_t total_buckets, cudaStream_t st);
+cudaError_t launch_query_order(const PnView &v, int64_t total_queries, int64_t total_buckets, cudaStream_t st,
+                               const PnQRange *rng = nullptr, int32_t nrng = 0);
 int search_max_budget();
 cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, int a_max, cudaStream_t st);
 }  // namespace pn

@@ -10,7 +10,8 @@
 struct PnSeries {
     int64_t x_off;        // first sample in the concatenated sample buffers
     int64_t n;            // samples
-    int64_t row_off;      // first cell of this series' profile rows [L][n]
+    int64_t row_off;      // first cell of this series' profile rows [L][ld]
+    int64_t ld;           // profile row stride: n for a request, the resident capacity for a stream
     int32_t m_min, m_max; // length interval
     int32_t excl;         // exclusion zone: a pair is valid iff |i - j| >= excl
     int32_t k;            // motifs requested
@@ -34,6 +35,15 @@ struct PnAnchor {
     int64_t bucket_base;  // first global bucket id of level 0
     int32_t level_begin;  // first level in the level table
     int32_t nlevels;      // dmax + 1
+};
+
+// A run of queries [q_lo, q_lo + count) of one anchor, placed at `off` in a
+// compact query space (the windows a stream append or snapshot searches).
+struct PnQRange {
+    int64_t off;
+    int64_t q_lo;
+    int32_t anchor;
+    int32_t _pad;
 };
 
 struct PnLevel {

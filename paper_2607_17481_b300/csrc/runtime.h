@@ -19,4 +19,8 @@ namespace pn_rt {
 int run(panache_ctx *ctx, const std::vector<PnSeriesIn> &in, std::vector<std::vector<panache_motif>> &res);
 // Device footprint of one series under ctx's configuration (admission estimate).
 int footprint(panache_ctx *ctx, const PnSeriesIn &s, uint64_t *bytes);
+// Resident capacity of a stream, and the capacity an append of `need` total
+// samples grows it to (the stream keeps its capacity when need fits).
+int64_t stream_capacity(const panache_stream *h);
+int64_t grow_capacity(int64_t cap, int64_t need);
 }  // namespace pn_rt

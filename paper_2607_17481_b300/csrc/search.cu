@@ -38,7 +38,6 @@ template <class Z>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {
     using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
-    __shared__ float lbbuf[SR_WARPS][32];
     __shared__ unsigned long long s_stat[3];
     extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -148,42 +147,61 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
             for (int r = lane; r < a; r += 32) zq[r] = Z::z(mq, xq[r]);
         }
         __syncwarp();
-        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.n;
+        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
         unsigned long long bestkey = PN_EMPTY_KEY;
         const float lbscale = 2.0f / (float)a;
-        // Bounds of 32 candidates at a time (rows read by 8 lanes each, 4 rows
-        // per step), then the threshold test with one candidate per lane.
-        // Survivors are compacted in place at the front of scand (never past a
-        // candidate not yet read), with their cell snapshots in snap.
-        float *slb = lbbuf[warp];
+        // Bounds of 32 candidates at a time: lane l owns candidate l of the
+        // block; its row is read by the 8 lanes of a group (4 rows per step,
+        // 8 steps, every load issued before the sums need it), the 8 partial
+        // sums of a lane are reduced across its group by a transposed
+        // butterfly (7 shuffles), and one more shuffle hands each lane its
+        // own candidate's bound.  Survivors are compacted in place at the
+        // front of scand (never past a candidate not yet read), with their
+        // cell snapshots in snap.
         int nsurv = 0, head = 0;
         for (int b32 = 0; b32 < taken; b32 += 32) {
             const int nblk = min(32, taken - b32);
-            for (int sub = 0; sub < nblk; sub += 4) {
-                const int k = sub + (lane >> 3);
-                const bool has = k < nblk;
-                float part = 0.0f;
-                if (has) {
-                    const uint32_t c = scand[b32 + k];
-                    const float4 fc =
-                        reinterpret_cast<const float4 *>(Fa + (size_t)pn_row32(c, v.cshift, nch) * PN_FEAT)[lane & 7];
-                    const float dx = fq.x - fc.x, dy = fq.y - fc.y, dz = fq.z - fc.z, dw = fq.w - fc.w;
-                    part = dx * dx + dy * dy + dz * dz + dw * dw;
-                }
-                part += __shfl_xor_sync(0xffffffffu, part, 1);
-                part += __shfl_xor_sync(0xffffffffu, part, 2);
-                part += __shfl_xor_sync(0xffffffffu, part, 4);
-                if (has && (lane & 7) == 0) slb[k] = part;
+            uint32_t c = 0, roff = 0;
+            if (lane < nblk) {
+                c = scand[b32 + lane];
+                roff = pn_row32(c, v.cshift, nch);
             }
-            __syncwarp();
-            uint32_t c = 0;
+            float4 fc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = 4 * j + (lane >> 3);
+                const uint32_t ro = __shfl_sync(0xffffffffu, roff, k);
+                fc[j] = k < nblk ? reinterpret_cast<const float4 *>(Fa + (size_t)ro * PN_FEAT)[lane & 7] : fq;
+            }
+            float acc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float dx = fq.x - fc[j].x, dy = fq.y - fc[j].y, dz = fq.z - fc[j].z, dw = fq.w - fc[j].w;
+                acc[j] = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, dw * dw)));
+            }
+            // transposed reduction over the 8 lanes of a group: afterwards lane L
+            // holds the sum of candidate 4 (L & 7) + (L >> 3)
+            const bool b2 = (lane & 4) != 0, b1 = (lane & 2) != 0, b0 = (lane & 1) != 0;
+            float r4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float send = b2 ? acc[i] : acc[i + 4];
+                r4[i] = (b2 ? acc[i + 4] : acc[i]) + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            float r2[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const float send = b1 ? r4[i] : r4[i + 2];
+                r2[i] = (b1 ? r4[i + 2] : r4[i]) + __shfl_xor_sync(0xffffffffu, send, 2);
+            }
+            const float tot = (b0 ? r2[1] : r2[0]) + __shfl_xor_sync(0xffffffffu, b0 ? r2[0] : r2[1], 1);
+            const float lbsq = __shfl_sync(0xffffffffu, tot, ((lane & 3) << 3) | (lane >> 2));
             unsigned long long kc = 0;
             float lbs = __int_as_float(0x7f800000);
             if (lane < nblk) {
-                c = scand[b32 + lane];
                 kc = __ldcg(&prow[c]);
-                lbs = shrink * sqrtf(lbscale * slb[lane]);
+                lbs = shrink * sqrtf(lbscale * lbsq);
             }
             const ZT cq = Z::cell(__ldcg(&prow[q]));
             // best-first start: while the query has no distance yet, the block's

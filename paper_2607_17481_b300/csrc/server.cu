@@ -35,21 +35,9 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-// Device samples of a live stream (FP64).  Snapshots taken by queued
-// requests share ownership, so growing the buffer never frees memory a
-// request still reads.
-struct DevSamples {
-    double *p = nullptr;
-    int64_t cap = 0;
-    ~DevSamples() {
-        if (p) cudaFree(p);
-    }
-};
-
 struct Job {
     uint64_t ticket = 0;
     std::vector<unsigned char> host;          // caller's samples, copied at submission
-    std::shared_ptr<DevSamples> dev;          // or a stream snapshot on the device
     PnSeriesIn s{};
     uint64_t footprint = 0;
     double t_submit = 0.0;
@@ -61,11 +49,22 @@ struct Result {
     double latency_ms = 0.0;
 };
 
+// A live stream: its whole index stays resident on the device (a resident
+// panache_stream on a context, and so a CUDA stream, of its own).  Appends
+// and snapshots run in the calling thread and overlap the slots' batches on
+// the GPU.  The resident state, plus the row copy a snapshot works on, is
+// reserved from the server's budget; an append that would grow it past the
+// budget is refused (EBUDGET).
 struct LiveStream {
     std::mutex mu;
-    std::shared_ptr<DevSamples> buf;
-    int64_t len = 0;
+    panache_ctx *ctx = nullptr;
+    panache_stream *h = nullptr;
+    uint64_t reserved = 0;
     int32_t m_min, m_max, k, excl;
+    ~LiveStream() {
+        if (h) panache_stream_close(h);
+        if (ctx) panache_destroy(ctx);
+    }
 };
 
 }  // namespace
@@ -131,7 +130,7 @@ void panache_server::worker(int slot) {
         std::vector<PnSeriesIn> in;
         for (auto &j : batch) {
             PnSeriesIn s = j.s;
-            s.ptr = j.dev ? (const void *)j.dev->p : (const void *)j.host.data();
+            s.ptr = (const void *)j.host.data();
             in.push_back(s);
         }
         std::vector<std::vector<panache_motif>> res;
@@ -220,6 +219,11 @@ void panache_server_destroy(panache_server *sv) {
     }
     sv->cv_work.notify_all();
     for (auto &t : sv->workers) t.join();
+    cudaSetDevice(sv->device);
+    {
+        std::lock_guard<std::mutex> lk(sv->streams_mu);
+        sv->streams.clear();
+    }
     for (auto *c : sv->ctxs) panache_destroy(c);
     delete sv;
 }
@@ -271,6 +275,12 @@ int panache_server_stream_open(panache_server *sv, int32_t m_min, int32_t m_max,
     ls->m_max = m_max;
     ls->k = k;
     ls->excl = excl;
+    cudaSetDevice(sv->device);
+    panache_config c = sv->cfg;
+    c.hbm_budget_bytes = 0;                       // the server's budget governs
+    int rc = panache_create(&c, &ls->ctx);
+    if (rc == PANACHE_OK) rc = panache_stream_open(ls->ctx, m_min, m_max, k, excl, &ls->h);
+    if (rc != PANACHE_OK) return rc;
     std::lock_guard<std::mutex> lk(sv->streams_mu);
     *stream_id = sv->next_stream++;
     sv->streams[*stream_id] = std::move(ls);
@@ -292,40 +302,81 @@ int panache_server_append(panache_server *sv, uint64_t stream_id, const void *ch
     if (!len) return PANACHE_OK;
     cudaSetDevice(sv->device);
     std::lock_guard<std::mutex> lk(ls->mu);
-    if (!ls->buf || ls->len + len > ls->buf->cap) {
-        // grow into a new buffer; snapshots of queued requests keep the old one
-        auto nb = std::make_shared<DevSamples>();
-        nb->cap = std::max<int64_t>(std::max<int64_t>(4096, 2 * (ls->buf ? ls->buf->cap : 0)), ls->len + len);
-        if (cudaMalloc((void **)&nb->p, sizeof(double) * nb->cap) != cudaSuccess) return PANACHE_ENOMEM;
-        if (ls->len && cudaMemcpy(nb->p, ls->buf->p, sizeof(double) * ls->len, cudaMemcpyDeviceToDevice) != cudaSuccess)
-            return PANACHE_ECUDA;
-        ls->buf = nb;
+    const int64_t have = panache_stream_length(ls->h), cap = pn_rt::stream_capacity(ls->h);
+    const int64_t ncap = pn_rt::grow_capacity(cap, have + len);
+    if (ncap != cap) {
+        // reserve the grown state (and its snapshot row copy) before growing
+        uint64_t fp = 0;
+        const PnSeriesIn s{chunk, dt, ncap, ls->m_min, ls->m_max, ls->k, ls->excl};
+        int rc = pn_rt::footprint(ls->ctx, s, &fp);
+        if (rc != PANACHE_OK) return rc;
+        fp += (uint64_t)(ls->m_max - ls->m_min + 1) * (uint64_t)ncap * 8u;
+        std::lock_guard<std::mutex> g(sv->mu);
+        if (sv->in_use - ls->reserved + fp > sv->budget) return PANACHE_EBUDGET;
+        sv->in_use = sv->in_use - ls->reserved + fp;
+        sv->peak_in_use = std::max(sv->peak_in_use, sv->in_use);
+        ls->reserved = fp;
     }
-    std::vector<double> tmp;
-    const double *src = (const double *)chunk;
-    if (dt == PANACHE_F32) {
-        tmp.resize(len);
-        for (int64_t t = 0; t < len; ++t) tmp[t] = ((const float *)chunk)[t];
-        src = tmp.data();
-    }
-    if (cudaMemcpy(ls->buf->p + ls->len, src, sizeof(double) * len, cudaMemcpyHostToDevice) != cudaSuccess)
-        return PANACHE_ECUDA;
-    ls->len += len;
-    return PANACHE_OK;
+    return panache_append(ls->h, chunk, dtype, len);
 }
 
 int panache_server_stream_topk(panache_server *sv, uint64_t stream_id, uint64_t *ticket) {
     if (!sv || !ticket) return PANACHE_EINVAL;
     LiveStream *ls = find_stream(sv, stream_id);
     if (!ls) return PANACHE_EINVAL;
-    Job j;
+    cudaSetDevice(sv->device);
+    const double t0 = now_ms();
+    Result r;
+    int64_t n = 0;
     {
         std::lock_guard<std::mutex> lk(ls->mu);
-        j.dev = ls->buf;
-        j.s = PnSeriesIn{nullptr, PANACHE_F64 | PANACHE_DEVICE, ls->len, ls->m_min, ls->m_max, ls->k, ls->excl};
+        n = panache_stream_length(ls->h);
+        if (n == 0) return PANACHE_ESTATE;
+        std::vector<panache_motif> out((size_t)ls->k * (size_t)(ls->m_max - ls->m_min + 1));
+        int64_t got = 0;
+        r.rc = panache_stream_topk(ls->h, out.data(), (int64_t)out.size(), &got);
+        if (r.rc == PANACHE_OK) r.motifs.assign(out.begin(), out.begin() + got);
     }
-    if (!j.dev) return PANACHE_ESTATE;
-    return enqueue(sv, std::move(j), ticket);
+    const double t = now_ms();
+    r.latency_ms = t - t0;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        *ticket = sv->next_ticket++;
+        if (!sv->submitted) sv->t_first = t0;
+        ++sv->submitted;
+        if (r.rc == PANACHE_OK) {
+            ++sv->completed;
+            sv->wl += (uint64_t)windows_lengths(PnSeriesIn{nullptr, 0, n, ls->m_min, ls->m_max, ls->k, ls->excl});
+            sv->latencies.push_back(r.latency_ms);
+        } else {
+            ++sv->failed;
+        }
+        sv->t_last = t;
+        sv->done[*ticket] = std::move(r);
+    }
+    sv->cv_done.notify_all();
+    return PANACHE_OK;
+}
+
+int panache_server_stream_close(panache_server *sv, uint64_t stream_id) {
+    if (!sv) return PANACHE_EINVAL;
+    std::unique_ptr<LiveStream> ls;
+    {
+        std::lock_guard<std::mutex> lk(sv->streams_mu);
+        auto it = sv->streams.find(stream_id);
+        if (it == sv->streams.end()) return PANACHE_EINVAL;
+        ls = std::move(it->second);
+        sv->streams.erase(it);
+    }
+    {
+        std::lock_guard<std::mutex> lk(ls->mu);     // no append or snapshot of this stream in flight
+    }
+    cudaSetDevice(sv->device);
+    const uint64_t r = ls->reserved;
+    ls.reset();
+    std::lock_guard<std::mutex> g(sv->mu);
+    sv->in_use -= r;
+    return PANACHE_OK;
 }
 
 int panache_server_get_stats(panache_server *sv, panache_server_stats *out) {

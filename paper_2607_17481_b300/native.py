@@ -21,14 +21,16 @@ PLAIN_FP64, MIXED = 0, 1
 TOPK_GLOBAL, TOPK_PER_LENGTH = 0, 1
 FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING, FLAG_INDEX_ONLY = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_FP64_ANCHORS = 0x20
+FLAG_GRAPH = 0x40
 
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
-            "panache_stream_length", "panache_stream_close", "panache_last_stats", "panache_profile_rows",
+            "panache_stream_length", "panache_stream_close", "panache_stream_checkpoint", "panache_last_stats",
+            "panache_profile_rows",
             "panache_anchor_state", "panache_projections", "panache_strerror", "panache_topk_row_noalloc",
             "panache_server_create", "panache_server_destroy", "panache_server_submit", "panache_server_wait",
             "panache_server_stream_open", "panache_server_append", "panache_server_stream_topk",
-            "panache_server_get_stats")
+            "panache_server_stream_close", "panache_server_get_stats")
 
 
 class Config(ctypes.Structure):
@@ -97,6 +99,7 @@ def lib():
         L.panache_stream_length.argtypes = [vp]
         L.panache_stream_length.restype = i64
         L.panache_stream_close.argtypes = [vp]
+        L.panache_stream_checkpoint.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
         L.panache_stream_close.restype = None
         L.panache_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.panache_profile_rows.argtypes = [vp, i32, vp, i64]
@@ -113,6 +116,7 @@ def lib():
         L.panache_server_stream_open.argtypes = [vp, i32, i32, i32, i32, u64p]
         L.panache_server_append.argtypes = [vp, ctypes.c_uint64, vp, i32, i64]
         L.panache_server_stream_topk.argtypes = [vp, ctypes.c_uint64, u64p]
+        L.panache_server_stream_close.argtypes = [vp, ctypes.c_uint64]
         L.panache_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         L.panache_strerror.argtypes = [ctypes.c_int]
         L.panache_strerror.restype = ctypes.c_char_p
@@ -250,7 +254,7 @@ class Context:
 
 
 class Stream:
-    """A live series: appends of any size, top-k on request."""
+    """A live series with its index resident on the device: appends of any size, top-k on request."""
 
     def __init__(self, ctx: Context, m_min: int, m_max: int, k: int, excl: int):
         self.ctx = ctx
@@ -265,6 +269,15 @@ class Stream:
 
     def __len__(self):
         return int(lib().panache_stream_length(self._h))
+
+    def checkpoint(self) -> np.ndarray:
+        """The stream's samples (FP64): appending them to a fresh stream resumes it."""
+        n = len(self)
+        out = np.zeros(max(1, n), dtype=np.float64)
+        ln = ctypes.c_int64()
+        _check(lib().panache_stream_checkpoint(self._h, out.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(ln)),
+               "stream_checkpoint")
+        return out[:ln.value]
 
     def topk(self) -> np.ndarray:
         cap = self.k * self.L
@@ -336,6 +349,10 @@ class Server:
         _check(lib().panache_server_stream_topk(self._h, sid, ctypes.byref(t)), "stream_topk")
         self._caps[t.value] = self._caps.get(("s", sid), 4096)
         return t.value
+
+    def stream_close(self, sid: int):
+        _check(lib().panache_server_stream_close(self._h, sid), "stream_close")
+        self._caps.pop(("s", sid), None)
 
     def stats(self) -> dict:
         s = ServerStats()

@@ -256,3 +256,20 @@ def test_autotune_picks_a_valid_chunk(pn):
     tested = sorted(r["drift"], reverse=True)
     assert all(r["drift"][c] > 1e-5 for c in tested if c > r["chunk"])
     assert r["grid_mult"] in (4, 8)
+
+
+def test_graph_replay_equals_eager(pn, small):
+    """Requests of one shape replay a captured graph of the index and search
+    steps; each replay reads the new samples and matches the eager path."""
+    s = small
+    eager = pn.Context(topk_mode=1)
+    graph = pn.Context(topk_mode=1, flags=pn.FLAG_GRAPH)
+    rng = np.random.default_rng(21)
+    x2 = np.cumsum(rng.standard_normal(s.x.shape[0]))
+    x3 = np.cumsum(rng.standard_normal(5000))
+    for x in (s.x, x2, s.x, x3, x2[:5000], torch.from_numpy(x2).cuda()):
+        n = x.shape[0]
+        want = eager.pmp(x, s.m_min, s.m_max, s.k, s.excl)
+        got = graph.pmp(x, s.m_min, s.m_max, s.k, s.excl)
+        assert np.array_equal(got, want), n
+    assert graph.stats()["kernel_launches"] > 0
