@@ -366,6 +366,9 @@ def main():
     ap.add_argument("--batched-loop", type=int, default=64,
                     help="series of the same batch timed one pmp call at a time (0: skip)")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
+    ap.add_argument("--fast-steps", type=int, default=1,
+                    help="timed steps of the paper's fastest settings (s=6, alpha=4, one completion round; "
+                         "K=4, s=8), 0: skip")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -389,8 +392,8 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def make_ctx(precision):
-        ctx = pn.Context(precision=precision, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_TIMING)
+    def make_ctx(precision, **over):
+        ctx = pn.Context(precision=precision, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_TIMING, **over)
         ctx.set_stream(stream.cuda_stream)
         return ctx
 
@@ -438,6 +441,18 @@ def main():
         plain = {"value": W * world / (statistics.mean(pms) / 1e3), "ms_per_step": statistics.mean(pms),
                  "same_motifs": bool(np.array_equal(pmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                  "step_ms": pstats[-1]["step_ms"]}
+    fast = None
+    if args.fast_steps > 0:
+        fast = {}
+        for name, over in (("s6_alpha4_rounds1", dict(stride=6, alpha=4, rounds=1)), ("K4_s8", dict(K=4, stride=8))):
+            fctx = make_ctx(args.precision, **over)
+            fms, fst, fmot = timed(fctx, args.fast_steps, 1, x_dev)
+            ref_cells = {(int(r["m"]), int(r["i"]), int(r["j"])) for r in motifs}
+            got_cells = {(int(r["m"]), int(r["i"]), int(r["j"])) for r in fmot}
+            fast[name] = {"value": W * world / (statistics.mean(fms) / 1e3), "ms_per_step": statistics.mean(fms),
+                          "same_motifs": bool(np.array_equal(fmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
+                          "recall_vs_default": len(ref_cells & got_cells) / max(1, len(ref_cells)),
+                          "config": over}
     batched = run_batched(pn, stream, args.batched, args.batched_loop) if args.batched > 0 else None
     served = run_served(pn, args) if args.served_seconds > 0 and rank == 0 else None
     if rank != 0:
@@ -459,6 +474,7 @@ def main():
         "roofline": roofline(stats, peaks, psrc, measured_traffic(stats[-1]["queries"])),
         "clocks": clocks,
         "plain_fp64": plain,
+        "fast_settings": fast,
         "batched": batched,
         "served": served,
         "step_ms": stats[-1]["step_ms"],
