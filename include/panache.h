@@ -101,7 +101,7 @@ typedef struct {
     uint32_t d0;          /* probe reference depth */
     uint32_t probe_cap;   /* cap on Hamming-1 probes, 1..8 */
     uint32_t sieve_w;     /* sieve width w */
-    uint32_t dm, dp;      /* completion radii */
+    uint32_t dm, dp;      /* completion radii in length and position (each <= 16) */
     uint32_t rounds;      /* completion rounds P_max */
     uint32_t precision;   /* PANACHE_PLAIN_FP64 or PANACHE_MIXED */
     uint32_t topk_mode;   /* PANACHE_TOPK_GLOBAL or PANACHE_TOPK_PER_LENGTH */

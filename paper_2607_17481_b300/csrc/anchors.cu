@@ -215,7 +215,7 @@ cudaError_t launch_anchor_tc(const PnView &v, const int32_t *tile_anchor, const 
                              cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     const size_t sm = anchor_tc_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_anchor_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = pn_allow_smem(k_anchor_tc, sm);
     if (e != cudaSuccess) return e;
     k_anchor_tc<<<ntiles, AT_THREADS, sm, st>>>(v, tile_anchor, tile_row0);
     return cudaGetLastError();

@@ -209,7 +209,7 @@ int check_config(const panache_config &c) {
     if ((int)(c.gamma * c.alpha) > pn::search_max_budget() || c.alpha > (1u << 20)) return PANACHE_EINVAL;
     if (c.probe_cap < 1 || c.probe_cap > 8 || c.precision > 1 || c.topk_mode > 1) return PANACHE_EINVAL;
     if (c.chunk < 16 || c.chunk > 4096 || (c.chunk & (c.chunk - 1))) return PANACHE_EINVAL;
-    if (c.grid_mult > 64) return PANACHE_EINVAL;
+    if (c.grid_mult > 64 || c.dm > 16 || c.dp > 16) return PANACHE_EINVAL;
     if (!(c.lambda > 0.0 && c.lambda < 1.0) || !(c.eps0 >= 0.0)) return PANACHE_EINVAL;
     return PANACHE_OK;
 }
@@ -279,9 +279,12 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R,
                 R.total_buckets += (int64_t)1 << d;
                 R.lev.push_back(L);
             }
-            for (int64_t b = 0; b < A.nchunk; b += 128) {
+            const int64_t nch_now = (A.nw + C - 1) / C;
+            for (int64_t b = 0; b < nch_now; b += PN_FT_CHUNKS) {
                 R.blk_anchor.push_back((int32_t)R.anc.size());
                 R.blk_chunk0.push_back((int32_t)b);
+            }
+            for (int64_t b = 0; b < nch_now; b += 128) {
                 R.tile_anchor.push_back((int32_t)R.anc.size());
                 R.tile_row0.push_back((int32_t)b);
             }
@@ -674,6 +677,7 @@ int index_and_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const PnCo
     PN_TRY(tm.mark(1));
     PN_CU(pn::launch_runlen(v, R.total_samples, st));
     PN_CU(pn::launch_moments(v, R.total_samples, R.sq, st));
+    PN_CU(pn::launch_moment_table(v, R.total_windows, st));
     PN_TRY(tm.mark(2));
     if (R.tca) {
         PN_CU(pn::launch_anchor_tc(v, R.d_tile_anchor, R.d_tile_row0, (int32_t)R.tile_anchor.size(), st));
@@ -685,7 +689,7 @@ int index_and_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const PnCo
     PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
     PN_CU(pn::launch_query_order(v, R.total_windows, R.total_buckets, st));
     PN_TRY(tm.mark(4));
-    ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3;
+    ctx->launches += 3 + 5 + 1 + 5 + 2 + 4 * 3;
     if (!search) return PANACHE_OK;
     PN_CU(pn::launch_search(v, R.total_windows, ctx->sm_count * (int)c.grid_mult, R.a_max, st));
     ctx->launches += 1;
@@ -884,11 +888,12 @@ int stream_advance(panache_stream *h) {
     PnView v = make_view(ctx, R);
     PN_CU(pn::launch_runlen(v, n, st));
     PN_CU(pn::launch_moments(v, n, R.sq, st));
+    PN_CU(pn::launch_moment_table(v, R.total_windows, st));
     std::vector<int32_t> ba, bc, ta, tc;
     for (size_t ai = 0; ai < R.anc.size(); ++ai) {
         const PnAnchor &A = R.anc[ai];
         const int64_t c_lo = h->nw_feat[ai] / C, c_hi = (A.nw + C - 1) / C;
-        for (int64_t b = c_lo; b < c_hi; b += 128) {
+        for (int64_t b = c_lo; b < c_hi; b += PN_FT_CHUNKS) {
             ba.push_back((int32_t)ai);
             bc.push_back((int32_t)b);
         }
@@ -917,7 +922,7 @@ int stream_advance(panache_stream *h) {
     for (size_t ai = 0; ai < R.anc.size(); ++ai) h->nw_feat[ai] = R.anc[ai].nw;
     PN_CU(pn::launch_ranks(v, R.total_windows, st));
     PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
-    ctx->launches += 2 + 5 + 1 + 5 + 2 + 4 * 3;
+    ctx->launches += 3 + 5 + 1 + 5 + 2 + 4 * 3;
     const int beta = (c.beta > 0 && (int)c.beta < h->excl) ? (int)c.beta : h->excl;
     const int64_t nb = n / beta * beta;                // samples of complete batches
     std::vector<int64_t> q_ready(R.anc.size());

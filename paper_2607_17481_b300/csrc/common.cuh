@@ -3,6 +3,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Opts a kernel in to dynamic shared memory up to the device's per-block
+// limit (less the kernel's static shared memory), and checks that `need`
+// fits.  The value set is the same for every call, so host threads that
+// launch the same kernel concurrently with different sizes never see
+// another thread's smaller setting.
+template <class K>
+inline cudaError_t pn_allow_smem(K kernel, size_t need) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(kernel));
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if ((long long)need > (long long)lim) return cudaErrorInvalidValue;
+    if (fa.maxDynamicSharedSizeBytes == lim) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
 #define PN_WARP 32
 #define PN_FEAT 32            // floats per feature row: 2(K-1) <= 30 used, padded to 32 (128 B)
 #define PN_MAXB 24            // signature bits

@@ -197,19 +197,38 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
 // Local completion (Sec. 3.6): for each seed (m0, i0, j0) every admissible
 // (m, i, j) with |m-m0| <= dm, |i-i0| <= dp, |j-j0| <= dp, |i-j| >= excl is
 // evaluated exactly; both cells take the distance, and the partner written
-// is the hint later rounds re-cut from.  One block (8 warps) per seed.
+// is the hint later rounds re-cut from.  One block (8 warps) per seed.  The
+// box's (2dm+1)(2dp+1) windows on each side are normalised once into shared
+// memory (FP64 moments), then every triple reads its two windows from there.
 // ---------------------------------------------------------------------------
 __global__ void k_complete(PnView v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved) {
+    extern __shared__ __align__(16) unsigned char csm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
+    const int side = 2 * dp + 1;
+    const int nwin = (2 * dm + 1) * side;
+    PnWin *win_i = reinterpret_cast<PnWin *>(csm);
+    PnWin *win_j = win_i + nwin;
     unsigned long long n_ex = 0;
     int imp = 0;
     for (int sd = blockIdx.x; sd < nseeds; sd += gridDim.x) {
         const PnSeed sdv = seeds[sd];
         const int s = sdv.series;
         const PnSeries &S = v.series[s];
-        const int side = 2 * dp + 1;
         const int ntrip = (2 * dm + 1) * side * side;
+        __syncthreads();                                   // the previous seed's windows are no longer read
+        for (int t = threadIdx.x; t < 2 * nwin; t += blockDim.x) {
+            const int k = t < nwin ? t : t - nwin;
+            const int m = sdv.m + k / side - dm;
+            const int64_t p = (t < nwin ? sdv.i : sdv.j) + k % side - dp;
+            PnWin w;
+            w.mu = 0.0;
+            w.inv = 0.0;
+            w.mu_hi = w.mu_lo = w.invf = 0.0f;
+            if (m >= S.m_min && m <= S.m_max && p >= 0 && p <= S.n - m) w = pn_window(v, s, p, m);
+            (t < nwin ? win_i : win_j)[k] = w;
+        }
+        __syncthreads();
         for (int t = warp; t < ntrip; t += nwarps) {
             const int tm = t / (side * side);
             const int rem = t - tm * side * side;
@@ -220,8 +239,8 @@ __global__ void k_complete(PnView v, const PnSeed *seeds, int32_t nseeds, int dm
             if (i < 0 || j < 0 || i > S.n - m || j > S.n - m) continue;
             if (llabs(i - j) < S.excl) continue;
             if (v.runlen[S.x_off + i] >= m || v.runlen[S.x_off + j] >= m) continue;
-            const PnWin wi = pn_window(v, s, i, m);
-            const PnWin wj = pn_window(v, s, j, m);
+            const PnWin wi = win_i[tm * side + rem / side];
+            const PnWin wj = win_j[tm * side + rem % side];
             const double dd = pn_dist_warp(v, S.x_off, m, i, wi, j, wj, lane);
             n_ex += 1;
             if (lane == 0 && dd < __longlong_as_double(0x7ff0000000000000ll)) {
@@ -443,7 +462,7 @@ template <class Z>
 cudaError_t sieve_t(const PnView &v, const PnClass *cls, int64_t nmem, const uint32_t *keys, const uint32_t *vals,
                     int w, int exhaustive, int zcap, int64_t blocks, cudaStream_t st) {
     const size_t sm = sizeof(typename Z::T) * zcap * 8;
-    cudaError_t e = cudaFuncSetAttribute(k_sieve_pairs<Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = pn_allow_smem(k_sieve_pairs<Z>, sm);
     if (e != cudaSuccess) return e;
     k_sieve_pairs<Z><<<(unsigned)blocks, 256, sm, st>>>(v, cls, nmem, keys, vals, w, exhaustive, zcap);
     return cudaGetLastError();
@@ -521,7 +540,10 @@ cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds
                             int grid_blocks, cudaStream_t st) {
     if (nseeds <= 0) return cudaSuccess;
     int g = nseeds < grid_blocks ? nseeds : grid_blocks;
-    k_complete<<<g, 256, 0, st>>>(v, seeds, nseeds, dm, dp, improved);
+    const size_t sm = sizeof(PnWin) * 2 * (size_t)(2 * dm + 1) * (2 * dp + 1);
+    cudaError_t e = pn_allow_smem(k_complete, sm);
+    if (e != cudaSuccess) return e;
+    k_complete<<<g, 256, sm, st>>>(v, seeds, nseeds, dm, dp, improved);
     return cudaGetLastError();
 }
 
@@ -565,7 +587,7 @@ cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ng
         int npow2 = 1;
         while (npow2 < cap) npow2 <<= 1;
         size_t sm = sizeof(PnPoolEntry) * npow2 + sizeof(int32_t) * (kmax + 1) + sizeof(int64_t) * kmax + 16;
-        e = cudaFuncSetAttribute(k_sel_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = pn_allow_smem(k_sel_greedy, sm);
         if (e == cudaSuccess) {
             k_sel_greedy<<<ngrp, 1024, sm, st>>>(v, grp_dev, pool, pcnt, cap, npow2, out, out_cnt, kmax);
             e = cudaGetLastError();

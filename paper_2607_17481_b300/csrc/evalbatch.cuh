@@ -22,6 +22,8 @@ __device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T 
     const auto *x0 = Z::samples(v, x_off + c0), *x1 = Z::samples(v, x_off + c1);
     const auto *x2 = Z::samples(v, x_off + c2), *x3 = Z::samples(v, x_off + c3);
     ZT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    // two iterations in flight: eight independent sample loads per lane
+#pragma unroll 2
     for (int r = lane; r < a; r += 32) {
         const ZT zr = zq[r];
         const ZT d0 = zr - Z::z(m0, x0[r]);

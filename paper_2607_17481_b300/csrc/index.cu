@@ -49,188 +49,176 @@ __global__ void k_moment_place(PnView v, int64_t total, const double2 *incl, dou
 }
 
 // ---------------------------------------------------------------------------
+// Window moments table (Sec. 3.2: mu = S/m, sigma^2 = Q/m - mu^2 from the
+// FP64 prefix sums): per window (1/sigma, -mu/sigma), FP32 in the mixed form
+// and FP64 in the plain form; 1/sigma = 0 marks a constant or degenerate
+// window.  One thread per window.
+// ---------------------------------------------------------------------------
+__global__ void k_moment_table(PnView v, int64_t total) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= total) return;
+    const int ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
+    const PnAnchor &A = v.anchors[ai];
+    const int64_t q = w - A.win_off;
+    if (q >= A.nw) return;
+    const PnSeries &S = v.series[A.series];
+    const int a = A.a;
+    const double2 *sqp = v.sq + S.x_off + A.series;
+    const double2 pa = sqp[q], pb = sqp[q + a];
+    const double inv_a = 1.0 / (double)a;
+    const double ms = (pb.x - pa.x) * inv_a;
+    const double var = (pb.y - pa.y) * inv_a - ms * ms;
+    const double mu = ms + v.shift[A.series];
+    const bool ok = v.runlen[S.x_off + q] < a && var > 0.0;
+    if (v.precision == 0) {
+        const double inv = ok ? 1.0 / sqrt(var) : 0.0;
+        v.wmd[w] = make_double2(inv, -mu * inv);
+    } else {
+        const float invf = ok ? rsqrtf((float)var) : 0.0f;
+        // z = fma(x, 1/sigma, -mu/sigma): one rounding, no cancellation for |mu| >> sigma
+        v.wmf[w] = make_float2(invf, (float)(-mu * (double)invf));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Features and signatures (Sec. 3.2 online update, Sec. 3.4 SimHash key).
 //
-// One thread advances one chunk of C consecutive windows of one anchor.  The
-// chunk starts from a direct FP64 DFT of its first window (the periodic
-// recompute of Sec. 3.2, here every C slides), then slides C-1 times:
+// One warp advances one chunk of C consecutive windows of one anchor: lane k
+// (k < K') carries bin k+1 of the spectral state.  The chunk starts from a
+// direct DFT of its first window (the periodic recompute of Sec. 3.2, here
+// every C slides: tensor-core anchors in the mixed form, an FP64 direct DFT
+// otherwise), then slides C-1 times,
 //   X_{q+1,k} = e^{+2 pi i k/a} (X_{q,k} - t_q + t_{q+a}),
-// in FP64 (plain form) or FP32 (mixed form).  Each window's bins 1..K' are
-// scaled by 1/sigma (Lemma 1) into an FP32 row, and its B-bit key is
-// bit l = 1{<g_{a,l}, F> >= 0}.  Rows of the 32 chunks of a warp are staged
-// in shared memory and written as one contiguous 4 KB run (row layout
-// pn_row()).
+// in FP64 (plain form) or FP32 with a float-float rotation factor (mixed).
+// Per window the bins are scaled by 1/sigma (Lemma 1) into an FP32 row
+// written by the whole warp as one 128-byte store, and lane l < B computes
+// <g_{a,l}, F>: the B-bit key is the warp's ballot of the signs.  Every lane
+// works on every window, so the per-window latency is a few dozen warp
+// instructions rather than a thread's whole projection loop.
 // ---------------------------------------------------------------------------
-constexpr int FT_THREADS = 128;
-constexpr int FT_WARPS = FT_THREADS / 32;
+constexpr int FT_WARPS = PN_FT_CHUNKS;
+constexpr int FT_THREADS = FT_WARPS * 32;
 
 template <typename ST>
 __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t *blk_anchor,
                                                          const int32_t *blk_chunk0) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) float frow[FT_WARPS][PN_FEAT];
     const int ai = blk_anchor[blockIdx.x];
     const PnAnchor A = v.anchors[ai];
     const PnSeries S = v.series[A.series];
     const int a = A.a, kp = A.kp, B = v.B, C = v.C;
     const int dims = 2 * (v.K - 1);
     double2 *tw = reinterpret_cast<double2 *>(smem);                 // (cos, sin)(2 pi t / a)
-    float *gs = reinterpret_cast<float *>(tw + a);                   // B rows of PN_FEAT
-    float *stage = gs + B * PN_FEAT;                                 // [warps][32][33]
     for (int t = threadIdx.x; t < a; t += blockDim.x) {
         double sn, cs;
         sincospi(2.0 * (double)t / (double)a, &sn, &cs);
         tw[t] = make_double2(cs, sn);
     }
-    const float *gsrc = v.g + (int64_t)ai * (B + 1) * PN_FEAT;
-    for (int t = threadIdx.x; t < B * PN_FEAT; t += blockDim.x) gs[t] = gsrc[t];
     __syncthreads();
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t c = (int64_t)blk_chunk0[blockIdx.x] + threadIdx.x;
-    const bool chunk_ok = c < A.nchunk;
+    const int64_t c = (int64_t)blk_chunk0[blockIdx.x] + warp;
     const int64_t q0 = c * C;
-    const int64_t qend = chunk_ok ? min(A.nw, q0 + C) : q0;
+    if (c >= A.nchunk || q0 >= A.nw) return;                         // warp-uniform
+    const int64_t qend = min(A.nw, q0 + C);
     const double *xs = v.x + S.x_off;
     const double shift = v.shift[A.series];
     const int32_t *rl = v.runlen + S.x_off;
-    const double2 *sqp = v.sq + S.x_off + A.series;
-    const double inv_a = 1.0 / (double)a;
+    float *Fa = v.F + A.row_off * PN_FEAT;
+    float *fr = frow[warp];
+    const bool bin = lane < kp;
 
-    ST Xr[PN_MAXK - 1], Xi[PN_MAXK - 1];
+    // projection row of lane l (l < B), in registers
+    float g[PN_FEAT - 2];
+    {
+        const float *gsrc = v.g + ((int64_t)ai * (B + 1) + (lane < B ? lane : 0)) * PN_FEAT;
 #pragma unroll
-    for (int k = 0; k < PN_MAXK - 1; ++k) {
-        Xr[k] = 0;
-        Xi[k] = 0;
+        for (int t = 0; t < PN_FEAT - 2; ++t) g[t] = gsrc[t];
     }
+    // chunk anchor of bin lane+1
+    ST Xr = 0, Xi = 0;
+    bool have = false;
     if constexpr (sizeof(ST) == 4) {
-        if (q0 < qend && v.anc) {      // mixed form: chunk anchor from the tensor-core kernel
+        if (v.anc) {
             const float *an = v.anc + (A.chunk_off + c) * PN_FEAT;
-#pragma unroll
-            for (int k = 0; k < PN_MAXK - 1; ++k) {
-                Xr[k] = an[2 * k];
-                Xi[k] = an[2 * k + 1];
+            if (bin) {
+                Xr = an[2 * lane];
+                Xi = an[2 * lane + 1];
             }
+            have = true;
         }
     }
-    if (q0 < qend && !(sizeof(ST) == 4 && v.anc)) {
-        double dr[PN_MAXK - 1], di[PN_MAXK - 1];
-        int idx[PN_MAXK - 1];
-#pragma unroll
-        for (int k = 0; k < PN_MAXK - 1; ++k) {
-            dr[k] = 0.0;
-            di[k] = 0.0;
-            idx[k] = 0;
-        }
+    if (!have && bin) {
+        double dr = 0.0, di = 0.0;
+        int idx = 0;
         for (int r = 0; r < a; ++r) {
             const double t = xs[q0 + r] - shift;
-#pragma unroll
-            for (int k = 0; k < PN_MAXK - 1; ++k) {
-                if (k < kp) {
-                    const double2 w = tw[idx[k]];
-                    dr[k] = fma(t, w.x, dr[k]);
-                    di[k] = fma(-t, w.y, di[k]);
-                    idx[k] += k + 1;
-                    if (idx[k] >= a) idx[k] -= a;
-                }
-            }
+            const double2 w = tw[idx];
+            dr = fma(t, w.x, dr);
+            di = fma(-t, w.y, di);
+            idx += lane + 1;
+            if (idx >= a) idx -= a;
         }
-#pragma unroll
-        for (int k = 0; k < PN_MAXK - 1; ++k) {
-            Xr[k] = (ST)dr[k];
-            Xi[k] = (ST)di[k];
-        }
+        Xr = (ST)dr;
+        Xi = (ST)di;
     }
+    // rotation factor of bin lane+1
+    const double2 wk = tw[bin ? lane + 1 : 0];
+    const float ch = (float)wk.x, sh = (float)wk.y;
+    const float cl = (float)(wk.x - (double)ch), sl = (float)(wk.y - (double)sh);
 
-    float *st_w = stage + warp * 32 * 33;
-    const int64_t warp_c0 = (int64_t)blk_chunk0[blockIdx.x] + warp * 32;
-    float *Fa = v.F + A.row_off * PN_FEAT;
-    for (int s = 0; s < C; ++s) {
-        const int64_t q = q0 + s;
-        const bool act = q < qend;
-        float f[PN_FEAT];
-#pragma unroll
-        for (int t = 0; t < PN_FEAT; ++t) f[t] = 0.0f;
-        if (act) {
-            // moments from the FP64 prefix sums; the mixed form normalises in FP32
-            const double2 pa = sqp[q], pb = sqp[q + a];
-            const double ms = (pb.x - pa.x) * inv_a;
-            const double var = (pb.y - pa.y) * inv_a - ms * ms;
-            const double mu = ms + shift;
-            const bool nonconst = rl[q] < a;
-            const bool ok = nonconst && var > 0.0;
-            if (v.precision == 0) {
-                const double inv = ok ? 1.0 / sqrt(var) : 0.0;
-                v.wmd[A.win_off + q] = make_double2(inv, -mu * inv);
-                if (ok) {
-#pragma unroll
-                    for (int k = 0; k < PN_MAXK - 1; ++k) {
-                        if (k < kp) {
-                            f[2 * k] = (float)((double)Xr[k] * inv);
-                            f[2 * k + 1] = (float)((double)Xi[k] * inv);
-                        }
-                    }
-                }
-            } else {
-                const float invf = ok ? rsqrtf((float)var) : 0.0f;
-                // z = fma(x, 1/sigma, -mu/sigma): one rounding, no cancellation for |mu| >> sigma
-                v.wmf[A.win_off + q] = make_float2(invf, (float)(-mu * (double)invf));
-                if (ok) {
-#pragma unroll
-                    for (int k = 0; k < PN_MAXK - 1; ++k) {
-                        if (k < kp) {
-                            f[2 * k] = (float)Xr[k] * invf;
-                            f[2 * k + 1] = (float)Xi[k] * invf;
-                        }
-                    }
-                }
+    for (int64_t q = q0; q < qend; ++q) {
+        const bool nonconst = rl[q] < a;
+        float f_re = 0.0f, f_im = 0.0f;
+        if (v.precision == 0) {
+            const double inv = v.wmd[A.win_off + q].x;
+            if (bin && inv != 0.0) {
+                f_re = (float)((double)Xr * inv);
+                f_im = (float)((double)Xi * inv);
             }
-            uint32_t key = 0;
-            if (nonconst) {
-                for (int l = 0; l < B; ++l) {
-                    float mg = pn_margin(gs + l * PN_FEAT, f, dims);
-                    key |= (mg >= 0.0f ? 1u : 0u) << (B - 1 - l);
-                }
-            }
-            v.sig[A.win_off + q] = key;
-        }
-        // stage the 32 rows of this warp and write them as one contiguous run
-#pragma unroll
-        for (int t = 0; t < PN_FEAT; ++t) st_w[lane * 33 + t] = f[t];
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int r = 4 * j + (lane >> 3);
-            const int f4 = lane & 7;
-            const int64_t cr = warp_c0 + r;
-            if (cr < A.nchunk) {
-                float4 o;
-                o.x = st_w[r * 33 + 4 * f4 + 0];
-                o.y = st_w[r * 33 + 4 * f4 + 1];
-                o.z = st_w[r * 33 + 4 * f4 + 2];
-                o.w = st_w[r * 33 + 4 * f4 + 3];
-                reinterpret_cast<float4 *>(Fa + ((int64_t)s * A.nchunk + cr) * PN_FEAT)[f4] = o;
+        } else {
+            const float invf = v.wmf[A.win_off + q].x;
+            if (bin && invf != 0.0f) {
+                f_re = (float)Xr * invf;
+                f_im = (float)Xi * invf;
             }
         }
+        if (lane < PN_FEAT / 2) {
+            fr[2 * lane] = f_re;
+            fr[2 * lane + 1] = f_im;
+        }
         __syncwarp();
-        if (act && q + 1 < qend) {
+        Fa[(int64_t)pn_row(q, C, A.nchunk) * PN_FEAT + lane] = fr[lane];
+        // <g_l, F> in the fixed FMA order of pn_margin, then the key by ballot
+        float mg = 0.0f;
+        const float4 *f4 = reinterpret_cast<const float4 *>(fr);
+#pragma unroll
+        for (int t4 = 0; t4 < (PN_FEAT - 2 + 3) / 4; ++t4) {
+            const float4 f = f4[t4];
+            const float fv[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = 4 * t4 + u;
+                if (t < PN_FEAT - 2 && t < dims) mg = fmaf(g[t], fv[u], mg);
+            }
+        }
+        const uint32_t bits = __ballot_sync(0xffffffffu, lane < B && mg >= 0.0f);
+        if (lane == 0) v.sig[A.win_off + q] = nonconst ? (__brev(bits) >> (32 - B)) : 0u;
+        __syncwarp();
+        if (q + 1 < qend) {
             const ST delta = (ST)(xs[q + a] - xs[q]);
-#pragma unroll
-            for (int k = 0; k < PN_MAXK - 1; ++k) {
-                if (k < kp) {
-                    const double2 w = tw[k + 1];
-                    const ST re = Xr[k] + delta;
-                    const ST im = Xi[k];
-                    if constexpr (sizeof(ST) == 8) {
-                        Xr[k] = re * (ST)w.x - im * (ST)w.y;
-                        Xi[k] = re * (ST)w.y + im * (ST)w.x;
-                    } else {
-                        // FP32 state: the rotation factor as a float-float pair, so its
-                        // rounding does not compound into a phase drift over the chunk
-                        const float ch = (float)w.x, sh = (float)w.y;
-                        const float cl = (float)(w.x - (double)ch), sl = (float)(w.y - (double)sh);
-                        Xr[k] = fmaf(re, ch, fmaf(-im, sh, fmaf(re, cl, -im * sl)));
-                        Xi[k] = fmaf(re, sh, fmaf(im, ch, fmaf(re, sl, im * cl)));
-                    }
+            if (bin) {
+                const ST re = Xr + delta;
+                const ST im = Xi;
+                if constexpr (sizeof(ST) == 8) {
+                    Xr = re * (ST)wk.x - im * (ST)wk.y;
+                    Xi = re * (ST)wk.y + im * (ST)wk.x;
+                } else {
+                    // FP32 state: the rotation factor as a float-float pair, so its
+                    // rounding does not compound into a phase drift over the chunk
+                    Xr = fmaf(re, ch, fmaf(-im, sh, fmaf(re, cl, -im * sl)));
+                    Xi = fmaf(re, sh, fmaf(im, ch, fmaf(re, sl, im * cl)));
                 }
             }
         }
@@ -352,7 +340,14 @@ cudaError_t launch_moments(const PnView &v, int64_t total, double2 *sq_out, cuda
 }
 
 size_t features_smem(int a_max, int B) {
-    return sizeof(double2) * a_max + sizeof(float) * B * PN_FEAT + sizeof(float) * FT_WARPS * 32 * 33;
+    (void)B;
+    return sizeof(double2) * a_max;
+}
+
+cudaError_t launch_moment_table(const PnView &v, int64_t total_windows, cudaStream_t st) {
+    if (total_windows <= 0) return cudaSuccess;
+    k_moment_table<<<grid_for(total_windows, 256), 256, 0, st>>>(v, total_windows);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_features(const PnView &v, const int32_t *blk_anchor, const int32_t *blk_chunk0,
@@ -361,11 +356,11 @@ cudaError_t launch_features(const PnView &v, const int32_t *blk_anchor, const in
     size_t sm = features_smem(a_max, v.B);
     cudaError_t e;
     if (v.precision == 0) {
-        e = cudaFuncSetAttribute(k_features<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = pn_allow_smem(k_features<double>, sm);
         if (e != cudaSuccess) return e;
         k_features<double><<<nblocks, FT_THREADS, sm, st>>>(v, blk_anchor, blk_chunk0);
     } else {
-        e = cudaFuncSetAttribute(k_features<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        e = pn_allow_smem(k_features<float>, sm);
         if (e != cudaSuccess) return e;
         k_features<float><<<nblocks, FT_THREADS, sm, st>>>(v, blk_anchor, blk_chunk0);
     }

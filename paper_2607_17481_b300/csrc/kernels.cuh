@@ -52,6 +52,7 @@ struct PnView {
     unsigned long long *stats;
 };
 
+#define PN_FT_CHUNKS 4         // chunks (one warp each) per block of the feature kernel
 #define PN_ERR_TC_TIMEOUT 1   // a tensor-core anchor tile's bounded wait ran out
 
 enum PnStat {
@@ -111,6 +112,7 @@ namespace pn {
 cudaError_t launch_runlen(const PnView &v, int64_t total, cudaStream_t st);
 cudaError_t launch_moments(const PnView &v, int64_t total, double2 *sq_out, cudaStream_t st);
 size_t features_smem(int a_max, int B);
+cudaError_t launch_moment_table(const PnView &v, int64_t total_windows, cudaStream_t st);
 cudaError_t launch_features(const PnView &v, const int32_t *blk_anchor, const int32_t *blk_chunk0,
                             int32_t nblocks, int a_max, cudaStream_t st);
 cudaError_t launch_ranks(const PnView &v, int64_t total_windows, cudaStream_t st);

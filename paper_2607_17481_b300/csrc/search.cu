@@ -269,7 +269,7 @@ cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max,
     const int zcap = (a_max + 3) & ~3;
     const size_t sm = (sizeof(unsigned long long) + sizeof(uint32_t)) * (size_t)v.R * SR_WARPS +
                       sizeof(typename Z::T) * (size_t)zcap * SR_WARPS;
-    cudaError_t e = cudaFuncSetAttribute(k_search<Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = pn_allow_smem(k_search<Z>, sm);
     if (e != cudaSuccess) return e;
     int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
     unsigned g = (unsigned)(need < grid_blocks ? need : grid_blocks);
