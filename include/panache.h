@@ -236,6 +236,23 @@ int panache_profile_rows(const panache_ctx *ctx, int32_t series_index, uint64_t 
 int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *a_out,
                          float *features, uint32_t *keys, int64_t cap_windows);
 
+/* Spectral-width calibration (Sec. 3.2, "Spectral width selection"): the
+ * width K is fixed before insertion as the smallest K in [2, 16] with
+ *   E[(2/m^2) sum_{k<=K'(m)} |X^_k|^2] >= eta          (retained energy)
+ *   n E[(1 - theta_K/pi)^B] <= 2 gamma alpha           (accidental collisions)
+ * over sampled windows: up to 256 evenly spaced non-constant windows at each
+ * of m_min, (m_min+m_max)/2 and m_max; angles theta_K between the K-width
+ * features of two windows of one length, pairs whose full-width bound is
+ * below 0.1 sqrt(2m) (near-duplicates) left out; K = 16 when no width
+ * qualifies.  B, gamma and alpha come from the context's configuration; eta
+ * 0 means 0.85.  *K_out receives K; energy[0..14] and collision_prob[0..14]
+ * (either may be null) receive the two sample means E[...] for K = 2..16.
+ * The series is host or device memory (dtype as panache_pmp).  Use K in the
+ * configuration of the context that then runs the series.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+int panache_calibrate_width(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min,
+                            int32_t m_max, double eta, int32_t *K_out, double *energy, double *collision_prob);
+
 /* Writes the FP32 Gaussian projections g_{a,l} (l = 1..B+1, row-major
  * [B+1][32], dimensions >= 2(K-1) zero) that a context with configuration
  * cfg (null: defaults) draws for anchor length a (Sec. 3.4).  Host-only: no

@@ -14,9 +14,11 @@ Contents
   spectral  -- direct-DFT features, the Parseval bound, Philox-drawn SimHash
                projections and signatures, the depth rule, probe order and
                budget selection (Sec. 3.2, 3.4).
+  calibrate -- the spectral-width calibration: energy and accidental-
+               collision conditions on sampled windows (Sec. 3.2).
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, brute force on tiny inputs, invariants or published
 known-answer vectors; none is "parity unpinned".
 """
-from . import exact, spectral, topk  # noqa: F401
+from . import calibrate, exact, spectral, topk  # noqa: F401

@@ -1285,6 +1285,96 @@ int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t a
     return PANACHE_OK;
 }
 
+int panache_calibrate_width(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min,
+                            int32_t m_max, double eta, int32_t *K_out, double *energy, double *collisions) {
+    if (!ctx || !K_out) return PANACHE_EINVAL;
+    SeriesIn si{series, dtype, n, m_min, m_max, 1, 1};
+    PN_TRY(check_series(si));
+    if (eta == 0.0) eta = 0.85;
+    if (!(eta > 0.0 && eta <= 1.0)) return PANACHE_EINVAL;
+    const panache_config &c = ctx->cfg;
+    cudaStream_t st = ctx->st;
+    // sample: at m_min, the midpoint and m_max, up to 256 evenly spaced starts each
+    std::vector<int> lengths;
+    for (int m : {m_min, (m_min + m_max) / 2, m_max})
+        if (std::find(lengths.begin(), lengths.end(), m) == lengths.end()) lengths.push_back(m);
+    std::vector<PnCalWin> win;
+    std::vector<int> g_off, g_cnt, row_g, row_a;
+    for (size_t g = 0; g < lengths.size(); ++g) {
+        const int m = lengths[g];
+        const int64_t nw = n - m + 1;
+        g_off.push_back((int)win.size());
+        if (nw > 0) {
+            const int64_t S = std::min<int64_t>(256, nw);
+            int64_t last = -1;
+            for (int64_t t = 0; t < S; ++t) {
+                const int64_t s0 = S == 1 ? 0 : t * (nw - 1) / (S - 1);
+                if (s0 == last) continue;
+                last = s0;
+                win.push_back(PnCalWin{s0, m, (int32_t)g});
+            }
+        }
+        g_cnt.push_back((int)win.size() - g_off.back());
+        for (int a = 0; a + 1 < g_cnt.back(); ++a) {
+            row_g.push_back((int)g);
+            row_a.push_back(a);
+        }
+    }
+    // the series as FP64 on the device
+    const int dt = dtype & 0xFF;
+    const size_t es = dt == PANACHE_F32 ? 4 : 8;
+    void *stage = nullptr;
+    double *x = nullptr;
+    PnCalWin *dwin = nullptr;
+    int *dgo = nullptr, *dgc = nullptr, *drg = nullptr, *dra = nullptr;
+    double *dout = nullptr;
+    std::vector<double> hout(2 * (PN_MAXK - 1) + 1, 0.0);
+    int rc = PANACHE_OK;
+    do {
+        const void *src = series;
+        if (!(dtype & PANACHE_DEVICE) && n) {
+            if ((rc = from_cuda(cudaMallocAsync(&stage, (size_t)n * es, st)))) break;
+            if ((rc = from_cuda(cudaMemcpyAsync(stage, series, (size_t)n * es, cudaMemcpyHostToDevice, st)))) break;
+            src = stage;
+        }
+        if ((rc = from_cuda(cudaMallocAsync((void **)&x, sizeof(double) * std::max<int64_t>(1, n), st)))) break;
+        float2 *scratch = nullptr;
+        if ((rc = from_cuda(cudaMallocAsync((void **)&scratch, sizeof(float2) * std::max<int64_t>(1, n), st)))) break;
+        if (n) k_put<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, dtype, n, 0, x, scratch);
+        cudaFreeAsync(scratch, st);
+        if ((rc = upload_tmp(st, win, dwin))) break;
+        if ((rc = upload_tmp(st, g_off, dgo))) break;
+        if ((rc = upload_tmp(st, g_cnt, dgc))) break;
+        if ((rc = upload_tmp(st, row_g, drg))) break;
+        if ((rc = upload_tmp(st, row_a, dra))) break;
+        if ((rc = from_cuda(cudaMallocAsync((void **)&dout, sizeof(double) * hout.size(), st)))) break;
+        if ((rc = from_cuda(pn::launch_calibration(x, dwin, (int)win.size(), dgo, dgc, drg, dra, (int)row_g.size(),
+                                                   (int)c.B, dout, st))))
+            break;
+        if ((rc = from_cuda(cudaMemcpyAsync(hout.data(), dout, sizeof(double) * hout.size(), cudaMemcpyDeviceToHost,
+                                            st))))
+            break;
+        rc = from_cuda(cudaStreamSynchronize(st));
+    } while (false);
+    for (void *p : {(void *)stage, (void *)x, (void *)dwin, (void *)dgo, (void *)dgc, (void *)drg, (void *)dra,
+                    (void *)dout})
+        if (p) cudaFreeAsync(p, st);
+    PN_TRY(rc);
+    // the smallest width meeting both conditions, else the largest
+    const int nk = PN_MAXK - 1;
+    int K = PN_MAXK;
+    for (int t = 0; t < nk; ++t) {
+        if (hout[t] >= eta && (double)n * hout[nk + t] <= 2.0 * (double)c.gamma * (double)c.alpha) {
+            K = t + 2;
+            break;
+        }
+    }
+    *K_out = K;
+    if (energy) memcpy(energy, hout.data(), sizeof(double) * nk);
+    if (collisions) memcpy(collisions, hout.data() + nk, sizeof(double) * nk);
+    return PANACHE_OK;
+}
+
 int panache_projections(const panache_config *cfg, int32_t a, float *g, int64_t cap) {
     if (!g || a < 1) return PANACHE_EINVAL;
     panache_config c;

@@ -123,5 +123,9 @@ cudaError_t launch_anchor_tc(const PnView &v, const int32_t *tile_anchor, const 
 cudaError_t launch_query_order(const PnView &v, int64_t total_queries, int64_t total_buckets, cudaStream_t st,
                                const PnQRange *rng = nullptr, int32_t nrng = 0);
 int search_max_budget();
+// Spectral-width calibration statistics: out[0..14] energy means and
+// out[15..29] collision-probability means for K = 2..16, out[30] pairs.
+cudaError_t launch_calibration(const double *x, const PnCalWin *win, int nwin, const int *g_off, const int *g_cnt,
+                               const int *row_g, const int *row_a, int nrows, int B, double *out, cudaStream_t st);
 cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, int a_max, cudaStream_t st);
 }  // namespace pn

@@ -46,6 +46,13 @@ struct PnQRange {
     int32_t _pad;
 };
 
+// One sampled window of the spectral-width calibration.
+struct PnCalWin {
+    int64_t start;
+    int32_t m;
+    int32_t group;        // index of its length among the calibration lengths
+};
+
 struct PnLevel {
     int32_t anchor;       // owning anchor
     int32_t d;            // depth

@@ -27,7 +27,8 @@ EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "pana
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
             "panache_stream_length", "panache_stream_close", "panache_stream_checkpoint", "panache_last_stats",
             "panache_profile_rows",
-            "panache_anchor_state", "panache_projections", "panache_strerror", "panache_topk_row_noalloc",
+            "panache_anchor_state", "panache_projections", "panache_calibrate_width", "panache_strerror",
+            "panache_topk_row_noalloc",
             "panache_server_create", "panache_server_destroy", "panache_server_submit", "panache_server_wait",
             "panache_server_stream_open", "panache_server_append", "panache_server_stream_topk",
             "panache_server_stream_close", "panache_server_get_stats")
@@ -118,6 +119,8 @@ def lib():
         L.panache_server_stream_topk.argtypes = [vp, ctypes.c_uint64, u64p]
         L.panache_server_stream_close.argtypes = [vp, ctypes.c_uint64]
         L.panache_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.panache_calibrate_width.argtypes = [vp, vp, i32, i64, i32, i32, ctypes.c_double, ctypes.POINTER(i32),
+                                              vp, vp]
         L.panache_strerror.argtypes = [ctypes.c_int]
         L.panache_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -248,6 +251,18 @@ class Context:
 
     def projections(self, a: int) -> np.ndarray:
         return projections(a, self.config)
+
+    def calibrate_width(self, x, m_min: int, m_max: int, eta: float = 0.0):
+        """(K, energy[K=2..16], collision_prob[K=2..16]): the spectral-width calibration of series x."""
+        ptr, dt, n, keep = _series_arg(x)
+        K = ctypes.c_int32()
+        e = np.zeros(15)
+        c = np.zeros(15)
+        _check(lib().panache_calibrate_width(self._h, ptr, dt, n, m_min, m_max, eta, ctypes.byref(K),
+                                             e.ctypes.data_as(ctypes.c_void_p), c.ctypes.data_as(ctypes.c_void_p)),
+               "calibrate_width")
+        del keep
+        return K.value, e, c
 
     def stream(self, m_min: int, m_max: int, k: int, excl: int) -> "Stream":
         return Stream(self, m_min, m_max, k, excl)

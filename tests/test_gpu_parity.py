@@ -273,3 +273,26 @@ def test_graph_replay_equals_eager(pn, small):
         got = graph.pmp(x, s.m_min, s.m_max, s.k, s.excl)
         assert np.array_equal(got, want), n
     assert graph.stats()["kernel_launches"] > 0
+
+
+@pytest.mark.parametrize("kind", ["wafer", "walk", "noise"])
+def test_width_calibration_matches_oracle(pn, kind):
+    """Spectral-width calibration (Sec. 3.2): the device statistics equal the
+    oracle's sample means to FP64 rounding, and the chosen width is the same."""
+    from oracle import calibrate
+    rng = np.random.default_rng(8)
+    if kind == "wafer":
+        x, lo, hi = workloads.wafer_like(30_000, seed=3).x, 100, 150
+    elif kind == "walk":
+        x, lo, hi = np.cumsum(rng.standard_normal(20_000)), 32, 64
+    else:
+        x, lo, hi = rng.standard_normal(20_000), 40, 80
+    ctx = pn.Context()
+    K, e, c = ctx.calibrate_width(x, lo, hi)
+    eo, co, _ = calibrate.statistics(np.asarray(x, dtype=np.float64), lo, hi)
+    assert np.allclose(e, eo, rtol=1e-9, atol=1e-12)
+    assert np.allclose(c, co, rtol=1e-9, atol=1e-15)
+    assert K == calibrate.select_width(eo, co, len(x))
+    # the device path reads device series too
+    K2, e2, _ = ctx.calibrate_width(torch.from_numpy(np.ascontiguousarray(x)).cuda(), lo, hi)
+    assert K2 == K and np.array_equal(e2, e)
