@@ -393,7 +393,9 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def make_ctx(precision, **over):
-        ctx = pn.Context(precision=precision, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_TIMING, **over)
+        over = dict(over)
+        flags = pn.FLAG_TIMING | over.pop("flags", 0)
+        ctx = pn.Context(precision=precision, topk_mode=pn.TOPK_GLOBAL, flags=flags, **over)
         ctx.set_stream(stream.cuda_stream)
         return ctx
 
@@ -444,11 +446,16 @@ def main():
     fast = None
     if args.fast_steps > 0:
         fast = {}
-        for name, over in (("s6_alpha4_rounds1", dict(stride=6, alpha=4, rounds=1)), ("K4_s8", dict(K=4, stride=8))):
+        for name, over in (("s6_alpha4_rounds1", dict(stride=6, alpha=4, rounds=1)),
+                           ("s6_alpha4_rounds1_exhaustive_sieve", dict(stride=6, alpha=4, rounds=1,
+                                                                       flags=pn.FLAG_EXHAUSTIVE_SIEVE)),
+                           ("K4_s8", dict(K=4, stride=8))):
             fctx = make_ctx(args.precision, **over)
             fms, fst, fmot = timed(fctx, args.fast_steps, 1, x_dev)
             ref_cells = {(int(r["m"]), int(r["i"]), int(r["j"])) for r in motifs}
             got_cells = {(int(r["m"]), int(r["i"]), int(r["j"])) for r in fmot}
+            over = {k: v for k, v in over.items() if k != "flags"} | ({"exhaustive_sieve": True}
+                                                                      if "flags" in over else {})
             fast[name] = {"value": W * world / (statistics.mean(fms) / 1e3), "ms_per_step": statistics.mean(fms),
                           "same_motifs": bool(np.array_equal(fmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                           "recall_vs_default": len(ref_cells & got_cells) / max(1, len(ref_cells)),
