@@ -1,5 +1,7 @@
 // Emit stage (Sec. 3.6, Algorithm 2): hot-class sieve, local completion and
 // the zero-snapped top-k selection with FP64 re-verification.
+#include <algorithm>
+
 #include "distance.cuh"
 #include "emit.cuh"
 #include "zops.cuh"
@@ -191,6 +193,166 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
         __syncwarp();
     }
     if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);
+}
+
+// ---------------------------------------------------------------------------
+// Exhaustive sieve, mixed form: every valid pair of every hot class (the
+// wide variant of S_hot, Sec. 3.6), as a tiled all-pairs computation.  A
+// class of s members is cut into 64-member blocks; block pair (bu, bv),
+// bu <= bv, is one tile of 64 x 64 pairs.  The tile's z-normalised windows
+// are staged 32 samples at a time in shared memory and each thread
+// accumulates 4 x 4 squared differences in registers, so every staged
+// sample feeds 64 pairs instead of one.  Both cells of every valid pair
+// take the distance (row minima by shuffles, column minima through shared
+// memory, then atomicMin).  No bound test is needed: every pair is
+// evaluated, so the result is the minimum over all of them.
+// ---------------------------------------------------------------------------
+constexpr int ST_B = 64;          // members per tile side
+constexpr int ST_K = 32;          // samples staged per step
+
+__global__ void k_tile_count(const PnClass *cls, int32_t ncls, uint32_t *cnt) {
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= ncls) return;
+    const uint32_t nb = (cls[ci].size + ST_B - 1) / ST_B;
+    cnt[ci] = nb * (nb + 1) / 2;
+}
+
+// One warp per class writes its tiles (class, bu, bv) at the class's offset.
+__global__ void k_tile_fill(const PnClass *cls, int32_t ncls, const uint32_t *off, uint32_t *tiles) {
+    const int ci = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (ci >= ncls) return;
+    const uint32_t nb = (cls[ci].size + ST_B - 1) / ST_B;
+    const uint32_t total = nb * (nb + 1) / 2;
+    for (uint32_t t = lane; t < total; t += 32) {
+        // row bu holds nb - bu tiles; find bu for the t-th tile
+        uint32_t bu = 0, rem = t;
+        while (rem >= nb - bu) {
+            rem -= nb - bu;
+            ++bu;
+        }
+        const uint32_t bv = bu + rem;
+        uint4 *dst = reinterpret_cast<uint4 *>(tiles) + off[ci] + t;
+        *dst = make_uint4((uint32_t)ci, bu, bv, 0u);
+    }
+}
+
+template <class Z>
+__global__ void __launch_bounds__(256) k_sieve_tiles(PnView v, const PnClass *cls, const uint4 *tiles,
+                                                     int64_t ntiles, const uint32_t *members) {
+    __shared__ float zu[ST_K][ST_B + 1];
+    __shared__ float zv[ST_K][ST_B + 1];
+    __shared__ uint32_t su[ST_B], sv[ST_B];
+    __shared__ float2 mu_u[ST_B], mu_v[ST_B];
+    __shared__ unsigned long long colmin[ST_B];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    unsigned long long n_ex = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint4 tl = tiles[t];
+        const PnClass &c = cls[tl.x];
+        const PnAnchor &A = v.anchors[c.anchor];
+        const PnSeries &S = v.series[A.series];
+        const int a = A.a;
+        const int u0 = (int)tl.y * ST_B, v0 = (int)tl.z * ST_B;
+        const int nu = min(ST_B, (int)c.size - u0), nv = min(ST_B, (int)c.size - v0);
+        __syncthreads();                                    // the previous tile's staging is no longer read
+        if (tid < ST_B) {
+            const uint32_t xu = tid < nu ? members[c.moff + u0 + tid] : 0u;
+            const uint32_t xv = tid < nv ? members[c.moff + v0 + tid] : 0u;
+            su[tid] = xu;
+            sv[tid] = xv;
+            const auto mu = Z::load(v, A.win_off + xu), mv = Z::load(v, A.win_off + xv);
+            mu_u[tid] = tid < nu ? make_float2(mu.x, mu.y) : make_float2(0.0f, 0.0f);
+            mu_v[tid] = tid < nv ? make_float2(mv.x, mv.y) : make_float2(0.0f, 0.0f);
+            colmin[tid] = PN_EMPTY_KEY;
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        const auto *xs = Z::samples(v, S.x_off);
+        for (int k0 = 0; k0 < a; k0 += ST_K) {
+            // stage: 64 windows x 32 samples per side, z = fma(x, 1/sigma, -mu/sigma)
+            for (int e = tid; e < ST_B * ST_K; e += blockDim.x) {
+                const int row = e / ST_K, r = e - row * ST_K;
+                const int k = k0 + r;
+                float a_ = 0.0f, b_ = 0.0f;
+                if (k < a) {
+                    const float2 m1 = mu_u[row], m2 = mu_v[row];
+                    typename Z::M z1, z2;
+                    z1.x = m1.x;
+                    z1.y = m1.y;
+                    z2.x = m2.x;
+                    z2.y = m2.y;
+                    if (row < nu) a_ = Z::z(z1, xs[su[row] + k]);
+                    if (row < nv) b_ = Z::z(z2, xs[sv[row] + k]);
+                }
+                zu[r][row] = a_;
+                zv[r][row] = b_;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int r = 0; r < ST_K; ++r) {
+                float pu[4], pv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    pu[i] = zu[r][ty * 4 + i];
+                    pv[i] = zv[r][tx * 4 + i];
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float d = pu[i] - pv[j];
+                        acc[i][j] = fmaf(d, d, acc[i][j]);
+                    }
+            }
+            __syncthreads();
+        }
+        // keys of the valid pairs: row minima by shuffles, column minima in shared memory
+        const bool diag = tl.y == tl.z;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int ur = ty * 4 + i;
+            unsigned long long rowk = PN_EMPTY_KEY;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int vc = tx * 4 + j;
+                bool ok = ur < nu && vc < nv && (!diag || ur < vc) && mu_u[ur].x != 0.0f && mu_v[vc].x != 0.0f;
+                if (ok) ok = llabs((int64_t)su[ur] - (int64_t)sv[vc]) >= S.excl;
+                if (ok) {
+                    const float d = sqrtf(acc[i][j]);
+                    const unsigned long long ku = pn_pack_f(d, sv[vc]), kv = pn_pack_f(d, su[ur]);
+                    rowk = ku < rowk ? ku : rowk;
+                    atomicMin(&colmin[vc], kv);
+                    ++n_ex;
+                }
+            }
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, rowk, o);
+                rowk = other < rowk ? other : rowk;
+            }
+            if (tx == 0 && rowk != PN_EMPTY_KEY) {
+                unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
+                atomicMin(&prow[su[ur]], rowk);
+            }
+        }
+        __syncthreads();
+        if (tid < nv && colmin[tid] != PN_EMPTY_KEY) {
+            unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
+            atomicMin(&prow[sv[tid]], colmin[tid]);
+        }
+    }
+    // counts per block
+    __shared__ unsigned long long s_ex;
+    if (tid == 0) s_ex = 0;
+    __syncthreads();
+    if (n_ex) atomicAdd(&s_ex, n_ex);
+    __syncthreads();
+    if (tid == 0 && v.stats && s_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], s_ex);
 }
 
 // ---------------------------------------------------------------------------
@@ -458,6 +620,34 @@ __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry 
     }
 }
 
+// Exhaustive sieve of the mixed form: tile table, then the tiled all-pairs kernel.
+template <class Z>
+cudaError_t sieve_tiles_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int grid_blocks,
+                          cudaStream_t st) {
+    uint32_t *cnt = nullptr, *off = nullptr, *tot = nullptr, *tiles = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&cnt, 4 * (size_t)ncls, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&off, 4 * (size_t)ncls, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot, 4, st);
+    if (e == cudaSuccess) {
+        k_tile_count<<<grid_for(ncls, 256), 256, 0, st>>>(cls, ncls, cnt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = excl_scan_u32(cnt, off, ncls, tot, st);
+    uint32_t ntiles = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ntiles, tot, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && ntiles > 0) e = cudaMallocAsync((void **)&tiles, sizeof(uint4) * (size_t)ntiles, st);
+    if (e == cudaSuccess && ntiles > 0) {
+        k_tile_fill<<<grid_for((int64_t)ncls * 32, 256), 256, 0, st>>>(cls, ncls, off, tiles);
+        const int64_t g = std::min<int64_t>((int64_t)ntiles, (int64_t)grid_blocks);
+        k_sieve_tiles<Z><<<(unsigned)g, 256, 0, st>>>(v, cls, reinterpret_cast<const uint4 *>(tiles), ntiles, vals);
+        e = cudaGetLastError();
+    }
+    for (void *p : {(void *)cnt, (void *)off, (void *)tot, (void *)tiles})
+        if (p) cudaFreeAsync(p, st);
+    return e;
+}
+
 template <class Z>
 cudaError_t sieve_t(const PnView &v, const PnClass *cls, int64_t nmem, const uint32_t *keys, const uint32_t *vals,
                     int w, int exhaustive, int zcap, int64_t blocks, cudaStream_t st) {
@@ -519,6 +709,8 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             const int zcap = (a_max + 3) & ~3;
             // after the class sort, keys[p] is the class of member p
             if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
+            else if (exhaustive && v.x1) e = sieve_tiles_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);
+            else if (exhaustive) e = sieve_tiles_t<ZMix2>(v, cls, ncls, vals, grid_blocks, st);
             else if (v.x1) e = sieve_t<ZMix1>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             else e = sieve_t<ZMix2>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             if (e == cudaSuccess) e = cudaGetLastError();

@@ -296,3 +296,35 @@ def test_width_calibration_matches_oracle(pn, kind):
     # the device path reads device series too
     K2, e2, _ = ctx.calibrate_width(torch.from_numpy(np.ascontiguousarray(x)).cuda(), lo, hi)
     assert K2 == K and np.array_equal(e2, e)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_exhaustive_sieve(pn, small, small_exact, precision):
+    """The exhaustive sieve evaluates every valid pair of every hot class (the
+    mixed form as 64 x 64 tiles): with completion off (whose seeds depend on
+    the rows), every cell is at most the default sieve's up to the in-stream
+    rounding, the rows stay sound, and with completion the global top-k
+    equals the oracle's."""
+    s = small
+    P, I = small_exact
+    base, _ = run(pn, s, precision=precision, topk_mode=1, flags=pn.FLAG_NO_COMPLETION)
+    L = s.m_max - s.m_min + 1
+    d0, _ = pn.unpack_keys(base.profile_rows(0, s.x.shape[0], L))
+    ctx, _ = run(pn, s, precision=precision, topk_mode=1, flags=pn.FLAG_EXHAUSTIVE_SIEVE | pn.FLAG_NO_COMPLETION)
+    d1, j1 = pn.unpack_keys(ctx.profile_rows(0, s.x.shape[0], L))
+    assert ctx.stats()["exact_sieve"] >= base.stats()["exact_sieve"]
+    rtol, atol = (2.0 ** -25, 1e-12) if precision == 0 else (2e-5, 2e-5)
+    fin0 = np.isfinite(d0)
+    assert np.all(np.isfinite(d1[fin0]))
+    assert np.all(d1[fin0] <= d0[fin0] * (1 + 2 * rtol) + atol)
+    fin = np.isfinite(d1)
+    assert np.all(d1[fin] >= P[fin] * (1 - rtol) - atol)
+    ms, iis = np.nonzero(fin)
+    assert np.all(np.abs(iis - j1[ms, iis]) >= s.excl)
+    # global top-k: exact at the paper's defaults (per length, stride 2 misses
+    # up to 1% of cells with or without the exhaustive sieve; see the recall test)
+    _, got = run(pn, s, precision=precision, topk_mode=0, flags=pn.FLAG_EXHAUSTIVE_SIEVE)
+    ref = topk.select(P, I, s.m_min, s.k, topk.GLOBAL)
+    from parity import compare
+    r = compare(s.x, got, ref)
+    assert r["misses"] == 0 and r["bad_dist"] == 0, r

@@ -96,3 +96,15 @@ def test_full_size_reported_cells_are_exact(pn, wafer):
         for b in range(a):
             if got[a]["m"] == got[b]["m"]:
                 assert 2 * abs(int(got[a]["i"]) - int(got[b]["i"])) > int(got[a]["m"])
+
+
+def test_prefix_fastest_settings_with_exhaustive_sieve(pn, wafer, golden):
+    """The paper's fastest settings (anchor stride 6, alpha 4, one completion
+    round) lose part of the global top-20 on this workload; the exhaustive
+    sieve over the over-budget buckets recovers all of it."""
+    from parity import compare
+    x, got = _prefix_run(pn, wafer, precision=1, topk_mode=0, stride=6, alpha=4, rounds=1,
+                         flags=pn.FLAG_EXHAUSTIVE_SIEVE)
+    r = compare(x.astype(np.float64), got, golden[0])
+    assert r["misses"] == 0, r["miss_list"]
+    assert r["bad_dist"] == 0
