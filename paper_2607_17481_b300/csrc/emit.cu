@@ -196,6 +196,144 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
 }
 
 // ---------------------------------------------------------------------------
+// Sieve of the mixed form as a band (Sec. 3.6: pairs within w positions of
+// the projected order).  The members of all hot classes lie in one flat
+// array sorted by (class, projection); block b takes the 64 members
+// b*64 .. b*64+63 as the first element u of its pairs and the w members
+// after each as v, so its pairs live in a band of 64 + w consecutive
+// members.  Those windows are staged 32 samples at a time in shared memory
+// (each member z-normalised by its own anchor's moments), every thread
+// accumulates the squared differences of its band pairs, and each window
+// read feeds up to 2w pairs.  Pairs across a class boundary or inside the
+// exclusion zone are skipped.  Every band pair is evaluated (no bound
+// test): the cells are the minimum over the same pairs the bound-filtered
+// form admits.
+// ---------------------------------------------------------------------------
+constexpr int SB_U = 64;          // first elements per block
+constexpr int SB_WMAX = 16;       // widest band of this kernel
+constexpr int SB_K = 32;          // samples staged per step
+
+template <class Z>
+__global__ void __launch_bounds__(256) k_sieve_band(PnView v, const PnClass *cls, int64_t nmem,
+                                                    const uint32_t *member_class, const uint32_t *members, int w) {
+    __shared__ float zs[SB_K][SB_U + SB_WMAX + 1];
+    __shared__ uint32_t s_x[SB_U + SB_WMAX], s_cls[SB_U + SB_WMAX];
+    __shared__ int32_t s_a[SB_U + SB_WMAX];
+    __shared__ float2 s_m[SB_U + SB_WMAX];
+    __shared__ int64_t s_xoff[SB_U + SB_WMAX];
+    __shared__ unsigned long long colmin[SB_U + SB_WMAX];
+    __shared__ unsigned long long s_ex;
+    const int tid = threadIdx.x;
+    const int npair = SB_U * w;                            // pair e: u = e / w, v = u + 1 + e % w
+    const int per = (npair + blockDim.x - 1) / blockDim.x; // pairs per thread (<= 4)
+    const int nrow = SB_U + w;
+    if (tid == 0) s_ex = 0;
+    for (int64_t b = blockIdx.x; b * SB_U < nmem; b += gridDim.x) {
+        const int64_t p0 = b * SB_U;
+        __syncthreads();
+        if (tid < nrow) {
+            const int64_t p = p0 + tid;
+            uint32_t x = 0, ci = 0xFFFFFFFFu;
+            int a = 0;
+            float2 m = make_float2(0.0f, 0.0f);
+            int64_t xoff = 0;
+            if (p < nmem) {
+                ci = member_class[p];
+                x = members[p];
+                const PnAnchor &A = v.anchors[cls[ci].anchor];
+                a = A.a;
+                const auto mm = Z::load(v, A.win_off + x);
+                m = make_float2(mm.x, mm.y);
+                xoff = v.series[A.series].x_off;
+            }
+            s_x[tid] = x;
+            s_cls[tid] = ci;
+            s_a[tid] = a;
+            s_m[tid] = m;
+            s_xoff[tid] = xoff;
+            colmin[tid] = PN_EMPTY_KEY;
+        }
+        __syncthreads();
+        int amax = 0;
+        for (int r = 0; r < nrow; ++r) amax = max(amax, s_a[r]);
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int k0 = 0; k0 < amax; k0 += SB_K) {
+            for (int e = tid; e < nrow * SB_K; e += blockDim.x) {
+                const int row = e / SB_K, r = e - row * SB_K;
+                const int k = k0 + r;
+                float z = 0.0f;
+                if (k < s_a[row]) {
+                    typename Z::M mm;
+                    mm.x = s_m[row].x;
+                    mm.y = s_m[row].y;
+                    z = Z::z(mm, Z::samples(v, s_xoff[row] + s_x[row])[k]);
+                }
+                zs[r][row] = z;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + q * blockDim.x;
+                if (q < per && e < npair) {
+                    const int u = e / w, vv = u + 1 + e % w;
+#pragma unroll 8
+                    for (int r = 0; r < SB_K; ++r) {
+                        const float d = zs[r][u] - zs[r][vv];
+                        acc[q] = fmaf(d, d, acc[q]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // keys: u's minimum over its w pairs by shuffles (pairs e = u*w .. u*w+w-1
+        // sit in consecutive threads when w divides 32), v's through shared memory
+        unsigned long long n_here = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * blockDim.x;
+            const int u = e / w, vv = u + 1 + e % w;
+            unsigned long long ku = PN_EMPTY_KEY;
+            const bool in = q < per && e < npair;
+            if (in && p0 + vv < nmem && s_cls[u] == s_cls[vv] && s_m[u].x != 0.0f && s_m[vv].x != 0.0f) {
+                const PnAnchor &A = v.anchors[cls[s_cls[u]].anchor];
+                const PnSeries &S = v.series[A.series];
+                if (llabs((int64_t)s_x[u] - (int64_t)s_x[vv]) >= S.excl) {
+                    const float d = sqrtf(acc[q]);
+                    ku = pn_pack_f(d, s_x[vv]);
+                    atomicMin(&colmin[vv], pn_pack_f(d, s_x[u]));
+                    ++n_here;
+                }
+            }
+            // every u owns w consecutive pair slots; reduce over them when they share a warp
+            if ((w & (w - 1)) == 0 && w <= 32) {
+                for (int o = 1; o < w; o <<= 1) {
+                    const unsigned long long other = __shfl_xor_sync(0xffffffffu, ku, o);
+                    ku = other < ku ? other : ku;
+                }
+                if (in && (e % w) == 0 && ku != PN_EMPTY_KEY) {
+                    const PnAnchor &A = v.anchors[cls[s_cls[u]].anchor];
+                    const PnSeries &S = v.series[A.series];
+                    atomicMin(&v.prof[S.row_off + (int64_t)(A.a - S.m_min) * S.ld + s_x[u]], ku);
+                }
+            } else if (ku != PN_EMPTY_KEY) {
+                const PnAnchor &A = v.anchors[cls[s_cls[u]].anchor];
+                const PnSeries &S = v.series[A.series];
+                atomicMin(&v.prof[S.row_off + (int64_t)(A.a - S.m_min) * S.ld + s_x[u]], ku);
+            }
+        }
+        if (n_here) atomicAdd(&s_ex, n_here);
+        __syncthreads();
+        if (tid < nrow && p0 + tid < nmem && colmin[tid] != PN_EMPTY_KEY) {
+            const PnAnchor &A = v.anchors[cls[s_cls[tid]].anchor];
+            const PnSeries &S = v.series[A.series];
+            atomicMin(&v.prof[S.row_off + (int64_t)(A.a - S.m_min) * S.ld + s_x[tid]], colmin[tid]);
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && v.stats && s_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], s_ex);
+}
+
+// ---------------------------------------------------------------------------
 // Exhaustive sieve, mixed form: every valid pair of every hot class (the
 // wide variant of S_hot, Sec. 3.6), as a tiled all-pairs computation.  A
 // class of s members is cut into 64-member blocks; block pair (bu, bv),
@@ -620,6 +758,15 @@ __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry 
     }
 }
 
+template <class Z>
+cudaError_t sieve_band_t(const PnView &v, const PnClass *cls, int64_t nmem, const uint32_t *keys,
+                         const uint32_t *vals, int w, int grid_blocks, cudaStream_t st) {
+    const int64_t need = (nmem + SB_U - 1) / SB_U;
+    const int64_t g = std::min<int64_t>(need, (int64_t)grid_blocks * 2);
+    k_sieve_band<Z><<<(unsigned)g, 256, 0, st>>>(v, cls, nmem, keys, vals, w);
+    return cudaGetLastError();
+}
+
 // Exhaustive sieve of the mixed form: tile table, then the tiled all-pairs kernel.
 template <class Z>
 cudaError_t sieve_tiles_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int grid_blocks,
@@ -711,6 +858,8 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             else if (exhaustive && v.x1) e = sieve_tiles_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);
             else if (exhaustive) e = sieve_tiles_t<ZMix2>(v, cls, ncls, vals, grid_blocks, st);
+            else if (w <= SB_WMAX && v.x1) e = sieve_band_t<ZMix1>(v, cls, nmem, keys, vals, w, grid_blocks, st);
+            else if (w <= SB_WMAX) e = sieve_band_t<ZMix2>(v, cls, nmem, keys, vals, w, grid_blocks, st);
             else if (v.x1) e = sieve_t<ZMix1>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             else e = sieve_t<ZMix2>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             if (e == cudaSuccess) e = cudaGetLastError();
