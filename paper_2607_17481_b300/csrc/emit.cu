@@ -579,22 +579,44 @@ __device__ __forceinline__ int group_of(const PnView &v, const PnSelGroup *grp, 
     return pn_find(grp, ngrp, cell, [](const PnSelGroup &g) { return g.cell_off; });
 }
 
-__global__ void k_sel_hist(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_t total, double eps0, int level,
-                           const uint32_t *b1, uint32_t *hist) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool ok = t < total;
-    unsigned long long key = ok ? v.prof[t] : PN_EMPTY_KEY;
-    int gi = 0;
-    uint32_t bin = 0;
-    if (ok) {
-        gi = group_of(v, grp, ngrp, t);
-        ok = key != PN_EMPTY_KEY && t < grp[gi].cell_off + grp[gi].ncell;
+// Histogram of the level-0 (or, within the level-0 bin b1, level-1) key
+// bits of every group.  Block b takes the contiguous cells
+// [b per_block, (b+1) per_block); the groups tile the cell space, so the
+// range splits into a few group segments, each counted in a shared-memory
+// histogram (warp-aggregated atomics) and flushed once to the group's
+// global histogram.
+__global__ void __launch_bounds__(256) k_sel_hist(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_t total,
+                                                  double eps0, int level, const uint32_t *b1, uint32_t *hist,
+                                                  int64_t per_block) {
+    __shared__ uint32_t sh[4096];
+    const int64_t lo = (int64_t)blockIdx.x * per_block;
+    const int64_t hi = min(total, lo + per_block);
+    int64_t t0 = lo;
+    while (t0 < hi) {
+        const int gi = group_of(v, grp, ngrp, t0);
+        const int64_t gend = grp[gi].cell_off + grp[gi].ncell;
+        const int64_t seg_end = gend > t0 ? min(hi, gend) : min(hi, gi + 1 < ngrp ? grp[gi + 1].cell_off : hi);
+        const bool in_group = gend > t0;
+        for (int b = threadIdx.x; b < 4096; b += blockDim.x) sh[b] = 0u;
+        __syncthreads();
+        const uint32_t want = (in_group && level == 1) ? b1[gi] : 0u;
+        for (int64_t base = t0; base < seg_end; base += blockDim.x) {
+            const int64_t t = base + threadIdx.x;
+            bool ok = in_group && t < seg_end;
+            const unsigned long long key = ok ? __ldcs(&v.prof[t]) : PN_EMPTY_KEY;
+            ok = ok && key != PN_EMPTY_KEY;
+            if (ok && level == 1) ok = sel_bits(key, eps0, 0) == want;
+            const uint32_t bin = ok ? sel_bits(key, eps0, level) : 0u;
+            const unsigned peers = __match_any_sync(0xffffffffu, ok ? bin : 0xFFFFFFFFu - (threadIdx.x & 31));
+            if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh[bin], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        if (in_group)
+            for (int b = threadIdx.x; b < 4096; b += blockDim.x)
+                if (sh[b]) atomicAdd(&hist[(int64_t)gi * 4096 + b], sh[b]);
+        __syncthreads();
+        t0 = seg_end > t0 ? seg_end : hi;
     }
-    if (ok && level == 1) ok = sel_bits(key, eps0, 0) == b1[gi];
-    if (ok) bin = sel_bits(key, eps0, level);
-    unsigned long long tag = ok ? (((unsigned long long)gi << 12) | bin) : (0xFFFFFFFF00000000ull | threadIdx.x);
-    unsigned peers = __match_any_sync(0xffffffffu, tag);
-    if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[(int64_t)gi * 4096 + bin], (uint32_t)__popc(peers));
 }
 
 // One thread per group: first bin whose cumulative count reaches `need`.
@@ -902,15 +924,18 @@ cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ng
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&carry, 4 * ngrp, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&pcnt, 4 * ngrp, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&pool, sizeof(PnPoolEntry) * (int64_t)cap * ngrp, st);
+    // histogram blocks: contiguous ranges of at least 16 cells per thread
+    const int64_t hist_blocks = std::max<int64_t>(1, std::min<int64_t>((total + 4095) / 4096, (int64_t)grid_blocks));
+    const int64_t per_block = ((total + hist_blocks - 1) / hist_blocks + 255) / 256 * 256;
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4096 * ngrp, st);
     if (e == cudaSuccess) {
-        k_sel_hist<<<grid_for(total, 256), 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, 0, nullptr, hist);
+        k_sel_hist<<<(unsigned)hist_blocks, 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, 0, nullptr, hist, per_block);
         k_sel_pick<<<grid_for(ngrp, 128), 128, 0, st>>>(grp_dev, ngrp, hist, nullptr, b1, carry);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4096 * ngrp, st);
     if (e == cudaSuccess) {
-        k_sel_hist<<<grid_for(total, 256), 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, 1, b1, hist);
+        k_sel_hist<<<(unsigned)hist_blocks, 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, 1, b1, hist, per_block);
         k_sel_pick<<<grid_for(ngrp, 128), 128, 0, st>>>(grp_dev, ngrp, hist, carry, b2, nullptr);
         e = cudaGetLastError();
     }
