@@ -32,7 +32,6 @@ namespace {
 constexpr int SR_WARPS = 8;
 constexpr int SR_THREADS = SR_WARPS * 32;
 constexpr int SR_MAXR = 512;   // largest supported budget R
-constexpr int SR_MAXPROBE = 9; // exact bucket + up to 8 Hamming-1 buckets
 
 template <class Z>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {

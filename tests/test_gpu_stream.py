@@ -166,3 +166,27 @@ def test_stream_survives_context_destruction(pn, small):
         st.append(s.x[1000:1100])
     assert e.value.code == -6                        # ESTATE: the context's device state is gone
     st.close()
+
+
+def test_stream_checkpoint_and_calibration_argument_errors(pn, small):
+    s = small
+    ctx = pn.Context(topk_mode=0)
+    st = ctx.stream(s.m_min, s.m_max, s.k, s.excl)
+    st.append(s.x[:500])
+    lib = pn.native.lib()
+    import ctypes
+    n = ctypes.c_int64()
+    buf = np.zeros(10)
+    # a checkpoint buffer smaller than the stream: ETRUNC with the length needed
+    rc = lib.panache_stream_checkpoint(st._h, buf.ctypes.data_as(ctypes.c_void_p), 10, ctypes.byref(n))
+    assert rc == -5 and n.value == 500
+    K = ctypes.c_int32()
+    x = np.ascontiguousarray(s.x)
+    # eta outside (0, 1], lengths below 3, m_max < m_min
+    for eta, lo, hi in ((1.5, 32, 64), (-0.1, 32, 64), (0.85, 2, 64), (0.85, 40, 32)):
+        rc = lib.panache_calibrate_width(ctx._h, x.ctypes.data_as(ctypes.c_void_p), pn.F64, len(x), lo, hi, eta,
+                                         ctypes.byref(K), None, None)
+        assert rc == -1, (eta, lo, hi)
+    # a series shorter than every length: every window set is empty, K falls back to 16
+    K2, e, c = ctx.calibrate_width(s.x[:20], 32, 64)
+    assert K2 == 16 and np.all(e == 0) and np.all(c == 0)
