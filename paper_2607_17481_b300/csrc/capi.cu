@@ -109,7 +109,7 @@ struct PnRequest {
     uint32_t *sig = nullptr, *cnt = nullptr, *nclist = nullptr, *qorder = nullptr;
     float2 *wmf = nullptr;
     double2 *wmd = nullptr;
-    float *g = nullptr;
+    float *g = nullptr, *gT = nullptr;
     uint32_t *dir_keys = nullptr, *dir_vals = nullptr, *bstart = nullptr;
     unsigned long long *prof = nullptr, *stats = nullptr;
     int *flagbuf = nullptr;
@@ -356,6 +356,7 @@ PnView make_view(panache_ctx *ctx, PnRequest &R) {
     v.wmf = R.wmf;
     v.wmd = R.wmd;
     v.g = R.g;
+    v.gT = R.gT;
     v.anc = R.tca;
     v.err = R.err;
     v.dir_keys = R.dir_keys;
@@ -501,6 +502,7 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) 
     if (c.precision == PANACHE_PLAIN_FP64) PN_CU(R.alloc(R.wmd, R.total_windows));
     else PN_CU(R.alloc(R.wmf, R.total_windows));
     PN_CU(R.alloc(R.g, nanc * (c.B + 1) * PN_FEAT));
+    PN_CU(R.alloc(R.gT, nanc * PN_FEAT * 32));
     PN_CU(R.alloc(R.dir_keys, R.total_items));
     PN_CU(R.alloc(R.dir_vals, R.total_items));
     PN_CU(R.alloc(R.bstart, R.total_buckets + 1));
@@ -523,6 +525,13 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) 
         const std::vector<float> &g = ctx->proj(R.anc[a].a);
         std::copy(g.begin(), g.end(), hg.begin() + a * (c.B + 1) * PN_FEAT);
     }
+    // transposed copy: element (t, l) = dimension t of projection l, so that
+    // lane l of a warp reads its projection's dimensions with coalesced loads
+    std::vector<float> hgT((size_t)nanc * PN_FEAT * 32, 0.0f);
+    for (int64_t a = 0; a < nanc; ++a)
+        for (int l = 0; l <= (int)c.B; ++l)
+            for (int t = 0; t < PN_FEAT; ++t)
+                hgT[(a * PN_FEAT + t) * 32 + l] = hg[(a * (c.B + 1) + l) * PN_FEAT + t];
     PN_CU(cudaMemcpyAsync(R.d_ser, R.ser.data(), sizeof(PnSeries) * nser, cudaMemcpyHostToDevice, st));
     if (nanc) {
         PN_CU(cudaMemcpyAsync(R.d_anc, R.anc.data(), sizeof(PnAnchor) * nanc, cudaMemcpyHostToDevice, st));
@@ -541,6 +550,7 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) 
             }
         }
         PN_CU(cudaMemcpyAsync(R.g, hg.data(), 4 * hg.size(), cudaMemcpyHostToDevice, st));
+        PN_CU(cudaMemcpyAsync(R.gT, hgT.data(), 4 * hgT.size(), cudaMemcpyHostToDevice, st));
     }
     PN_CU(cudaMemsetAsync(R.prof, 0xFF, sizeof(unsigned long long) * std::max<int64_t>(1, R.total_cells), st));
     PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));

@@ -40,6 +40,7 @@ struct PnView {
     double2 *wmd;         // plain form: per-window (1/sigma, -mu/sigma)
     uint32_t *qorder;     // search order of the flat query space (grouped by probe bucket)
     const float *g;       // projections [nanchors][B+1][PN_FEAT]
+    const float *gT;      // the same, transposed per anchor: [nanchors][PN_FEAT][32] (projection l in lane l)
     float *anc;           // mixed form: tensor-core chunk anchors, [flat chunk][PN_FEAT] (null: FP64 direct DFT)
     int *err;             // device error word (PN_ERR_*), 0 when every bounded wait succeeded
     // directory

@@ -76,7 +76,12 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         __syncwarp();
         float mg = __int_as_float(0x7f800000);
         if (lane < d) {
-            mg = fabsf(pn_margin(v.g + ((int64_t)ai * (v.B + 1) + lane) * PN_FEAT, sF[warp], dims));
+            // <g_lane, F> in the FMA order of pn_margin, the projection read from
+            // the transposed copy (one coalesced 128-byte row per dimension)
+            const float *gt = v.gT + (int64_t)ai * PN_FEAT * 32 + lane;
+            float acc = 0.0f;
+            for (int t = 0; t < dims; ++t) acc = fmaf(gt[t * 32], sF[warp][t], acc);
+            mg = fabsf(acc);
             if (!(mg <= 3.0e38f)) mg = 3.0e38f;            // non-finite input: still a bit below d
         }
         const uint32_t sgq = v.sig[w];
