@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
     using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
     __shared__ unsigned long long s_stat[3];
+    __shared__ uint32_t sprobe[SR_WARPS][32];
     extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int R = v.R;
@@ -88,23 +89,17 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         const uint32_t pre = d > 0 ? (sgq >> (v.B - d)) : 0u;
         const int h = d <= 0 ? 0 : min(d, min(v.probe_cap, 1 + max(0, d - v.d0)));
         // lane j (0 <= j <= h) owns probe j: the exact prefix, then Hamming-1
-        // buckets in increasing margin (ties to the lower bit)
-        uint32_t my_probe = pre;
-        for (int j = 0; j < h; ++j) {
-            float bm = mg;
-            int bl = lane;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                float om = __shfl_xor_sync(0xffffffffu, bm, o);
-                int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-                if (om < bm || (om == bm && ol < bl)) {
-                    bm = om;
-                    bl = ol;
-                }
-            }
-            if (lane == j + 1) my_probe = pre ^ (1u << (d - 1 - bl));
-            if (lane == bl) mg = __int_as_float(0x7f800000);
+        // buckets in increasing margin (ties to the lower bit).  Each bit lane
+        // ranks its margin among the d bits; the lane of rank r flips its bit
+        // for probe r + 1, handed to lane r + 1 through shared memory.
+        int rank = 0;
+        for (int k = 0; k < d; ++k) {
+            const float o = __shfl_sync(0xffffffffu, mg, k);
+            rank += (o < mg || (o == mg && k < lane)) ? 1 : 0;
         }
+        if (lane < d && rank < h) sprobe[warp][rank + 1] = pre ^ (1u << (d - 1 - lane));
+        __syncwarp();
+        const uint32_t my_probe = (lane >= 1 && lane <= h) ? sprobe[warp][lane] : pre;
         // every probe's bucket range and valid prefix (start <= q - excl), in parallel
         const int64_t qmax = q - S.excl;
         uint32_t my_lo = 0, my_sz = 0;
