@@ -252,17 +252,18 @@ def run_batched(pn, stream, n_series: int, n_loop: int):
     return out
 
 
-def run_served(pn, args):
+def run_served(pn, args, rate=None):
     """The served form: Poisson arrivals of batched-workload series plus live
     streams (random walk or ECG-like, starting at 50,000 samples, lengths
     64..128, top-20, exclusion 128) receiving 1,024-sample appends at 50 Hz,
     each stream asked for its top-20 once a second; one request server with
     4 slots under a 120 GB budget.  Latency: submission to motifs on the host."""
     import numpy as np
+    rate = args.served_rate if rate is None else rate
     rng = np.random.default_rng(99)
-    n_req = int(args.served_rate * args.served_seconds * 1.3) + 8
+    n_req = int(rate * args.served_seconds * 1.3) + 8
     reqs = workloads.batched_workload(n_req, seed=5)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.served_rate, size=n_req))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     arrivals = arrivals[arrivals < args.served_seconds]
     live = []
     for sidx in range(args.served_streams):
@@ -304,7 +305,7 @@ def run_served(pn, args):
     sv.close()
     return {"requests": int(next_req), "stream_topk_requests": int(len(tickets) - next_req),
             "live_streams": len(live), "appended_samples": int(sum(f - 50_000 for f in fed)),
-            "arrival_rate_per_s": args.served_rate, "window_s": args.served_seconds,
+            "arrival_rate_per_s": rate, "window_s": args.served_seconds,
             "completed": int(st["completed"]), "failed": int(st["failed"]),
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
             "windows_lengths": int(st["windows_lengths"]),
@@ -462,6 +463,8 @@ def main():
                           "config": over}
     batched = run_batched(pn, stream, args.batched, args.batched_loop) if args.batched > 0 else None
     served = run_served(pn, args) if args.served_seconds > 0 and rank == 0 else None
+    # the same mix at a quarter of the arrival rate: latency when the server is not saturated
+    served_light = run_served(pn, args, args.served_rate / 4) if args.served_seconds > 0 and rank == 0 else None
     if rank != 0:
         return 0
     peaks, psrc = measured_peaks()
@@ -484,6 +487,7 @@ def main():
         "fast_settings": fast,
         "batched": batched,
         "served": served,
+        "served_quarter_rate": served_light,
         "step_ms": stats[-1]["step_ms"],
         "counters": {k: v for k, v in stats[-1].items() if k != "step_ms"},
         "motifs": [[int(r["m"]), int(r["i"]), int(r["j"]), float(r["d"])] for r in motifs],
