@@ -273,11 +273,22 @@ def run_served(pn, args, rate=None):
         x = workloads.random_walk(g, total) if kind == "random_walk" else workloads.ecg_like(g, total)
         live.append(x.astype(np.float32))
     sv = pn.Server(slots=4, hbm_budget_bytes=120 * 10 ** 9, precision=1, topk_mode=pn.TOPK_GLOBAL)
-    sids = []
+    # live streams reserve their resident state from the budget; one that
+    # does not fit is refused (EBUDGET) and left out, and a stream whose
+    # growth is refused keeps its samples and stops taking appends
+    sids, kept, refused = [], [], 0
     for x in live:
         sid = sv.stream_open(64, 128, 20, 128)
-        sv.append(sid, x[:50_000])
+        try:
+            sv.append(sid, x[:50_000])
+        except pn.PanacheError:
+            refused += 1
+            sv.stream_close(sid)
+            continue
         sids.append(sid)
+        kept.append(x)
+    live = kept
+    growing = [True] * len(live)
     tickets = []
     t0 = time.perf_counter()
     next_req, tick = 0, 0
@@ -292,19 +303,29 @@ def run_served(pn, args, rate=None):
             next_req += 1
         if now >= tick * 0.02:                     # 50 Hz append round
             for i, sid in enumerate(sids):
-                sv.append(sid, live[i][fed[i]:fed[i] + 1024])
-                fed[i] += 1024
+                if not growing[i]:
+                    continue
+                try:
+                    sv.append(sid, live[i][fed[i]:fed[i] + 1024])
+                    fed[i] += 1024
+                except pn.PanacheError:
+                    growing[i] = False
+                    refused += 1
             if tick % 50 == 49:                    # once a second: top-20 of every live stream
                 tickets.extend(sv.stream_topk(sid) for sid in sids)
             tick += 1
         time.sleep(0.0005)
     tickets.extend(sv.stream_topk(sid) for sid in sids)
     for t in tickets:
-        sv.wait(t)
+        try:
+            sv.wait(t)
+        except pn.PanacheError:
+            pass                                   # counted by the server as failed (refused)
     st = sv.stats()
     sv.close()
     return {"requests": int(next_req), "stream_topk_requests": int(len(tickets) - next_req),
-            "live_streams": len(live), "appended_samples": int(sum(f - 50_000 for f in fed)),
+            "live_streams": len(live), "live_streams_requested": args.served_streams,
+            "stream_admissions_refused": refused, "appended_samples": int(sum(f - 50_000 for f in fed)),
             "arrival_rate_per_s": rate, "window_s": args.served_seconds,
             "completed": int(st["completed"]), "failed": int(st["failed"]),
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],

@@ -267,7 +267,10 @@ const char *panache_strerror(int code);
  * stream, so requests of different slots overlap on the GPU.  A request
  * reserves its device footprint (the planner's estimate) from the budget
  * before it runs and releases it when its motifs are on the host; one larger
- * than the whole budget is refused at submission (EBUDGET).  A free slot
+ * than the whole budget is refused at submission (EBUDGET), and one that
+ * does not fit beside the live streams' reservations while no batch is
+ * running is refused when it reaches the head of the queue (its wait returns
+ * EBUDGET) rather than waiting for streams to close.  A free slot
  * takes, in arrival order, every queued request that fits the free budget
  * and the slot's share of it (budget / slots) and runs them as one batch.
  * Results do not depend on which requests share a batch or run alongside.

@@ -108,10 +108,23 @@ void panache_server::worker(int slot) {
         uint64_t fp = 0;
         {
             std::unique_lock<std::mutex> lk(mu);
+            // a request that does not fit while no batch runs can only wait for
+            // live streams to close: it is refused (EBUDGET) instead of waiting
             cv_work.wait(lk, [&] {
-                return (!queue.empty() && in_use + queue.front().footprint <= budget) || (stop && queue.empty());
+                return (!queue.empty() && (in_use + queue.front().footprint <= budget || running == 0)) ||
+                       (stop && queue.empty());
             });
             if (queue.empty()) return;                    // stopping and drained
+            if (in_use + queue.front().footprint > budget) {
+                Result r;
+                r.rc = PANACHE_EBUDGET;
+                r.latency_ms = now_ms() - queue.front().t_submit;
+                ++failed;
+                done[queue.front().ticket] = std::move(r);
+                queue.pop_front();
+                cv_done.notify_all();
+                continue;
+            }
             while (!queue.empty()) {
                 const Job &j = queue.front();
                 const bool fits = in_use + fp + j.footprint <= budget;
