@@ -107,3 +107,31 @@ def test_live_stream_topk_equals_offline(pn):
     snap, _ = sv.wait(mid_ticket)
     assert np.array_equal(snap, ctx.pmp(s.x[:mid_len], s.m_min, s.m_max, s.k, s.excl))
     sv.close()
+
+
+def test_request_that_cannot_fit_beside_streams_is_refused(pn):
+    """Live streams hold their reservation; a request that no longer fits
+    beside them while nothing else runs is refused, not left waiting."""
+    s = workloads.planted_random_walk()
+    big = _series(1, seed=31, n_hi=60000)[0]
+    need = _footprint(pn, big)
+    stream_probe = pn.Server(slots=1, hbm_budget_bytes=10 << 30)
+    sid = stream_probe.stream_open(s.m_min, s.m_max, s.k, s.excl)
+    stream_probe.append(sid, s.x)
+    res = stream_probe.stats()["peak_reserved_bytes"]         # the stream's reservation
+    stream_probe.close()
+    assert 0 < res
+    # a budget that holds the stream, and the request alone, but not both
+    budget = max(need, res) + min(need, res) // 2
+    sv = pn.Server(slots=2, hbm_budget_bytes=budget)
+    sid = sv.stream_open(s.m_min, s.m_max, s.k, s.excl)
+    sv.append(sid, s.x)
+    t = sv.submit(big.x, big.m_min, big.m_max, big.k, big.excl)
+    with pytest.raises(pn.PanacheError) as e:
+        sv.wait(t, timeout_ms=60_000)
+    assert e.value.code == -3
+    # once the stream is closed the same request runs
+    sv.stream_close(sid)
+    got, _ = sv.wait(sv.submit(big.x, big.m_min, big.m_max, big.k, big.excl), timeout_ms=60_000)
+    assert len(got) > 0
+    sv.close()
