@@ -378,6 +378,7 @@ def main():
     ap.add_argument("--impl", default="panache", choices=("panache", "reference"))
     ap.add_argument("--precision", type=int, default=1, help="1 mixed (default), 0 plain FP64")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 form")
+    ap.add_argument("--half-steps", type=int, default=2, help="timed steps with half-precision feature rows")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batched", type=int, default=256,
@@ -465,6 +466,16 @@ def main():
         plain = {"value": W * world / (statistics.mean(pms) / 1e3), "ms_per_step": statistics.mean(pms),
                  "same_motifs": bool(np.array_equal(pmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                  "step_ms": pstats[-1]["step_ms"]}
+    half = None
+    if args.half_steps > 0 and args.precision != 0:
+        hctx = make_ctx(args.precision, flags=pn.FLAG_HALF_FEATURES)
+        hms, hst, hmot = timed(hctx, args.half_steps, 1, x_dev)
+        half = {"value": W * world / (statistics.mean(hms) / 1e3), "ms_per_step": statistics.mean(hms),
+                "same_motifs": bool(np.array_equal(hmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
+                "device_bytes": int(hst[-1]["device_bytes"]),
+                "device_bytes_fp32_rows": int(stats[-1]["device_bytes"]),
+                "exact_distances": int(hst[-1]["exact_stream"]),
+                "exact_distances_fp32_rows": int(stats[-1]["exact_stream"]), "step_ms": hst[-1]["step_ms"]}
     fast = None
     if args.fast_steps > 0:
         fast = {}
@@ -505,6 +516,7 @@ def main():
         "roofline": roofline(stats, peaks, psrc, measured_traffic(stats[-1]["queries"])),
         "clocks": clocks,
         "plain_fp64": plain,
+        "half_feature_rows": half,
         "fast_settings": fast,
         "batched": batched,
         "served": served,

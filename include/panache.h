@@ -86,6 +86,16 @@ extern "C" {
                                               (series lengths, dtypes, length intervals, k, excl): the
                                               context keeps that request's buffers, copies each new
                                               request's samples into them and launches the graph once */
+#define PANACHE_FLAG_HALF_FEATURES 0x80   /* mixed form: the feature-row cache (Sec. 3.2) held in half
+                                              precision, 64 B per window and anchor instead of 128 B.  The
+                                              rows are the FP32 rows rounded to nearest; the keys and the
+                                              sieve order come from the FP32 rows before rounding.  Every
+                                              Parseval bound read from half rows is tested with an additive
+                                              margin 4 sqrt(m) 2^-11 (the absolute inflation bound in the
+                                              proof of Lemma 5), so no pair is pruned that the FP32 rows'
+                                              bound keeps.  The query's probe margins read its half row, so
+                                              Hamming-1 probes may reorder where margins nearly tie.
+                                              EINVAL with the plain form. */
 
 /* Tunables.  A zero field takes the paper's default (Sec. 4):
  * alpha 16, gamma 8 (R = 128), stride 2, K 16, B 24, d0 12, probe cap 8,
@@ -230,8 +240,9 @@ int panache_last_stats(const panache_ctx *ctx, panache_stats *out);
 int panache_profile_rows(const panache_ctx *ctx, int32_t series_index, uint64_t *keys, int64_t cap);
 
 /* Copies anchor `anchor_index` (0-based in A of series `series_index`) of
- * the last request: its length, the FP32 feature rows [nw][32] (bins
- * re, im interleaved / sigma, zero padded) and the B-bit keys [nw].  Either
+ * the last request: its length, the feature rows [nw][32] as floats (bins
+ * re, im interleaved / sigma, zero padded; the half rows widened under
+ * PANACHE_FLAG_HALF_FEATURES) and the B-bit keys [nw].  Either
  * output may be null.  Used by the parity tests. */
 int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *a_out,
                          float *features, uint32_t *keys, int64_t cap_windows);

@@ -106,6 +106,8 @@ struct PnRequest {
     double *shift = nullptr;
     int32_t *runlen = nullptr;
     float *F = nullptr;
+    __half *Fh = nullptr;      // half-precision rows (PANACHE_FLAG_HALF_FEATURES) in place of F
+    float *sproj = nullptr;    // with Fh: per-window sieve projections from the FP32 rows
     uint32_t *sig = nullptr, *cnt = nullptr, *nclist = nullptr, *qorder = nullptr;
     float2 *wmf = nullptr;
     double2 *wmd = nullptr;
@@ -208,6 +210,7 @@ int check_config(const panache_config &c) {
     if (c.K < 2 || c.K > PN_MAXK || c.B < 1 || c.B > PN_MAXB) return PANACHE_EINVAL;
     if ((int)(c.gamma * c.alpha) > pn::search_max_budget() || c.alpha > (1u << 20)) return PANACHE_EINVAL;
     if (c.probe_cap < 1 || c.probe_cap > 8 || c.precision > 1 || c.topk_mode > 1) return PANACHE_EINVAL;
+    if ((c.flags & PANACHE_FLAG_HALF_FEATURES) && c.precision != PANACHE_MIXED) return PANACHE_EINVAL;
     if (c.chunk < 16 || c.chunk > 4096 || (c.chunk & (c.chunk - 1))) return PANACHE_EINVAL;
     if (c.grid_mult > 64 || c.dm > 16 || c.dp > 16) return PANACHE_EINVAL;
     if (!(c.lambda > 0.0 && c.lambda < 1.0) || !(c.eps0 >= 0.0)) return PANACHE_EINVAL;
@@ -308,7 +311,9 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R,
     // device footprint: resident arrays plus the largest transient (radix sort of the directory)
     size_t b = 0;
     b += (size_t)R.total_samples * (8 + 8 + 16 + 4 + 8);   // x, xs, sq, runlen, staging
-    b += (size_t)R.total_rows * PN_FEAT * 4;                // features
+    const bool half = (c.flags & PANACHE_FLAG_HALF_FEATURES) != 0;
+    b += (size_t)R.total_rows * PN_FEAT * (half ? 2 : 4);   // features
+    if (half) b += (size_t)R.total_windows * 4;             // sieve projections
     b += (size_t)R.total_windows * (16 + 16);               // sig, cnt, nclist, qorder, moments
     b += (size_t)R.total_items * 8 * 2;                     // directory + sort scratch
     b += (size_t)R.total_buckets * 4 + (size_t)R.total_items / 4096 * 1024;
@@ -349,6 +354,9 @@ PnView make_view(panache_ctx *ctx, PnRequest &R) {
     v.shift = R.shift;
     v.runlen = R.runlen;
     v.F = R.F;
+    v.Fh = R.Fh;
+    v.sproj = R.sproj;
+    v.lb_eps = R.Fh ? 4.8828125e-4f : 0.0f;   // round to nearest half: relative error <= 2^-11
     v.sig = R.sig;
     v.cnt = R.cnt;
     v.nclist = R.nclist;
@@ -494,7 +502,12 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) 
     PN_CU(R.alloc(R.sq, R.total_samples + nser));
     PN_CU(R.alloc(R.shift, nser));
     PN_CU(R.alloc(R.runlen, R.total_samples));
-    PN_CU(R.alloc(R.F, R.total_rows * PN_FEAT));
+    if (c.flags & PANACHE_FLAG_HALF_FEATURES) {
+        PN_CU(R.alloc(R.Fh, R.total_rows * PN_FEAT));
+        PN_CU(R.alloc(R.sproj, R.total_windows));
+    } else {
+        PN_CU(R.alloc(R.F, R.total_rows * PN_FEAT));
+    }
     PN_CU(R.alloc(R.sig, R.total_windows));
     PN_CU(R.alloc(R.cnt, R.total_windows));
     PN_CU(R.alloc(R.nclist, R.total_windows));
@@ -1287,7 +1300,14 @@ int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t a
     const int C = (int)ctx->cfg.chunk;
     if (features) {
         std::vector<float> blk((size_t)A.nchunk * C * PN_FEAT);
-        PN_CU(cudaMemcpy(blk.data(), R.F + A.row_off * PN_FEAT, 4 * blk.size(), cudaMemcpyDeviceToHost));
+        if (R.Fh) {
+            std::vector<__half> hb(blk.size());
+            PN_CU(cudaMemcpy(hb.data(), R.Fh + A.row_off * PN_FEAT, sizeof(__half) * hb.size(),
+                             cudaMemcpyDeviceToHost));
+            for (size_t t = 0; t < hb.size(); ++t) blk[t] = __half2float(hb[t]);
+        } else {
+            PN_CU(cudaMemcpy(blk.data(), R.F + A.row_off * PN_FEAT, 4 * blk.size(), cudaMemcpyDeviceToHost));
+        }
         for (int64_t q = 0; q < A.nw; ++q)
             memcpy(features + q * PN_FEAT, blk.data() + pn_row(q, C, A.nchunk) * PN_FEAT, 4 * PN_FEAT);
     }

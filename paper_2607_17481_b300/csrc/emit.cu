@@ -66,9 +66,13 @@ __global__ void k_sieve_keys(PnView v, const PnClass *cls, int32_t ncls, int64_t
     const PnClass &c = cls[ci];
     const PnAnchor &A = v.anchors[c.anchor];
     uint32_t x = v.dir_vals[c.lo + (t - c.moff)];
-    const float *f = v.F + (A.row_off + pn_row(x, v.C, A.nchunk)) * PN_FEAT;
-    const float *g = v.g + ((int64_t)c.anchor * (v.B + 1) + v.B) * PN_FEAT;
-    keys[t] = pn_float_order(pn_margin(g, f, 2 * (v.K - 1)));
+    if (v.Fh) {
+        keys[t] = pn_float_order(v.sproj[A.win_off + x]);   // taken from the FP32 row
+    } else {
+        const float *f = v.F + (A.row_off + pn_row(x, v.C, A.nchunk)) * PN_FEAT;
+        const float *g = v.g + ((int64_t)c.anchor * (v.B + 1) + v.B) * PN_FEAT;
+        keys[t] = pn_float_order(pn_margin(g, f, 2 * (v.K - 1)));
+    }
     vals[t] = (uint32_t)t;
 }
 

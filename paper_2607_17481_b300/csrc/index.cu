@@ -125,14 +125,15 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
     const double *xs = v.x + S.x_off;
     const double shift = v.shift[A.series];
     const int32_t *rl = v.runlen + S.x_off;
-    float *Fa = v.F + A.row_off * PN_FEAT;
+    float *Fa = v.F ? v.F + A.row_off * PN_FEAT : nullptr;
+    __half *Fha = v.Fh ? v.Fh + A.row_off * PN_FEAT : nullptr;
     float *fr = frow[warp];
     const bool bin = lane < kp;
 
-    // projection row of lane l (l < B), in registers
+    // projection row of lane l (l < B; lane B: the sieve direction), in registers
     float g[PN_FEAT - 2];
     {
-        const float *gsrc = v.g + ((int64_t)ai * (B + 1) + (lane < B ? lane : 0)) * PN_FEAT;
+        const float *gsrc = v.g + ((int64_t)ai * (B + 1) + (lane <= B ? lane : 0)) * PN_FEAT;
 #pragma unroll
         for (int t = 0; t < PN_FEAT - 2; ++t) g[t] = gsrc[t];
     }
@@ -189,7 +190,8 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
             fr[2 * lane + 1] = f_im;
         }
         __syncwarp();
-        Fa[(int64_t)pn_row(q, C, A.nchunk) * PN_FEAT + lane] = fr[lane];
+        if (Fha) Fha[(int64_t)pn_row(q, C, A.nchunk) * PN_FEAT + lane] = __float2half_rn(fr[lane]);
+        else Fa[(int64_t)pn_row(q, C, A.nchunk) * PN_FEAT + lane] = fr[lane];
         // <g_l, F> in the fixed FMA order of pn_margin, then the key by ballot
         float mg = 0.0f;
         const float4 *f4 = reinterpret_cast<const float4 *>(fr);
@@ -205,6 +207,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
         }
         const uint32_t bits = __ballot_sync(0xffffffffu, lane < B && mg >= 0.0f);
         if (lane == 0) v.sig[A.win_off + q] = nonconst ? (__brev(bits) >> (32 - B)) : 0u;
+        if (Fha && lane == B) v.sproj[A.win_off + q] = mg;   // sieve key source of the half-row form
         __syncwarp();
         if (q + 1 < qend) {
             const ST delta = (ST)(xs[q + a] - xs[q]);

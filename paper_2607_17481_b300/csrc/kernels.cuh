@@ -1,5 +1,6 @@
 // Kernel-side view of one request and the launch wrappers of every step.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,7 +33,11 @@ struct PnView {
     const double *shift;  // per series shift subtracted before the prefix sums
     const int32_t *runlen;// equal-value run length from each sample, capped at the series' m_max
     // per-window arrays (indexed by anchor.win_off + q)
-    float *F;             // feature rows, anchor.row_off + row(q), PN_FEAT floats each
+    float *F;             // feature rows, anchor.row_off + row(q), PN_FEAT floats each (null with Fh)
+    __half *Fh;           // the same rows rounded to half precision (PANACHE_FLAG_HALF_FEATURES), else null
+    float *sproj;         // with Fh: per window, its projection on the sieve direction g_{a,B+1}
+                          // taken from the FP32 row before rounding
+    float lb_eps;         // relative precision of Fh against the FP32 rows (2^-11), 0 without Fh
     uint32_t *sig;        // B-bit SimHash keys
     uint32_t *cnt;        // inclusive count of non-constant windows with start <= q
     uint32_t *nclist;     // start of the r-th non-constant window
@@ -77,6 +82,48 @@ __host__ __device__ __forceinline__ int64_t pn_row(int64_t q, int32_t C, int64_t
 // The same row with C = 2^cshift and 32-bit window indices (kernels' hot loops).
 __device__ __forceinline__ uint32_t pn_row32(uint32_t q, int cshift, uint32_t nchunk) {
     return (q & ((1u << cshift) - 1u)) * nchunk + (q >> cshift);
+}
+
+// Feature rows in either storage precision: the row block of an anchor
+// (anchor.row_off), then row r of it widened to float, as components
+// 4j..4j+3 (16 B of FP32 row or 8 B of half row) or as component t alone.
+template <bool HALF>
+__device__ __forceinline__ const void *pn_rows(const PnView &v, int64_t row_off) {
+    if constexpr (HALF) return v.Fh + row_off * PN_FEAT;
+    else return v.F + row_off * PN_FEAT;
+}
+
+template <bool HALF>
+__device__ __forceinline__ float4 pn_row_quad(const void *rows, uint32_t r, int j) {
+    if constexpr (HALF) {
+        const uint2 u = reinterpret_cast<const uint2 *>(static_cast<const __half *>(rows) + (size_t)r * PN_FEAT)[j];
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        return make_float4(lo.x, lo.y, hi.x, hi.y);
+    } else {
+        return reinterpret_cast<const float4 *>(static_cast<const float *>(rows) + (size_t)r * PN_FEAT)[j];
+    }
+}
+
+template <bool HALF>
+__device__ __forceinline__ float pn_row_elem(const void *rows, uint32_t r, int t) {
+    if constexpr (HALF) return __half2float(static_cast<const __half *>(rows)[(size_t)r * PN_FEAT + t]);
+    else return static_cast<const float *>(rows)[(size_t)r * PN_FEAT + t];
+}
+
+// Additive margin on a bound read from rows rounded, at relative precision
+// eps, from the FP32 rows.  The proof of Lemma 5 bounds the absolute inflation
+// of the computed bound by 4 sqrt(m) eps, using S = || |a| + |b| || <= sqrt(2) m
+// (the stored bins of a z-normalised window hold at most m^2 / 2 of energy,
+// Parseval).  The feature gap itself moves by at most eps S (each rounded
+// difference is off by at most eps (|a_k| + |b_k|); triangle inequality), so
+// the constant holds with a factor 2 to spare, which also covers the FP32
+// rows' own rounding of that energy.  Subnormal halves add at most 2^-24 per
+// component difference: sqrt(2n/m) 2^-24 in bound units.  A bound that minus
+// this margin still clears a threshold is one the FP32 rows' bound clears.
+__device__ __forceinline__ float pn_row_margin(float eps, int m) {
+    if (eps <= 0.0f) return 0.0f;
+    return 4.0f * sqrtf((float)m) * eps + sqrtf(2.0f * (float)PN_FEAT / (float)m) * 5.9604645e-8f;
 }
 
 // <g_l, F> in a fixed order of fused multiply-adds; the feature kernel and

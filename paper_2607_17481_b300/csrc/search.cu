@@ -33,7 +33,9 @@ constexpr int SR_WARPS = 8;
 constexpr int SR_THREADS = SR_WARPS * 32;
 constexpr int SR_MAXR = 512;   // largest supported budget R
 
-template <class Z>
+// HALF: the rows are read from the half-precision copy, and every bound test
+// carries the rounding margin of pn_row_margin.
+template <class Z, bool HALF>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {
     using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
@@ -71,9 +73,9 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         const int d = pn_depth_dev(P, (uint32_t)v.alpha, v.B);
         const PnLevel &L = v.levels[A.level_begin + d];
 
-        const float *Fa = v.F + A.row_off * PN_FEAT;
+        const void *Fa = pn_rows<HALF>(v, A.row_off);
         const uint32_t nch = (uint32_t)A.nchunk;
-        sF[warp][lane] = Fa[(size_t)pn_row32((uint32_t)q, v.cshift, nch) * PN_FEAT + lane];
+        sF[warp][lane] = pn_row_elem<HALF>(Fa, pn_row32((uint32_t)q, v.cshift, nch), lane);
         __syncwarp();
         float mg = __int_as_float(0x7f800000);
         if (lane < d) {
@@ -150,6 +152,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
         unsigned long long bestkey = PN_EMPTY_KEY;
         const float lbscale = 2.0f / (float)a;
+        const ZT lbmargin = HALF ? (ZT)(shrink * pn_row_margin(v.lb_eps, a)) : (ZT)0;
         // Bounds of 32 candidates at a time: lane l owns candidate l of the
         // block; its row is read by the 8 lanes of a group (4 rows per step,
         // 8 steps, every load issued before the sums need it), the 8 partial
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
             for (int j = 0; j < 8; ++j) {
                 const int k = 4 * j + (lane >> 3);
                 const uint32_t ro = __shfl_sync(0xffffffffu, roff, k);
-                fc[j] = k < nblk ? reinterpret_cast<const float4 *>(Fa + (size_t)ro * PN_FEAT)[lane & 7] : fq;
+                fc[j] = k < nblk ? pn_row_quad<HALF>(Fa, ro, lane & 7) : fq;
             }
             float acc[8];
 #pragma unroll
@@ -220,14 +223,20 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
                 }
                 const uint32_t cb = __shfl_sync(0xffffffffu, c, bl);
                 const unsigned long long kb = __shfl_sync(0xffffffffu, kc, bl);
-                if (bl < nblk && (ZT)bm < Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kb))) {
+                ZT tb = Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kb));
+                if constexpr (HALF) tb += lbmargin;
+                if (bl < nblk && (ZT)bm < tb) {
                     eval_one<Z>(v, zq, cb, kb, S.x_off, A.win_off, a, (uint32_t)q, prow, bestkey, lane);
                     n_lb += 1;
                 }
                 if (lane == bl) lbs = __int_as_float(0x7f800000);   // done: not retested
             }
             bool surv = false;
-            if (lane < nblk) surv = (ZT)lbs < Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kc));
+            if (lane < nblk) {
+                ZT tc = Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kc));
+                if constexpr (HALF) tc += lbmargin;
+                surv = (ZT)lbs < tc;
+            }
             const uint32_t sm = __ballot_sync(0xffffffffu, surv);
             __syncwarp();
             if (surv) {
@@ -263,16 +272,16 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
     }
 }
 
-template <class Z>
+template <class Z, bool HALF>
 cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     const int zcap = (a_max + 3) & ~3;
     const size_t sm = (sizeof(unsigned long long) + sizeof(uint32_t)) * (size_t)v.R * SR_WARPS +
                       sizeof(typename Z::T) * (size_t)zcap * SR_WARPS;
-    cudaError_t e = pn_allow_smem(k_search<Z>, sm);
+    cudaError_t e = pn_allow_smem(k_search<Z, HALF>, sm);
     if (e != cudaSuccess) return e;
     int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
     unsigned g = (unsigned)(need < grid_blocks ? need : grid_blocks);
-    k_search<Z><<<g, SR_THREADS, sm, st>>>(v, total, zcap);
+    k_search<Z, HALF><<<g, SR_THREADS, sm, st>>>(v, total, zcap);
     return cudaGetLastError();
 }
 
@@ -282,8 +291,12 @@ int search_max_budget() { return SR_MAXR; }
 
 cudaError_t launch_search(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;
-    if (v.precision == 0) return launch_t<ZPlain>(v, total, grid_blocks, a_max, st);
-    return v.x1 ? launch_t<ZMix1>(v, total, grid_blocks, a_max, st) : launch_t<ZMix2>(v, total, grid_blocks, a_max, st);
+    if (v.precision == 0) return launch_t<ZPlain, false>(v, total, grid_blocks, a_max, st);
+    if (v.Fh)   // half rows: the mixed form only (checked at configuration)
+        return v.x1 ? launch_t<ZMix1, true>(v, total, grid_blocks, a_max, st)
+                    : launch_t<ZMix2, true>(v, total, grid_blocks, a_max, st);
+    return v.x1 ? launch_t<ZMix1, false>(v, total, grid_blocks, a_max, st)
+                : launch_t<ZMix2, false>(v, total, grid_blocks, a_max, st);
 }
 
 }  // namespace pn

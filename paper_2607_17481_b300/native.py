@@ -22,6 +22,7 @@ TOPK_GLOBAL, TOPK_PER_LENGTH = 0, 1
 FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING, FLAG_INDEX_ONLY = 0x1, 0x2, 0x4, 0x8, 0x10
 FLAG_FP64_ANCHORS = 0x20
 FLAG_GRAPH = 0x40
+FLAG_HALF_FEATURES = 0x80
 
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",

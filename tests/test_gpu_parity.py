@@ -328,3 +328,45 @@ def test_exhaustive_sieve(pn, small, small_exact, precision):
     from parity import compare
     r = compare(s.x, got, ref)
     assert r["misses"] == 0 and r["bad_dist"] == 0, r
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_half_feature_rows(pn, small, small_exact, mode):
+    """Half-precision feature rows (the row cache of Sec. 3.2 at half the
+    bytes): the rows are the FP32 rows rounded to nearest, the keys come from
+    the FP32 rows, and every bound read from half rows carries the absolute
+    inflation margin of Lemma 5's proof.  The margin's premises are checked on
+    the rows, the motifs equal the FP32-row form's (global mode: the
+    oracle's), and the device footprint shrinks."""
+    s = small
+    full, got_full = run(pn, s, precision=1, topk_mode=mode)
+    half, got_half = run(pn, s, precision=1, topk_mode=mode, flags=pn.FLAG_HALF_FEATURES)
+    assert np.array_equal(got_half[["m", "i", "j"]], got_full[["m", "i", "j"]])
+    assert np.allclose(got_half["d"], got_full["d"], rtol=1e-12, atol=0)
+    assert half.stats()["device_bytes"] < full.stats()["device_bytes"]
+    for ai in (0, 5, 16):
+        a = spectral.anchors(s.m_min, s.m_max)[ai]
+        nw = s.x.shape[0] - a + 1
+        a0, F0, k0 = full.anchor_state(0, ai, nw)
+        a1, F1, k1 = half.anchor_state(0, ai, nw)
+        assert a0 == a1 == a and np.array_equal(k0, k1)          # keys from the FP32 rows
+        # round to nearest even, as numpy's float16 conversion
+        assert np.array_equal(F1, F0.astype(np.float16).astype(np.float32))
+        # the margin's premises: the stored bins of a z-normalised window hold
+        # at most a^2 / 2 of energy (Parseval), and a bound read from half rows
+        # is within 4 sqrt(a) 2^-11 of the FP32 rows' bound
+        E = (F0.astype(np.float64) ** 2).sum(axis=1)
+        assert E.max() <= 0.5 * a * a * (1 + 1e-3)
+        rng = np.random.default_rng(ai)
+        i, j = rng.integers(0, nw, 8192), rng.integers(0, nw, 8192)
+        lb0 = np.sqrt(2.0 / a * ((F0[i].astype(np.float64) - F0[j]) ** 2).sum(axis=1))
+        lb1 = np.sqrt(2.0 / a * ((F1[i].astype(np.float64) - F1[j]) ** 2).sum(axis=1))
+        assert np.all(np.abs(lb1 - lb0) <= spectral.lb_inflation_bound(a, 2.0 ** -11))
+    if mode == 0:
+        from parity import compare
+        P, I = small_exact
+        r = compare(s.x, got_half, topk.select(P, I, s.m_min, s.k, topk.GLOBAL))
+        assert r["misses"] == 0 and r["bad_dist"] == 0, r
+    with pytest.raises(pn.PanacheError) as e:
+        pn.Context(precision=0, flags=pn.FLAG_HALF_FEATURES)      # the plain form keeps FP32 rows
+    assert e.value.code == -1

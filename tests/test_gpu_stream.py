@@ -63,6 +63,18 @@ def test_snapshots_equal_offline_prefixes(pn, small, precision, mode):
     st.close()
 
 
+def test_half_feature_rows_stream_equals_offline(pn, small):
+    """Half-precision rows in a resident stream: the rows grow with the stream
+    like the FP32 rows, and the snapshot equals the offline request."""
+    s = small
+    ctx = pn.Context(topk_mode=0, precision=1, flags=pn.FLAG_HALF_FEATURES)
+    st = ctx.stream(s.m_min, s.m_max, s.k, s.excl)
+    for a, b in chunks(s.x.shape[0], 15, 200, 1500):
+        st.append(s.x[a:b])
+    assert np.array_equal(st.topk(), ctx.pmp(s.x, s.m_min, s.m_max, s.k, s.excl))
+    st.close()
+
+
 def test_stream_matches_oracle_global(pn, small):
     s = small
     ctx = pn.Context(topk_mode=0)

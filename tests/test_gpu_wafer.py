@@ -59,6 +59,15 @@ def test_prefix_global_top20(pn, wafer, golden, precision):
     assert r["bad_dist"] == 0
 
 
+def test_prefix_global_top20_half_feature_rows(pn, wafer, golden):
+    """Half-precision feature rows on the wafer-like prefix: the same golden top-20."""
+    from parity import compare
+    x, got = _prefix_run(pn, wafer, precision=1, topk_mode=0, flags=pn.FLAG_HALF_FEATURES)
+    r = compare(x.astype(np.float64), got, golden[0])
+    assert r["misses"] == 0, r["miss_list"]
+    assert r["bad_dist"] == 0
+
+
 def test_prefix_per_length_top20(pn, wafer, golden):
     """Anchor stride 1: all 1020 cells.  The paper's stride 2 is reported separately."""
     from parity import compare
