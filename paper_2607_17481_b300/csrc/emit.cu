@@ -1,6 +1,7 @@
 // Emit stage (Sec. 3.6, Algorithm 2): hot-class sieve, local completion and
 // the zero-snapped top-k selection with FP64 re-verification.
 #include <algorithm>
+#include <type_traits>
 
 #include "distance.cuh"
 #include "emit.cuh"
@@ -93,8 +94,9 @@ __global__ void k_sieve_rekey(PnView v, const PnClass *cls, int32_t ncls, int64_
 // bound-filtered, exact.  The same machinery as the streaming search: u's
 // z-normalised window staged once, bounds of up to 32 neighbours with each
 // row read by 8 lanes, threshold tests lane-parallel, survivors evaluated
-// four at a time against the staged window, both cells updated.
-template <class Z>
+// four at a time against the staged window, both cells updated.  HALF: rows
+// read from the half-precision copy, every bound test with its rounding margin.
+template <class Z, bool HALF>
 __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass *cls, int64_t total,
                                                         const uint32_t *member_class, const uint32_t *members, int w,
                                                         int exhaustive, int zcap) {
@@ -120,9 +122,9 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
         const uint32_t xu = members[p];
         const auto mu_ = Z::load(v, A.win_off + xu);
         if (Z::degenerate(mu_)) continue;
-        const float *Fa = v.F + A.row_off * PN_FEAT;
+        const void *Fa = pn_rows<HALF>(v, A.row_off);
         const uint32_t nch = (uint32_t)A.nchunk;
-        sF[warp][lane] = Fa[(size_t)pn_row32(xu, v.cshift, nch) * PN_FEAT + lane];
+        sF[warp][lane] = pn_row_elem<HALF>(Fa, pn_row32(xu, v.cshift, nch), lane);
         {
             const auto *xs = Z::samples(v, S.x_off + xu);
             for (int r = lane; r < a; r += 32) zu[r] = Z::z(mu_, xs[r]);
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
         const float lbscale = 2.0f / (float)a;
+        const ZT lbmargin = HALF ? (ZT)(shrink * pn_row_margin(v.lb_eps, a)) : (ZT)0;
         unsigned long long bestkey = PN_EMPTY_KEY;
         for (int64_t b0 = u + 1; b0 < vend; b0 += 32) {
             const int nblk = (int)min((int64_t)32, vend - b0);
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
             for (int j = 0; j < 8; ++j) {
                 const int k = 4 * j + (lane >> 3);
                 const uint32_t ro = __shfl_sync(0xffffffffu, roff, k);
-                fc[j] = k < nblk ? reinterpret_cast<const float4 *>(Fa + (size_t)ro * PN_FEAT)[lane & 7] : fq;
+                fc[j] = k < nblk ? pn_row_quad<HALF>(Fa, ro, lane & 7) : fq;
             }
             float acc[8];
 #pragma unroll
@@ -176,7 +179,9 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
                     kc = __ldcg(&prow[xv]);
                     const float lbs = shrink * sqrtf(lbscale * lbsq);
                     const ZT tu = Z::fmn(Z::cell(bestkey), Z::cell(__ldcg(&prow[xu])));
-                    surv = (ZT)lbs < Z::fmx(tu, Z::cell(kc));
+                    ZT tt = Z::fmx(tu, Z::cell(kc));
+                    if constexpr (HALF) tt += lbmargin;
+                    surv = (ZT)lbs < tt;
                 }
             }
             const uint32_t sm = __ballot_sync(0xffffffffu, surv);
@@ -821,14 +826,24 @@ cudaError_t sieve_tiles_t(const PnView &v, const PnClass *cls, int32_t ncls, con
     return e;
 }
 
+template <class Z, bool HALF>
+cudaError_t sieve_pairs_t(const PnView &v, const PnClass *cls, int64_t nmem, const uint32_t *keys,
+                          const uint32_t *vals, int w, int exhaustive, int zcap, int64_t blocks, cudaStream_t st) {
+    const size_t sm = sizeof(typename Z::T) * zcap * 8;
+    cudaError_t e = pn_allow_smem(k_sieve_pairs<Z, HALF>, sm);
+    if (e != cudaSuccess) return e;
+    k_sieve_pairs<Z, HALF><<<(unsigned)blocks, 256, sm, st>>>(v, cls, nmem, keys, vals, w, exhaustive, zcap);
+    return cudaGetLastError();
+}
+
+// Per-member sieve: the plain form always, the mixed form for bands wider
+// than the band kernel's; half rows only occur in the mixed form.
 template <class Z>
 cudaError_t sieve_t(const PnView &v, const PnClass *cls, int64_t nmem, const uint32_t *keys, const uint32_t *vals,
                     int w, int exhaustive, int zcap, int64_t blocks, cudaStream_t st) {
-    const size_t sm = sizeof(typename Z::T) * zcap * 8;
-    cudaError_t e = pn_allow_smem(k_sieve_pairs<Z>, sm);
-    if (e != cudaSuccess) return e;
-    k_sieve_pairs<Z><<<(unsigned)blocks, 256, sm, st>>>(v, cls, nmem, keys, vals, w, exhaustive, zcap);
-    return cudaGetLastError();
+    if constexpr (!std::is_same<Z, ZPlain>::value)
+        if (v.Fh) return sieve_pairs_t<Z, true>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
+    return sieve_pairs_t<Z, false>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
 }
 
 }  // namespace

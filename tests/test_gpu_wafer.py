@@ -68,6 +68,17 @@ def test_prefix_global_top20_half_feature_rows(pn, wafer, golden):
     assert r["bad_dist"] == 0
 
 
+def test_prefix_wide_sieve_half_feature_rows(pn, wafer):
+    """A sieve band wider than the band kernel's (w = 32) runs the per-member
+    sieve in the mixed form; with half rows it reads them with the rounding
+    margin and reports the FP32-row form's motifs."""
+    x, full = _prefix_run(pn, wafer, precision=1, topk_mode=0, sieve_w=32)
+    ctx = pn.Context(precision=1, topk_mode=0, sieve_w=32, flags=pn.FLAG_HALF_FEATURES)
+    half = ctx.pmp(x, 100, 150, 20, 150)
+    assert ctx.stats()["exact_sieve"] > 0
+    assert np.array_equal(half[["m", "i", "j"]], full[["m", "i", "j"]])
+
+
 def test_prefix_per_length_top20(pn, wafer, golden):
     """Anchor stride 1: all 1020 cells.  The paper's stride 2 is reported separately."""
     from parity import compare
