@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
     __shared__ uint32_t scand[8][32];
     __shared__ unsigned long long snap[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    ZT *zu = reinterpret_cast<ZT *>(zsm) + warp * zcap;
+    typename Z::Q *zu = reinterpret_cast<typename Z::Q *>(zsm) + warp * zcap;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const float shrink = 1.0f - v.lam;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
         sF[warp][lane] = pn_row_elem<HALF>(Fa, pn_row32(xu, v.cshift, nch), lane);
         {
             const auto *xs = Z::samples(v, S.x_off + xu);
-            for (int r = lane; r < a; r += 32) zu[r] = Z::z(mu_, xs[r]);
+            for (int r = lane; r < a; r += 32) zu[r] = Z::stage(Z::z(mu_, xs[r]));
         }
         __syncwarp();
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
@@ -829,7 +829,7 @@ cudaError_t sieve_tiles_t(const PnView &v, const PnClass *cls, int32_t ncls, con
 template <class Z, bool HALF>
 cudaError_t sieve_pairs_t(const PnView &v, const PnClass *cls, int64_t nmem, const uint32_t *keys,
                           const uint32_t *vals, int w, int exhaustive, int zcap, int64_t blocks, cudaStream_t st) {
-    const size_t sm = sizeof(typename Z::T) * zcap * 8;
+    const size_t sm = sizeof(typename Z::Q) * zcap * 8;
     cudaError_t e = pn_allow_smem(k_sieve_pairs<Z, HALF>, sm);
     if (e != cudaSuccess) return e;
     k_sieve_pairs<Z, HALF><<<(unsigned)blocks, 256, sm, st>>>(v, cls, nmem, keys, vals, w, exhaustive, zcap);

@@ -1,6 +1,8 @@
 // Exact-distance evaluation of bound survivors against one staged window,
 // shared by the streaming search and the hot-class sieve.
 #pragma once
+#include <type_traits>
+
 #include "zops.cuh"
 
 namespace pn {
@@ -11,7 +13,7 @@ namespace pn {
 // only when the new key is below the snapshot read for the bound test (cells
 // only decrease, so a key at or above the snapshot cannot change the cell).
 template <class Z>
-__device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T *zq, const uint32_t *sc,
+__device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::Q *zq, const uint32_t *sc,
                                            const unsigned long long *sk, int nb, int64_t x_off, int64_t win_off,
                                            int a, uint32_t q, unsigned long long *prow,
                                            unsigned long long &bestkey, int lane) {
@@ -22,18 +24,42 @@ __device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T 
     const auto *x0 = Z::samples(v, x_off + c0), *x1 = Z::samples(v, x_off + c1);
     const auto *x2 = Z::samples(v, x_off + c2), *x3 = Z::samples(v, x_off + c3);
     ZT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    // two iterations in flight: eight independent sample loads per lane
+    if constexpr (std::is_same<typename Z::X, float>::value) {
+        // Float32 series: packed two-wide FP32, survivors (0, 1) and (2, 3)
+        // side by side, the staged sample (z, z) one 8-byte load.
+        // fma(x, -1/sigma, mu/sigma) is exactly -z, so zr + (-z) is exactly
+        // zr - z: the sums are the scalar loop's bit for bit, at half the FP32
+        // instructions.  (Float64 series keep the scalar loop: their (hi, lo)
+        // samples need more registers than the packed form leaves.)
+        const float2 ns01 = make_float2(-m0.x, -m1.x), no01 = make_float2(-m0.y, -m1.y);
+        const float2 ns23 = make_float2(-m2.x, -m3.x), no23 = make_float2(-m2.y, -m3.y);
+        float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
 #pragma unroll 2
-    for (int r = lane; r < a; r += 32) {
-        const ZT zr = zq[r];
-        const ZT d0 = zr - Z::z(m0, x0[r]);
-        const ZT d1 = zr - Z::z(m1, x1[r]);
-        const ZT d2 = zr - Z::z(m2, x2[r]);
-        const ZT d3 = zr - Z::z(m3, x3[r]);
-        a0 = fma(d0, d0, a0);
-        a1 = fma(d1, d1, a1);
-        a2 = fma(d2, d2, a2);
-        a3 = fma(d3, d3, a3);
+        for (int r = lane; r < a; r += 32) {
+            const float2 zz = zq[r];
+            const float2 d01 = __fadd2_rn(zz, Z::nz2(x0[r], x1[r], ns01, no01));
+            const float2 d23 = __fadd2_rn(zz, Z::nz2(x2[r], x3[r], ns23, no23));
+            s01 = __ffma2_rn(d01, d01, s01);
+            s23 = __ffma2_rn(d23, d23, s23);
+        }
+        a0 = s01.x;
+        a1 = s01.y;
+        a2 = s23.x;
+        a3 = s23.y;
+    } else {
+        // two iterations in flight: eight independent sample loads per lane
+#pragma unroll 2
+        for (int r = lane; r < a; r += 32) {
+            const ZT zr = Z::qval(zq[r]);
+            const ZT d0 = zr - Z::z(m0, x0[r]);
+            const ZT d1 = zr - Z::z(m1, x1[r]);
+            const ZT d2 = zr - Z::z(m2, x2[r]);
+            const ZT d3 = zr - Z::z(m3, x3[r]);
+            a0 = fma(d0, d0, a0);
+            a1 = fma(d1, d1, a1);
+            a2 = fma(d2, d2, a2);
+            a3 = fma(d3, d3, a3);
+        }
     }
     // transposed reduction of the four sums (6 shuffles): afterwards lanes
     // 8v..8v+7 hold the total of survivor v
@@ -67,7 +93,7 @@ __device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::T 
 
 // Exact distance of one candidate (warp-cooperative), same updates as eval_batch.
 template <class Z>
-__device__ __forceinline__ void eval_one(const PnView &v, const typename Z::T *zq, uint32_t c,
+__device__ __forceinline__ void eval_one(const PnView &v, const typename Z::Q *zq, uint32_t c,
                                          unsigned long long snapkey, int64_t x_off, int64_t win_off, int a,
                                          uint32_t q, unsigned long long *prow, unsigned long long &bestkey,
                                          int lane) {
@@ -77,7 +103,7 @@ __device__ __forceinline__ void eval_one(const PnView &v, const typename Z::T *z
     const auto *x = Z::samples(v, x_off + c);
     ZT acc = 0;
     for (int r = lane; r < a; r += 32) {
-        const ZT dz = zq[r] - Z::z(m, x[r]);
+        const ZT dz = Z::qval(zq[r]) - Z::z(m, x[r]);
         acc = fma(dz, dz, acc);
     }
     const ZT dd = Z::finish(acc);

@@ -45,8 +45,9 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int R = v.R;
     unsigned long long *snap = reinterpret_cast<unsigned long long *>(dsm) + warp * R;
-    ZT *zq = reinterpret_cast<ZT *>(reinterpret_cast<unsigned long long *>(dsm) + SR_WARPS * R) + warp * zcap;
-    uint32_t *scand = reinterpret_cast<uint32_t *>(reinterpret_cast<ZT *>(reinterpret_cast<unsigned long long *>(dsm) +
+    using ZQ = typename Z::Q;
+    ZQ *zq = reinterpret_cast<ZQ *>(reinterpret_cast<unsigned long long *>(dsm) + SR_WARPS * R) + warp * zcap;
+    uint32_t *scand = reinterpret_cast<uint32_t *>(reinterpret_cast<ZQ *>(reinterpret_cast<unsigned long long *>(dsm) +
                                                                         SR_WARPS * R) + SR_WARPS * zcap) + warp * R;
     if (threadIdx.x < 3) s_stat[threadIdx.x] = 0ull;
     __syncthreads();
@@ -145,11 +146,12 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         {
             const auto mq = Z::load(v, w);
             const auto *xq = Z::samples(v, S.x_off + q);
-            for (int r = lane; r < a; r += 32) zq[r] = Z::z(mq, xq[r]);
+            for (int r = lane; r < a; r += 32) zq[r] = Z::stage(Z::z(mq, xq[r]));
         }
         __syncwarp();
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
+        const float2 nfxy = make_float2(-fq.x, -fq.y), nfzw = make_float2(-fq.z, -fq.w);
         unsigned long long bestkey = PN_EMPTY_KEY;
         const float lbscale = 2.0f / (float)a;
         const ZT lbmargin = HALF ? (ZT)(shrink * pn_row_margin(v.lb_eps, a)) : (ZT)0;
@@ -176,11 +178,16 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
                 const uint32_t ro = __shfl_sync(0xffffffffu, roff, k);
                 fc[j] = k < nblk ? pn_row_quad<HALF>(Fa, ro, lane & 7) : fq;
             }
+            // squared differences of a quarter row, packed two-wide: (c - q) is
+            // the exact negation of (q - c); the four squares are summed as
+            // (dx^2 + dz^2) + (dy^2 + dw^2)
             float acc[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float dx = fq.x - fc[j].x, dy = fq.y - fc[j].y, dz = fq.z - fc[j].z, dw = fq.w - fc[j].w;
-                acc[j] = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, dw * dw)));
+                const float2 dxy = __fadd2_rn(make_float2(fc[j].x, fc[j].y), nfxy);
+                const float2 dzw = __fadd2_rn(make_float2(fc[j].z, fc[j].w), nfzw);
+                const float2 s2 = __ffma2_rn(dxy, dxy, __fmul2_rn(dzw, dzw));
+                acc[j] = s2.x + s2.y;
             }
             // transposed reduction over the 8 lanes of a group: afterwards lane L
             // holds the sum of candidate 4 (L & 7) + (L >> 3)
@@ -276,7 +283,7 @@ template <class Z, bool HALF>
 cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     const int zcap = (a_max + 3) & ~3;
     const size_t sm = (sizeof(unsigned long long) + sizeof(uint32_t)) * (size_t)v.R * SR_WARPS +
-                      sizeof(typename Z::T) * (size_t)zcap * SR_WARPS;
+                      sizeof(typename Z::Q) * (size_t)zcap * SR_WARPS;
     cudaError_t e = pn_allow_smem(k_search<Z, HALF>, sm);
     if (e != cudaSuccess) return e;
     int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
