@@ -54,10 +54,19 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
     unsigned long long n_q = 0, n_c = 0, n_lb = 0;
     const int dims = 2 * (v.K - 1);
     const float shrink = 1.0f - v.lam;
+    // anchor of the previous query and its window range [a_lo, a_hi): the
+    // query order keeps each anchor's queries together, so the search over
+    // the anchor table is mostly skipped
+    int ai = 0;
+    int64_t a_lo = 1, a_hi = 0;
 
     for (int64_t it = (int64_t)blockIdx.x * SR_WARPS + warp; it < total; it += (int64_t)gridDim.x * SR_WARPS) {
         const int64_t w = v.qorder[it];
-        const int ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
+        if (w < a_lo || w >= a_hi) {
+            ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
+            a_lo = v.anchors[ai].win_off;
+            a_hi = ai + 1 < v.nanchors ? v.anchors[ai + 1].win_off : INT64_MAX;
+        }
         const PnAnchor &A = v.anchors[ai];
         const int s = A.series;
         const PnSeries &S = v.series[s];
@@ -84,7 +93,9 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
             // the transposed copy (one coalesced 128-byte row per dimension)
             const float *gt = v.gT + (int64_t)ai * PN_FEAT * 32 + lane;
             float acc = 0.0f;
-            for (int t = 0; t < dims; ++t) acc = fmaf(gt[t * 32], sF[warp][t], acc);
+#pragma unroll
+            for (int t = 0; t < PN_FEAT - 2; ++t)
+                if (t < dims) acc = fmaf(gt[t * 32], sF[warp][t], acc);
             mg = fabsf(acc);
             if (!(mg <= 3.0e38f)) mg = 3.0e38f;            // non-finite input: still a bit below d
         }
@@ -128,7 +139,11 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
             // split as rest = qh h2 + rh so only t rh (< 2^18) is divided
             const int h1 = (rem + 1) / 2, h2 = rem / 2, h2d = max(1, h2);
             const int rest = sz - h1;
-            const int qh = rest / h2d, rh = rest - qh * h2d;
+            int qh = 0, rh = 0;
+            if (sz > rem) {                                // warp-uniform: only an overflowing bucket divides
+                qh = rest / h2d;
+                rh = rest - qh * h2d;
+            }
             for (int t = lane; t < cnt; t += 32) {
                 int pos;
                 if (sz <= rem) pos = t;
