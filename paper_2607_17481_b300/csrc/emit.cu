@@ -280,16 +280,26 @@ __global__ void __launch_bounds__(256) k_sieve_band(PnView v, const PnClass *cls
                 zs[r][row] = z;
             }
             __syncthreads();
+            // pairs q and q + 1 of a thread side by side in packed two-wide
+            // FP32: fma(z_v, -1, z_u) is exactly z_u - z_v, so the sums are
+            // the scalar ones bit for bit
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int e = tid + q * blockDim.x;
-                if (q < per && e < npair) {
-                    const int u = e / w, vv = u + 1 + e % w;
+            for (int q = 0; q < 4; q += 2) {
+                const int e0 = tid + q * blockDim.x, e1 = e0 + blockDim.x;
+                const bool in0 = q < per && e0 < npair, in1 = q + 1 < per && e1 < npair;
+                if (in0) {
+                    const int u0 = e0 / w, v0 = u0 + 1 + e0 % w;
+                    const int u1 = in1 ? e1 / w : 0, v1 = in1 ? u1 + 1 + e1 % w : 0;
+                    const float2 neg1 = make_float2(-1.0f, -1.0f);
+                    float2 s2 = make_float2(acc[q], acc[q + 1]);
 #pragma unroll 8
                     for (int r = 0; r < SB_K; ++r) {
-                        const float d = zs[r][u] - zs[r][vv];
-                        acc[q] = fmaf(d, d, acc[q]);
+                        const float2 d = __ffma2_rn(make_float2(zs[r][v0], zs[r][v1]), neg1,
+                                                    make_float2(zs[r][u0], zs[r][u1]));
+                        s2 = __ffma2_rn(d, d, s2);
                     }
+                    acc[q] = s2.x;
+                    acc[q + 1] = s2.y;
                 }
             }
             __syncthreads();
