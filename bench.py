@@ -272,7 +272,8 @@ def run_served(pn, args, rate=None):
         total = 50_000 + 1024 * int(50 * args.served_seconds + 2)
         x = workloads.random_walk(g, total) if kind == "random_walk" else workloads.ecg_like(g, total)
         live.append(x.astype(np.float32))
-    sv = pn.Server(slots=4, hbm_budget_bytes=120 * 10 ** 9, precision=1, topk_mode=pn.TOPK_GLOBAL)
+    sv = pn.Server(slots=4, hbm_budget_bytes=120 * 10 ** 9, precision=1, topk_mode=pn.TOPK_GLOBAL,
+                   flags=pn.FLAG_HALF_FEATURES if args.served_half else 0)
     # live streams reserve their resident state from the budget; one that
     # does not fit is refused (EBUDGET) and left out, and a stream whose
     # growth is refused keeps its samples and stops taking appends
@@ -325,7 +326,8 @@ def run_served(pn, args, rate=None):
     sv.close()
     return {"requests": int(next_req), "stream_topk_requests": int(len(tickets) - next_req),
             "live_streams": len(live), "live_streams_requested": args.served_streams,
-            "stream_admissions_refused": refused, "appended_samples": int(sum(f - 50_000 for f in fed)),
+            "stream_admissions_refused": refused, "feature_rows": "half" if args.served_half else "fp32",
+            "appended_samples": int(sum(f - 50_000 for f in fed)),
             "arrival_rate_per_s": rate, "window_s": args.served_seconds,
             "completed": int(st["completed"]), "failed": int(st["failed"]),
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
@@ -386,6 +388,8 @@ def main():
     ap.add_argument("--served-seconds", type=float, default=2.0, help="arrival window of the served leg (0: skip)")
     ap.add_argument("--served-rate", type=float, default=200.0, help="Poisson request arrivals per second")
     ap.add_argument("--served-streams", type=int, default=32, help="live streams (the workload names 256)")
+    ap.add_argument("--served-half", action="store_true",
+                    help="served leg with half-precision feature rows (smaller stream reservations)")
     ap.add_argument("--batched-loop", type=int, default=64,
                     help="series of the same batch timed one pmp call at a time (0: skip)")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])
