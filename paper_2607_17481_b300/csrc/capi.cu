@@ -107,7 +107,7 @@ struct PnRequest {
     int32_t *runlen = nullptr;
     float *F = nullptr;
     __half *Fh = nullptr;      // half-precision rows (PANACHE_FLAG_HALF_FEATURES) in place of F
-    float *sproj = nullptr;    // with Fh: per-window sieve projections from the FP32 rows
+    float *sproj = nullptr;    // per-window sieve projections, from the FP32 rows
     uint32_t *sig = nullptr, *cnt = nullptr, *nclist = nullptr, *qorder = nullptr;
     float2 *wmf = nullptr;
     double2 *wmd = nullptr;
@@ -313,7 +313,7 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R,
     b += (size_t)R.total_samples * (8 + 8 + 16 + 4 + 8);   // x, xs, sq, runlen, staging
     const bool half = (c.flags & PANACHE_FLAG_HALF_FEATURES) != 0;
     b += (size_t)R.total_rows * PN_FEAT * (half ? 2 : 4);   // features
-    if (half) b += (size_t)R.total_windows * 4;             // sieve projections
+    b += (size_t)R.total_windows * 4;                       // sieve projections
     b += (size_t)R.total_windows * (16 + 16);               // sig, cnt, nclist, qorder, moments
     b += (size_t)R.total_items * 8 * 2;                     // directory + sort scratch
     b += (size_t)R.total_buckets * 4 + (size_t)R.total_items / 4096 * 1024;
@@ -502,12 +502,9 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) 
     PN_CU(R.alloc(R.sq, R.total_samples + nser));
     PN_CU(R.alloc(R.shift, nser));
     PN_CU(R.alloc(R.runlen, R.total_samples));
-    if (c.flags & PANACHE_FLAG_HALF_FEATURES) {
-        PN_CU(R.alloc(R.Fh, R.total_rows * PN_FEAT));
-        PN_CU(R.alloc(R.sproj, R.total_windows));
-    } else {
-        PN_CU(R.alloc(R.F, R.total_rows * PN_FEAT));
-    }
+    if (c.flags & PANACHE_FLAG_HALF_FEATURES) PN_CU(R.alloc(R.Fh, R.total_rows * PN_FEAT));
+    else PN_CU(R.alloc(R.F, R.total_rows * PN_FEAT));
+    PN_CU(R.alloc(R.sproj, R.total_windows));
     PN_CU(R.alloc(R.sig, R.total_windows));
     PN_CU(R.alloc(R.cnt, R.total_windows));
     PN_CU(R.alloc(R.nclist, R.total_windows));

@@ -58,7 +58,8 @@ __global__ void k_hot_compact(PnView v, const int64_t *slot_off, int64_t total, 
     cls[cid[t]] = c;
 }
 
-// Sort key of a member: its projection on the sieve direction g_{a,B+1}.
+// Sort key of a member: its projection on the sieve direction g_{a,B+1},
+// stored per window by the feature kernel (one 4-byte read, not a row).
 __global__ void k_sieve_keys(PnView v, const PnClass *cls, int32_t ncls, int64_t total, uint32_t *keys,
                              uint32_t *vals) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -67,13 +68,7 @@ __global__ void k_sieve_keys(PnView v, const PnClass *cls, int32_t ncls, int64_t
     const PnClass &c = cls[ci];
     const PnAnchor &A = v.anchors[c.anchor];
     uint32_t x = v.dir_vals[c.lo + (t - c.moff)];
-    if (v.Fh) {
-        keys[t] = pn_float_order(v.sproj[A.win_off + x]);   // taken from the FP32 row
-    } else {
-        const float *f = v.F + (A.row_off + pn_row(x, v.C, A.nchunk)) * PN_FEAT;
-        const float *g = v.g + ((int64_t)c.anchor * (v.B + 1) + v.B) * PN_FEAT;
-        keys[t] = pn_float_order(pn_margin(g, f, 2 * (v.K - 1)));
-    }
+    keys[t] = pn_float_order(v.sproj[A.win_off + x]);
     vals[t] = (uint32_t)t;
 }
 
@@ -229,7 +224,7 @@ __global__ void __launch_bounds__(256) k_sieve_band(PnView v, const PnClass *cls
     __shared__ uint32_t s_x[SB_U + SB_WMAX], s_cls[SB_U + SB_WMAX];
     __shared__ int32_t s_a[SB_U + SB_WMAX];
     __shared__ float2 s_m[SB_U + SB_WMAX];
-    __shared__ int64_t s_xoff[SB_U + SB_WMAX];
+    __shared__ const typename Z::X *s_xp[SB_U + SB_WMAX];   // first sample of each row's window
     __shared__ unsigned long long colmin[SB_U + SB_WMAX];
     __shared__ unsigned long long s_ex;
     const int tid = threadIdx.x;
@@ -245,7 +240,7 @@ __global__ void __launch_bounds__(256) k_sieve_band(PnView v, const PnClass *cls
             uint32_t x = 0, ci = 0xFFFFFFFFu;
             int a = 0;
             float2 m = make_float2(0.0f, 0.0f);
-            int64_t xoff = 0;
+            const typename Z::X *xp = nullptr;
             if (p < nmem) {
                 ci = member_class[p];
                 x = members[p];
@@ -253,13 +248,13 @@ __global__ void __launch_bounds__(256) k_sieve_band(PnView v, const PnClass *cls
                 a = A.a;
                 const auto mm = Z::load(v, A.win_off + x);
                 m = make_float2(mm.x, mm.y);
-                xoff = v.series[A.series].x_off;
+                xp = Z::samples(v, v.series[A.series].x_off + x);
             }
             s_x[tid] = x;
             s_cls[tid] = ci;
             s_a[tid] = a;
             s_m[tid] = m;
-            s_xoff[tid] = xoff;
+            s_xp[tid] = xp;
             colmin[tid] = PN_EMPTY_KEY;
         }
         __syncthreads();
@@ -275,7 +270,7 @@ __global__ void __launch_bounds__(256) k_sieve_band(PnView v, const PnClass *cls
                     typename Z::M mm;
                     mm.x = s_m[row].x;
                     mm.y = s_m[row].y;
-                    z = Z::z(mm, Z::samples(v, s_xoff[row] + s_x[row])[k]);
+                    z = Z::z(mm, s_xp[row][k]);
                 }
                 zs[r][row] = z;
             }

@@ -34,13 +34,21 @@ __device__ __forceinline__ void eval_batch(const PnView &v, const typename Z::Q 
         const float2 ns01 = make_float2(-m0.x, -m1.x), no01 = make_float2(-m0.y, -m1.y);
         const float2 ns23 = make_float2(-m2.x, -m3.x), no23 = make_float2(-m2.y, -m3.y);
         float2 s01 = make_float2(0.0f, 0.0f), s23 = make_float2(0.0f, 0.0f);
+        if (nb > 2) {
 #pragma unroll 2
-        for (int r = lane; r < a; r += 32) {
-            const float2 zz = zq[r];
-            const float2 d01 = __fadd2_rn(zz, Z::nz2(x0[r], x1[r], ns01, no01));
-            const float2 d23 = __fadd2_rn(zz, Z::nz2(x2[r], x3[r], ns23, no23));
-            s01 = __ffma2_rn(d01, d01, s01);
-            s23 = __ffma2_rn(d23, d23, s23);
+            for (int r = lane; r < a; r += 32) {
+                const float2 zz = zq[r];
+                const float2 d01 = __fadd2_rn(zz, Z::nz2(x0[r], x1[r], ns01, no01));
+                const float2 d23 = __fadd2_rn(zz, Z::nz2(x2[r], x3[r], ns23, no23));
+                s01 = __ffma2_rn(d01, d01, s01);
+                s23 = __ffma2_rn(d23, d23, s23);
+            }
+        } else {   // a trailing batch of one or two: the second pair is not evaluated
+#pragma unroll 2
+            for (int r = lane; r < a; r += 32) {
+                const float2 d01 = __fadd2_rn(zq[r], Z::nz2(x0[r], x1[r], ns01, no01));
+                s01 = __ffma2_rn(d01, d01, s01);
+            }
         }
         a0 = s01.x;
         a1 = s01.y;

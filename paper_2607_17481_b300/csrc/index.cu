@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
         }
         const uint32_t bits = __ballot_sync(0xffffffffu, lane < B && mg >= 0.0f);
         if (lane == 0) v.sig[A.win_off + q] = nonconst ? (__brev(bits) >> (32 - B)) : 0u;
-        if (Fha && lane == B) v.sproj[A.win_off + q] = mg;   // sieve key source of the half-row form
+        if (lane == B) v.sproj[A.win_off + q] = mg;          // the sieve's sort key
         __syncwarp();
         if (q + 1 < qend) {
             const ST delta = (ST)(xs[q + a] - xs[q]);

@@ -35,8 +35,8 @@ struct PnView {
     // per-window arrays (indexed by anchor.win_off + q)
     float *F;             // feature rows, anchor.row_off + row(q), PN_FEAT floats each (null with Fh)
     __half *Fh;           // the same rows rounded to half precision (PANACHE_FLAG_HALF_FEATURES), else null
-    float *sproj;         // with Fh: per window, its projection on the sieve direction g_{a,B+1}
-                          // taken from the FP32 row before rounding
+    float *sproj;         // per window, its projection on the sieve direction g_{a,B+1}, from the
+                          // FP32 row (before rounding, with Fh): the sieve's sort key
     float lb_eps;         // relative precision of Fh against the FP32 rows (2^-11), 0 without Fh
     uint32_t *sig;        // B-bit SimHash keys
     uint32_t *cnt;        // inclusive count of non-constant windows with start <= q
