@@ -614,15 +614,22 @@ __global__ void __launch_bounds__(256) k_sel_hist(PnView v, const PnSelGroup *gr
         for (int b = threadIdx.x; b < 4096; b += blockDim.x) sh[b] = 0u;
         __syncthreads();
         const uint32_t want = (in_group && level == 1) ? b1[gi] : 0u;
-        for (int64_t base = t0; base < seg_end; base += blockDim.x) {
-            const int64_t t = base + threadIdx.x;
-            bool ok = in_group && t < seg_end;
-            const unsigned long long key = ok ? __ldcs(&v.prof[t]) : PN_EMPTY_KEY;
-            ok = ok && key != PN_EMPTY_KEY;
-            if (ok && level == 1) ok = sel_bits(key, eps0, 0) == want;
-            const uint32_t bin = ok ? sel_bits(key, eps0, level) : 0u;
-            const unsigned peers = __match_any_sync(0xffffffffu, ok ? bin : 0xFFFFFFFFu - (threadIdx.x & 31));
-            if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh[bin], (uint32_t)__popc(peers));
+        // four independent coalesced key loads in flight per thread
+        for (int64_t base = t0; base < seg_end; base += 4 * (int64_t)blockDim.x) {
+            unsigned long long key[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t t = base + threadIdx.x + (int64_t)u * blockDim.x;
+                key[u] = (in_group && t < seg_end) ? __ldcs(&v.prof[t]) : PN_EMPTY_KEY;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                bool ok = key[u] != PN_EMPTY_KEY;
+                if (ok && level == 1) ok = sel_bits(key[u], eps0, 0) == want;
+                const uint32_t bin = ok ? sel_bits(key[u], eps0, level) : 0u;
+                const unsigned peers = __match_any_sync(0xffffffffu, ok ? bin : 0xFFFFFFFFu - (threadIdx.x & 31));
+                if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh[bin], (uint32_t)__popc(peers));
+            }
         }
         __syncthreads();
         if (in_group)
@@ -761,34 +768,47 @@ __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry 
             __syncthreads();
         }
     }
+    // Greedy suppression in pool order, 32 entries at a time: each lane
+    // decodes one entry and tests it against the cells accepted before the
+    // chunk; then the chunk is resolved in order, an accepted entry marking
+    // the later lanes it suppresses.  An entry is accepted exactly when the
+    // one-at-a-time scan would accept it.
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         int nacc = 0;
         const int k = min(G.k, kmax);
         const int64_t base = G.cell_off - S.row_off;
-        for (int t = 0; t < cnt && nacc < k; ++t) {
-            const int64_t cell = base + e[t].cell;
-            const int m = S.m_min + (int)(cell / S.ld);
-            const int64_t i = cell % S.ld;
-            bool clash = false;
-            for (int u = lane; u < nacc; u += 32)
-                if (acc_m[u] == m && 2 * llabs(i - acc_i[u]) <= m) clash = true;
-            clash = __any_sync(0xffffffffu, clash);
+        for (int t0 = 0; t0 < cnt && nacc < k; t0 += 32) {
+            const int t = t0 + lane;
+            int m = 0;
+            int64_t i = 0;
+            bool clash = t >= cnt;
             if (!clash) {
+                const int64_t cell = base + e[t].cell;
+                m = S.m_min + (int)(cell / S.ld);
+                i = cell % S.ld;
+                for (int u = 0; u < nacc; ++u)
+                    if (acc_m[u] == m && 2 * llabs(i - acc_i[u]) <= m) clash = true;
+            }
+            for (int l = 0; l < 32 && nacc < k; ++l) {
+                if (__shfl_sync(0xffffffffu, clash ? 1 : 0, l)) continue;
+                const int ml = __shfl_sync(0xffffffffu, m, l);
+                const int64_t il = __shfl_sync(0xffffffffu, i, l);
                 if (lane == 0) {
-                    acc_m[nacc] = m;
-                    acc_i[nacc] = i;
+                    acc_m[nacc] = ml;
+                    acc_i[nacc] = il;
                     PnPick pk;
                     pk.series = G.series;
-                    pk.m = m;
-                    pk.i = i;
-                    pk.j = e[t].j;
-                    pk.d = e[t].d;
+                    pk.m = ml;
+                    pk.i = il;
+                    pk.j = e[t0 + l].j;
+                    pk.d = e[t0 + l].d;
                     out[(int64_t)gi * kmax + nacc] = pk;
                 }
                 ++nacc;
-                __syncwarp();
+                if (lane > l && m == ml && 2 * llabs(i - il) <= m) clash = true;
             }
+            __syncwarp();
         }
         if (lane == 0) out_cnt[gi] = nacc;
     }
