@@ -23,7 +23,9 @@ __device__ __forceinline__ PnWin pn_window(const PnView &v, int s, int64_t i, in
 
 // Warp-cooperative distance.  Plain form: FP64 throughout.  Mixed form: the
 // samples are (hi, lo) float pairs and the centring is done in float-float,
-// (x_hi - mu_hi) + (x_lo - mu_lo), before the FP32 scaling and sum.
+// (x_hi - mu_hi) + (x_lo - mu_lo), before the FP32 scaling and sum; the root
+// of the FP32 sum is taken in FP32 too (a float distance, as the streaming
+// search packs it), since a warp-wide FP64 root costs the FP64 pipe far more.
 // Returns +inf when either window is degenerate (sigma = 0).
 __device__ __forceinline__ double pn_dist_warp(const PnView &v, int64_t x_off, int m, int64_t i, const PnWin &wi,
                                                int64_t j, const PnWin &wj, int lane) {
@@ -48,7 +50,7 @@ __device__ __forceinline__ double pn_dist_warp(const PnView &v, int64_t x_off, i
             float dz = za - zb;
             acc = fmaf(dz, dz, acc);
         }
-        return sqrt((double)pn_warp_sum(acc));
+        return (double)sqrtf(pn_warp_sum(acc));
     }
 }
 

@@ -640,24 +640,60 @@ __global__ void __launch_bounds__(256) k_sel_hist(PnView v, const PnSelGroup *gr
     }
 }
 
-// One thread per group: first bin whose cumulative count reaches `need`.
+// One warp per group: the first bin whose cumulative count (after carry_in)
+// reaches `need`, and the count below it; bin 4095 and the full count when
+// no bin does.  Lane l sums bins [128 l, 128 l + 128) with 16-byte loads, a
+// warp scan of the lane sums finds the lane whose range crosses `need`, and
+// that lane's bins are scanned 32 at a time.
 __global__ void k_sel_pick(const PnSelGroup *grp, int32_t ngrp, const uint32_t *hist, const uint32_t *carry_in,
                            uint32_t *bin_out, uint32_t *carry_out) {
-    int gi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= ngrp) return;
-    uint32_t need = grp[gi].need;
-    uint32_t run = carry_in ? carry_in[gi] : 0u;
-    uint32_t b = 4095;
-    for (int t = 0; t < 4096; ++t) {
-        uint32_t c = hist[(int64_t)gi * 4096 + t];
-        if (run + c >= need) {
-            b = t;
-            break;
-        }
-        run += c;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int gi = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (gi >= ngrp) return;                                // warp-uniform
+    const uint32_t need = grp[gi].need;
+    const uint32_t run0 = carry_in ? carry_in[gi] : 0u;
+    const uint32_t *hg = hist + (int64_t)gi * 4096;
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(hg) + lane * 32;
+    uint32_t s = 0;
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+        const uint4 u = h4[q];
+        s += u.x + u.y + u.z + u.w;
     }
-    bin_out[gi] = b;
-    if (carry_out) carry_out[gi] = run;
+    uint32_t incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned hit = __ballot_sync(full, run0 + incl >= need);
+    uint32_t b = 4095, carry = run0 + __shfl_sync(full, incl, 31);
+    if (hit) {
+        const int L = __ffs(hit) - 1;
+        uint32_t base = run0 + __shfl_sync(full, incl - s, L);
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t val = hg[128 * L + 32 * c + lane];
+            uint32_t in2 = val;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(full, in2, o);
+                if (lane >= o) in2 += y;
+            }
+            const unsigned h2 = __ballot_sync(full, base + in2 >= need);
+            if (h2) {
+                const int L2 = __ffs(h2) - 1;
+                b = (uint32_t)(128 * L + 32 * c + L2);
+                carry = base + __shfl_sync(full, in2 - val, L2);
+                break;
+            }
+            base += __shfl_sync(full, in2, 31);
+        }
+    }
+    if (lane == 0) {
+        bin_out[gi] = b;
+        if (carry_out) carry_out[gi] = carry;
+    }
 }
 
 __global__ void k_sel_pool(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_t total, double eps0,
@@ -974,13 +1010,13 @@ cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ng
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4096 * ngrp, st);
     if (e == cudaSuccess) {
         k_sel_hist<<<(unsigned)hist_blocks, 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, 0, nullptr, hist, per_block);
-        k_sel_pick<<<grid_for(ngrp, 128), 128, 0, st>>>(grp_dev, ngrp, hist, nullptr, b1, carry);
+        k_sel_pick<<<grid_for((int64_t)ngrp * 32, 128), 128, 0, st>>>(grp_dev, ngrp, hist, nullptr, b1, carry);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * 4096 * ngrp, st);
     if (e == cudaSuccess) {
         k_sel_hist<<<(unsigned)hist_blocks, 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, 1, b1, hist, per_block);
-        k_sel_pick<<<grid_for(ngrp, 128), 128, 0, st>>>(grp_dev, ngrp, hist, carry, b2, nullptr);
+        k_sel_pick<<<grid_for((int64_t)ngrp * 32, 128), 128, 0, st>>>(grp_dev, ngrp, hist, carry, b2, nullptr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(pcnt, 0, 4 * ngrp, st);
