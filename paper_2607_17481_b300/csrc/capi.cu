@@ -592,8 +592,12 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
     }
     const GroupSet out_groups = make_groups(R, (int)c.topk_mode, kser);
     if (!(c.flags & PANACHE_FLAG_NO_COMPLETION)) {
+        // Seeds: the top-kseed cells in the output's mode.  In per-length mode
+        // this already holds the global top-kseed: suppression acts within one
+        // length, so the global greedy list restricted to a length is a
+        // prefix of that length's own greedy list, and no length contributes
+        // more than kseed cells to it.
         const GroupSet seed_mode = make_groups(R, (int)c.topk_mode, kseed);
-        const GroupSet seed_global = make_groups(R, PANACHE_TOPK_GLOBAL, kseed);
         PnSeed *dseeds = nullptr;
         size_t seeds_cap = 0;
         for (uint32_t round = 0; round < c.rounds; ++round) {
@@ -602,11 +606,6 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
             PN_TRY(run_select(ctx, R, v, seed_mode, false, picks));
             for (auto &gp : picks)
                 for (auto &p : gp) seeds.push_back(PnSeed{p.series, p.m, p.i, p.j});
-            if (c.topk_mode == PANACHE_TOPK_PER_LENGTH) {
-                PN_TRY(run_select(ctx, R, v, seed_global, false, picks));
-                for (auto &gp : picks)
-                    for (auto &p : gp) seeds.push_back(PnSeed{p.series, p.m, p.i, p.j});
-            }
             if (seeds.empty()) break;
             if (seeds.size() > seeds_cap) {
                 if (dseeds) PN_CU(cudaFreeAsync(dseeds, st));
