@@ -202,41 +202,46 @@ __global__ void __launch_bounds__(256, 3) k_sieve_pairs(PnView v, const PnClass 
 // ---------------------------------------------------------------------------
 // Sieve of the mixed form as a band (Sec. 3.6: pairs within w positions of
 // the projected order).  The members of all hot classes lie in one flat
-// array sorted by (class, projection); block b takes the 64 members
-// b*64 .. b*64+63 as the first element u of its pairs and the w members
-// after each as v, so its pairs live in a band of 64 + w consecutive
-// members.  Those windows are staged 32 samples at a time in shared memory
-// (each member z-normalised by its own anchor's moments), every thread
-// accumulates the squared differences of its band pairs, and each window
-// read feeds up to 2w pairs.  Pairs across a class boundary or inside the
-// exclusion zone are skipped.  Every band pair is evaluated (no bound
-// test): the cells are the minimum over the same pairs the bound-filtered
-// form admits.
+// array sorted by (class, projection); block b takes the 256 members
+// b*256 .. b*256+255 as the first element u of its pairs, one per thread,
+// and the w members after each as v, so its pairs live in a band of
+// 256 + w consecutive members.  Those windows are staged 32 samples at a time
+// in shared memory as float4 runs of four consecutive samples (each member
+// z-normalised by its own anchor's moments); thread u reads its own run and
+// the runs of its w partners, one 16-byte load per window and four samples,
+// and keeps the w squared-difference sums in registers, in ascending sample
+// order.  Pairs across a class boundary or inside the exclusion zone are
+// skipped.  Every band pair is evaluated (no bound test): the cells are the
+// minimum over the same pairs the bound-filtered form admits.
 // ---------------------------------------------------------------------------
-constexpr int SB_U = 64;          // first elements per block
+constexpr int SB_U = 256;         // first elements per block, one per thread
 constexpr int SB_WMAX = 16;       // widest band of this kernel
 constexpr int SB_K = 32;          // samples staged per step
+constexpr int SB_ROWS = SB_U + SB_WMAX;
 
 template <class Z>
-__global__ void __launch_bounds__(256) k_sieve_band(PnView v, const PnClass *cls, int64_t nmem,
-                                                    const uint32_t *member_class, const uint32_t *members, int w) {
-    __shared__ float zs[SB_K][SB_U + SB_WMAX + 1];
-    __shared__ uint32_t s_x[SB_U + SB_WMAX], s_cls[SB_U + SB_WMAX];
-    __shared__ int32_t s_a[SB_U + SB_WMAX];
-    __shared__ float2 s_m[SB_U + SB_WMAX];
-    __shared__ const typename Z::X *s_xp[SB_U + SB_WMAX];   // first sample of each row's window
-    __shared__ unsigned long long colmin[SB_U + SB_WMAX];
+__global__ void __launch_bounds__(SB_U) k_sieve_band(PnView v, const PnClass *cls, int64_t nmem,
+                                                     const uint32_t *member_class, const uint32_t *members, int w) {
+    // row stride of SB_ROWS + 1 float4 (4 mod 32 words): the staging stores of
+    // 8 lanes (one row, 8 runs) fall in distinct banks
+    __shared__ float4 zs[SB_K / 4][SB_ROWS + 1];
+    __shared__ uint32_t s_x[SB_ROWS], s_cls[SB_ROWS];
+    __shared__ int32_t s_a[SB_ROWS];
+    __shared__ float2 s_m[SB_ROWS];
+    __shared__ const typename Z::X *s_xp[SB_ROWS];   // first sample of each row's window
+    __shared__ unsigned long long colmin[SB_ROWS];
+    __shared__ int s_amax;
     __shared__ unsigned long long s_ex;
     const int tid = threadIdx.x;
-    const int npair = SB_U * w;                            // pair e: u = e / w, v = u + 1 + e % w
-    const int per = (npair + blockDim.x - 1) / blockDim.x; // pairs per thread (<= 4)
     const int nrow = SB_U + w;
     if (tid == 0) s_ex = 0;
     for (int64_t b = blockIdx.x; b * SB_U < nmem; b += gridDim.x) {
         const int64_t p0 = b * SB_U;
         __syncthreads();
-        if (tid < nrow) {
-            const int64_t p = p0 + tid;
+        if (tid == 0) s_amax = 0;
+        __syncthreads();
+        for (int row = tid; row < nrow; row += SB_U) {
+            const int64_t p = p0 + row;
             uint32_t x = 0, ci = 0xFFFFFFFFu;
             int a = 0;
             float2 m = make_float2(0.0f, 0.0f);
@@ -249,98 +254,91 @@ __global__ void __launch_bounds__(256) k_sieve_band(PnView v, const PnClass *cls
                 const auto mm = Z::load(v, A.win_off + x);
                 m = make_float2(mm.x, mm.y);
                 xp = Z::samples(v, v.series[A.series].x_off + x);
+                atomicMax(&s_amax, a);
             }
-            s_x[tid] = x;
-            s_cls[tid] = ci;
-            s_a[tid] = a;
-            s_m[tid] = m;
-            s_xp[tid] = xp;
-            colmin[tid] = PN_EMPTY_KEY;
+            s_x[row] = x;
+            s_cls[row] = ci;
+            s_a[row] = a;
+            s_m[row] = m;
+            s_xp[row] = xp;
+            colmin[row] = PN_EMPTY_KEY;
         }
         __syncthreads();
-        int amax = 0;
-        for (int r = 0; r < nrow; ++r) amax = max(amax, s_a[r]);
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        const int amax = s_amax;
+        float acc[SB_WMAX];
+#pragma unroll
+        for (int j = 0; j < SB_WMAX; ++j) acc[j] = 0.0f;
         for (int k0 = 0; k0 < amax; k0 += SB_K) {
-            for (int e = tid; e < nrow * SB_K; e += blockDim.x) {
-                const int row = e / SB_K, r = e - row * SB_K;
-                const int k = k0 + r;
-                float z = 0.0f;
-                if (k < s_a[row]) {
+            // run e: samples k0 + 4 (e & 7) .. + 3 of row e >> 3; zero past the window
+            for (int e = tid; e < nrow * (SB_K / 4); e += SB_U) {
+                const int row = e >> 3, q4 = e & 7;
+                const int k = k0 + 4 * q4;
+                const int a = s_a[row];
+                float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (k < a) {
                     typename Z::M mm;
                     mm.x = s_m[row].x;
                     mm.y = s_m[row].y;
-                    z = Z::z(mm, s_xp[row][k]);
+                    const typename Z::X *xp = s_xp[row] + k;
+                    z.x = Z::z(mm, xp[0]);
+                    if (k + 1 < a) z.y = Z::z(mm, xp[1]);
+                    if (k + 2 < a) z.z = Z::z(mm, xp[2]);
+                    if (k + 3 < a) z.w = Z::z(mm, xp[3]);
                 }
-                zs[r][row] = z;
+                zs[q4][row] = z;
             }
             __syncthreads();
-            // pairs q and q + 1 of a thread side by side in packed two-wide
-            // FP32: fma(z_v, -1, z_u) is exactly z_u - z_v, so the sums are
-            // the scalar ones bit for bit
+#pragma unroll 2
+            for (int q4 = 0; q4 < SB_K / 4; ++q4) {
+                const float4 zu = zs[q4][tid];
 #pragma unroll
-            for (int q = 0; q < 4; q += 2) {
-                const int e0 = tid + q * blockDim.x, e1 = e0 + blockDim.x;
-                const bool in0 = q < per && e0 < npair, in1 = q + 1 < per && e1 < npair;
-                if (in0) {
-                    const int u0 = e0 / w, v0 = u0 + 1 + e0 % w;
-                    const int u1 = in1 ? e1 / w : 0, v1 = in1 ? u1 + 1 + e1 % w : 0;
-                    const float2 neg1 = make_float2(-1.0f, -1.0f);
-                    float2 s2 = make_float2(acc[q], acc[q + 1]);
-#pragma unroll 8
-                    for (int r = 0; r < SB_K; ++r) {
-                        const float2 d = __ffma2_rn(make_float2(zs[r][v0], zs[r][v1]), neg1,
-                                                    make_float2(zs[r][u0], zs[r][u1]));
-                        s2 = __ffma2_rn(d, d, s2);
+                for (int j = 0; j < SB_WMAX; ++j) {
+                    if (j < w) {
+                        const float4 zv = zs[q4][tid + 1 + j];
+                        float d = zu.x - zv.x;
+                        acc[j] = fmaf(d, d, acc[j]);
+                        d = zu.y - zv.y;
+                        acc[j] = fmaf(d, d, acc[j]);
+                        d = zu.z - zv.z;
+                        acc[j] = fmaf(d, d, acc[j]);
+                        d = zu.w - zv.w;
+                        acc[j] = fmaf(d, d, acc[j]);
                     }
-                    acc[q] = s2.x;
-                    acc[q + 1] = s2.y;
                 }
             }
             __syncthreads();
         }
-        // keys: u's minimum over its w pairs by shuffles (pairs e = u*w .. u*w+w-1
-        // sit in consecutive threads when w divides 32), v's through shared memory
+        // u's own cell: the minimum over its w pairs; each partner's through
+        // shared memory, flushed once per row
         unsigned long long n_here = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = tid + q * blockDim.x;
-            const int u = e / w, vv = u + 1 + e % w;
+        if (p0 + tid < nmem && s_m[tid].x != 0.0f) {
+            const uint32_t cu = s_cls[tid];
+            const PnAnchor &A = v.anchors[cls[cu].anchor];
+            const PnSeries &S = v.series[A.series];
+            const uint32_t xu = s_x[tid];
             unsigned long long ku = PN_EMPTY_KEY;
-            const bool in = q < per && e < npair;
-            if (in && p0 + vv < nmem && s_cls[u] == s_cls[vv] && s_m[u].x != 0.0f && s_m[vv].x != 0.0f) {
-                const PnAnchor &A = v.anchors[cls[s_cls[u]].anchor];
-                const PnSeries &S = v.series[A.series];
-                if (llabs((int64_t)s_x[u] - (int64_t)s_x[vv]) >= S.excl) {
-                    const float d = sqrtf(acc[q]);
-                    ku = pn_pack_f(d, s_x[vv]);
-                    atomicMin(&colmin[vv], pn_pack_f(d, s_x[u]));
+#pragma unroll
+            for (int j = 0; j < SB_WMAX; ++j) {
+                const int vv = tid + 1 + j;
+                if (j < w && p0 + vv < nmem && s_cls[vv] == cu && s_m[vv].x != 0.0f &&
+                    llabs((int64_t)xu - (int64_t)s_x[vv]) >= S.excl) {
+                    const float d = sqrtf(acc[j]);
+                    const unsigned long long kv = pn_pack_f(d, s_x[vv]);
+                    ku = kv < ku ? kv : ku;
+                    atomicMin(&colmin[vv], pn_pack_f(d, xu));
                     ++n_here;
                 }
             }
-            // every u owns w consecutive pair slots; reduce over them when they share a warp
-            if ((w & (w - 1)) == 0 && w <= 32) {
-                for (int o = 1; o < w; o <<= 1) {
-                    const unsigned long long other = __shfl_xor_sync(0xffffffffu, ku, o);
-                    ku = other < ku ? other : ku;
-                }
-                if (in && (e % w) == 0 && ku != PN_EMPTY_KEY) {
-                    const PnAnchor &A = v.anchors[cls[s_cls[u]].anchor];
-                    const PnSeries &S = v.series[A.series];
-                    atomicMin(&v.prof[S.row_off + (int64_t)(A.a - S.m_min) * S.ld + s_x[u]], ku);
-                }
-            } else if (ku != PN_EMPTY_KEY) {
-                const PnAnchor &A = v.anchors[cls[s_cls[u]].anchor];
-                const PnSeries &S = v.series[A.series];
-                atomicMin(&v.prof[S.row_off + (int64_t)(A.a - S.m_min) * S.ld + s_x[u]], ku);
-            }
+            if (ku != PN_EMPTY_KEY) atomicMin(&v.prof[S.row_off + (int64_t)(A.a - S.m_min) * S.ld + xu], ku);
         }
         if (n_here) atomicAdd(&s_ex, n_here);
         __syncthreads();
-        if (tid < nrow && p0 + tid < nmem && colmin[tid] != PN_EMPTY_KEY) {
-            const PnAnchor &A = v.anchors[cls[s_cls[tid]].anchor];
-            const PnSeries &S = v.series[A.series];
-            atomicMin(&v.prof[S.row_off + (int64_t)(A.a - S.m_min) * S.ld + s_x[tid]], colmin[tid]);
+        for (int row = tid; row < nrow; row += SB_U) {
+            if (p0 + row < nmem && colmin[row] != PN_EMPTY_KEY) {
+                const PnAnchor &A = v.anchors[cls[s_cls[row]].anchor];
+                const PnSeries &S = v.series[A.series];
+                atomicMin(&v.prof[S.row_off + (int64_t)(A.a - S.m_min) * S.ld + s_x[row]], colmin[row]);
+            }
         }
     }
     __syncthreads();
@@ -855,7 +853,7 @@ cudaError_t sieve_band_t(const PnView &v, const PnClass *cls, int64_t nmem, cons
                          const uint32_t *vals, int w, int grid_blocks, cudaStream_t st) {
     const int64_t need = (nmem + SB_U - 1) / SB_U;
     const int64_t g = std::min<int64_t>(need, (int64_t)grid_blocks * 2);
-    k_sieve_band<Z><<<(unsigned)g, 256, 0, st>>>(v, cls, nmem, keys, vals, w);
+    k_sieve_band<Z><<<(unsigned)g, SB_U, 0, st>>>(v, cls, nmem, keys, vals, w);
     return cudaGetLastError();
 }
 
