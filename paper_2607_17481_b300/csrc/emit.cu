@@ -219,9 +219,13 @@ constexpr int SB_WMAX = 16;       // widest band of this kernel
 constexpr int SB_K = 32;          // samples staged per step
 constexpr int SB_ROWS = SB_U + SB_WMAX;
 
-template <class Z>
+// WC: the band width as a compile-time constant (the default 8), so the
+// partner loop unrolls without predicates; 0 takes w at run time.
+template <class Z, int WC>
 __global__ void __launch_bounds__(SB_U) k_sieve_band(PnView v, const PnClass *cls, int64_t nmem,
-                                                     const uint32_t *member_class, const uint32_t *members, int w) {
+                                                     const uint32_t *member_class, const uint32_t *members, int w_rt) {
+    constexpr int WMAXC = WC ? WC : SB_WMAX;
+    const int w = WC ? WC : w_rt;
     // row stride of SB_ROWS + 1 float4 (4 mod 32 words): the staging stores of
     // 8 lanes (one row, 8 runs) fall in distinct banks
     __shared__ float4 zs[SB_K / 4][SB_ROWS + 1];
@@ -265,9 +269,9 @@ __global__ void __launch_bounds__(SB_U) k_sieve_band(PnView v, const PnClass *cl
         }
         __syncthreads();
         const int amax = s_amax;
-        float acc[SB_WMAX];
+        float acc[WMAXC];
 #pragma unroll
-        for (int j = 0; j < SB_WMAX; ++j) acc[j] = 0.0f;
+        for (int j = 0; j < WMAXC; ++j) acc[j] = 0.0f;
         for (int k0 = 0; k0 < amax; k0 += SB_K) {
             // run e: samples k0 + 4 (e & 7) .. + 3 of row e >> 3; zero past the window
             for (int e = tid; e < nrow * (SB_K / 4); e += SB_U) {
@@ -292,8 +296,8 @@ __global__ void __launch_bounds__(SB_U) k_sieve_band(PnView v, const PnClass *cl
             for (int q4 = 0; q4 < SB_K / 4; ++q4) {
                 const float4 zu = zs[q4][tid];
 #pragma unroll
-                for (int j = 0; j < SB_WMAX; ++j) {
-                    if (j < w) {
+                for (int j = 0; j < WMAXC; ++j) {
+                    if (WC || j < w) {
                         const float4 zv = zs[q4][tid + 1 + j];
                         float d = zu.x - zv.x;
                         acc[j] = fmaf(d, d, acc[j]);
@@ -318,9 +322,9 @@ __global__ void __launch_bounds__(SB_U) k_sieve_band(PnView v, const PnClass *cl
             const uint32_t xu = s_x[tid];
             unsigned long long ku = PN_EMPTY_KEY;
 #pragma unroll
-            for (int j = 0; j < SB_WMAX; ++j) {
+            for (int j = 0; j < WMAXC; ++j) {
                 const int vv = tid + 1 + j;
-                if (j < w && p0 + vv < nmem && s_cls[vv] == cu && s_m[vv].x != 0.0f &&
+                if ((WC || j < w) && p0 + vv < nmem && s_cls[vv] == cu && s_m[vv].x != 0.0f &&
                     llabs((int64_t)xu - (int64_t)s_x[vv]) >= S.excl) {
                     const float d = sqrtf(acc[j]);
                     const unsigned long long kv = pn_pack_f(d, s_x[vv]);
@@ -853,7 +857,8 @@ cudaError_t sieve_band_t(const PnView &v, const PnClass *cls, int64_t nmem, cons
                          const uint32_t *vals, int w, int grid_blocks, cudaStream_t st) {
     const int64_t need = (nmem + SB_U - 1) / SB_U;
     const int64_t g = std::min<int64_t>(need, (int64_t)grid_blocks * 2);
-    k_sieve_band<Z><<<(unsigned)g, SB_U, 0, st>>>(v, cls, nmem, keys, vals, w);
+    if (w == 8) k_sieve_band<Z, 8><<<(unsigned)g, SB_U, 0, st>>>(v, cls, nmem, keys, vals, w);
+    else k_sieve_band<Z, 0><<<(unsigned)g, SB_U, 0, st>>>(v, cls, nmem, keys, vals, w);
     return cudaGetLastError();
 }
 
