@@ -624,13 +624,23 @@ __global__ void __launch_bounds__(256) k_sel_hist(PnView v, const PnSelGroup *gr
                 const int64_t t = base + threadIdx.x + (int64_t)u * blockDim.x;
                 key[u] = (in_group && t < seg_end) ? __ldcs(&v.prof[t]) : PN_EMPTY_KEY;
             }
+            // warp-aggregated counts, one distinct bin per step: the keys of a
+            // warp fall in few bins (level 0 is mostly the distance's
+            // exponent; level 1 counts only the keys inside bin b1)
+            const int lane = threadIdx.x & 31;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 bool ok = key[u] != PN_EMPTY_KEY;
                 if (ok && level == 1) ok = sel_bits(key[u], eps0, 0) == want;
                 const uint32_t bin = ok ? sel_bits(key[u], eps0, level) : 0u;
-                const unsigned peers = __match_any_sync(0xffffffffu, ok ? bin : 0xFFFFFFFFu - (threadIdx.x & 31));
-                if (ok && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh[bin], (uint32_t)__popc(peers));
+                unsigned pending = __ballot_sync(0xffffffffu, ok);
+                while (pending) {
+                    const int leader = __ffs(pending) - 1;
+                    const uint32_t b = __shfl_sync(0xffffffffu, bin, leader);
+                    const unsigned same = __ballot_sync(0xffffffffu, ok && bin == b);
+                    if (lane == leader) atomicAdd(&sh[b], (uint32_t)__popc(same));
+                    pending &= ~same;
+                }
             }
         }
         __syncthreads();
