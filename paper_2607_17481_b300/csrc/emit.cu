@@ -800,17 +800,18 @@ __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry 
         }
     }
     __syncthreads();
+    // bitonic network: each stage's npow2/2 compare-exchanges enumerated
+    // directly (the lower index t of pair i has bit jj clear), no idle half
     for (int kk = 2; kk <= npow2; kk <<= 1) {
         for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-            for (int t = threadIdx.x; t < npow2; t += blockDim.x) {
-                int p = t ^ jj;
-                if (p > t) {
-                    bool up = (t & kk) == 0;
-                    PnPoolEntry A = e[t], Bv = e[p];
-                    if (pool_less(Bv, A) == up) {
-                        e[t] = Bv;
-                        e[p] = A;
-                    }
+            for (int i = threadIdx.x; i < (npow2 >> 1); i += blockDim.x) {
+                const int t = ((i & ~(jj - 1)) << 1) | (i & (jj - 1));
+                const int p = t | jj;
+                const bool up = (t & kk) == 0;
+                PnPoolEntry A = e[t], Bv = e[p];
+                if (pool_less(Bv, A) == up) {
+                    e[t] = Bv;
+                    e[p] = A;
                 }
             }
             __syncthreads();
