@@ -232,3 +232,36 @@ def test_anchor_set():
     assert len(sp.anchors(32, 64)) == 17
     assert len(sp.anchors(100, 150)) == 26
     assert sp.anchors(100, 151) == list(range(100, 151, 2)) + [151]
+
+
+def test_half_precision_inflation_bound():
+    """Proof of Lemma 5 at half precision (eps = 2^-11): rounding every stored
+    feature of exact FP64 rows to float16 moves the computed bound by at most
+    the absolute inflation bound 4 sqrt(m) eps (plus 2^-24 per component for
+    subnormal halves); the triangle inequality gives half of it, the slack the
+    half-row search keeps.  The stored bins of a z-normalised window hold at
+    most m^2 / 2 of energy (Parseval), and above the lemma's threshold the
+    (1 - lambda) shrink alone covers the rounding."""
+    eps, lam = 2.0 ** -11, 0.02
+    rng = np.random.default_rng(11)
+    n = 1200
+    series = {
+        "walk": np.cumsum(rng.standard_normal(n)),
+        "noise": rng.standard_normal(n),
+        "tone": np.sin(2 * np.pi * np.arange(n) / 37.0) + 0.05 * rng.standard_normal(n),
+    }
+    for name, x in series.items():
+        for m in (32, 100, 150):
+            F = sp.dft_features(x, m)
+            assert np.all((F ** 2).sum(axis=1) <= 0.5 * m * m * (1 + 1e-12)), (name, m)
+            Fh = F.astype(np.float16).astype(np.float64)
+            nw = F.shape[0]
+            i, j = rng.integers(0, nw, 4000), rng.integers(0, nw, 4000)
+            lb = sp.lower_bound(F[i], F[j], m)
+            lbh = sp.lower_bound(Fh[i], Fh[j], m)
+            sub = math.sqrt(2.0 * F.shape[1] / m) * 2.0 ** -24
+            gap = np.abs(lbh - lb)
+            assert np.all(gap <= sp.lb_inflation_bound(m, eps) + sub), (name, m, float(gap.max()))
+            assert np.all(gap <= 0.5 * sp.lb_inflation_bound(m, eps) + sub), (name, m, float(gap.max()))
+            big = lb >= sp.lb_safe_threshold(m, eps, lam)
+            assert np.all((1 - lam) * lbh[big] <= lb[big] + 1e-12), (name, m)
