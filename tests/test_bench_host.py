@@ -1,0 +1,53 @@
+"""Host-side arithmetic of the benchmark line (no GPU).
+
+The roofline object divides the search's algorithmic bytes -- a 128-byte
+feature row per query and per inspected candidate -- by its mean launch time,
+against the HBM copy peak; the DRAM traffic figure comes from the committed
+ncu record only while the kernel's sources still hash to the captured ones.
+"""
+import hashlib
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def _stats(queries, candidates, search_ms, features_ms=1.0):
+    return {"queries": queries, "candidates": candidates,
+            "step_ms": {"search": search_ms, "features": features_ms}}
+
+
+def test_roofline_arithmetic():
+    steps = [_stats(1_000_000, 99_000_000, 2.0), _stats(1_000_000, 99_000_000, 4.0)]
+    r = bench.roofline(steps, {"hbm_gbs": 8000.0}, "measured", None)
+    # 128 B x (1e6 + 99e6) per launch over a 3 ms mean launch: 4266.7 GB/s
+    assert r["bytes_per_launch"] == 128.0 * 100_000_000
+    assert r["achieved"] == pytest.approx(128.0 * 1e8 / 3e-3 / 1e9, rel=1e-4)
+    assert r["frac"] == pytest.approx(4266.67 / 8000.0, rel=1e-3)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
+    assert r["peak_source"].startswith("measured")
+
+
+def test_peaks_fall_back_when_unmeasured(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, src = bench.measured_peaks()
+    assert src == "fallback" and peaks["hbm_gbs"] == 6400.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6469.6, "bf16_tflops": 1839.8}))
+    peaks, src = bench.measured_peaks()
+    assert src == "measured" and peaks["hbm_gbs"] == 6469.6
+
+
+def test_traffic_record_follows_kernel_sources(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic(10) is None                       # no record
+    src = tmp_path / "k.cu"
+    src.write_bytes(b"kernel v1")
+    os.makedirs(tmp_path / "profiles")
+    rec = {"k_search": {"dram_bytes_per_query": 352.0,
+                        "sources_sha256_16": {"k.cu": hashlib.sha256(b"kernel v1").hexdigest()[:16]}}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.measured_traffic(1000) == pytest.approx(352000.0)
+    src.write_bytes(b"kernel v2")                                   # source changed since the capture
+    assert bench.measured_traffic(1000) is None
