@@ -247,6 +247,20 @@ int panache_profile_rows(const panache_ctx *ctx, int32_t series_index, uint64_t 
 int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *a_out,
                          float *features, uint32_t *keys, int64_t cap_windows);
 
+/* Directory population and global depth that every window of anchor
+ * `anchor_index` of series `series_index` in the last request is searched
+ * with (Sec. 3.5 and Prop. 4): samples arrive in batches of beta, every
+ * window a batch completes is inserted before the batch's searches, so the
+ * query whose last sample is t sees the non-constant windows completed by
+ * the end of t's batch; its depth is the smallest d with population <=
+ * alpha 2^d, capped at B.  population[q] and depth[q] (q < nw, host arrays
+ * of cap_windows entries) are -1 for windows the search skips (constant
+ * windows, and q < excl).  The values are computed on the device by the
+ * search kernel's own rule.  ETRUNC when cap_windows < nw; ESTATE with no
+ * request yet.  Used by the parity tests. */
+int panache_query_levels(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *population,
+                         int32_t *depth, int64_t cap_windows);
+
 /* Spectral-width calibration (Sec. 3.2, "Spectral width selection"): the
  * width K is fixed before insertion as the smallest K in [2, 16] with
  *   E[(2/m^2) sum_{k<=K'(m)} |X^_k|^2] >= eta          (retained energy)
@@ -341,7 +355,7 @@ int panache_server_get_stats(panache_server *sv, panache_server_stats *out);
  *  m          the row's length (3 <= m <= min(n, 1024))
  *  keys       device row of n packed keys (layout of panache_profile_rows;
  *             cells past n - m and empty cells are 0xFFFFFFFFFFFFFFFF)
- *  k          motifs wanted; k * (m + 1) must stay at or below 6300
+ *  k          motifs wanted; k * (m + 1) <= PANACHE_NOALLOC_NEED_MAX (6300)
  *  eps0       zero-snap threshold (the library's default is 1e-6)
  *  out        device array of at least k motifs (written)
  *  out_count  device int32 (written): the number of motifs, or
@@ -355,7 +369,10 @@ int panache_server_get_stats(panache_server *sv, panache_server_stats *out);
  * only enqueues work: read out_count after synchronising the stream.  All
  * calls share the one array, so calls that overlap on the GPU (different
  * streams, or threads) race; serialise them.  Errors: EINVAL for sizes out
- * of range or null pointers, ENODEV, ECUDA. */
+ * of range or null pointers, ENODEV, ECUDA.  When the calling thread
+ * already has a CUDA error pending from earlier work, the call enqueues
+ * nothing, returns ECUDA and leaves that error pending for its owner. */
+#define PANACHE_NOALLOC_NEED_MAX 6300
 int panache_topk_row_noalloc(const double *x, int64_t n, int32_t m, const uint64_t *keys, int32_t k, double eps0,
                              panache_motif *out, int32_t *out_count, void *stream);
 

@@ -12,7 +12,7 @@ K-width features of two sampled windows, n the series length and
 R = gamma alpha the verification budget.  Near-duplicate pairs do not enter
 the collision estimate.  Plain FP64 numpy; each step in the paper's order.
 
-Readings of what the paper leaves open (also in the design notes):
+Readings of what the paper leaves open:
 * sample: at each of m_min, floor((m_min + m_max) / 2) and m_max (each length
   once), the starts floor(t (n - m) / (S - 1)), t = 0..S-1, S = min(256,
   n - m + 1), duplicates removed, constant windows (max == min) dropped;

@@ -24,8 +24,10 @@ paper's notation, with no blocking or fusion.
 * ``sieve_pairs``: pairs within w positions in the projected sort order of a
   hot class (Sec. 3.6).
 * ``completion_triples``: the re-cut box of one seed (Sec. 3.6).
+* ``stream_population``: the directory population a query sees under the
+  batched schedule of Algorithm 1 (Sec. 3.5).
 
-Readings of points the paper leaves open (also listed in the design notes):
+Readings of points the paper leaves open:
 the prefix is bits 1..d of the signature, read as an integer with bit 1 most
 significant; the initial depth is 0; the Hamming-1 cap is 8; margin ties go
 to the lower bit index; the even-interval half of the budget spreads over the

@@ -1311,6 +1311,30 @@ int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t a
     return PANACHE_OK;
 }
 
+int panache_query_levels(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *population,
+                         int32_t *depth, int64_t cap_windows) {
+    if (!ctx || !population || !depth) return PANACHE_EINVAL;
+    if (!ctx->last) return PANACHE_ESTATE;
+    PnRequest &R = *ctx->last;
+    if (series_index < 0 || series_index >= (int32_t)R.ser.size()) return PANACHE_EINVAL;
+    const PnSeries &S = R.ser[series_index];
+    if (anchor_index < 0 || anchor_index >= S.anchor_count) return PANACHE_EINVAL;
+    const int32_t ai = S.anchor_begin + anchor_index;
+    const int64_t nw = R.anc[ai].nw;
+    if (cap_windows < nw) return PANACHE_ETRUNC;
+    if (nw <= 0) return PANACHE_OK;
+    cudaStream_t st = ctx->st;
+    int32_t *dp = nullptr;
+    PN_CU(cudaMallocAsync((void **)&dp, sizeof(int32_t) * 2 * (size_t)nw, st));
+    const PnView v = make_view(const_cast<panache_ctx *>(ctx), R);
+    int rc = from_cuda(pn::launch_query_levels(v, ai, nw, dp, dp + nw, st));
+    if (rc == PANACHE_OK) rc = from_cuda(cudaMemcpyAsync(population, dp, 4 * nw, cudaMemcpyDeviceToHost, st));
+    if (rc == PANACHE_OK) rc = from_cuda(cudaMemcpyAsync(depth, dp + nw, 4 * nw, cudaMemcpyDeviceToHost, st));
+    cudaFreeAsync(dp, st);
+    if (rc == PANACHE_OK) rc = from_cuda(cudaStreamSynchronize(st));
+    return rc;
+}
+
 int panache_calibrate_width(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min,
                             int32_t m_max, double eta, int32_t *K_out, double *energy, double *collisions) {
     if (!ctx || !K_out) return PANACHE_EINVAL;

@@ -134,6 +134,21 @@ __device__ __forceinline__ float pn_margin(const float *g, const float *f, int d
     return acc;
 }
 
+// Directory population seen by query window q of anchor A (Sec. 3.5,
+// Algorithm 1): samples arrive in batches of beta (beta = excl unless a
+// smaller batch is configured), every window a batch completes is inserted
+// before that batch's searches, so q sees the non-constant windows whose last
+// sample lies at or before the end of the batch holding its own last sample
+// q + a - 1 (the last batch ends at the series' end).  cnt is inclusive.
+__device__ __forceinline__ uint32_t pn_query_population(const PnView &v, const PnAnchor &A, const PnSeries &S,
+                                                        int64_t q) {
+    const int beta = (v.beta > 0 && v.beta < S.excl) ? v.beta : S.excl;
+    const int64_t tau = q + A.a - 1;
+    const int64_t tend = min(S.n - 1, (tau / beta + 1) * beta - 1);
+    const int64_t last = tend - A.a + 1;
+    return v.cnt[A.win_off + last];
+}
+
 // Binary search: index of the last table entry whose `off` is <= key.
 template <class T, class F>
 __device__ __forceinline__ int pn_find(const T *tab, int count, int64_t key, F off) {
@@ -176,4 +191,9 @@ int search_max_budget();
 cudaError_t launch_calibration(const double *x, const PnCalWin *win, int nwin, const int *g_off, const int *g_cnt,
                                const int *row_g, const int *row_a, int nrows, int B, double *out, cudaStream_t st);
 cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, int a_max, cudaStream_t st);
+// Population and depth every window of anchor `anchor` would probe with, by
+// the search's own rule; -1 for windows that are not searched (constant, or
+// no valid earlier window).
+cudaError_t launch_query_levels(const PnView &v, int32_t anchor, int64_t nw, int32_t *population, int32_t *depth,
+                                cudaStream_t st);
 }  // namespace pn

@@ -24,6 +24,10 @@ namespace {
 constexpr int NA_BINS = 4096;
 constexpr int NA_POOL_MAX = 8192;       // pooled cells; k (m + 1) + slack must fit
 constexpr int NA_MAX_DEVICES = 64;
+// The largest k (m + 1) accepted: the pool must hold it plus the regular
+// selection's slack (a quarter more and one bin's worth, 256).
+static_assert(PANACHE_NOALLOC_NEED_MAX + PANACHE_NOALLOC_NEED_MAX / 4 + 256 <= NA_POOL_MAX,
+              "the pool must hold the largest accepted request with its slack");
 
 struct NaEntry {
     double d;
@@ -238,7 +242,10 @@ extern "C" int panache_topk_row_noalloc(const double *x, int64_t n, int32_t m, c
     if (n < 1 || n > PN_MAX_SERIES_LEN || m < 3 || m > n || m > 1024 || k < 1 || k > 1024 || !(eps0 >= 0.0))
         return PANACHE_EINVAL;
     const int64_t need = (int64_t)k * (m + 1);
-    if (need + need / 4 + 256 > NA_POOL_MAX) return PANACHE_EINVAL;
+    if (need > PANACHE_NOALLOC_NEED_MAX) return PANACHE_EINVAL;
+    // An error left pending by earlier work on this thread is not ours to
+    // report or to clear: refuse to enqueue anything and leave it in place.
+    if (cudaPeekAtLastError() != cudaSuccess) return PANACHE_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PANACHE_ENODEV;
     if (dev < 0 || dev >= NA_MAX_DEVICES) return PANACHE_ENODEV;
@@ -257,5 +264,6 @@ extern "C" int panache_topk_row_noalloc(const double *x, int64_t n, int32_t m, c
     k_na_verify<<<64, 256, 0, st>>>(x, m, eps0, s);
     const int sm = (int)(sizeof(NaEntry) * NA_POOL_MAX + sizeof(int64_t) * 1024);
     k_na_greedy<<<1, 1024, sm, st>>>(s, m, k, out, out_count);
+    // only this call's launches can have set an error since the check above
     return cudaGetLastError() == cudaSuccess ? PANACHE_OK : PANACHE_ECUDA;
 }

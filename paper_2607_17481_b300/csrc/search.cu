@@ -75,11 +75,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         if (v.runlen[S.x_off + q] >= a) continue;          // constant window
         if (q < S.excl) continue;                          // no valid earlier window
         // population seen by q: everything inserted by the end of its batch
-        const int beta = (v.beta > 0 && v.beta < S.excl) ? v.beta : S.excl;
-        const int64_t tau = q + a - 1;
-        const int64_t tend = min(S.n - 1, (tau / beta + 1) * beta - 1);
-        const int64_t last = tend - a + 1;
-        const uint32_t P = v.cnt[A.win_off + last];
+        const uint32_t P = pn_query_population(v, A, S, q);
         const int d = pn_depth_dev(P, (uint32_t)v.alpha, v.B);
         const PnLevel &L = v.levels[A.level_begin + d];
 
@@ -307,9 +303,33 @@ cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max,
     return cudaGetLastError();
 }
 
+// Introspection: the population and depth of every window of one anchor,
+// taken exactly as k_search takes them.
+__global__ void k_query_levels(PnView v, int32_t anchor, int64_t nw, int32_t *population, int32_t *depth) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nw) return;
+    const PnAnchor &A = v.anchors[anchor];
+    const PnSeries &S = v.series[A.series];
+    if (v.runlen[S.x_off + q] >= A.a || q < S.excl) {
+        population[q] = -1;
+        depth[q] = -1;
+        return;
+    }
+    const uint32_t P = pn_query_population(v, A, S, q);
+    population[q] = (int32_t)P;
+    depth[q] = pn_depth_dev(P, (uint32_t)v.alpha, v.B);
+}
+
 }  // namespace
 
 int search_max_budget() { return SR_MAXR; }
+
+cudaError_t launch_query_levels(const PnView &v, int32_t anchor, int64_t nw, int32_t *population, int32_t *depth,
+                                cudaStream_t st) {
+    if (nw <= 0) return cudaSuccess;
+    k_query_levels<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(v, anchor, nw, population, depth);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_search(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     if (total <= 0) return cudaSuccess;

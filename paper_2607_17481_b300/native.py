@@ -23,12 +23,13 @@ FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING, FLAG_INDE
 FLAG_FP64_ANCHORS = 0x20
 FLAG_GRAPH = 0x40
 FLAG_HALF_FEATURES = 0x80
+NOALLOC_NEED_MAX = 6300   # largest k (m + 1) of panache_topk_row_noalloc
 
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
             "panache_stream_length", "panache_stream_close", "panache_stream_checkpoint", "panache_last_stats",
             "panache_profile_rows",
-            "panache_anchor_state", "panache_projections", "panache_calibrate_width", "panache_strerror",
+            "panache_anchor_state", "panache_query_levels", "panache_projections", "panache_calibrate_width", "panache_strerror",
             "panache_topk_row_noalloc",
             "panache_server_create", "panache_server_destroy", "panache_server_submit", "panache_server_wait",
             "panache_server_stream_open", "panache_server_append", "panache_server_stream_topk",
@@ -106,6 +107,7 @@ def lib():
         L.panache_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.panache_profile_rows.argtypes = [vp, i32, vp, i64]
         L.panache_anchor_state.argtypes = [vp, i32, i32, ctypes.POINTER(i32), vp, vp, i64]
+        L.panache_query_levels.argtypes = [vp, i32, i32, vp, vp, i64]
         L.panache_projections.argtypes = [ctypes.POINTER(Config), i32, vp, i64]
         L.panache_topk_row_noalloc.argtypes = [vp, i64, i32, vp, i32, ctypes.c_double, vp, vp, vp]
         u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -250,6 +252,14 @@ class Context:
                                           nw), "anchor_state")
         return a.value, F, sig
 
+    def query_levels(self, series_index: int, anchor_index: int, nw: int):
+        """(population, depth) per window of one anchor of the last request, -1 where not searched."""
+        pop = np.empty(max(1, nw), dtype=np.int32)
+        dep = np.empty(max(1, nw), dtype=np.int32)
+        _check(lib().panache_query_levels(self._h, series_index, anchor_index, pop.ctypes.data_as(ctypes.c_void_p),
+                                          dep.ctypes.data_as(ctypes.c_void_p), nw), "query_levels")
+        return pop[:nw], dep[:nw]
+
     def projections(self, a: int) -> np.ndarray:
         return projections(a, self.config)
 
@@ -387,8 +397,36 @@ class Server:
             pass
 
 
+MOTIF_BYTES = ctypes.sizeof(Motif)
+
+
 def topk_row_noalloc(x_dev, keys_dev, m: int, k: int, eps0: float, out_dev, count_dev, stream_ptr: int = 0):
-    """Selection of one length row with no device allocation (all buffers are the caller's device tensors)."""
+    """Selection of one length row with no device allocation (all buffers are the caller's device tensors).
+
+    x_dev: contiguous float64 samples; keys_dev: contiguous int64/uint64 packed keys, one per sample;
+    out_dev: contiguous device buffer of at least k motifs (32 bytes each); count_dev: contiguous int32
+    device tensor.  All four must sit on the current CUDA device.  Anything else raises ValueError before
+    the library is called, since the kernels would read or write past the caller's buffers.  Returns the
+    library's status code."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t in (("x", x_dev), ("keys", keys_dev), ("out", out_dev), ("count", count_dev)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if x_dev.dtype != torch.float64:
+        raise ValueError("x must be float64")
+    if keys_dev.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)):
+        raise ValueError("keys must be int64 or uint64")
+    if keys_dev.numel() != x_dev.numel():
+        raise ValueError("keys must hold one key per sample of x")
+    if k < 1 or out_dev.numel() * out_dev.element_size() < k * MOTIF_BYTES:
+        raise ValueError(f"out must hold at least k = {k} motifs of {MOTIF_BYTES} bytes")
+    if count_dev.dtype != torch.int32 or count_dev.numel() < 1:
+        raise ValueError("count must be an int32 tensor of at least one element")
     return lib().panache_topk_row_noalloc(ctypes.c_void_p(x_dev.data_ptr()), x_dev.numel(), m,
                                           ctypes.c_void_p(keys_dev.data_ptr()), k, eps0,
                                           ctypes.c_void_p(out_dev.data_ptr()), ctypes.c_void_p(count_dev.data_ptr()),

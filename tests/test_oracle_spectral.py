@@ -265,3 +265,67 @@ def test_half_precision_inflation_bound():
             assert np.all(gap <= 0.5 * sp.lb_inflation_bound(m, eps) + sub), (name, m, float(gap.max()))
             big = lb >= sp.lb_safe_threshold(m, eps, lam)
             assert np.all((1 - lam) * lbh[big] <= lb[big] + 1e-12), (name, m)
+
+
+def _stream_simulation(n: int, a: int, beta: int, nonconst) -> dict:
+    """Algorithm 1's schedule, literally: samples arrive beta at a time; after
+    each arrival every window whose last sample has arrived is inserted (if
+    non-constant), then the windows completed by this arrival are searched
+    and see the directory as it stands."""
+    seen = {}
+    inserted = 0
+    next_window = 0
+    arrived = 0
+    while arrived < n:
+        arrived = min(n, arrived + beta)                   # samples [0, arrived) are here
+        done = []
+        while next_window + a <= arrived:                  # window fully arrived
+            if nonconst[next_window]:
+                inserted += 1
+            done.append(next_window)
+            next_window += 1
+        for q in done:
+            seen[q] = inserted
+    return seen
+
+
+def test_stream_population_hand_cases():
+    # n = 20, a = 4, beta = 5, no constant window: window w ends at sample w + 3
+    pre = np.arange(0, 18)                                 # nonconst_prefix[t] = t (17 windows)
+    # q = 0 ends at 3, batch [0, 5): windows ending at <= 4 are 0 and 1
+    assert sp.stream_population(0, 4, 20, 5, pre) == 2
+    assert sp.stream_population(1, 4, 20, 5, pre) == 2
+    # q = 2 ends at 5, batch [5, 10): windows 0..6
+    assert sp.stream_population(2, 4, 20, 5, pre) == 7
+    assert sp.stream_population(6, 4, 20, 5, pre) == 7
+    assert sp.stream_population(7, 4, 20, 5, pre) == 12
+    # last batch [15, 20): every one of the 17 windows
+    assert sp.stream_population(16, 4, 20, 5, pre) == 17
+    # a last partial batch: beta = 6, batches [0,6) [6,12) [12,18) [18,20)
+    assert sp.stream_population(14, 4, 20, 6, pre) == 15     # ends at 17, batch [12, 18)
+    assert sp.stream_population(15, 4, 20, 6, pre) == 17     # ends at 18, batch [18, 20) clipped
+    # beta = 1 (every sample its own batch): a query sees itself and all earlier windows
+    for q in range(17):
+        assert sp.stream_population(q, 4, 20, 1, pre) == q + 1
+    # constant windows 3..5 are never inserted
+    nc = np.ones(17, bool)
+    nc[3:6] = False
+    pre_c = np.concatenate([[0], np.cumsum(nc)])
+    assert sp.stream_population(2, 4, 20, 5, pre_c) == 4     # windows 0..6 less 3, 4, 5
+    assert sp.stream_population(16, 4, 20, 5, pre_c) == 14
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_stream_population_matches_simulation(seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(25):
+        a = int(rng.integers(3, 40))
+        n = int(rng.integers(a, 400))
+        beta = int(rng.integers(1, 90))
+        nw = n - a + 1
+        nonconst = rng.random(nw) < rng.uniform(0.3, 1.0)
+        pre = np.concatenate([[0], np.cumsum(nonconst)])
+        sim = _stream_simulation(n, a, beta, nonconst)
+        assert sorted(sim) == list(range(nw))
+        for q in range(nw):
+            assert sp.stream_population(q, a, n, beta, pre) == sim[q], (n, a, beta, q)
