@@ -1,11 +1,15 @@
 """Throughput of the Panache pan-motif path on one B300 (windows x lengths per second).
 
-Workload (the configuration the metric is quoted on): a 1,000,000-sample
-float32 wafer-like series (152-sample step/plateau segments, seed 0), lengths
-100..150 (51 lengths, 26 anchors), top-20 pan-motifs over the whole stack,
-exclusion zone 150.  One step = one full request: samples on the device ->
+Workload (the configuration the metric is quoted on): the precision form on
+a 5,000,000-sample float32 wafer-like series (152-sample step/plateau
+segments, seed 0), lengths 100..150 (51 lengths, 26 anchors), top-20
+pan-motifs over the whole stack, exclusion zone 150: FP32 sliding-DFT state
+re-anchored every 256 slides by 3xTF32 tensor-core contractions, FP64 prefix
+sums, FP32 bounds and in-stream distances, FP64 verification of every
+reported distance.  One step = one full request: samples on the device ->
 index (features, keys, directories) -> streaming search -> sieve ->
-completion -> FP64-verified top-20 on the host.
+completion -> FP64-verified top-20 on the host.  The plain FP64 form runs on
+the same series as the comparator.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -32,8 +36,9 @@ import workloads  # noqa: E402
 
 METRIC = "windows*lengths/sec to exact top-20 pan-motifs (recall 1.0) vs plain FP64 form; p50/p99"
 UNIT = "windows*lengths/s"
-WORKLOAD = dict(workload="wafer_like_1M", n=1_000_000, m_min=100, m_max=150, k=20, excl=150, seed=0,
+WORKLOAD = dict(workload="wafer_like_5M", n=5_000_000, m_min=100, m_max=150, k=20, excl=150, seed=0,
                 dtype="float32", topk="global")
+STRIDE = 2                       # the paper's anchor stride (the library's default for the global top-k)
 
 
 def rank_env():
@@ -120,6 +125,97 @@ def measured_traffic(queries: int):
             if hashlib.sha256(f.read()).hexdigest()[:16] != want:
                 return None
     return t["dram_bytes_per_query"] * queries
+
+
+def alu_peaks(pn) -> dict:
+    """Measured arithmetic ceilings of this GPU, TFLOP/s: the library's FMA
+    probes (FP32 scalar and packed two-wide, FP64) and cuBLAS TF32 (an 8192^3
+    float32 matmul with TF32 tensor cores allowed, best of 5, CUDA events)."""
+    import torch
+    out = {"fp32_fma": pn.alu_peak(0), "fp32x2_fma": pn.alu_peak(1), "fp64_fma": pn.alu_peak(2)}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.randn(8192, 8192, device="cuda")
+        b = torch.randn(8192, 8192, device="cuda")
+        best = None
+        for _ in range(6):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        out["tf32_cublas"] = 2.0 * 8192 ** 3 / (best * 1e-3) / 1e12
+        del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["fp32"] = max(out["fp32_fma"], out["fp32x2_fma"])
+    out["how"] = ("FP32/FP64: panache_alu_peak (8 FMA chains per thread, 8 blocks of 256 per SM, ~50 ms); "
+                  "TF32: torch.matmul 8192^3 float32 with allow_tf32 (cuBLAS), best of 5")
+    return {k: (round(v, 2) if isinstance(v, float) else v) for k, v in out.items()}
+
+
+def kernel_table(st: dict, kt: dict, n: int, anchors: list[int], peaks: dict, alu: dict, w: int = 8) -> list[dict]:
+    """Per-kernel roofline: algorithmic flops and bytes of each kernel for one
+    request, its CUDA-event time (library per-kernel timer, the last timed
+    step), and both fractions.  Per-unit costs (unit: window-anchor unless
+    stated):
+      k_anchor_tc   3 TF32 MMAs of 2 a 32 flop per chunk of 256 windows; reads
+                    the a samples of each chunk start (8 B each) and writes a
+                    128 B anchor row per chunk
+      k_features    1,650 flop (15 bins x 8 flop of complex update, 30
+                    normalisations, 25 projections x 30 FMAs); 164 B (128 B row,
+                    4 B key, 4 B sieve projection written; 8 B moments, 4 B run
+                    length, 16 B of samples read)
+      k_search      per inspected candidate a 30-wide bound (90 flop) and its
+                    128 B row; per query its own 128 B row; per survivor an
+                    exact distance of 5 flop per sample (normalise, subtract,
+                    multiply-add) at the mean anchor length
+      sieve eval    5 flop per sample per evaluated pair; each member's window
+                    (4 B per sample) once per band of w pairs
+      k_complete    3 flop per sample per box triple (its windows are
+                    normalised once in shared memory); bytes: per seed (1,053
+                    triples) the two runs of m + 2 dm + 2 dp samples its box
+                    covers, 8 B each
+      selection     three passes of 8 B per profile cell (two histogram
+                    passes, the pool pass) per selection call; flops negligible
+      refine        4 flop per sample per scanned partner (normalise,
+                    subtract, multiply-add); its samples (8 B) come from L1/L2
+                    shared by the 256 partners of a block, so 8 m B per 256
+    """
+    L = 51
+    a_mean = sum(anchors) / len(anchors)
+    nwa = sum(n - a + 1 for a in anchors)
+    q, c, e = st["queries"], st["candidates"], st["exact_stream"]
+    es, ec, rounds = st["exact_sieve"], st["exact_completion"], st["completion_rounds"]
+    chunks = sum((n - a + 1 + 255) // 256 for a in anchors)
+    m_mean = 125.0
+    rows = {
+        "anchor_tc": (3.0 * 2 * a_mean * 32 * chunks, chunks * (8.0 * a_mean + 128.0), "tf32"),
+        "features": (1650.0 * nwa, 164.0 * nwa, "fp32"),
+        "search": (90.0 * c + 5.0 * a_mean * e, 128.0 * (q + c), "fp32"),
+        "sieve": (5.0 * a_mean * es, 4.0 * a_mean * es / w, "fp32"),
+        "complete": (3.0 * m_mean * ec, (ec / 1053.0) * 2 * (m_mean + 2 * 6 + 2 * 4) * 8.0, "fp32"),
+        "select": (0.0, 24.0 * L * n * (rounds + 1 + st.get("refine_passes", 0)), "fp32"),
+        "refine": (4.0 * m_mean * st.get("exact_refine", 0), 8.0 * m_mean * st.get("exact_refine", 0) / 256.0,
+                   "fp32"),
+    }
+    out = []
+    for name, (fl, by, pipe) in rows.items():
+        ms, launches = kt.get(name, (0.0, 0))
+        if ms <= 0:
+            continue
+        tf = fl / (ms * 1e-3) / 1e12
+        gbs = by / (ms * 1e-3) / 1e9
+        peak_c = alu["tf32_cublas"] if pipe == "tf32" else alu["fp32"]
+        sig = lambda v: float(f"{v:.4g}")                          # noqa: E731  (4 significant digits)
+        out.append({"kernel": name, "launches": launches, "ms": round(ms, 3), "flops": fl, "bytes": by,
+                    "tflops": sig(tf), "gbs": sig(gbs),
+                    ("tf32_frac" if pipe == "tf32" else "fp32_frac"): sig(tf / peak_c),
+                    "hbm_frac": sig(gbs / peaks["hbm_gbs"])})
+    return out
 
 
 def roofline(stats_steps: list[dict], peaks: dict, peak_src: str, traffic: float | None):
@@ -252,6 +348,38 @@ def run_batched(pn, stream, n_series: int, n_loop: int):
     return out
 
 
+def run_walk(pn, stream):
+    """The small exact case: the planted random walk (n = 8,192 float64, 3
+    planted pairs, lengths 32..64, exclusion 64), top-20 per length (660
+    motifs) and over the whole stack, both precision forms, per call with the
+    series resident on the device.  Per-length mode runs at the library's
+    default anchor stride for that mode (1) and, for comparison, at the
+    paper's 2."""
+    import torch
+    s = workloads.planted_random_walk()
+    x = torch.from_numpy(s.x).cuda()
+    W = workloads.windows_lengths(len(s.x), s.m_min, s.m_max)
+    out = {"n": len(s.x), "lengths": f"{s.m_min}..{s.m_max}", "k": s.k, "excl": s.excl, "unit": UNIT}
+    for name, over in (("per_length_mixed", dict(precision=1, topk_mode=pn.TOPK_PER_LENGTH)),
+                       ("per_length_plain", dict(precision=0, topk_mode=pn.TOPK_PER_LENGTH)),
+                       ("per_length_mixed_stride2", dict(precision=1, topk_mode=pn.TOPK_PER_LENGTH, stride=2)),
+                       ("global_mixed", dict(precision=1, topk_mode=pn.TOPK_GLOBAL)),
+                       ("global_plain", dict(precision=0, topk_mode=pn.TOPK_GLOBAL))):
+        c = pn.Context(**over)
+        c.set_stream(stream.cuda_stream)
+        for _ in range(3):
+            got = c.pmp(x, s.m_min, s.m_max, s.k, s.excl)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            got = c.pmp(x, s.m_min, s.m_max, s.k, s.excl)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        out[name] = {"ms": round(ms, 3), "value": W / (ms / 1e3), "motifs": int(len(got))}
+    return out
+
+
 def run_served(pn, args, rate=None):
     """The served form: Poisson arrivals of batched-workload series plus live
     streams (random walk or ECG-like, starting at 50,000 samples, lengths
@@ -379,7 +507,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="panache", choices=("panache", "reference"))
     ap.add_argument("--precision", type=int, default=1, help="1 mixed (default), 0 plain FP64")
-    ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 form")
+    ap.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 form")
     ap.add_argument("--half-steps", type=int, default=2, help="timed steps with half-precision feature rows")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
@@ -426,7 +554,7 @@ def main():
         ctx.set_stream(stream.cuda_stream)
         return ctx
 
-    def timed(ctx, steps, warm, src):
+    def timed(ctx, steps, warm, src, kts=None):
         for _ in range(warm):
             ctx.pmp(src, wl["m_min"], wl["m_max"], wl["k"], wl["excl"])
         if dist:
@@ -443,14 +571,17 @@ def main():
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
             stats.append(ctx.stats())
+            if kts is not None:
+                kts.append(ctx.kernel_times())
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         return ms, stats, motifs
 
     ctx = make_ctx(args.precision)
+    kts = []
     with ClockSampler(local) as clk:
-        ms, stats, motifs = timed(ctx, args.steps, args.warmup, x_dev)
+        ms, stats, motifs = timed(ctx, args.steps, args.warmup, x_dev, kts)
     clocks = clk.summary()
     # end to end through the C ABI with host buffers: the H2D copy of the series
     # and the D2H copy of the motifs happen inside every call
@@ -497,6 +628,7 @@ def main():
                           "same_motifs": bool(np.array_equal(fmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                           "recall_vs_default": len(ref_cells & got_cells) / max(1, len(ref_cells)),
                           "config": over}
+    walk = run_walk(pn, stream) if rank == 0 else None
     batched = run_batched(pn, stream, args.batched, args.batched_loop) if args.batched > 0 else None
     served = run_served(pn, args) if args.served_seconds > 0 and rank == 0 else None
     # the same mix at a quarter of the arrival rate: latency when the server is not saturated
@@ -504,6 +636,13 @@ def main():
     if rank != 0:
         return 0
     peaks, psrc = measured_peaks()
+    alu = alu_peaks(pn)
+    anchors = list(range(wl["m_min"], wl["m_max"] + 1, STRIDE))
+    if anchors[-1] != wl["m_max"]:
+        anchors.append(wl["m_max"])
+    rl = roofline(stats, peaks, psrc, measured_traffic(stats[-1]["queries"]))
+    rl["kernels"] = kernel_table(stats[-1], kts[-1], wl["n"], anchors, peaks, alu)
+    rl["alu_peaks_tflops"] = alu
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
@@ -517,11 +656,12 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.x.nbytes),
                 "d2h_bytes_per_step": int(len(motifs) * 32)},
         "gpu_launches": int(sum(st["kernel_launches"] for st in stats)),
-        "roofline": roofline(stats, peaks, psrc, measured_traffic(stats[-1]["queries"])),
+        "roofline": rl,
         "clocks": clocks,
         "plain_fp64": plain,
         "half_feature_rows": half,
         "fast_settings": fast,
+        "planted_walk": walk,
         "batched": batched,
         "served": served,
         "served_quarter_rate": served_light,

@@ -96,16 +96,40 @@ extern "C" {
                                               bound keeps.  The query's probe margins read its half row, so
                                               Hamming-1 probes may reorder where margins nearly tie.
                                               EINVAL with the plain form. */
+#define PANACHE_FLAG_WARM_START 0x100     /* run a warm start before the search: every query evaluates exactly
+                                              the candidate of smallest bound among the 32 most recent valid
+                                              entries of its exact bucket (all of them candidates the search
+                                              admits), so that candidate cells hold a distance when the search
+                                              tests them against max(best_q, P[c]).  Results are the same either
+                                              way.  It pays where candidate cells would otherwise still be
+                                              empty (the planted walk: 64% fewer exact distances); on series
+                                              whose cells mostly hold large distances (the wafer-like series)
+                                              the bound passes the same pairs and the extra pass costs more
+                                              than it saves, so it is off by default. */
+#define PANACHE_FLAG_NO_REFINE 0x200      /* skip the exact row refinement of the top list.  After local
+                                              completion, every cell of the top seed_mult*k list (per group)
+                                              is scanned against all its valid partners at its length with the
+                                              in-stream arithmetic and lowered to the smallest distance found;
+                                              the list is reselected and new cells scanned until nothing
+                                              changes, so every reported cell holds its exact nearest
+                                              neighbour.  Not in the paper, whose emit stage never rescans a
+                                              row: a row costs n m multiply-adds, tens of microseconds on the
+                                              GPU. */
 
 /* Tunables.  A zero field takes the paper's default (Sec. 4):
  * alpha 16, gamma 8 (R = 128), stride 2, K 16, B 24, d0 12, probe cap 8,
  * sieve width 8, (dm, dp) = (6, 4), 8 completion rounds, lambda 1e-4,
  * eps0 1e-6, batch beta = excl, chunk 256 slides per direct-DFT anchor,
- * seed_mult 2, grid_mult 8. */
+ * seed_mult 2, grid_mult 8.  One exception: a zero stride is the paper's
+ * s = 2 in global top-k mode but s = 1 in per-length mode, where every
+ * length's own list must be exact (at s = 2 a length between anchors is
+ * reached only through local completion, which can miss a cell whose best
+ * pair no anchor's search found); panache_default_config leaves the stride
+ * 0 and the context resolves it from the mode. */
 typedef struct {
     uint32_t alpha;       /* occupancy target, the analyst's one knob ("budget") */
     uint32_t gamma;       /* R = gamma * alpha candidate inspections per query (R <= 512) */
-    uint32_t stride;      /* anchor stride s */
+    uint32_t stride;      /* anchor stride s (0: 2 for global top-k, 1 for per-length top-k) */
     uint32_t K;           /* spectral width, 2..16 (bins 1..K-1 kept) */
     uint32_t B;           /* signature bits, 1..24 */
     uint32_t d0;          /* probe reference depth */
@@ -156,6 +180,8 @@ typedef struct {
     uint64_t device_bytes;       /* device footprint of the request (admission estimate) */
     uint64_t kernel_launches;    /* kernels launched by the request */
     uint64_t waves;              /* waves a batch was split into to fit the HBM budget */
+    uint64_t refine_passes;      /* passes of the row refinement (reselect, scan new top cells) */
+    uint64_t exact_refine;       /* exact evaluations of the row refinement */
     /* With PANACHE_FLAG_TIMING: device time of each step in ms (CUDA events on
      * the context's stream): 0 sample upload and conversion, 1 run lengths and
      * FP64 prefix moments, 2 features and keys, 3 ranks and directories,
@@ -247,6 +273,39 @@ int panache_profile_rows(const panache_ctx *ctx, int32_t series_index, uint64_t 
 int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *a_out,
                          float *features, uint32_t *keys, int64_t cap_windows);
 
+/* Fault injection for tests of the failure paths (the paper has no
+ * counterpart).  Arms one failure, made on the host, of a later operation of
+ * the given kind in this process; `after` operations of that kind succeed
+ * first, then one fails and the hook disarms itself:
+ *   PANACHE_FAULT_ALLOC    a device allocation of a request's state: the
+ *                          call returns ENOMEM
+ *   PANACHE_FAULT_COPY     the upload of a request's samples: the call
+ *                          returns ECUDA without the copy being issued
+ *   PANACHE_FAULT_TC_WAIT  the next tensor-core anchor launch (mixed form)
+ *                          issues no MMA and every CTA's bounded wait runs
+ *                          out after a few tries: the kernel records the
+ *                          timeout, zeroes its anchor rows, frees its tensor
+ *                          memory and returns; the call returns ETIMEOUT
+ *                          (never armed into a graph being captured)
+ * PANACHE_FAULT_NONE disarms.  No GPU is faulted: the context stays usable
+ * and its next request runs normally.  Errors: EINVAL. */
+#define PANACHE_FAULT_NONE 0
+#define PANACHE_FAULT_ALLOC 1
+#define PANACHE_FAULT_COPY 2
+#define PANACHE_FAULT_TC_WAIT 3
+int panache_inject_fault(int32_t kind, int32_t after);
+
+/* Device time of individual kernels in the last request made with
+ * PANACHE_FLAG_TIMING (CUDA events on the context's stream around each
+ * launch, summed; the last wave of a batch): ms[k] and launches[k] for
+ * k = 0 tensor-core chunk anchors, 1 sliding DFT + normalisation + keys,
+ * 2 streaming search, 3 hot-class sieve evaluation (without its sorts),
+ * 4 local completion (without its seed selections), 5 selection (every
+ * seed selection and the final top-k), 6 exact row refinement.  Zero
+ * without the flag.  ETRUNC when cap < 7. */
+#define PANACHE_KERNEL_TIMES 7
+int panache_kernel_times(const panache_ctx *ctx, double *ms, uint64_t *launches, int32_t cap);
+
 /* Directory population and global depth that every window of anchor
  * `anchor_index` of series `series_index` in the last request is searched
  * with (Sec. 3.5 and Prop. 4): samples arrive in batches of beta, every
@@ -285,6 +344,14 @@ int panache_calibrate_width(panache_ctx *ctx, const void *series, int32_t dtype,
 int panache_projections(const panache_config *cfg, int32_t a, float *g, int64_t cap);
 
 const char *panache_strerror(int code);
+
+/* Measured throughput, in TFLOP/s, of one arithmetic pipe on the current
+ * device: kind 0 FP32 fused multiply-add, 1 packed two-wide FP32 fused
+ * multiply-add, 2 FP64 fused multiply-add (2 flop per multiply-add, one
+ * launch of about 50 ms after a warm-up, CUDA events).  These are the
+ * denominators of the per-kernel roofline fractions; the paper has no
+ * counterpart.  Errors: EINVAL, ENODEV, ENOMEM, ECUDA. */
+int panache_alu_peak(int32_t kind, double *tflops);
 
 /* ---- request server (continuous batching under an HBM budget) ----
  *

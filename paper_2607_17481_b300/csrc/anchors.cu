@@ -57,9 +57,9 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(r);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, int spin) {
     uint32_t done = 0;
-    for (int it = 0; it < AT_SPIN && !done; ++it) {
+    for (int it = 0; it < spin && !done; ++it) {
         asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
                      : "=r"(done)
                      : "r"(mbar), "r"(phase)
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
     const int ai = tile_anchor[blockIdx.x];
     const PnAnchor A = v.anchors[ai];
     const PnSeries S = v.series[A.series];
-    const int a = A.a, kp = A.kp, C = v.C;
+    const int a = A.a, C = v.C;
     const int64_t c0 = tile_row0[blockIdx.x];
     const int kg = AT_KS / 4;
 
@@ -114,6 +114,9 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
     const uint32_t taddr = taddr_s;
     const double *xs = v.x + S.x_off;
     const uint32_t idesc = umma_idesc_tf32(AT_ROWS, AT_N);
+    // wait limit; an injected fault (host-side test hook) issues no MMA and
+    // gives up after a few tries, so the timeout path runs
+    const int spin = v.tc_fault ? 64 : AT_SPIN;
 
     uint32_t phase = 0;
     bool ok = true;
@@ -130,17 +133,12 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
             Ahi[kmaj(m, k, kg)] = hi;
             Alo[kmaj(m, k, kg)] = val - hi;
         }
-        // B slice: twiddles of bins 1..K' (rows 2k-2: cos, 2k-1: -sin)
+        // B slice: twiddles of bins 1..K' (rows 2k-2: cos, 2k-1: -sin), from
+        // the request's table (zero past K' and past a)
+        const float *twa = v.twb + (int64_t)ai * AT_N * v.twb_ld;
         for (int t = tid; t < AT_N * AT_KS; t += AT_THREADS) {
             const int n = t / AT_KS, k = t - n * AT_KS, r = r0 + k;
-            const int bin = (n >> 1) + 1;
-            float val = 0.0f;
-            if (bin <= kp && r < a) {
-                const int ph = (int)(((int64_t)bin * r) % a);
-                double sn, cs;
-                sincospi(2.0 * (double)ph / (double)a, &sn, &cs);
-                val = (n & 1) ? (float)(-sn) : (float)cs;
-            }
+            const float val = r < a ? twa[(int64_t)n * v.twb_ld + r] : 0.0f;
             const float hi = tf32_hi(val);
             Bhi[kmaj(n, k, kg)] = hi;
             Blo[kmaj(n, k, kg)] = val - hi;
@@ -148,7 +146,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
+        if (tid == 0 && !v.tc_fault) {
             const uint32_t lbo = 128, sbo = kg * 128;
             for (int s = 0; s < AT_KS / 8; ++s) {
                 const uint32_t off = (uint32_t)(s * 2 * 32 * sizeof(float));
@@ -169,7 +167,7 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
                          : "memory");
         }
         // the next slice overwrites the operands: wait until the MMAs have read them
-        if (!mbar_wait(smem_u32(&mbar), phase)) {
+        if (!mbar_wait(smem_u32(&mbar), phase, spin)) {
             if (lane == 0) atomicExch(&fail_s, 1);
         }
         phase ^= 1u;
@@ -197,9 +195,19 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
                 dst[t] = make_float4(__uint_as_float(r[4 * t]), __uint_as_float(r[4 * t + 1]),
                                      __uint_as_float(r[4 * t + 2]), __uint_as_float(r[4 * t + 3]));
         }
-    } else if (tid == 0) {
+    } else {
+        // the tile's anchors are unknown: zero rows keep later steps finite
+        // (the request reports ETIMEOUT)
+        const int64_t c = c0 + warp * 32 + lane;
+        if (c * C < A.nw) {
+            float4 *dst = reinterpret_cast<float4 *>(v.anc + (A.chunk_off + c) * PN_FEAT);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) dst[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
+    if (!ok && tid == 0) {
         atomicExch(v.err, PN_ERR_TC_TIMEOUT);
-        mbar_wait(smem_u32(&mbar), phase ^ 1u);     // let any MMA still in flight finish (bounded)
+        mbar_wait(smem_u32(&mbar), phase ^ 1u, spin);   // let any MMA still in flight finish (bounded)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -207,7 +215,34 @@ __global__ void __launch_bounds__(AT_THREADS) k_anchor_tc(PnView v, const int32_
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(AT_N));
 }
 
+// The B operand of every anchor, once per request: row 2k-2 holds
+// cos(2 pi k r / a) and row 2k-1 holds -sin(2 pi k r / a) for k = 1..K',
+// r < a, rounded from FP64 to FP32; other entries are zero.  Layout
+// [anchor][32][ld], ld >= every anchor length.
+__global__ void k_twiddles(const PnAnchor *anc, int32_t nanc, int32_t ld, float *tw) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nanc * AT_N * ld) return;
+    const int ai = (int)(t / ((int64_t)AT_N * ld));
+    const int n = (int)((t / ld) % AT_N), r = (int)(t % ld);
+    const int a = anc[ai].a, bin = (n >> 1) + 1;
+    float val = 0.0f;
+    if (bin <= anc[ai].kp && r < a) {
+        const int ph = (int)(((int64_t)bin * r) % a);
+        double sn, cs;
+        sincospi(2.0 * (double)ph / (double)a, &sn, &cs);
+        val = (n & 1) ? (float)(-sn) : (float)cs;
+    }
+    tw[t] = val;
+}
+
 }  // namespace
+
+cudaError_t launch_twiddles(const PnAnchor *anc_dev, int32_t nanc, int32_t ld, float *tw, cudaStream_t st) {
+    const int64_t total = (int64_t)nanc * AT_N * ld;
+    if (total <= 0) return cudaSuccess;
+    k_twiddles<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(anc_dev, nanc, ld, tw);
+    return cudaGetLastError();
+}
 
 size_t anchor_tc_smem() { return sizeof(float) * (2 * AT_ROWS * AT_KS + 2 * AT_N * AT_KS); }
 

@@ -1,11 +1,13 @@
 // Host runtime and C ABI: planning, admission, device buffers and the
 // order of the steps (Algorithm 1 over all anchors, then Algorithm 2).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
 #include <set>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "emit.cuh"
@@ -31,6 +33,18 @@ int from_cuda(cudaError_t e) {
         if (rc_ != PANACHE_OK) return rc_;   \
     } while (0)
 #define PN_CU(expr) PN_TRY(from_cuda(expr))
+
+// Host-side fault injection (panache_inject_fault): the armed kind and how
+// many matching operations still succeed before it fires once.
+std::atomic<int> g_fault_kind{PANACHE_FAULT_NONE};
+std::atomic<int> g_fault_after{0};
+
+bool fault_fires(int kind) {
+    if (g_fault_kind.load() != kind) return false;
+    if (g_fault_after.fetch_sub(1) > 0) return false;
+    int k = kind;
+    return g_fault_kind.compare_exchange_strong(k, PANACHE_FAULT_NONE);
+}
 
 int64_t next_pow2(int64_t v) {
     int64_t p = 1;
@@ -97,6 +111,7 @@ struct PnRequest {
     int32_t *d_blk_anchor = nullptr, *d_blk_chunk0 = nullptr;
     int32_t *d_tile_anchor = nullptr, *d_tile_row0 = nullptr;
     float *tca = nullptr;      // tensor-core chunk anchors
+    float *twb = nullptr;      // their twiddle operand, [anchor][32][a_max]
     int *err = nullptr;
     int64_t *d_slot_off = nullptr;
     double *x = nullptr;
@@ -126,6 +141,7 @@ struct PnRequest {
     template <class T>
     cudaError_t alloc(T *&p, int64_t count) {
         p = nullptr;
+        if (fault_fires(PANACHE_FAULT_ALLOC)) return cudaErrorMemoryAllocation;
         if (count <= 0) count = 1;
         cudaError_t e = cudaMallocAsync((void **)&p, sizeof(T) * (size_t)count, st);
         if (e == cudaSuccess) allocs.push_back(p);
@@ -144,6 +160,7 @@ struct panache_ctx {
     std::map<int, std::vector<float>> gcache;
     std::set<panache_stream *> streams;   // open streams: their state is freed with the context
     uint64_t launches = 0;
+    PnKTimer kt;                          // per-kernel device time of the last request (PANACHE_FLAG_TIMING)
     // PANACHE_FLAG_GRAPH: the captured index + search steps of `last`, the
     // request shape they were captured for, and the persistent input staging
     cudaGraphExec_t gexec = nullptr;
@@ -187,10 +204,16 @@ struct panache_stream {
 
 namespace {
 
-void fill_defaults(panache_config &c) {
+// Zero fields take their defaults.  The anchor stride's default depends on
+// the top-k mode, so panache_default_config leaves it 0 (`resolve` false)
+// and the context resolves it: the paper's s = 2 for the top-k over the whole
+// stack, s = 1 for per-length top-k, where every length's list must be
+// exact and a length without an anchor of its own is reached only through
+// local completion.
+void fill_defaults(panache_config &c, bool resolve = true) {
     if (!c.alpha) c.alpha = 16;
     if (!c.gamma) c.gamma = 8;
-    if (!c.stride) c.stride = 2;
+    if (!c.stride && resolve) c.stride = c.topk_mode == PANACHE_TOPK_PER_LENGTH ? 1u : 2u;
     if (!c.K) c.K = 16;
     if (!c.B) c.B = 24;
     if (!c.d0) c.d0 = 12;
@@ -320,6 +343,7 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R,
     b += (size_t)R.total_cells * 8;                         // profile rows
     b += (size_t)R.anc.size() * (c.B + 1) * PN_FEAT * 4;
     b += (size_t)R.total_chunks * PN_FEAT * 4;               // tensor-core anchors
+    b += (size_t)R.anc.size() * 32 * R.a_max * 4;            // their twiddle operand
     R.footprint = b;
     if (c.hbm_budget_bytes && b > c.hbm_budget_bytes) return PANACHE_EBUDGET;
     return PANACHE_OK;
@@ -366,12 +390,15 @@ PnView make_view(panache_ctx *ctx, PnRequest &R) {
     v.g = R.g;
     v.gT = R.gT;
     v.anc = R.tca;
+    v.twb = R.twb;
+    v.twb_ld = R.a_max;
     v.err = R.err;
     v.dir_keys = R.dir_keys;
     v.dir_vals = R.dir_vals;
     v.bstart = R.bstart;
     v.prof = R.prof;
     v.stats = R.stats;
+    v.kt = ctx->kt.on ? &ctx->kt : nullptr;
     return v;
 }
 
@@ -438,8 +465,10 @@ int run_select(panache_ctx *ctx, PnRequest &R, const PnView &v, const GroupSet &
     PN_CU(cudaMallocAsync((void **)&dcnt, sizeof(int32_t) * ng, st));
     PN_CU(cudaMemcpyAsync(dg, gs.g.data(), sizeof(PnSelGroup) * ng, cudaMemcpyHostToDevice, st));
     PN_CU(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
+    pn_kt_begin(v.kt, PN_KT_SELECT, st);
     PN_CU(pn::launch_select(v, dg, ng, 0, R.total_cells, (int32_t)cap, ctx->cfg.eps0, kmax, dout, dcnt, R.flagbuf,
                             ctx->sm_count * 8, st));
+    pn_kt_end(v.kt, PN_KT_SELECT, st);
     ctx->launches += 10;
     std::vector<PnPick> hout((size_t)ng * kmax);
     std::vector<int32_t> hcnt(ng);
@@ -521,7 +550,10 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) 
     PN_CU(R.alloc(R.flagbuf, 4));
     PN_CU(R.alloc(R.err, 1));
     const bool tc_anchors = c.precision == PANACHE_MIXED && !(c.flags & PANACHE_FLAG_FP64_ANCHORS);
-    if (tc_anchors) PN_CU(R.alloc(R.tca, R.total_chunks * PN_FEAT));
+    if (tc_anchors) {
+        PN_CU(R.alloc(R.tca, R.total_chunks * PN_FEAT));
+        PN_CU(R.alloc(R.twb, nanc * 32 * (int64_t)std::max(1, R.a_max)));
+    }
     if (full_tables) {
         PN_CU(R.alloc(R.d_blk_anchor, (int64_t)R.blk_anchor.size()));
         PN_CU(R.alloc(R.d_blk_chunk0, (int64_t)R.blk_chunk0.size()));
@@ -562,14 +594,71 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) 
         PN_CU(cudaMemcpyAsync(R.g, hg.data(), 4 * hg.size(), cudaMemcpyHostToDevice, st));
         PN_CU(cudaMemcpyAsync(R.gT, hgT.data(), 4 * hgT.size(), cudaMemcpyHostToDevice, st));
     }
+    if (tc_anchors && nanc) {
+        PN_CU(pn::launch_twiddles(R.d_anc, (int32_t)nanc, R.a_max, R.twb, st));
+        ctx->launches += 1;
+    }
     PN_CU(cudaMemsetAsync(R.prof, 0xFF, sizeof(unsigned long long) * std::max<int64_t>(1, R.total_cells), st));
     PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
     PN_CU(cudaMemsetAsync(R.err, 0, sizeof(int), st));
     return PANACHE_OK;
 }
 
+// Exact row refinement of the top list (refine.cu): the top-kseed cells of
+// every selection group are each scanned against all valid partners at
+// their length, then the list is reselected and any cell not yet scanned is
+// scanned, until a pass finds no new cell or lowers none.  The final top-k is
+// a prefix of that list (the same greedy rule), so every reported cell ends
+// with its exact nearest neighbour.
+int refine_rows(panache_ctx *ctx, PnRequest &R, const PnView &v, const GroupSet &groups) {
+    cudaStream_t st = R.st;
+    int64_t max_windows = 0;
+    int m_top = 3;
+    for (auto &S : R.ser) {
+        max_windows = std::max<int64_t>(max_windows, S.n - S.m_min + 1);
+        m_top = std::max(m_top, (int)S.m_max);
+    }
+    std::set<std::tuple<int32_t, int32_t, int64_t>> done;
+    PnSeed *dtg = nullptr;
+    size_t tg_cap = 0;
+    int rc = PANACHE_OK;
+    for (int pass = 0; pass < 16 && rc == PANACHE_OK; ++pass) {
+        std::vector<std::vector<PnPick>> picks;
+        rc = run_select(ctx, R, v, groups, false, picks);
+        if (rc != PANACHE_OK) break;
+        std::vector<PnSeed> tg;
+        for (auto &gp : picks)
+            for (auto &p : gp)
+                if (done.insert(std::make_tuple(p.series, p.m, p.i)).second) tg.push_back(PnSeed{p.series, p.m, p.i, p.j});
+        if (tg.empty()) break;
+        if (tg.size() > tg_cap) {
+            if (dtg) cudaFreeAsync(dtg, st);
+            dtg = nullptr;
+            tg_cap = tg.size();
+            rc = from_cuda(cudaMallocAsync((void **)&dtg, sizeof(PnSeed) * tg_cap, st));
+            if (rc != PANACHE_OK) break;
+        }
+        rc = from_cuda(cudaMemcpyAsync(dtg, tg.data(), sizeof(PnSeed) * tg.size(), cudaMemcpyHostToDevice, st));
+        if (rc == PANACHE_OK) rc = from_cuda(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
+        pn_kt_begin(v.kt, PN_KT_REFINE, st);
+        if (rc == PANACHE_OK)
+            rc = from_cuda(pn::launch_refine(v, dtg, (int32_t)tg.size(), max_windows, m_top, R.flagbuf,
+                                             ctx->sm_count * 2, st));
+        pn_kt_end(v.kt, PN_KT_REFINE, st);
+        ctx->launches += 1;
+        int improved = 0;
+        if (rc == PANACHE_OK) rc = from_cuda(cudaMemcpyAsync(&improved, R.flagbuf, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (rc == PANACHE_OK) rc = from_cuda(cudaStreamSynchronize(st));
+        ctx->stats.refine_passes = pass + 1;
+        if (!improved) break;
+    }
+    if (dtg) cudaFreeAsync(dtg, st);
+    return rc;
+}
+
 // Algorithm 2 on the profile rows `v.prof`: hot-class sieve, completion
-// rounds and the final selection; then the counters and the error word.
+// rounds, the row refinement and the final selection; then the counters and
+// the error word.
 int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
              std::vector<std::vector<panache_motif>> &res) {
     const panache_config &c = ctx->cfg;
@@ -591,13 +680,13 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
         kseed[s] = (int)std::max<int64_t>(1, std::min<int64_t>(want, 6000 / (R.ser[s].m_max + 1)));
     }
     const GroupSet out_groups = make_groups(R, (int)c.topk_mode, kser);
+    // Seeds: the top-kseed cells in the output's mode.  In per-length mode
+    // this already holds the global top-kseed: suppression acts within one
+    // length, so the global greedy list restricted to a length is a
+    // prefix of that length's own greedy list, and no length contributes
+    // more than kseed cells to it.
+    const GroupSet seed_mode = make_groups(R, (int)c.topk_mode, kseed);
     if (!(c.flags & PANACHE_FLAG_NO_COMPLETION)) {
-        // Seeds: the top-kseed cells in the output's mode.  In per-length mode
-        // this already holds the global top-kseed: suppression acts within one
-        // length, so the global greedy list restricted to a length is a
-        // prefix of that length's own greedy list, and no length contributes
-        // more than kseed cells to it.
-        const GroupSet seed_mode = make_groups(R, (int)c.topk_mode, kseed);
         PnSeed *dseeds = nullptr;
         size_t seeds_cap = 0;
         for (uint32_t round = 0; round < c.rounds; ++round) {
@@ -614,7 +703,9 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
             }
             PN_CU(cudaMemcpyAsync(dseeds, seeds.data(), sizeof(PnSeed) * seeds.size(), cudaMemcpyHostToDevice, st));
             PN_CU(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
+            pn_kt_begin(v.kt, PN_KT_COMPLETE, st);
             PN_CU(pn::launch_complete(v, dseeds, (int32_t)seeds.size(), (int)c.dm, (int)c.dp, R.flagbuf, grid, st));
+            pn_kt_end(v.kt, PN_KT_COMPLETE, st);
             ctx->launches += 1;
             int improved = 0;
             PN_CU(cudaMemcpyAsync(&improved, R.flagbuf, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -624,11 +715,13 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
         }
         if (dseeds) PN_CU(cudaFreeAsync(dseeds, st));
     }
+    if (!(c.flags & PANACHE_FLAG_NO_REFINE)) PN_TRY(refine_rows(ctx, R, v, seed_mode));
     PN_TRY(tm.mark(7));
     std::vector<std::vector<PnPick>> picks;
     PN_TRY(run_select(ctx, R, v, out_groups, true, picks));
     PN_TRY(tm.mark(8));
     PN_TRY(tm.read(ctx->stats.step_ms));
+    ctx->kt.collect();
     res.assign(nser, {});
     for (size_t gi = 0; gi < picks.size(); ++gi) {
         for (auto &p : picks[gi]) {
@@ -652,6 +745,7 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
     ctx->stats.exact_stream = hs[PN_ST_LB_PASSED];
     ctx->stats.exact_sieve = hs[PN_ST_EXACT_SIEVE];
     ctx->stats.exact_completion = hs[PN_ST_EXACT_COMPLETION];
+    ctx->stats.exact_refine = hs[PN_ST_EXACT_REFINE];
     ctx->stats.kernel_launches = ctx->launches;
     ctx->stats.waves = 1;
     return PANACHE_OK;
@@ -699,10 +793,19 @@ int index_and_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const PnCo
     PN_CU(pn::launch_moment_table(v, R.total_windows, st));
     PN_TRY(tm.mark(2));
     if (R.tca) {
-        PN_CU(pn::launch_anchor_tc(v, R.d_tile_anchor, R.d_tile_row0, (int32_t)R.tile_anchor.size(), st));
+        // an injected wait fault never fires into a graph being captured
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        PN_CU(cudaStreamIsCapturing(st, &cs));
+        PnView va = v;
+        va.tc_fault = (cs == cudaStreamCaptureStatusNone && fault_fires(PANACHE_FAULT_TC_WAIT)) ? 1 : 0;
+        pn_kt_begin(v.kt, PN_KT_ANCHOR_TC, st);
+        PN_CU(pn::launch_anchor_tc(va, R.d_tile_anchor, R.d_tile_row0, (int32_t)R.tile_anchor.size(), st));
+        pn_kt_end(v.kt, PN_KT_ANCHOR_TC, st);
         ctx->launches += 1;
     }
+    pn_kt_begin(v.kt, PN_KT_FEATURES, st);
     PN_CU(pn::launch_features(v, R.d_blk_anchor, R.d_blk_chunk0, (int32_t)R.blk_anchor.size(), R.a_max, st));
+    pn_kt_end(v.kt, PN_KT_FEATURES, st);
     PN_TRY(tm.mark(3));
     PN_CU(pn::launch_ranks(v, R.total_windows, st));
     PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
@@ -710,7 +813,11 @@ int index_and_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const PnCo
     PN_TRY(tm.mark(4));
     ctx->launches += 3 + 5 + 1 + 5 + 2 + 4 * 3;
     if (!search) return PANACHE_OK;
-    PN_CU(pn::launch_search(v, R.total_windows, ctx->sm_count * (int)c.grid_mult, R.a_max, st));
+    if (c.flags & PANACHE_FLAG_WARM_START) ctx->launches += 1;
+    pn_kt_begin(v.kt, PN_KT_SEARCH, st);
+    PN_CU(pn::launch_search(v, R.total_windows, ctx->sm_count * (int)c.grid_mult, R.a_max, st,
+                            (c.flags & PANACHE_FLAG_WARM_START) != 0));
+    pn_kt_end(v.kt, PN_KT_SEARCH, st);
     ctx->launches += 1;
     return PANACHE_OK;
 }
@@ -723,6 +830,7 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     if (graph && ctx->gexec && ctx->last && same_shape(ctx->gshape, in)) {
         // replay: new samples into the kept buffers, one graph launch, then Algorithm 2
         memset(&ctx->stats, 0, sizeof(ctx->stats));
+        ctx->kt.reset(false);
         ctx->launches = ctx->glaunches;
         PnRequest &R = *ctx->last;
         ctx->stats.device_bytes = R.footprint;
@@ -736,6 +844,7 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     delete ctx->last;
     ctx->last = nullptr;
     memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->kt.reset((c.flags & PANACHE_FLAG_TIMING) != 0);
     ctx->launches = 0;
     PnRequest *Rp = new (std::nothrow) PnRequest();
     if (!Rp) return PANACHE_ENOMEM;
@@ -781,6 +890,10 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
             if (in[s].n) {
                 const cudaMemcpyKind kind =
                     (in[s].dtype & PANACHE_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+                if (fault_fires(PANACHE_FAULT_COPY)) {          // as if the copy had been refused
+                    if (!graph) cudaFreeAsync(stage, st);
+                    return PANACHE_ECUDA;
+                }
                 PN_CU(cudaMemcpyAsync(stage + stage_off[s], in[s].ptr, in[s].n * es, kind, st));
             }
         }
@@ -821,6 +934,7 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     if (!search) {
         for (int t = 5; t <= 8; ++t) PN_TRY(tm.mark(t));
         PN_TRY(tm.read(ctx->stats.step_ms));
+        ctx->kt.collect();
         int herr = 0;
         PN_CU(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         PN_CU(cudaStreamSynchronize(st));
@@ -882,9 +996,10 @@ int stream_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const std::ve
     PnQRange *drng = nullptr;
     PN_TRY(upload_tmp(R.st, rng, drng));
     PN_CU(pn::launch_query_order(v, total, R.total_buckets, R.st, drng, (int32_t)rng.size()));
-    PN_CU(pn::launch_search(v, total, ctx->sm_count * (int)ctx->cfg.grid_mult, R.a_max, R.st));
+    PN_CU(pn::launch_search(v, total, ctx->sm_count * (int)ctx->cfg.grid_mult, R.a_max, R.st,
+                            (ctx->cfg.flags & PANACHE_FLAG_WARM_START) != 0));
     PN_CU(cudaFreeAsync(drng, R.st));
-    ctx->launches += 2 + 4 * 3;
+    ctx->launches += 2 + 4 * 3 + ((ctx->cfg.flags & PANACHE_FLAG_WARM_START) ? 1 : 0);
     return PANACHE_OK;
 }
 
@@ -904,6 +1019,7 @@ int stream_advance(panache_stream *h) {
     PN_CU(cudaMemcpyAsync(R.d_ser, R.ser.data(), sizeof(PnSeries), cudaMemcpyHostToDevice, st));
     PN_CU(cudaMemcpyAsync(R.d_anc, R.anc.data(), sizeof(PnAnchor) * R.anc.size(), cudaMemcpyHostToDevice, st));
     PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
+    ctx->kt.reset(false);
     PnView v = make_view(ctx, R);
     PN_CU(pn::launch_runlen(v, n, st));
     PN_CU(pn::launch_moments(v, n, R.sq, st));
@@ -1011,7 +1127,7 @@ extern "C" {
 int panache_default_config(panache_config *cfg) {
     if (!cfg) return PANACHE_EINVAL;
     memset(cfg, 0, sizeof(*cfg));
-    fill_defaults(*cfg);
+    fill_defaults(*cfg, false);
     return PANACHE_OK;
 }
 
@@ -1135,6 +1251,8 @@ int panache_pmp_batch(panache_ctx *ctx, const panache_request *reqs, int32_t nre
         total.completion_rounds = std::max(total.completion_rounds, st.completion_rounds);
         total.device_bytes = std::max(total.device_bytes, st.device_bytes);
         total.kernel_launches += st.kernel_launches;
+        total.refine_passes = std::max(total.refine_passes, st.refine_passes);
+        total.exact_refine += st.exact_refine;
         for (int t = 0; t < 8; ++t) total.step_ms[t] += st.step_ms[t];
         for (int32_t r = wv.first; r < wv.second; ++r) {
             int e = copy_out(res[r - wv.first], out ? out + (int64_t)r * out_cap_per_req : nullptr, out_cap_per_req,
@@ -1219,6 +1337,7 @@ int panache_stream_topk(panache_stream *h, panache_motif *out, int64_t out_cap, 
     PnRequest &R = *h->R;
     cudaStream_t st = R.st;
     memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->kt.reset((ctx->cfg.flags & PANACHE_FLAG_TIMING) != 0);
     ctx->launches = 0;
     ctx->stats.device_bytes = R.footprint;
     PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
@@ -1308,6 +1427,26 @@ int panache_anchor_state(const panache_ctx *ctx, int32_t series_index, int32_t a
             memcpy(features + q * PN_FEAT, blk.data() + pn_row(q, C, A.nchunk) * PN_FEAT, 4 * PN_FEAT);
     }
     if (keys) PN_CU(cudaMemcpy(keys, R.sig + A.win_off, 4 * A.nw, cudaMemcpyDeviceToHost));
+    return PANACHE_OK;
+}
+
+int panache_inject_fault(int32_t kind, int32_t after) {
+    if (kind < PANACHE_FAULT_NONE || kind > PANACHE_FAULT_TC_WAIT || after < 0) return PANACHE_EINVAL;
+    g_fault_kind.store(PANACHE_FAULT_NONE);
+    g_fault_after.store(after);
+    g_fault_kind.store(kind);
+    return PANACHE_OK;
+}
+
+static_assert(PN_KT_COUNT == PANACHE_KERNEL_TIMES, "kernel timer slots and the header's count differ");
+
+int panache_kernel_times(const panache_ctx *ctx, double *ms, uint64_t *launches, int32_t cap) {
+    if (!ctx || cap < 0 || (cap > 0 && (!ms || !launches))) return PANACHE_EINVAL;
+    if (cap < PN_KT_COUNT) return PANACHE_ETRUNC;
+    for (int k = 0; k < PN_KT_COUNT; ++k) {
+        ms[k] = ctx->kt.ms[k];
+        launches[k] = ctx->kt.launches[k];
+    }
     return PANACHE_OK;
 }
 

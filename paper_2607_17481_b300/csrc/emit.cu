@@ -970,6 +970,7 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             int64_t blocks = (warps_needed + 7) / 8;
             if (blocks > grid_blocks) blocks = grid_blocks;
             const int zcap = (a_max + 3) & ~3;
+            pn_kt_begin(v.kt, PN_KT_SIEVE, st);
             // after the class sort, keys[p] is the class of member p
             if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             else if (exhaustive && v.x1) e = sieve_tiles_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);
@@ -978,6 +979,7 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             else if (w <= SB_WMAX) e = sieve_band_t<ZMix2>(v, cls, nmem, keys, vals, w, grid_blocks, st);
             else if (v.x1) e = sieve_t<ZMix1>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             else e = sieve_t<ZMix2>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
+            pn_kt_end(v.kt, PN_KT_SIEVE, st);
             if (e == cudaSuccess) e = cudaGetLastError();
         }
     }

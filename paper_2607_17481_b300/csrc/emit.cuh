@@ -44,6 +44,11 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
                          int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out);
 cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved,
                             int grid_blocks, cudaStream_t st);
+// Exact row refinement: each target cell (series, m, i) scanned against
+// every valid partner at its length; `improved` set when a cell decreased.
+// max_windows bounds the partners of any target (the longest series).
+cudaError_t launch_refine(const PnView &v, const PnSeed *tg, int32_t ntg, int64_t max_windows, int m_max,
+                          int *improved, int blocks_per_target, cudaStream_t st);
 cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ngrp, int64_t cell_begin,
                           int64_t cell_end, int32_t cap, double eps0, int32_t kmax, PnPick *out, int32_t *out_cnt,
                           int *overflow, int grid_blocks, cudaStream_t st);

@@ -109,11 +109,17 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
     const PnSeries S = v.series[A.series];
     const int a = A.a, kp = A.kp, B = v.B, C = v.C;
     const int dims = 2 * (v.K - 1);
-    double2 *tw = reinterpret_cast<double2 *>(smem);                 // (cos, sin)(2 pi t / a)
-    for (int t = threadIdx.x; t < a; t += blockDim.x) {
-        double sn, cs;
-        sincospi(2.0 * (double)t / (double)a, &sn, &cs);
-        tw[t] = make_double2(cs, sn);
+    // (cos, sin)(2 pi t / a) for t < a, needed only where chunk anchors come
+    // from the FP64 direct DFT (plain form, or mixed form without
+    // tensor-core anchors); otherwise each lane takes its own bin's factor
+    double2 *tw = reinterpret_cast<double2 *>(smem);
+    const bool direct = sizeof(ST) == 8 || !v.anc;
+    if (direct) {
+        for (int t = threadIdx.x; t < a; t += blockDim.x) {
+            double sn, cs;
+            sincospi(2.0 * (double)t / (double)a, &sn, &cs);
+            tw[t] = make_double2(cs, sn);
+        }
     }
     __syncthreads();
 
@@ -164,12 +170,28 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
         Xr = (ST)dr;
         Xi = (ST)di;
     }
-    // rotation factor of bin lane+1
-    const double2 wk = tw[bin ? lane + 1 : 0];
+    // rotation factor of bin lane+1 (the table's arithmetic, bit for bit)
+    double2 wk;
+    if (direct) {
+        wk = tw[bin ? lane + 1 : 0];
+    } else {
+        double sn, cs;
+        sincospi(2.0 * (double)(bin ? lane + 1 : 0) / (double)a, &sn, &cs);
+        wk = make_double2(cs, sn);
+    }
     const float ch = (float)wk.x, sh = (float)wk.y;
     const float cl = (float)(wk.x - (double)ch), sl = (float)(wk.y - (double)sh);
 
+    // sample differences t_{q+a} - t_q of the slide after window q, taken in
+    // FP64 (exact for float32 series) and rounded to the state type once:
+    // lane l computes the one of window q + l for 32 windows at a time, and
+    // each slide takes its own by a shuffle
+    ST dlane = 0;
     for (int64_t q = q0; q < qend; ++q) {
+        if (((q - q0) & 31) == 0) {
+            const int64_t ql = q + lane;
+            dlane = ql + 1 < qend ? (ST)(xs[ql + a] - xs[ql]) : (ST)0;
+        }
         const bool nonconst = rl[q] < a;
         float f_re = 0.0f, f_im = 0.0f;
         if (v.precision == 0) {
@@ -209,8 +231,8 @@ __global__ void __launch_bounds__(FT_THREADS) k_features(PnView v, const int32_t
         if (lane == 0) v.sig[A.win_off + q] = nonconst ? (__brev(bits) >> (32 - B)) : 0u;
         if (lane == B) v.sproj[A.win_off + q] = mg;          // the sieve's sort key
         __syncwarp();
+        const ST delta = __shfl_sync(0xffffffffu, dlane, (int)((q - q0) & 31));
         if (q + 1 < qend) {
-            const ST delta = (ST)(xs[q + a] - xs[q]);
             if (bin) {
                 const ST re = Xr + delta;
                 const ST im = Xi;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "ktimer.h"
 #include "plan.h"
 
 // Everything a kernel needs to know about a request, passed by value.
@@ -47,6 +48,9 @@ struct PnView {
     const float *g;       // projections [nanchors][B+1][PN_FEAT]
     const float *gT;      // the same, transposed per anchor: [nanchors][PN_FEAT][32] (projection l in lane l)
     float *anc;           // mixed form: tensor-core chunk anchors, [flat chunk][PN_FEAT] (null: FP64 direct DFT)
+    const float *twb;     // with anc: the contraction's twiddle operand per anchor, [anchor][32][twb_ld]
+    int32_t twb_ld;       // row length of twb (>= every anchor length)
+    int32_t tc_fault;     // test hook: the anchor kernel issues no MMA and its waits give up quickly
     int *err;             // device error word (PN_ERR_*), 0 when every bounded wait succeeded
     // directory
     uint32_t *dir_keys;   // global bucket id of every item (sorted)
@@ -56,6 +60,8 @@ struct PnView {
     unsigned long long *prof;
     // counters (device)
     unsigned long long *stats;
+    // per-kernel event timer of the request (host object; null unless timing)
+    PnKTimer *kt;
 };
 
 #define PN_FT_CHUNKS 4         // chunks (one warp each) per block of the feature kernel
@@ -69,6 +75,7 @@ enum PnStat {
     PN_ST_EXACT_COMPLETION,
     PN_ST_HOT_CLASSES,
     PN_ST_IMPROVED,
+    PN_ST_EXACT_REFINE,
     PN_ST_COUNT
 };
 
@@ -181,6 +188,7 @@ cudaError_t launch_features(const PnView &v, const int32_t *blk_anchor, const in
 cudaError_t launch_ranks(const PnView &v, int64_t total_windows, cudaStream_t st);
 cudaError_t launch_directory(const PnView &v, int64_t total_items, int64_t total_buckets, cudaStream_t st);
 size_t anchor_tc_smem();
+cudaError_t launch_twiddles(const PnAnchor *anc_dev, int32_t nanc, int32_t ld, float *tw, cudaStream_t st);
 cudaError_t launch_anchor_tc(const PnView &v, const int32_t *tile_anchor, const int32_t *tile_row0, int32_t ntiles,
                              cudaStream_t st);
 cudaError_t launch_query_order(const PnView &v, int64_t total_queries, int64_t total_buckets, cudaStream_t st,
@@ -190,7 +198,10 @@ int search_max_budget();
 // out[15..29] collision-probability means for K = 2..16, out[30] pairs.
 cudaError_t launch_calibration(const double *x, const PnCalWin *win, int nwin, const int *g_off, const int *g_cnt,
                                const int *row_g, const int *row_a, int nrows, int B, double *out, cudaStream_t st);
-cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, int a_max, cudaStream_t st);
+// The streaming search of every query; with `warm`, the warm-start pass
+// (one exact distance per query, within its admitted candidates) runs first.
+cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, int a_max, cudaStream_t st,
+                          bool warm);
 // Population and depth every window of anchor `anchor` would probe with, by
 // the search's own rule; -1 for windows that are not searched (constant, or
 // no valid earlier window).

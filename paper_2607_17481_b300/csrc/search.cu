@@ -33,9 +33,22 @@ constexpr int SR_WARPS = 8;
 constexpr int SR_THREADS = SR_WARPS * 32;
 constexpr int SR_MAXR = 512;   // largest supported budget R
 
+constexpr int SR_WARM = 32;    // candidates a query's warm start inspects
+
 // HALF: the rows are read from the half-precision copy, and every bound test
 // carries the rounding margin of pn_row_margin.
-template <class Z, bool HALF>
+//
+// WARM: the warm start that runs before the search.  Each query takes the
+// SR_WARM most recent valid entries of its exact bucket -- a subset of the
+// candidates the search admits, whatever the budget split -- bounds them and
+// evaluates the one of smallest bound exactly, updating both cells.  Queries
+// run grouped by bucket, not in stream order, so without it many candidate
+// cells are still empty when a query tests them and the threshold
+// max(best_q, P[c]) rejects nothing; after it, nearly every cell holds the
+// exact distance of an admitted pair.  The final profile is unchanged (it
+// is the minimum over the admitted pairs); only the number of pairs the
+// bound lets through drops.
+template <class Z, bool HALF, bool WARM>
 __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {
     using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
@@ -84,7 +97,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         sF[warp][lane] = pn_row_elem<HALF>(Fa, pn_row32((uint32_t)q, v.cshift, nch), lane);
         __syncwarp();
         float mg = __int_as_float(0x7f800000);
-        if (lane < d) {
+        if (!WARM && lane < d) {
             // <g_lane, F> in the FMA order of pn_margin, the projection read from
             // the transposed copy (one coalesced 128-byte row per dimension)
             const float *gt = v.gT + (int64_t)ai * PN_FEAT * 32 + lane;
@@ -97,17 +110,19 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         }
         const uint32_t sgq = v.sig[w];
         const uint32_t pre = d > 0 ? (sgq >> (v.B - d)) : 0u;
-        const int h = d <= 0 ? 0 : min(d, min(v.probe_cap, 1 + max(0, d - v.d0)));
+        const int h = (WARM || d <= 0) ? 0 : min(d, min(v.probe_cap, 1 + max(0, d - v.d0)));
         // lane j (0 <= j <= h) owns probe j: the exact prefix, then Hamming-1
         // buckets in increasing margin (ties to the lower bit).  Each bit lane
         // ranks its margin among the d bits; the lane of rank r flips its bit
         // for probe r + 1, handed to lane r + 1 through shared memory.
-        int rank = 0;
-        for (int k = 0; k < d; ++k) {
-            const float o = __shfl_sync(0xffffffffu, mg, k);
-            rank += (o < mg || (o == mg && k < lane)) ? 1 : 0;
+        if (h > 0) {
+            int rank = 0;
+            for (int k = 0; k < d; ++k) {
+                const float o = __shfl_sync(0xffffffffu, mg, k);
+                rank += (o < mg || (o == mg && k < lane)) ? 1 : 0;
+            }
+            if (lane < d && rank < h) sprobe[warp][rank + 1] = pre ^ (1u << (d - 1 - lane));
         }
-        if (lane < d && rank < h) sprobe[warp][rank + 1] = pre ^ (1u << (d - 1 - lane));
         __syncwarp();
         const uint32_t my_probe = (lane >= 1 && lane <= h) ? sprobe[warp][lane] : pre;
         // every probe's bucket range and valid prefix (start <= q - excl), in parallel
@@ -126,7 +141,14 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
         }
         // budgeted candidate list, in probe order
         int taken = 0;
-        for (int j = 0; j <= h && taken < R; ++j) {
+        if constexpr (WARM) {
+            // the most recent valid entries of the exact bucket
+            const uint32_t lo = __shfl_sync(0xffffffffu, my_lo, 0);
+            const int sz = (int)__shfl_sync(0xffffffffu, my_sz, 0);
+            taken = min(sz, SR_WARM);
+            if (lane < taken) scand[lane] = v.dir_vals[lo + sz - taken + lane];
+        }
+        for (int j = 0; !WARM && j <= h && taken < R; ++j) {
             const uint32_t lo = __shfl_sync(0xffffffffu, my_lo, j);
             const int sz = (int)__shfl_sync(0xffffffffu, my_sz, j);
             const int rem = R - taken;
@@ -149,8 +171,10 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
             taken += cnt;
         }
         __syncwarp();
-        n_q += 1;
-        n_c += taken;
+        if (!WARM) {
+            n_q += 1;
+            n_c += taken;
+        }
         if (taken == 0) continue;
 
         // z-normalised query window, staged once
@@ -249,6 +273,7 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
                 }
                 if (lane == bl) lbs = __int_as_float(0x7f800000);   // done: not retested
             }
+            if constexpr (WARM) break;                      // the warm start evaluates one pair
             bool surv = false;
             if (lane < nblk) {
                 ZT tc = Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kc));
@@ -290,17 +315,26 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
     }
 }
 
-template <class Z, bool HALF>
-cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
+template <class Z, bool HALF, bool WARM>
+cudaError_t launch_one(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
     const int zcap = (a_max + 3) & ~3;
     const size_t sm = (sizeof(unsigned long long) + sizeof(uint32_t)) * (size_t)v.R * SR_WARPS +
                       sizeof(typename Z::Q) * (size_t)zcap * SR_WARPS;
-    cudaError_t e = pn_allow_smem(k_search<Z, HALF>, sm);
+    cudaError_t e = pn_allow_smem(k_search<Z, HALF, WARM>, sm);
     if (e != cudaSuccess) return e;
     int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
     unsigned g = (unsigned)(need < grid_blocks ? need : grid_blocks);
-    k_search<Z, HALF><<<g, SR_THREADS, sm, st>>>(v, total, zcap);
+    k_search<Z, HALF, WARM><<<g, SR_THREADS, sm, st>>>(v, total, zcap);
     return cudaGetLastError();
+}
+
+template <class Z, bool HALF>
+cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st, bool warm) {
+    if (warm) {
+        cudaError_t e = launch_one<Z, HALF, true>(v, total, grid_blocks, a_max, st);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_one<Z, HALF, false>(v, total, grid_blocks, a_max, st);
 }
 
 // Introspection: the population and depth of every window of one anchor,
@@ -331,14 +365,14 @@ cudaError_t launch_query_levels(const PnView &v, int32_t anchor, int64_t nw, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_search(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
+cudaError_t launch_search(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st, bool warm) {
     if (total <= 0) return cudaSuccess;
-    if (v.precision == 0) return launch_t<ZPlain, false>(v, total, grid_blocks, a_max, st);
+    if (v.precision == 0) return launch_t<ZPlain, false>(v, total, grid_blocks, a_max, st, warm);
     if (v.Fh)   // half rows: the mixed form only (checked at configuration)
-        return v.x1 ? launch_t<ZMix1, true>(v, total, grid_blocks, a_max, st)
-                    : launch_t<ZMix2, true>(v, total, grid_blocks, a_max, st);
-    return v.x1 ? launch_t<ZMix1, false>(v, total, grid_blocks, a_max, st)
-                : launch_t<ZMix2, false>(v, total, grid_blocks, a_max, st);
+        return v.x1 ? launch_t<ZMix1, true>(v, total, grid_blocks, a_max, st, warm)
+                    : launch_t<ZMix2, true>(v, total, grid_blocks, a_max, st, warm);
+    return v.x1 ? launch_t<ZMix1, false>(v, total, grid_blocks, a_max, st, warm)
+                : launch_t<ZMix2, false>(v, total, grid_blocks, a_max, st, warm);
 }
 
 }  // namespace pn

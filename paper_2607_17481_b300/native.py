@@ -23,14 +23,18 @@ FLAG_EXHAUSTIVE_SIEVE, FLAG_NO_SIEVE, FLAG_NO_COMPLETION, FLAG_TIMING, FLAG_INDE
 FLAG_FP64_ANCHORS = 0x20
 FLAG_GRAPH = 0x40
 FLAG_HALF_FEATURES = 0x80
+FLAG_WARM_START = 0x100
+FLAG_NO_REFINE = 0x200
 NOALLOC_NEED_MAX = 6300   # largest k (m + 1) of panache_topk_row_noalloc
+FAULT_NONE, FAULT_ALLOC, FAULT_COPY, FAULT_TC_WAIT = 0, 1, 2, 3
 
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
             "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
             "panache_stream_length", "panache_stream_close", "panache_stream_checkpoint", "panache_last_stats",
             "panache_profile_rows",
-            "panache_anchor_state", "panache_query_levels", "panache_projections", "panache_calibrate_width", "panache_strerror",
-            "panache_topk_row_noalloc",
+            "panache_anchor_state", "panache_query_levels", "panache_projections", "panache_calibrate_width",
+            "panache_strerror",
+            "panache_topk_row_noalloc", "panache_alu_peak", "panache_kernel_times", "panache_inject_fault",
             "panache_server_create", "panache_server_destroy", "panache_server_submit", "panache_server_wait",
             "panache_server_stream_open", "panache_server_append", "panache_server_stream_topk",
             "panache_server_stream_close", "panache_server_get_stats")
@@ -62,12 +66,15 @@ class Request(ctypes.Structure):
 
 
 STEP_NAMES = ("upload", "moments", "features", "directory", "search", "sieve", "completion", "select")
+KERNEL_NAMES = ("anchor_tc", "features", "search", "sieve", "complete", "select", "refine")
+KERNEL_TIMES = len(KERNEL_NAMES)
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in (
         "queries", "candidates", "exact_stream", "exact_sieve", "exact_completion", "hot_classes",
-        "completion_rounds", "device_bytes", "kernel_launches", "waves")] + [("step_ms", ctypes.c_double * 8)]
+        "completion_rounds", "device_bytes", "kernel_launches", "waves", "refine_passes", "exact_refine")] + \
+        [("step_ms", ctypes.c_double * 8)]
 
 
 class ServerStats(ctypes.Structure):
@@ -108,6 +115,9 @@ def lib():
         L.panache_profile_rows.argtypes = [vp, i32, vp, i64]
         L.panache_anchor_state.argtypes = [vp, i32, i32, ctypes.POINTER(i32), vp, vp, i64]
         L.panache_query_levels.argtypes = [vp, i32, i32, vp, vp, i64]
+        L.panache_kernel_times.argtypes = [vp, vp, vp, i32]
+        L.panache_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+        L.panache_inject_fault.argtypes = [i32, i32]
         L.panache_projections.argtypes = [ctypes.POINTER(Config), i32, vp, i64]
         L.panache_topk_row_noalloc.argtypes = [vp, i64, i32, vp, i32, ctypes.c_double, vp, vp, vp]
         u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -236,6 +246,14 @@ class Context:
         out = {name: int(getattr(s, name)) for name, _ in Stats._fields_ if name != "step_ms"}
         out["step_ms"] = {nm: float(s.step_ms[t]) for t, nm in enumerate(STEP_NAMES)}
         return out
+
+    def kernel_times(self) -> dict:
+        """{kernel: (ms, launches)} of the last request made with FLAG_TIMING."""
+        ms = np.zeros(KERNEL_TIMES)
+        ln = np.zeros(KERNEL_TIMES, dtype=np.uint64)
+        _check(lib().panache_kernel_times(self._h, ms.ctypes.data_as(ctypes.c_void_p),
+                                          ln.ctypes.data_as(ctypes.c_void_p), KERNEL_TIMES), "kernel_times")
+        return {nm: (float(ms[k]), int(ln[k])) for k, nm in enumerate(KERNEL_NAMES)}
 
     def profile_rows(self, series_index: int, n: int, L: int) -> np.ndarray:
         keys = np.empty(n * L, dtype=np.uint64)
@@ -431,6 +449,18 @@ def topk_row_noalloc(x_dev, keys_dev, m: int, k: int, eps0: float, out_dev, coun
                                           ctypes.c_void_p(keys_dev.data_ptr()), k, eps0,
                                           ctypes.c_void_p(out_dev.data_ptr()), ctypes.c_void_p(count_dev.data_ptr()),
                                           ctypes.c_void_p(stream_ptr))
+
+
+def inject_fault(kind: int, after: int = 0):
+    """Arms one host-made failure of a later operation (test hook; FAULT_NONE disarms)."""
+    _check(lib().panache_inject_fault(kind, after), "inject_fault")
+
+
+def alu_peak(kind: int) -> float:
+    """Measured TFLOP/s of one pipe on the current device: 0 FP32 FMA, 1 packed FP32 FMA, 2 FP64 FMA."""
+    t = ctypes.c_double()
+    _check(lib().panache_alu_peak(kind, ctypes.byref(t)), "alu_peak")
+    return t.value
 
 
 def unpack_keys(keys: np.ndarray):

@@ -35,7 +35,8 @@ def test_every_declared_symbol_exported(lib):
 
 def test_default_config_is_the_papers(lib):
     c = native.default_config()
-    assert (c.alpha, c.gamma, c.stride, c.K, c.B, c.d0, c.probe_cap, c.sieve_w) == (16, 8, 2, 16, 24, 12, 8, 8)
+    assert (c.alpha, c.gamma, c.stride, c.K, c.B, c.d0, c.probe_cap, c.sieve_w) == (16, 8, 0, 16, 24, 12, 8, 8)
+    # stride 0: resolved by the context from the top-k mode (2 global, 1 per length)
     assert (c.dm, c.dp, c.rounds) == (6, 4, 8)
     assert c.lambda_ == 1e-4 and c.eps0 == 1e-6
 
@@ -72,3 +73,11 @@ def test_no_cpu_fallback_when_library_missing(tmp_path, monkeypatch):
     monkeypatch.setattr(native, "_lib", None)
     with pytest.raises(ImportError):
         native.lib()
+
+
+def test_inject_fault_arguments():
+    """The fault hook validates its arguments and disarms (no device needed)."""
+    from paper_2607_17481_b300 import native
+    assert native.lib().panache_inject_fault(99, 0) == native.EINVAL
+    assert native.lib().panache_inject_fault(native.FAULT_ALLOC, -1) == native.EINVAL
+    assert native.lib().panache_inject_fault(native.FAULT_NONE, 0) == native.OK

@@ -51,3 +51,26 @@ def test_traffic_record_follows_kernel_sources(tmp_path, monkeypatch):
     assert bench.measured_traffic(1000) == pytest.approx(352000.0)
     src.write_bytes(b"kernel v2")                                   # source changed since the capture
     assert bench.measured_traffic(1000) is None
+
+
+def test_kernel_table_arithmetic():
+    """Per-kernel fractions: algorithmic flops and bytes per request over the
+    kernel's event time, against the measured FP32 / TF32 and HBM ceilings."""
+    st = {"queries": 1000, "candidates": 100_000, "exact_stream": 40_000, "exact_sieve": 8000,
+          "exact_completion": 10_530, "completion_rounds": 3}
+    kt = {"anchor_tc": (0.5, 1), "features": (1.0, 1), "search": (10.0, 1), "sieve": (2.0, 1),
+          "complete": (1.0, 3), "select": (0.5, 4)}
+    anchors = [100, 150]
+    n = 10_000
+    rows = {r["kernel"]: r for r in bench.kernel_table(st, kt, n, anchors, {"hbm_gbs": 8000.0},
+                                                       {"fp32": 100.0, "tf32_cublas": 500.0})}
+    s = rows["search"]
+    assert s["flops"] == 90.0 * 100_000 + 5.0 * 125.0 * 40_000
+    assert s["bytes"] == 128.0 * 101_000
+    assert s["fp32_frac"] == pytest.approx(s["flops"] / 10e-3 / 1e12 / 100.0, rel=1e-3)
+    assert s["hbm_frac"] == pytest.approx(s["bytes"] / 10e-3 / 1e9 / 8000.0, rel=1e-3)
+    f = rows["features"]
+    nwa = (n - 99) + (n - 149)
+    assert f["flops"] == 1650.0 * nwa and f["bytes"] == 164.0 * nwa
+    assert "tf32_frac" in rows["anchor_tc"] and "fp32_frac" not in rows["anchor_tc"]
+    assert rows["select"]["bytes"] == 24.0 * 51 * n * 4

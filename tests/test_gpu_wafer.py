@@ -80,21 +80,41 @@ def test_prefix_wide_sieve_half_feature_rows(pn, wafer):
 
 
 def test_prefix_per_length_top20(pn, wafer, golden):
-    """Anchor stride 1: all 1020 cells.  The paper's stride 2 is reported separately."""
+    """All 1020 per-length cells at the library's defaults (anchor stride 1 in per-length mode)."""
     from parity import compare
-    x, got = _prefix_run(pn, wafer, precision=1, topk_mode=1, stride=1)
+    x, got = _prefix_run(pn, wafer, precision=1, topk_mode=1)
     r = compare(x.astype(np.float64), got, golden[1])
     assert r["misses"] == 0, r["miss_list"]
     assert r["bad_dist"] == 0
 
 
-def test_prefix_per_length_paper_defaults(pn, wafer, golden):
+def test_prefix_per_length_paper_stride(pn, wafer, golden):
+    """The paper's stride 2 in per-length mode, reported: three cells of one
+    pair that no anchor's search brings together are missed."""
     from parity import compare
-    x, got = _prefix_run(pn, wafer, precision=1, topk_mode=1)
+    x, got = _prefix_run(pn, wafer, precision=1, topk_mode=1, stride=2)
     r = compare(x.astype(np.float64), got, golden[1])
-    print("per-length recall at the paper's defaults:", (r["hits"] + r["ties"]) / r["n"], r["miss_list"])
+    print("per-length recall at stride 2:", (r["hits"] + r["ties"]) / r["n"], r["miss_list"])
     assert r["misses"] <= 0.005 * r["n"]
     assert r["bad_dist"] == 0
+
+
+def test_5m_reported_cells_are_exact(pn):
+    """The benchmark's workload (5,000,000 samples, mixed precision): every
+    reported motif's distance is the oracle's exact nearest-neighbour distance
+    of its cell (FP64, over all valid neighbours), within 1e-6."""
+    w = workloads.wafer_like(5_000_000, seed=0)
+    ctx = pn.Context(precision=1, topk_mode=0)
+    got = ctx.pmp(w.x, 100, 150, 20, 150)
+    assert len(got) == 20
+    x = w.x.astype(np.float64)
+    for r in got:
+        m, i, j, d = int(r["m"]), int(r["i"]), int(r["j"]), float(r["d"])
+        assert abs(i - j) >= 150
+        P, I = exact.pmp_cells(x, m, 150, [i])
+        assert abs(d - P[0]) <= 1e-6 * P[0], (m, i, j, d, P[0])
+        if I[0] != j:
+            assert abs(exact.dist(x, m, i, j) - P[0]) <= 1e-12 * P[0]
 
 
 def test_full_size_reported_cells_are_exact(pn, wafer):

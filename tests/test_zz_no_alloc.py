@@ -41,10 +41,11 @@ def _pool():
 
 
 def _pool_marks_reset():
+    from cuda.bindings import driver
     cudart, pool = _pool()
     for attr in (cudart.cudaMemPoolAttr.cudaMemPoolAttrUsedMemHigh,
                  cudart.cudaMemPoolAttr.cudaMemPoolAttrReservedMemHigh):
-        err, = cudart.cudaMemPoolSetAttribute(pool, attr, cudart.cuuint64_t(0))
+        err, = cudart.cudaMemPoolSetAttribute(pool, attr, driver.cuuint64_t(0))
         assert err == cudart.cudaError_t.cudaSuccess
 
 
