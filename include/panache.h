@@ -107,7 +107,7 @@ extern "C" {
                                               the bound passes the same pairs and the extra pass costs more
                                               than it saves, so it is off by default. */
 #define PANACHE_FLAG_NO_REFINE 0x200      /* skip the exact row refinement of the top list.  After local
-                                              completion, every cell of the top seed_mult*k list (per group)
+                                              completion, every cell of the top refine_mult*k list (per group)
                                               is scanned against all its valid partners at its length with the
                                               in-stream arithmetic and lowered to the smallest distance found;
                                               the list is reselected and new cells scanned until nothing
@@ -120,7 +120,7 @@ extern "C" {
  * alpha 16, gamma 8 (R = 128), stride 2, K 16, B 24, d0 12, probe cap 8,
  * sieve width 8, (dm, dp) = (6, 4), 8 completion rounds, lambda 1e-4,
  * eps0 1e-6, batch beta = excl, chunk 256 slides per direct-DFT anchor,
- * seed_mult 2, grid_mult 8.  One exception: a zero stride is the paper's
+ * seed_mult 2, grid_mult 8, refine_mult 4.  One exception: a zero stride is the paper's
  * s = 2 in global top-k mode but s = 1 in per-length mode, where every
  * length's own list must be exact (at s = 2 a length between anchors is
  * reached only through local completion, which can miss a cell whose best
@@ -144,6 +144,9 @@ typedef struct {
     uint32_t beta;        /* batch length of the streaming schedule (0: excl; capped at excl) */
     uint32_t seed_mult;   /* completion seeds per round: the top seed_mult*k cells (per length in per-length mode) */
     uint32_t grid_mult;   /* resident-block multiple of the search and sieve grids (blocks = SMs * grid_mult) */
+    uint32_t refine_mult; /* the row refinement scans the top refine_mult*k cells of each selection group
+                             (capped, like the completion seeds, so that the pool holds them) */
+    uint32_t _reserved;
     uint64_t seed;        /* seed of the Gaussian projections */
     uint64_t hbm_budget_bytes; /* admission limit on a request's device footprint (0: none) */
     double lambda;        /* bound shrink */
@@ -214,6 +217,29 @@ int panache_set_stream(panache_ctx *ctx, void *cuda_stream);
  * the count needed).  Errors: EINVAL, ENOMEM, EBUDGET, ECUDA, EPOOL. */
 int panache_pmp(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min, int32_t m_max,
                 int32_t k, int32_t excl, panache_motif *out, int64_t out_cap, int64_t *out_len);
+
+/* Anchor sharding of one series across ranks, one process per GPU (Sec. 3.5:
+ * every anchor owns its spectral state, directory and profile row and
+ * shares nothing with the others).  panache_pmp_anchor_shard indexes,
+ * searches and sieves only the anchors at positions p of
+ * A = (m_min, m_min + s, ..., m_max) with p mod world == rank, and copies
+ * the resulting profile rows (the layout of panache_profile_rows:
+ * [m_max - m_min + 1][n] packed keys, empty cells all ones) into the host
+ * array rows[0..cap).  The ranks' rows merge by the elementwise minimum of
+ * the keys as unsigned 64-bit integers; panache_pmp_from_rows runs the rest
+ * of the emit stage (local completion, row refinement, selection) on merged
+ * host rows, with the series present, and writes the motifs as panache_pmp
+ * does.  The motifs equal panache_pmp's on the same series and
+ * configuration: the stream and sieve rows of a length come from its own
+ * anchor alone, and the profile is the minimum over the admitted pairs
+ * whatever the schedule.  Errors: EINVAL (rank outside [0, world), sizes),
+ * ETRUNC (cap < L n), the others as panache_pmp. */
+int panache_pmp_anchor_shard(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min,
+                             int32_t m_max, int32_t k, int32_t excl, int32_t rank, int32_t world, uint64_t *rows,
+                             int64_t cap);
+int panache_pmp_from_rows(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min, int32_t m_max,
+                          int32_t k, int32_t excl, const uint64_t *rows, panache_motif *out, int64_t out_cap,
+                          int64_t *out_len);
 
 /* Many independent series in one set of launches (the batched form).  The
  * motifs of request r go to out[r * out_cap_per_req ...], their count to

@@ -225,6 +225,7 @@ void fill_defaults(panache_config &c, bool resolve = true) {
     if (!c.chunk) c.chunk = 256;
     if (!c.seed_mult) c.seed_mult = 2;
     if (!c.grid_mult) c.grid_mult = 8;
+    if (!c.refine_mult) c.refine_mult = 4;
     if (c.lambda == 0.0) c.lambda = 1e-4;
     if (c.eps0 == 0.0) c.eps0 = 1e-6;
 }
@@ -235,7 +236,7 @@ int check_config(const panache_config &c) {
     if (c.probe_cap < 1 || c.probe_cap > 8 || c.precision > 1 || c.topk_mode > 1) return PANACHE_EINVAL;
     if ((c.flags & PANACHE_FLAG_HALF_FEATURES) && c.precision != PANACHE_MIXED) return PANACHE_EINVAL;
     if (c.chunk < 16 || c.chunk > 4096 || (c.chunk & (c.chunk - 1))) return PANACHE_EINVAL;
-    if (c.grid_mult > 64 || c.dm > 16 || c.dp > 16) return PANACHE_EINVAL;
+    if (c.grid_mult > 64 || c.dm > 16 || c.dp > 16 || c.refine_mult > 64) return PANACHE_EINVAL;
     if (!(c.lambda > 0.0 && c.lambda < 1.0) || !(c.eps0 >= 0.0)) return PANACHE_EINVAL;
     return PANACHE_OK;
 }
@@ -250,12 +251,24 @@ int check_series(const SeriesIn &s) {
     return PANACHE_OK;
 }
 
+// Anchor sharding of one series across ranks (Sec. 3.5: each anchor owns its
+// state and shares nothing): a rank indexes, searches and sieves the anchors
+// at positions p of A with p mod world == rank and hands out its profile
+// rows (rows_out); the merged rows (elementwise minimum over the ranks) come
+// back through rows_in for the emit stage's completion, refinement and
+// selection.
+struct PnShard {
+    int32_t rank = 0, world = 1;
+    const uint64_t *rows_in = nullptr;   // emit only: the merged rows [L][n]
+    uint64_t *rows_out = nullptr;        // shard: this rank's rows [L][n]
+};
+
 // Builds every table of a request and its device footprint.  With `caps`,
 // series s is laid out for caps[s] >= n samples (a resident stream): every
 // per-window array, feature block, directory level and profile row is sized
 // for the capacity, while n, nw and the launches cover the samples present.
 int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R,
-         const std::vector<int64_t> *caps = nullptr) {
+         const std::vector<int64_t> *caps = nullptr, const PnShard *sh = nullptr) {
     const int C = (int)c.chunk;
     int64_t x_off = 0, row_off = 0;
     for (size_t s = 0; s < in.size(); ++s) {
@@ -276,6 +289,12 @@ int plan(const panache_config &c, const std::vector<SeriesIn> &in, PnRequest &R,
         std::vector<int> al;
         for (int a = si.m_min; a <= si.m_max; a += (int)c.stride) al.push_back(a);
         if (al.back() != si.m_max) al.push_back(si.m_max);
+        if (sh && sh->world > 1) {
+            std::vector<int> mine;
+            for (size_t p = 0; p < al.size(); ++p)
+                if ((int32_t)(p % (size_t)sh->world) == sh->rank) mine.push_back(al[p]);
+            al.swap(mine);
+        }
         for (int a : al) {
             const int64_t nwc = ncap - a + 1;             // windows at capacity
             if (nwc <= 0) continue;
@@ -517,10 +536,28 @@ struct StepTimer {
 
 // Device buffers of a planned request (or of a resident stream), its tables,
 // projections and initial state: profile rows unset, counters and error word zero.
-int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) {
+int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables, bool emit_only = false) {
     const panache_config &c = ctx->cfg;
     cudaStream_t st = R.st;
-    const int64_t nser = (int64_t)R.ser.size(), nanc = (int64_t)R.anc.size();
+    const int64_t nser = (int64_t)R.ser.size(), nanc = emit_only ? 0 : (int64_t)R.anc.size();
+    if (emit_only) {
+        // the emit stage alone reads samples, prefix sums, run lengths and rows
+        PN_CU(R.alloc(R.d_ser, nser));
+        PN_CU(R.alloc(R.x, R.total_samples));
+        PN_CU(R.alloc(R.xs, R.total_samples));
+        if (want_x1) PN_CU(R.alloc(R.x1, R.total_samples));
+        PN_CU(R.alloc(R.sq, R.total_samples + nser));
+        PN_CU(R.alloc(R.shift, nser));
+        PN_CU(R.alloc(R.runlen, R.total_samples));
+        PN_CU(R.alloc(R.prof, R.total_cells));
+        PN_CU(R.alloc(R.stats, PN_ST_COUNT));
+        PN_CU(R.alloc(R.flagbuf, 4));
+        PN_CU(R.alloc(R.err, 1));
+        PN_CU(cudaMemcpyAsync(R.d_ser, R.ser.data(), sizeof(PnSeries) * nser, cudaMemcpyHostToDevice, st));
+        PN_CU(cudaMemsetAsync(R.stats, 0, sizeof(unsigned long long) * PN_ST_COUNT, st));
+        PN_CU(cudaMemsetAsync(R.err, 0, sizeof(int), st));
+        return PANACHE_OK;
+    }
     PN_CU(R.alloc(R.d_ser, nser));
     PN_CU(R.alloc(R.d_anc, nanc));
     PN_CU(R.alloc(R.d_lev, (int64_t)R.lev.size()));
@@ -604,8 +641,8 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables) 
     return PANACHE_OK;
 }
 
-// Exact row refinement of the top list (refine.cu): the top-kseed cells of
-// every selection group are each scanned against all valid partners at
+// Exact row refinement of the top list (refine.cu): the top refine_mult*k
+// cells of every selection group are each scanned against all valid partners at
 // their length, then the list is reselected and any cell not yet scanned is
 // scanned, until a pass finds no new cell or lowers none.  The final top-k is
 // a prefix of that list (the same greedy rule), so every reported cell ends
@@ -659,25 +696,55 @@ int refine_rows(panache_ctx *ctx, PnRequest &R, const PnView &v, const GroupSet 
 // Algorithm 2 on the profile rows `v.prof`: hot-class sieve, completion
 // rounds, the row refinement and the final selection; then the counters and
 // the error word.
+enum { PN_EMIT_SIEVE = 1, PN_EMIT_REST = 2, PN_EMIT_ALL = 3 };
+
+int read_counters(panache_ctx *ctx, PnRequest &R) {
+    unsigned long long hs[PN_ST_COUNT];
+    int herr = 0;
+    PN_CU(cudaMemcpyAsync(hs, R.stats, sizeof(hs), cudaMemcpyDeviceToHost, R.st));
+    PN_CU(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, R.st));
+    PN_CU(cudaStreamSynchronize(R.st));
+    if (herr) return PANACHE_ETIMEOUT;
+    ctx->stats.queries = hs[PN_ST_QUERIES];
+    ctx->stats.candidates = hs[PN_ST_CANDIDATES];
+    ctx->stats.exact_stream = hs[PN_ST_LB_PASSED];
+    ctx->stats.exact_sieve = hs[PN_ST_EXACT_SIEVE];
+    ctx->stats.exact_completion = hs[PN_ST_EXACT_COMPLETION];
+    ctx->stats.exact_refine = hs[PN_ST_EXACT_REFINE];
+    ctx->stats.kernel_launches = ctx->launches;
+    ctx->stats.waves = 1;
+    return PANACHE_OK;
+}
+
 int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
-             std::vector<std::vector<panache_motif>> &res) {
+             std::vector<std::vector<panache_motif>> &res, int stages = PN_EMIT_ALL) {
     const panache_config &c = ctx->cfg;
     cudaStream_t st = R.st;
     const int64_t nser = (int64_t)R.ser.size();
     const int grid = ctx->sm_count * (int)c.grid_mult;
     int32_t ncls = 0;
-    if (!(c.flags & PANACHE_FLAG_NO_SIEVE)) {
+    if ((stages & PN_EMIT_SIEVE) && !(c.flags & PANACHE_FLAG_NO_SIEVE)) {
         PN_CU(pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w,
                                (c.flags & PANACHE_FLAG_EXHAUSTIVE_SIEVE) ? 1 : 0, grid, R.a_max, st, &ncls));
         ctx->launches += 6 + (ncls ? 4 + 2 * 12 : 0);
     }
     ctx->stats.hot_classes = (uint64_t)ncls;
+    if (!(stages & PN_EMIT_REST)) {
+        for (int t = 6; t <= 8; ++t) PN_TRY(tm.mark(t));
+        PN_TRY(tm.read(ctx->stats.step_ms));
+        ctx->kt.collect();
+        res.assign(nser, {});
+        return read_counters(ctx, R);
+    }
     PN_TRY(tm.mark(6));
-    std::vector<int> kser(nser), kseed(nser);
+    // seeds and refinement targets per group, capped so that k (m_max + 1)
+    // stays within the selection pool
+    std::vector<int> kser(nser), kseed(nser), kref(nser);
     for (int64_t s = 0; s < nser; ++s) {
         kser[s] = R.ser[s].k;
-        const int64_t want = (int64_t)c.seed_mult * R.ser[s].k;
-        kseed[s] = (int)std::max<int64_t>(1, std::min<int64_t>(want, 6000 / (R.ser[s].m_max + 1)));
+        const int64_t cap = 6000 / (R.ser[s].m_max + 1);
+        kseed[s] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c.seed_mult * R.ser[s].k, cap));
+        kref[s] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c.refine_mult * R.ser[s].k, cap));
     }
     const GroupSet out_groups = make_groups(R, (int)c.topk_mode, kser);
     // Seeds: the top-kseed cells in the output's mode.  In per-length mode
@@ -715,7 +782,7 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
         }
         if (dseeds) PN_CU(cudaFreeAsync(dseeds, st));
     }
-    if (!(c.flags & PANACHE_FLAG_NO_REFINE)) PN_TRY(refine_rows(ctx, R, v, seed_mode));
+    if (!(c.flags & PANACHE_FLAG_NO_REFINE)) PN_TRY(refine_rows(ctx, R, v, make_groups(R, (int)c.topk_mode, kref)));
     PN_TRY(tm.mark(7));
     std::vector<std::vector<PnPick>> picks;
     PN_TRY(run_select(ctx, R, v, out_groups, true, picks));
@@ -734,21 +801,7 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
             res[out_groups.owner[gi]].push_back(mo);
         }
     }
-    unsigned long long hs[PN_ST_COUNT];
-    int herr = 0;
-    PN_CU(cudaMemcpyAsync(hs, R.stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-    PN_CU(cudaMemcpyAsync(&herr, R.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PN_CU(cudaStreamSynchronize(st));
-    if (herr) return PANACHE_ETIMEOUT;
-    ctx->stats.queries = hs[PN_ST_QUERIES];
-    ctx->stats.candidates = hs[PN_ST_CANDIDATES];
-    ctx->stats.exact_stream = hs[PN_ST_LB_PASSED];
-    ctx->stats.exact_sieve = hs[PN_ST_EXACT_SIEVE];
-    ctx->stats.exact_completion = hs[PN_ST_EXACT_COMPLETION];
-    ctx->stats.exact_refine = hs[PN_ST_EXACT_REFINE];
-    ctx->stats.kernel_launches = ctx->launches;
-    ctx->stats.waves = 1;
-    return PANACHE_OK;
+    return read_counters(ctx, R);
 }
 
 bool same_shape(const std::vector<SeriesIn> &a, const std::vector<SeriesIn> &b) {
@@ -823,10 +876,13 @@ int index_and_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const PnCo
 }
 
 // The whole path for a list of series; results per series.
-int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<std::vector<panache_motif>> &res) {
+int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<std::vector<panache_motif>> &res,
+                const PnShard *sh = nullptr) {
     const panache_config &c = ctx->cfg;
     for (auto &s : in) PN_TRY(check_series(s));
-    const bool graph = (c.flags & PANACHE_FLAG_GRAPH) && !(c.flags & (PANACHE_FLAG_INDEX_ONLY | PANACHE_FLAG_TIMING));
+    const bool emit_only = sh && sh->rows_in;
+    const bool graph = !sh && (c.flags & PANACHE_FLAG_GRAPH) &&
+                       !(c.flags & (PANACHE_FLAG_INDEX_ONLY | PANACHE_FLAG_TIMING));
     if (graph && ctx->gexec && ctx->last && same_shape(ctx->gshape, in)) {
         // replay: new samples into the kept buffers, one graph launch, then Algorithm 2
         memset(&ctx->stats, 0, sizeof(ctx->stats));
@@ -852,12 +908,12 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PnRequest &R = *Rp;
     cudaStream_t st = ctx->st;
     R.st = st;
-    PN_TRY(plan(ctx->cfg, in, R));
+    PN_TRY(plan(ctx->cfg, in, R, nullptr, sh));
     ctx->stats.device_bytes = R.footprint;
     const int64_t nser = (int64_t)R.ser.size();
     bool all_f32 = true;
     for (auto &si : in) all_f32 = all_f32 && (si.dtype & 0xFF) == PANACHE_F32;
-    PN_TRY(alloc_state(ctx, R, all_f32 && c.precision == PANACHE_MIXED, true));
+    PN_TRY(alloc_state(ctx, R, all_f32 && c.precision == PANACHE_MIXED, true, emit_only));
     StepTimer tm;
     PN_TRY(tm.start((c.flags & PANACHE_FLAG_TIMING) != 0, st));
 
@@ -903,6 +959,23 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
     PN_CU(cudaMemcpyAsync(dcv, cv.data(), sizeof(PnConv) * nser, cudaMemcpyHostToDevice, st));
     PnView v = make_view(ctx, R);
     const bool search = !(c.flags & PANACHE_FLAG_INDEX_ONLY);
+    if (emit_only) {
+        // samples, run lengths and prefix sums; the given rows; then the emit
+        // stage after the sieve (each rank sieved its own anchors)
+        if (R.total_samples > 0) {
+            k_convert<<<(unsigned)((R.total_samples + 255) / 256), 256, 0, st>>>(dcv, (int32_t)nser, R.total_samples,
+                                                                                R.x, R.xs, R.x1);
+            PN_CU(cudaGetLastError());
+        }
+        PN_CU(pn::launch_runlen(v, R.total_samples, st));
+        PN_CU(pn::launch_moments(v, R.total_samples, R.sq, st));
+        ctx->launches += 1 + 3 + 5;
+        PN_CU(cudaMemcpyAsync(R.prof, sh->rows_in, sizeof(uint64_t) * (size_t)R.total_cells, cudaMemcpyHostToDevice,
+                              st));
+        if (stage) cudaFreeAsync(stage, st);
+        for (int t = 1; t <= 5; ++t) PN_TRY(tm.mark(t));
+        return run_emit(ctx, R, v, tm, res, PN_EMIT_REST);
+    }
     if (graph) {
         // capture once; this and every later request of the same shape launch it
         cudaGraph_t g = nullptr;
@@ -945,6 +1018,14 @@ int run_request(panache_ctx *ctx, const std::vector<SeriesIn> &in, std::vector<s
         return PANACHE_OK;
     }
     PN_TRY(tm.mark(5));
+    if (sh && sh->rows_out) {
+        // this rank's rows after its anchors' search and sieve
+        PN_TRY(run_emit(ctx, R, v, tm, res, PN_EMIT_SIEVE));
+        PN_CU(cudaMemcpyAsync(sh->rows_out, R.prof, sizeof(uint64_t) * (size_t)R.total_cells, cudaMemcpyDeviceToHost,
+                              st));
+        PN_CU(cudaStreamSynchronize(st));
+        return PANACHE_OK;
+    }
     return run_emit(ctx, R, v, tm, res);
 }
 
@@ -1187,6 +1268,34 @@ int panache_pmp(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, 
     std::vector<SeriesIn> in{SeriesIn{series, dtype, n, m_min, m_max, k, excl}};
     std::vector<std::vector<panache_motif>> res;
     PN_TRY(run_request(ctx, in, res));
+    return copy_out(res[0], out, out_cap, out_len);
+}
+
+int panache_pmp_anchor_shard(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min,
+                             int32_t m_max, int32_t k, int32_t excl, int32_t rank, int32_t world, uint64_t *rows,
+                             int64_t cap) {
+    if (!ctx || !rows || world < 1 || rank < 0 || rank >= world) return PANACHE_EINVAL;
+    SeriesIn si{series, dtype, n, m_min, m_max, k, excl};
+    PN_TRY(check_series(si));
+    if (cap < (int64_t)(m_max - m_min + 1) * n) return PANACHE_ETRUNC;
+    PnShard sh;
+    sh.rank = rank;
+    sh.world = world;
+    sh.rows_out = rows;
+    std::vector<std::vector<panache_motif>> res;
+    return run_request(ctx, std::vector<SeriesIn>{si}, res, &sh);
+}
+
+int panache_pmp_from_rows(panache_ctx *ctx, const void *series, int32_t dtype, int64_t n, int32_t m_min, int32_t m_max,
+                          int32_t k, int32_t excl, const uint64_t *rows, panache_motif *out, int64_t out_cap,
+                          int64_t *out_len) {
+    if (!ctx || !rows || !out_len) return PANACHE_EINVAL;
+    SeriesIn si{series, dtype, n, m_min, m_max, k, excl};
+    PN_TRY(check_series(si));
+    PnShard sh;
+    sh.rows_in = rows;
+    std::vector<std::vector<panache_motif>> res;
+    PN_TRY(run_request(ctx, std::vector<SeriesIn>{si}, res, &sh));
     return copy_out(res[0], out, out_cap, out_len);
 }
 

@@ -29,7 +29,7 @@ NOALLOC_NEED_MAX = 6300   # largest k (m + 1) of panache_topk_row_noalloc
 FAULT_NONE, FAULT_ALLOC, FAULT_COPY, FAULT_TC_WAIT = 0, 1, 2, 3
 
 EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "panache_set_stream", "panache_pmp",
-            "panache_pmp_batch", "panache_stream_open", "panache_append", "panache_stream_topk",
+            "panache_pmp_batch", "panache_pmp_anchor_shard", "panache_pmp_from_rows", "panache_stream_open", "panache_append", "panache_stream_topk",
             "panache_stream_length", "panache_stream_close", "panache_stream_checkpoint", "panache_last_stats",
             "panache_profile_rows",
             "panache_anchor_state", "panache_query_levels", "panache_projections", "panache_calibrate_width",
@@ -47,6 +47,7 @@ class Config(ctypes.Structure):
                 ("dp", ctypes.c_uint32), ("rounds", ctypes.c_uint32), ("precision", ctypes.c_uint32),
                 ("topk_mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("beta", ctypes.c_uint32), ("seed_mult", ctypes.c_uint32), ("grid_mult", ctypes.c_uint32),
+                ("refine_mult", ctypes.c_uint32), ("_reserved", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("lambda_", ctypes.c_double), ("eps0", ctypes.c_double)]
 
@@ -103,6 +104,8 @@ def lib():
         L.panache_set_stream.argtypes = [vp, vp]
         L.panache_pmp.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32, vp, i64, ctypes.POINTER(i64)]
         L.panache_pmp_batch.argtypes = [vp, vp, i32, vp, i64, vp]
+        L.panache_pmp_anchor_shard.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32, i32, i32, vp, i64]
+        L.panache_pmp_from_rows.argtypes = [vp, vp, i32, i64, i32, i32, i32, i32, vp, vp, i64, ctypes.POINTER(i64)]
         L.panache_stream_open.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(vp)]
         L.panache_append.argtypes = [vp, vp, i32, i64]
         L.panache_stream_topk.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
@@ -220,6 +223,32 @@ class Context:
         rc = lib().panache_pmp(self._h, ptr, dt, n, m_min, m_max, k, excl,
                                out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(ln))
         _check(rc, "pmp")
+        del keep
+        return out[:ln.value]
+
+    def pmp_anchor_shard(self, x, m_min: int, m_max: int, k: int, excl: int, rank: int, world: int) -> np.ndarray:
+        """This rank's profile rows [L][n] (packed keys) after its anchors' search and sieve."""
+        ptr, dt, n, keep = _series_arg(x)
+        L = m_max - m_min + 1
+        rows = np.empty((L, n), dtype=np.uint64)
+        _check(lib().panache_pmp_anchor_shard(self._h, ptr, dt, n, m_min, m_max, k, excl, rank, world,
+                                              rows.ctypes.data_as(ctypes.c_void_p), rows.size), "pmp_anchor_shard")
+        del keep
+        return rows
+
+    def pmp_from_rows(self, x, m_min: int, m_max: int, k: int, excl: int, rows: np.ndarray) -> np.ndarray:
+        """Motifs from merged profile rows [L][n]: completion, refinement and selection."""
+        ptr, dt, n, keep = _series_arg(x)
+        rows = np.ascontiguousarray(rows, dtype=np.uint64)
+        L = m_max - m_min + 1
+        if rows.shape != (L, n):
+            raise ValueError(f"rows must have shape {(L, n)}")
+        cap = max(0, k) * L
+        out = np.zeros(max(cap, 1), dtype=MOTIF_DTYPE)
+        ln = ctypes.c_int64()
+        _check(lib().panache_pmp_from_rows(self._h, ptr, dt, n, m_min, m_max, k, excl,
+                                           rows.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                                           cap, ctypes.byref(ln)), "pmp_from_rows")
         del keep
         return out[:ln.value]
 
