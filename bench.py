@@ -267,43 +267,56 @@ def cpu_baseline(x: np.ndarray, lengths=(100, 125, 150), excl=150, target_s=12.0
                       f"{len(x)}-sample series the oracle's rate would be about {n_sample / len(x):.3f}x this"}
 
 
-def run_batched(pn, stream, n_series: int, n_loop: int):
+def run_batched(pn, stream, n_series: int, n_loop: int, n_graph: int = 256):
     """The batched form: the first n_series series of the batched workload
     (4096 log-uniform lengths in [2000, 200000], per-series length intervals,
-    top-10, exclusion m_max) in one pmp_batch call (waves under the HBM
-    budget), against n_loop of them run one pmp call at a time."""
+    top-10, exclusion m_max) in one pmp_batch call from host buffers (waves
+    under the HBM budget), timed once after a warm-up on 64 of them; the
+    first n_loop series run one pmp call at a time; the first n_graph series
+    with the index and search steps replayed from a captured CUDA graph; and
+    64 small series of one shape one call each, eager and replayed."""
     import torch
-    series = workloads.batched_workload(4096, seed=0, indices=range(n_series))
-    params = [(q.m_min, q.m_max, q.k, q.excl) for q in series]
-    xs = [torch.from_numpy(q.x).cuda() for q in series]
-    W = sum(workloads.windows_lengths(len(q.x), q.m_min, q.m_max) for q in series)
-    ctx = pn.Context(precision=1, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_TIMING)
-    ctx.set_stream(stream.cuda_stream)
     from paper_2607_17481_b300 import shard
+    t_gen = time.perf_counter()
+    series = workloads.batched_workload(4096, seed=0, indices=range(n_series))
+    t_gen = time.perf_counter() - t_gen
+    params = [(q.m_min, q.m_max, q.k, q.excl) for q in series]
+    hosts = [q.x for q in series]
+    W = sum(workloads.windows_lengths(len(q.x), q.m_min, q.m_max) for q in series)
+    # chunk length and search grid from the autotuner (cached per shape class)
+    from paper_2607_17481_b300 import autotune
+    t_tune = time.perf_counter()
+    tuned = autotune.config_for_batch(hosts, params, sample=64)
+    t_tune = time.perf_counter() - t_tune
+    ctx = pn.Context(precision=1, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_TIMING, chunk=tuned["chunk"],
+                     grid_mult=tuned["grid_mult"])
+    ctx.set_stream(stream.cuda_stream)
 
-    def run_all():
+    def run_all(xs, ps, c):
         # every rank runs its shard of the batch (no collective on the data path)
-        return shard.run_sharded(xs, params, lambda s_, p_: ctx.pmp_batch(s_, p_))
+        return shard.run_sharded(xs, ps, lambda s_, p_: c.pmp_batch(s_, p_))
 
-    run_all()                                      # warm-up
-    times = []
-    for _ in range(2):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        run_all()
-        torch.cuda.synchronize()
-        times.append(1e3 * (time.perf_counter() - t0))
+    run_all(hosts[:64], params[:64], ctx)                      # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run_all(hosts, params, ctx)
+    torch.cuda.synchronize()
+    ms = 1e3 * (time.perf_counter() - t0)
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
-        t = torch.tensor(times, device="cuda")
+        t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = t.tolist()
+        ms = float(t.item())
     st = ctx.stats()
     out = {"series": n_series, "samples": int(sum(len(q.x) for q in series)), "windows_lengths": W,
-           "value": W / (statistics.mean(times) / 1e3), "unit": UNIT, "ms_per_batch": statistics.mean(times),
-           "waves": st["waves"], "kernel_launches": st["kernel_launches"], "step_ms": st["step_ms"],
+           "value": W / (ms / 1e3), "unit": UNIT, "ms_per_batch": ms, "inputs": "host buffers (H2D inside)",
+           "generation_s": round(t_gen, 1), "waves": st["waves"], "kernel_launches": st["kernel_launches"],
+           "autotuned": {"chunk": tuned["chunk"], "grid_mult": tuned["grid_mult"], "tuning_s": round(t_tune, 1),
+                         "search_ms_by_grid_mult": tuned["search_ms"],
+                         "drift_by_chunk": {str(k): v for k, v in tuned["drift"].items()}},
            "workload": "batched_workload(4096, seed=0)[:n]: random walk / ECG-like / sine mix, 0-5 planted "
                        "motifs, lengths m_min~U{16..128} with 20-64 lengths, top-10, excl=m_max"}
+    xs = [torch.from_numpy(q.x).cuda() for q in series[:max(n_loop, n_graph)]]
     if n_loop > 0:
         sub = list(range(min(n_loop, n_series)))
         Wl = sum(workloads.windows_lengths(len(series[i].x), series[i].m_min, series[i].m_max) for i in sub)
@@ -316,18 +329,24 @@ def run_batched(pn, stream, n_series: int, n_loop: int):
         e1.record(stream)
         e1.synchronize()
         out["one_at_a_time"] = {"series": len(sub), "value": Wl / (e0.elapsed_time(e1) / 1e3), "unit": UNIT}
-    # the same batch with the index and search steps replayed from a captured CUDA graph
-    ctx_g = pn.Context(precision=1, topk_mode=pn.TOPK_GLOBAL, flags=pn.FLAG_GRAPH)
-    ctx_g.set_stream(stream.cuda_stream)
-    shard.run_sharded(xs, params, lambda s_, p_: ctx_g.pmp_batch(s_, p_))      # capture
-    gt = []
-    for _ in range(2):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        shard.run_sharded(xs, params, lambda s_, p_: ctx_g.pmp_batch(s_, p_))
-        torch.cuda.synchronize()
-        gt.append(1e3 * (time.perf_counter() - t0))
-    out["graph"] = {"value": W / (statistics.mean(gt) / 1e3), "unit": UNIT, "ms_per_batch": statistics.mean(gt)}
+    if n_graph > 0:
+        ng = min(n_graph, n_series)
+        Wg = sum(workloads.windows_lengths(len(series[i].x), series[i].m_min, series[i].m_max) for i in range(ng))
+        res = {}
+        for name, flags in (("eager", 0), ("graph", pn.FLAG_GRAPH)):
+            c = pn.Context(precision=1, topk_mode=pn.TOPK_GLOBAL, flags=flags, chunk=tuned["chunk"],
+                           grid_mult=tuned["grid_mult"])
+            c.set_stream(stream.cuda_stream)
+            run_all(xs[:ng], params[:ng], c)                   # capture (graph) / warm-up
+            gt = []
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                run_all(xs[:ng], params[:ng], c)
+                torch.cuda.synchronize()
+                gt.append(1e3 * (time.perf_counter() - t0))
+            res[name] = {"value": Wg / (statistics.mean(gt) / 1e3), "ms_per_batch": statistics.mean(gt)}
+        out["device_inputs_first"] = {"series": ng, "unit": UNIT, **res}
     # many small series of one shape, one call each: eager launches vs graph replay
     fleet = [workloads.random_walk(np.random.default_rng([77, i]), 8192) for i in range(64)]
     fl = [torch.from_numpy(f).cuda() for f in fleet]
@@ -385,7 +404,11 @@ def run_served(pn, args, rate=None):
     streams (random walk or ECG-like, starting at 50,000 samples, lengths
     64..128, top-20, exclusion 128) receiving 1,024-sample appends at 50 Hz,
     each stream asked for its top-20 once a second; one request server with
-    4 slots under a 120 GB budget.  Latency: submission to motifs on the host."""
+    4 slots under a 120 GB budget and a request deadline (submissions whose
+    predicted wait exceeds it are refused, EBUSY).  Appends and snapshots are
+    queued and applied by the server's stream workers.  Latency: submission
+    to motifs on the host (requests), call to motifs on the host
+    (snapshots)."""
     import numpy as np
     rate = args.served_rate if rate is None else rate
     rng = np.random.default_rng(99)
@@ -405,20 +428,23 @@ def run_served(pn, args, rate=None):
     # live streams reserve their resident state from the budget; one that
     # does not fit is refused (EBUDGET) and left out, and a stream whose
     # growth is refused keeps its samples and stops taking appends
-    sids, kept, refused = [], [], 0
+    sids, kept, refused, opened_refused = [], [], 0, 0
     for x in live:
         sid = sv.stream_open(64, 128, 20, 128)
         try:
             sv.append(sid, x[:50_000])
         except pn.PanacheError:
-            refused += 1
+            opened_refused += 1
             sv.stream_close(sid)
             continue
         sids.append(sid)
         kept.append(x)
     live = kept
+    for sid in sids:                                   # the initial index of every stream is built
+        sv.wait(sv.stream_topk(sid))
+    sv.set_deadline(args.served_deadline_ms)
     growing = [True] * len(live)
-    tickets = []
+    tickets, busy = [], 0
     t0 = time.perf_counter()
     next_req, tick = 0, 0
     fed = [50_000] * len(live)
@@ -428,7 +454,12 @@ def run_served(pn, args, rate=None):
             break
         while next_req < len(arrivals) and arrivals[next_req] <= now:
             q = reqs[next_req]
-            tickets.append(sv.submit(q.x, q.m_min, q.m_max, q.k, q.excl))
+            try:
+                tickets.append(sv.submit(q.x, q.m_min, q.m_max, q.k, q.excl))
+            except pn.PanacheError as e:
+                if e.code != pn.native.EBUSY:
+                    raise
+                busy += 1
             next_req += 1
         if now >= tick * 0.02:                     # 50 Hz append round
             for i, sid in enumerate(sids):
@@ -441,29 +472,43 @@ def run_served(pn, args, rate=None):
                     growing[i] = False
                     refused += 1
             if tick % 50 == 49:                    # once a second: top-20 of every live stream
-                tickets.extend(sv.stream_topk(sid) for sid in sids)
+                for sid in sids:
+                    try:
+                        tickets.append(sv.stream_topk(sid))
+                    except pn.PanacheError as e:
+                        if e.code != pn.native.EBUSY:
+                            raise
             tick += 1
         time.sleep(0.0005)
+    sv.set_deadline(0.0)                           # the final snapshots are always served
     tickets.extend(sv.stream_topk(sid) for sid in sids)
+    failures = {}
     for t in tickets:
         try:
             sv.wait(t)
-        except pn.PanacheError:
-            pass                                   # counted by the server as failed (refused)
+        except pn.PanacheError as e:
+            failures[e.code] = failures.get(e.code, 0) + 1
     st = sv.stats()
     sv.close()
-    return {"requests": int(next_req), "stream_topk_requests": int(len(tickets) - next_req),
+    return {"requests": int(next_req), "admitted": int(next_req - busy), "refused_by_deadline": busy,
+            "deadline_ms": args.served_deadline_ms,
+            "stream_topk_requests": int(len(tickets) - next_req + busy),
             "live_streams": len(live), "live_streams_requested": args.served_streams,
-            "stream_admissions_refused": refused, "feature_rows": "half" if args.served_half else "fp32",
+            "live_streams_refused_at_open": opened_refused,
+            "stream_appends_refused": refused, "refused_snapshots": int(st["refused_snapshots"]),
+            "failures_by_code": {str(k): v for k, v in failures.items()},
+            "feature_rows": "half" if args.served_half else "fp32",
             "appended_samples": int(sum(f - 50_000 for f in fed)),
             "arrival_rate_per_s": rate, "window_s": args.served_seconds,
             "completed": int(st["completed"]), "failed": int(st["failed"]),
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "snapshot_p50_ms": st["snap_p50_ms"], "snapshot_p99_ms": st["snap_p99_ms"],
             "windows_lengths": int(st["windows_lengths"]),
             "sustained_value": st["windows_lengths"] / (st["span_ms"] / 1e3) if st["span_ms"] else None,
             "unit": UNIT, "batches": int(st["batches"]), "max_concurrent_batches": int(st["max_concurrent_batches"]),
             "peak_reserved_bytes": int(st["peak_reserved_bytes"]), "budget_bytes": int(st["budget_bytes"]),
-            "note": "stream top-k requests process each stream's samples received so far"}
+            "note": "stream top-k requests process each stream's samples received so far; p50/p99 are of "
+                    "admitted requests"}
 
 
 def run_reference(args):
@@ -511,13 +556,15 @@ def main():
     ap.add_argument("--half-steps", type=int, default=2, help="timed steps with half-precision feature rows")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--batched", type=int, default=256,
+    ap.add_argument("--batched", type=int, default=4096,
                     help="series of the batched workload timed as one pmp_batch (0: skip)")
     ap.add_argument("--served-seconds", type=float, default=2.0, help="arrival window of the served leg (0: skip)")
     ap.add_argument("--served-rate", type=float, default=200.0, help="Poisson request arrivals per second")
-    ap.add_argument("--served-streams", type=int, default=32, help="live streams (the workload names 256)")
-    ap.add_argument("--served-half", action="store_true",
-                    help="served leg with half-precision feature rows (smaller stream reservations)")
+    ap.add_argument("--served-streams", type=int, default=256, help="live streams")
+    ap.add_argument("--served-fp32", dest="served_half", action="store_false",
+                    help="served leg with FP32 feature rows (default: half-precision rows)")
+    ap.add_argument("--served-deadline-ms", type=float, default=1000.0,
+                    help="server deadline: requests predicted to wait longer are refused (0: off)")
     ap.add_argument("--batched-loop", type=int, default=64,
                     help="series of the same batch timed one pmp call at a time (0: skip)")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"])

@@ -59,6 +59,7 @@ extern "C" {
 #define PANACHE_EPOOL (-7)    /* top-k pool overflow (massive exact ties); results withheld */
 #define PANACHE_ENODEV (-8)   /* no CUDA device, or the device is not sm_103 */
 #define PANACHE_ETIMEOUT (-9) /* a wait ran out of time before the result was ready */
+#define PANACHE_EBUSY (-10)   /* refused at admission: the server's predicted wait exceeds its deadline */
 
 /* ---- sample types (low byte) and pointer location flag ---- */
 #define PANACHE_F32 1
@@ -399,14 +400,18 @@ typedef struct panache_server panache_server;
 
 typedef struct {
     uint64_t submitted, completed, failed, queued, batches;
-    uint64_t windows_lengths;      /* sum over completed requests */
+    uint64_t windows_lengths;      /* sum over completed requests and snapshots */
     uint64_t budget_bytes, peak_reserved_bytes;
     uint32_t max_concurrent_batches, _pad;
     double span_ms;                /* first submission to last completion */
-    double p50_ms, p99_ms, mean_ms;   /* request latency of completed requests */
+    double p50_ms, p99_ms, mean_ms;   /* request latency of completed requests (snapshots apart) */
+    uint64_t refused;              /* requests refused at submission by the deadline (EBUSY) */
+    double snap_p50_ms, snap_p99_ms;  /* stream snapshot latency: call to motifs on the host */
+    uint64_t refused_snapshots;    /* stream snapshots refused by the deadline (EBUSY) */
 } panache_server_stats;
 
-/* hbm_budget_bytes 0: 60% of the free device memory.  1 <= slots <= 64. */
+/* hbm_budget_bytes 0: 60% of the free device memory.  1 <= slots <= 64.
+ * The server also runs max(2, slots) stream worker threads. */
 int panache_server_create(const panache_config *cfg, int32_t slots, uint64_t hbm_budget_bytes,
                           panache_server **out);
 /* Drains the queue, stops the workers and frees everything. */
@@ -421,21 +426,35 @@ int panache_server_wait(panache_server *sv, uint64_t ticket, int32_t timeout_ms,
                         int64_t *out_len, double *latency_ms);
 /* Live streams: each is a resident stream (panache_stream_open) on a
  * context and CUDA stream of its own, so its appends and snapshots overlap
- * the slots' batches on the GPU.  Appends (host chunks, FP32 or FP64) and
- * snapshots run in the calling thread; calls on one stream are serialised.
- * The resident state plus the row copy a snapshot uses are reserved from
- * the budget; an append that would grow them past it fails with EBUDGET
- * (the stream keeps its samples).  panache_server_stream_topk computes the
- * top-k over the samples received so far and files the result under a
- * ticket for panache_server_wait (latency: the snapshot's own time).
- * ESTATE when the stream has no samples.  panache_server_stream_close
- * frees the stream and its reservation. */
+ * one another and the slots' batches on the GPU.  panache_server_append
+ * copies the chunk (host, FP32 or FP64) and queues it; stream worker
+ * threads apply each stream's queued operations in order, a run of
+ * consecutive appends as one append.  The resident state plus the row copy
+ * a snapshot uses are reserved from the budget when the append is accepted;
+ * an append that would grow them past it fails at the call with EBUDGET
+ * (the stream keeps its samples).  A failure while an append is applied is
+ * kept and returned by the stream's later appends and snapshots.
+ * panache_server_stream_topk queues a top-k over every sample accepted
+ * before it and returns its ticket for panache_server_wait (latency: from
+ * the call to the motifs on the host).  ESTATE when the stream has no
+ * samples.  panache_server_stream_close applies the stream's pending
+ * operations, then frees it and its reservation. */
 int panache_server_stream_open(panache_server *sv, int32_t m_min, int32_t m_max, int32_t k, int32_t excl,
                                uint64_t *stream_id);
 int panache_server_append(panache_server *sv, uint64_t stream_id, const void *chunk, int32_t dtype, int64_t len);
 int panache_server_stream_topk(panache_server *sv, uint64_t stream_id, uint64_t *ticket);
 int panache_server_stream_close(panache_server *sv, uint64_t stream_id);
 int panache_server_get_stats(panache_server *sv, panache_server_stats *out);
+/* Deadline admission (0, the default: off).  A request whose predicted wait
+ * -- the windows x lengths queued ahead of it plus its own, over the
+ * server's measured request throughput (what completed in the last two
+ * seconds; before that, a smoothed per-batch rate times the slots) --
+ * exceeds deadline_ms is refused at submission with EBUSY.  A stream
+ * snapshot is refused with EBUSY when the snapshots queued ahead of it and
+ * itself, at the measured time per snapshot spread over the stream workers,
+ * exceed the deadline.  Above its capacity the server then sheds load
+ * instead of letting the queues, and every latency, grow.  Errors: EINVAL. */
+int panache_server_set_deadline(panache_server *sv, double deadline_ms);
 
 /* Top-k motifs of ONE length row from profile keys already on the device,
  * with no device memory allocated by the call.  For callers that cannot call

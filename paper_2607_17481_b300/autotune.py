@@ -61,3 +61,35 @@ def tune(x, m_min: int, m_max: int, lam: float = 1e-4, chunks=(4096, 2048, 1024,
         ctx.close()
     best_g = min(times, key=times.get)
     return {"chunk": chosen, "grid_mult": best_g, "drift": drift, "search_ms": times, "lambda": lam}
+
+
+_CACHE: dict = {}
+
+
+def shape_key(n: int, m_min: int, m_max: int, dtype) -> tuple:
+    """Requests of one shape class share a tuned configuration: the series
+    length to the nearest power of two, the length interval and the sample type."""
+    return (int(np.round(np.log2(max(2, n)))), int(m_min), int(m_max), np.dtype(dtype).name)
+
+
+def tuned(x, m_min: int, m_max: int, **kw) -> dict:
+    """tune() once per shape class (cached for the process)."""
+    x = np.asarray(x)
+    key = shape_key(x.shape[0], m_min, m_max, x.dtype)
+    if key not in _CACHE:
+        _CACHE[key] = tune(x, m_min, m_max, **kw)
+    return _CACHE[key]
+
+
+def config_for_batch(series: list, params: list, sample: int = 64, **kw) -> dict:
+    """The configuration one batched request runs with: the tuned chunk and
+    grid multiple of the batch's largest series among the first `sample`
+    (by windows x lengths), from the per-shape cache."""
+    best, best_w = None, -1
+    for x, (m_min, m_max, _, _) in list(zip(series, params))[:sample]:
+        w = sum(max(0, len(x) - m + 1) for m in range(m_min, m_max + 1))
+        if w > best_w:
+            best, best_w = (x, m_min, m_max), w
+    x, m_min, m_max = best
+    x = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+    return tuned(x, m_min, m_max, **kw)

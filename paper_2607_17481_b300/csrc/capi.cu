@@ -1203,6 +1203,62 @@ int footprint(panache_ctx *ctx, const PnSeriesIn &s_in, uint64_t *bytes) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+namespace {
+
+// Appends `len` samples; when they outgrow the capacity the state is rebuilt
+// at `cap_to` (when it holds them) or at grow_capacity's choice.
+int stream_append(panache_stream *h, const void *chunk, int32_t dtype, int64_t len, int64_t cap_to) {
+    if (!h || len < 0 || (len > 0 && !chunk)) return PANACHE_EINVAL;
+    const int dt = dtype & 0xFF;
+    if ((dt != PANACHE_F32 && dt != PANACHE_F64) || (dtype & ~0x1FF)) return PANACHE_EINVAL;
+    if (len == 0) return PANACHE_OK;
+    if (h->len + len > PN_MAX_SERIES_LEN) return PANACHE_EINVAL;
+    panache_ctx *ctx = h->ctx;
+    if (!ctx) return PANACHE_ESTATE;
+    cudaStream_t st = ctx->st;
+    ctx->launches = 0;
+    if (h->len + len > h->cap) {
+        // grow: a fresh state at twice the capacity, rebuilt from the samples
+        // (every step is a function of the samples, so the rebuilt state
+        // equals the one the appends would have produced)
+        const int64_t nc = cap_to >= h->len + len && cap_to <= PN_MAX_SERIES_LEN
+                               ? cap_to : pn_rt::grow_capacity(h->cap, h->len + len);
+        PnRequest *R2 = nullptr;
+        PN_TRY(stream_alloc(h, nc, R2));
+        if (h->len) {
+            k_put<<<(unsigned)((h->len + 255) / 256), 256, 0, st>>>(h->R->x, PANACHE_F64, h->len, 0, R2->x, R2->xs);
+            PN_CU(cudaGetLastError());
+        }
+        delete h->R;
+        h->R = R2;
+        h->cap = nc;
+        h->q_done.assign(R2->anc.size(), 0);
+        h->nw_feat.assign(R2->anc.size(), 0);
+    }
+    PnRequest &R = *h->R;
+    const int es = dt == PANACHE_F32 ? 4 : 8;
+    const void *src = chunk;
+    void *stage = nullptr;
+    if (!(dtype & PANACHE_DEVICE)) {
+        PN_CU(cudaMallocAsync(&stage, (size_t)len * es, st));
+        PN_CU(cudaMemcpyAsync(stage, chunk, (size_t)len * es, cudaMemcpyHostToDevice, st));
+        src = stage;
+    }
+    k_put<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(src, dtype, len, h->len, R.x, R.xs);
+    PN_CU(cudaGetLastError());
+    if (stage) PN_CU(cudaFreeAsync(stage, st));
+    h->len += len;
+    return stream_advance(h);
+}
+
+}  // namespace
+
+namespace pn_rt {
+int append_to(panache_stream *h, const void *chunk, int32_t dtype, int64_t len, int64_t cap) {
+    return stream_append(h, chunk, dtype, len, cap);
+}
+}  // namespace pn_rt
+
 extern "C" {
 
 int panache_default_config(panache_config *cfg) {
@@ -1393,46 +1449,7 @@ int panache_stream_open(panache_ctx *ctx, int32_t m_min, int32_t m_max, int32_t 
 }
 
 int panache_append(panache_stream *h, const void *chunk, int32_t dtype, int64_t len) {
-    if (!h || len < 0 || (len > 0 && !chunk)) return PANACHE_EINVAL;
-    const int dt = dtype & 0xFF;
-    if ((dt != PANACHE_F32 && dt != PANACHE_F64) || (dtype & ~0x1FF)) return PANACHE_EINVAL;
-    if (len == 0) return PANACHE_OK;
-    if (h->len + len > PN_MAX_SERIES_LEN) return PANACHE_EINVAL;
-    panache_ctx *ctx = h->ctx;
-    if (!ctx) return PANACHE_ESTATE;
-    cudaStream_t st = ctx->st;
-    ctx->launches = 0;
-    if (h->len + len > h->cap) {
-        // grow: a fresh state at twice the capacity, rebuilt from the samples
-        // (every step is a function of the samples, so the rebuilt state
-        // equals the one the appends would have produced)
-        const int64_t nc = pn_rt::grow_capacity(h->cap, h->len + len);
-        PnRequest *R2 = nullptr;
-        PN_TRY(stream_alloc(h, nc, R2));
-        if (h->len) {
-            k_put<<<(unsigned)((h->len + 255) / 256), 256, 0, st>>>(h->R->x, PANACHE_F64, h->len, 0, R2->x, R2->xs);
-            PN_CU(cudaGetLastError());
-        }
-        delete h->R;
-        h->R = R2;
-        h->cap = nc;
-        h->q_done.assign(R2->anc.size(), 0);
-        h->nw_feat.assign(R2->anc.size(), 0);
-    }
-    PnRequest &R = *h->R;
-    const int es = dt == PANACHE_F32 ? 4 : 8;
-    const void *src = chunk;
-    void *stage = nullptr;
-    if (!(dtype & PANACHE_DEVICE)) {
-        PN_CU(cudaMallocAsync(&stage, (size_t)len * es, st));
-        PN_CU(cudaMemcpyAsync(stage, chunk, (size_t)len * es, cudaMemcpyHostToDevice, st));
-        src = stage;
-    }
-    k_put<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(src, dtype, len, h->len, R.x, R.xs);
-    PN_CU(cudaGetLastError());
-    if (stage) PN_CU(cudaFreeAsync(stage, st));
-    h->len += len;
-    return stream_advance(h);
+    return stream_append(h, chunk, dtype, len, 0);
 }
 
 int panache_stream_topk(panache_stream *h, panache_motif *out, int64_t out_cap, int64_t *out_len) {
@@ -1696,6 +1713,8 @@ const char *panache_strerror(int code) {
         case PANACHE_ESTATE: return "invalid state for this call";
         case PANACHE_EPOOL: return "top-k selection pool overflow";
         case PANACHE_ENODEV: return "no sm_103 CUDA device";
+        case PANACHE_ETIMEOUT: return "a wait ran out of time";
+        case PANACHE_EBUSY: return "refused at admission: the predicted wait exceeds the server's deadline";
         default: return "unknown error";
     }
 }

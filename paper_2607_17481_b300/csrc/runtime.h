@@ -23,4 +23,8 @@ int footprint(panache_ctx *ctx, const PnSeriesIn &s, uint64_t *bytes);
 // samples grows it to (the stream keeps its capacity when need fits).
 int64_t stream_capacity(const panache_stream *h);
 int64_t grow_capacity(int64_t cap, int64_t need);
+// panache_append, except that an append that outgrows the capacity rebuilds
+// the state at exactly `cap` (when cap holds the samples): several appends
+// applied as one then reach the capacity reserved for them one by one.
+int append_to(panache_stream *h, const void *chunk, int32_t dtype, int64_t len, int64_t cap);
 }  // namespace pn_rt

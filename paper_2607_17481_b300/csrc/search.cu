@@ -48,8 +48,14 @@ constexpr int SR_WARM = 32;    // candidates a query's warm start inspects
 // exact distance of an admitted pair.  The final profile is unchanged (it
 // is the minimum over the admitted pairs); only the number of pairs the
 // bound lets through drops.
+constexpr int SR_TILE = 4;     // queries a warp takes from the work queue at a time
+
+// A persistent kernel: SMs x grid_mult blocks, and each warp takes the next
+// SR_TILE queries of the query order from a global work counter until the
+// order is exhausted, so warps that draw cheap queries take more of them.
 template <class Z, bool HALF, bool WARM>
-__global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap) {
+__global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap,
+                                                        unsigned long long *work) {
     using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
     __shared__ unsigned long long s_stat[3];
@@ -73,7 +79,16 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
     int ai = 0;
     int64_t a_lo = 1, a_hi = 0;
 
-    for (int64_t it = (int64_t)blockIdx.x * SR_WARPS + warp; it < total; it += (int64_t)gridDim.x * SR_WARPS) {
+    int64_t tile = 0, tile_end = 0;
+    for (int64_t it = 0;; ++it) {
+        if (it >= tile_end) {                              // warp-uniform: next tile of the queue
+            unsigned long long t0 = 0;
+            if (lane == 0) t0 = atomicAdd(work, (unsigned long long)SR_TILE);
+            tile = (int64_t)__shfl_sync(0xffffffffu, t0, 0);
+            if (tile >= total) break;
+            it = tile;
+            tile_end = min(total, tile + SR_TILE);
+        }
         const int64_t w = v.qorder[it];
         if (w < a_lo || w >= a_hi) {
             ai = pn_find(v.anchors, v.nanchors, w, [](const PnAnchor &A) { return A.win_off; });
@@ -316,25 +331,30 @@ __global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t tota
 }
 
 template <class Z, bool HALF, bool WARM>
-cudaError_t launch_one(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st) {
+cudaError_t launch_one(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st,
+                       unsigned long long *work) {
     const int zcap = (a_max + 3) & ~3;
     const size_t sm = (sizeof(unsigned long long) + sizeof(uint32_t)) * (size_t)v.R * SR_WARPS +
                       sizeof(typename Z::Q) * (size_t)zcap * SR_WARPS;
     cudaError_t e = pn_allow_smem(k_search<Z, HALF, WARM>, sm);
     if (e != cudaSuccess) return e;
-    int64_t need = (total + SR_WARPS - 1) / SR_WARPS;
+    e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    int64_t need = (total + SR_WARPS * SR_TILE - 1) / (SR_WARPS * SR_TILE);
     unsigned g = (unsigned)(need < grid_blocks ? need : grid_blocks);
-    k_search<Z, HALF, WARM><<<g, SR_THREADS, sm, st>>>(v, total, zcap);
+    k_search<Z, HALF, WARM><<<g, SR_THREADS, sm, st>>>(v, total, zcap, work);
     return cudaGetLastError();
 }
 
 template <class Z, bool HALF>
 cudaError_t launch_t(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st, bool warm) {
-    if (warm) {
-        cudaError_t e = launch_one<Z, HALF, true>(v, total, grid_blocks, a_max, st);
-        if (e != cudaSuccess) return e;
-    }
-    return launch_one<Z, HALF, false>(v, total, grid_blocks, a_max, st);
+    unsigned long long *work = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&work, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (warm) e = launch_one<Z, HALF, true>(v, total, grid_blocks, a_max, st, work + 1);
+    if (e == cudaSuccess) e = launch_one<Z, HALF, false>(v, total, grid_blocks, a_max, st, work);
+    cudaFreeAsync(work, st);
+    return e;
 }
 
 // Introspection: the population and depth of every window of one anchor,

@@ -6,12 +6,23 @@
 // Admission: a request reserves its device footprint (the planner's
 // estimate) from the server budget before it runs and releases it when its
 // results are on the host; a request larger than the whole budget is refused
-// at submission (PANACHE_EBUDGET).
+// at submission (PANACHE_EBUDGET).  With a deadline set, a request whose
+// predicted wait -- the work queued ahead of it and its own, in
+// windows x lengths, over the server's measured throughput -- exceeds the
+// deadline is refused at submission (PANACHE_EBUSY): above capacity the
+// server sheds load instead of letting every request's latency grow.  A
+// stream snapshot is refused the same way when the snapshots queued ahead
+// of it, at the measured time per snapshot, would keep it past the deadline.
 // Continuous batching: a free slot takes, in arrival order, every queued
 // request that still fits both the free budget and the slot's share of it,
 // and runs them as one batch (one set of launches); requests that arrive
 // while others are on the GPU wait only for the next free slot.
-// Latency of a request: from submission to its motifs being on the host.
+// Live streams: appends and snapshots are queued per stream and applied by
+// stream worker threads, each stream on a context (and CUDA stream) of its
+// own, so they overlap one another and the slots' batches; consecutive
+// pending appends of a stream are applied as one.
+// Latency of a request: from submission to its motifs being on the host; of
+// a snapshot: from its call to its motifs being on the host.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -27,6 +38,8 @@
 
 #include "panache.h"
 #include "runtime.h"
+
+#define PN_STREAM_MAX_LEN ((int64_t)((1ull << 26) - 1))
 
 namespace {
 
@@ -49,14 +62,29 @@ struct Result {
     double latency_ms = 0.0;
 };
 
+// One pending operation of a live stream, applied in order by a stream worker.
+struct StreamOp {
+    bool snapshot = false;
+    std::vector<double> samples;             // an append's samples (FP64)
+    int64_t cap_after = 0;                   // the capacity reserved for the stream after this append
+    uint64_t ticket = 0;                     // a snapshot's ticket
+    double t_enq = 0.0;
+};
+
 // A live stream: its whole index stays resident on the device (a resident
 // panache_stream on a context, and so a CUDA stream, of its own).  Appends
-// and snapshots run in the calling thread and overlap the slots' batches on
-// the GPU.  The resident state, plus the row copy a snapshot works on, is
-// reserved from the server's budget; an append that would grow it past the
-// budget is refused (EBUDGET).
+// and snapshots are queued (ops) and applied by a stream worker.  The
+// resident state, plus the row copy a snapshot works on, is reserved from the
+// server's budget when an append is accepted; an append that would grow it
+// past the budget is refused (EBUDGET) at the call.
 struct LiveStream {
-    std::mutex mu;
+    std::mutex ops_mu;                       // ops, accepted, planned_cap, scheduled, err
+    std::deque<StreamOp> ops;
+    int64_t accepted = 0;                    // samples accepted (applied or pending)
+    int64_t planned_cap = 0;                 // capacity after every accepted append
+    bool scheduled = false;                  // on the server's stream work list
+    int err = PANACHE_OK;                    // first failure of an applied append (sticky)
+    std::mutex exec_mu;                      // held while a worker applies ops
     panache_ctx *ctx = nullptr;
     panache_stream *h = nullptr;
     uint64_t reserved = 0;
@@ -82,15 +110,40 @@ struct panache_server {
     std::vector<panache_ctx *> ctxs;
     bool stop = false;
     uint64_t next_ticket = 1, next_stream = 1;
-    std::unordered_map<uint64_t, std::unique_ptr<LiveStream>> streams;
+    std::unordered_map<uint64_t, std::shared_ptr<LiveStream>> streams;
     std::mutex streams_mu;
+    // stream workers: streams with pending ops, in the order they were scheduled
+    std::deque<std::shared_ptr<LiveStream>> stream_work;
+    std::condition_variable cv_stream;
+    std::vector<std::thread> stream_workers;
+    // deadline admission: queued work and the measured throughput
+    double deadline_ms = 0.0;
+    uint64_t queued_wl = 0;
+    double rate_wl_per_ms = 0.0;             // per batch, smoothed; times the slots for the server
+    std::deque<std::pair<double, uint64_t>> recent;   // (completion time, windows x lengths), last 2 s
+    uint64_t snaps_queued = 0;               // snapshots accepted and not yet served
+    double snap_ms = 0.0;                    // smoothed time a stream worker spends on one snapshot
+    int n_stream_workers = 2;
+
+    // Requests' throughput in windows x lengths per ms: what completed in the
+    // last two seconds (it includes every other use of the GPU), or, before
+    // that window fills, the smoothed per-batch rate times the slots.
+    double request_rate(double now) const {
+        if (recent.size() >= 3 && now - recent.front().first >= 250.0) {
+            uint64_t w = 0;
+            for (auto &e : recent) w += e.second;
+            return (double)w / (now - recent.front().first);
+        }
+        return rate_wl_per_ms * (double)slots;
+    }
     // statistics
-    uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, wl = 0;
-    std::vector<double> latencies;
+    uint64_t submitted = 0, completed = 0, failed = 0, refused = 0, refused_snaps = 0, batches = 0, wl = 0;
+    std::vector<double> latencies, snap_latencies;
     double t_first = 0.0, t_last = 0.0;
     int max_concurrent = 0, running = 0;
 
     void worker(int slot);
+    void stream_worker();
 };
 
 static int64_t windows_lengths(const PnSeriesIn &s) {
@@ -131,6 +184,7 @@ void panache_server::worker(int slot) {
                 const bool in_share = batch.empty() || fp + j.footprint <= share;
                 if (!fits || !in_share) break;
                 fp += j.footprint;
+                queued_wl -= std::min<uint64_t>(queued_wl, (uint64_t)windows_lengths(j.s));
                 batch.push_back(std::move(queue.front()));
                 queue.pop_front();
             }
@@ -147,12 +201,19 @@ void panache_server::worker(int slot) {
             in.push_back(s);
         }
         std::vector<std::vector<panache_motif>> res;
+        const double t_start = now_ms();
         const int rc = pn_rt::run(ctx, in, res);
         const double t = now_ms();
         {
             std::lock_guard<std::mutex> lk(mu);
             in_use -= fp;
             --running;
+            if (rc == PANACHE_OK && t > t_start) {
+                uint64_t bw = 0;
+                for (auto &j : batch) bw += (uint64_t)windows_lengths(j.s);
+                const double r = (double)bw / (t - t_start);
+                rate_wl_per_ms = rate_wl_per_ms > 0.0 ? 0.8 * rate_wl_per_ms + 0.2 * r : r;
+            }
             for (size_t b = 0; b < batch.size(); ++b) {
                 Result r;
                 r.rc = rc;
@@ -162,15 +223,112 @@ void panache_server::worker(int slot) {
                     ++completed;
                     wl += (uint64_t)windows_lengths(batch[b].s);
                     latencies.push_back(r.latency_ms);
+                    recent.emplace_back(t, (uint64_t)windows_lengths(batch[b].s));
                 } else {
                     ++failed;
                 }
                 t_last = t;
                 done[batch[b].ticket] = std::move(r);
             }
+            while (!recent.empty() && t - recent.front().first > 2000.0) recent.pop_front();
         }
         cv_done.notify_all();
         cv_work.notify_all();
+    }
+}
+
+// Files a stream snapshot's result under its ticket.
+static void file_snapshot(panache_server *sv, uint64_t ticket, Result &&r, int64_t n, const LiveStream &ls) {
+    const double t = now_ms();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (r.rc == PANACHE_OK) {
+            ++sv->completed;
+            sv->wl += (uint64_t)windows_lengths(PnSeriesIn{nullptr, 0, n, ls.m_min, ls.m_max, ls.k, ls.excl});
+            sv->snap_latencies.push_back(r.latency_ms);
+        } else {
+            ++sv->failed;
+        }
+        sv->t_last = t;
+        sv->done[ticket] = std::move(r);
+    }
+    sv->cv_done.notify_all();
+}
+
+// Applies the pending ops of one stream at a time: runs of consecutive
+// appends as one append (to the capacity reserved for the last of them),
+// snapshots in their place in the order.
+void panache_server::stream_worker() {
+    cudaSetDevice(device);
+    for (;;) {
+        std::shared_ptr<LiveStream> ls;
+        {
+            std::unique_lock<std::mutex> lk(streams_mu);
+            cv_stream.wait(lk, [&] { return !stream_work.empty() || stop; });
+            if (stream_work.empty()) return;             // stopping and drained
+            ls = std::move(stream_work.front());
+            stream_work.pop_front();
+        }
+        std::lock_guard<std::mutex> ex(ls->exec_mu);
+        for (;;) {
+            std::vector<StreamOp> run;
+            {
+                std::lock_guard<std::mutex> o(ls->ops_mu);
+                if (ls->ops.empty()) {
+                    ls->scheduled = false;
+                    break;
+                }
+                if (ls->ops.front().snapshot) {
+                    run.push_back(std::move(ls->ops.front()));
+                    ls->ops.pop_front();
+                } else {
+                    while (!ls->ops.empty() && !ls->ops.front().snapshot) {
+                        run.push_back(std::move(ls->ops.front()));
+                        ls->ops.pop_front();
+                    }
+                }
+            }
+            if (run[0].snapshot) {
+                const double t_snap = now_ms();
+                Result r;
+                int64_t n = panache_stream_length(ls->h);
+                {
+                    std::lock_guard<std::mutex> o(ls->ops_mu);
+                    r.rc = ls->err;
+                }
+                if (r.rc == PANACHE_OK && n == 0) r.rc = PANACHE_ESTATE;
+                if (r.rc == PANACHE_OK) {
+                    std::vector<panache_motif> out((size_t)ls->k * (size_t)(ls->m_max - ls->m_min + 1));
+                    int64_t got = 0;
+                    r.rc = panache_stream_topk(ls->h, out.data(), (int64_t)out.size(), &got);
+                    if (r.rc == PANACHE_OK) r.motifs.assign(out.begin(), out.begin() + got);
+                }
+                const double t_end = now_ms();
+                r.latency_ms = t_end - run[0].t_enq;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    const double took = t_end - t_snap;
+                    snap_ms = snap_ms > 0.0 ? 0.8 * snap_ms + 0.2 * took : took;
+                    if (snaps_queued) --snaps_queued;
+                }
+                file_snapshot(this, run[0].ticket, std::move(r), n, *ls);
+                continue;
+            }
+            size_t total = 0;
+            for (auto &op : run) total += op.samples.size();
+            std::vector<double> buf;
+            const double *src = run[0].samples.data();
+            if (run.size() > 1) {
+                buf.reserve(total);
+                for (auto &op : run) buf.insert(buf.end(), op.samples.begin(), op.samples.end());
+                src = buf.data();
+            }
+            const int rc = pn_rt::append_to(ls->h, src, PANACHE_F64, (int64_t)total, run.back().cap_after);
+            if (rc != PANACHE_OK) {
+                std::lock_guard<std::mutex> o(ls->ops_mu);
+                if (ls->err == PANACHE_OK) ls->err = rc;
+            }
+        }
     }
 }
 
@@ -180,12 +338,23 @@ static int enqueue(panache_server *sv, Job &&j, uint64_t *ticket) {
     if (rc != PANACHE_OK) return rc;
     if (fp > sv->budget) return PANACHE_EBUDGET;
     j.footprint = fp;
+    const uint64_t w = (uint64_t)windows_lengths(j.s);
     {
         std::lock_guard<std::mutex> lk(sv->mu);
+        const double rate = sv->request_rate(now_ms());
+        if (sv->deadline_ms > 0.0 && rate > 0.0) {
+            // predicted wait: the work queued ahead and this request's own, at
+            // the server's measured throughput
+            if ((double)(sv->queued_wl + w) / rate > sv->deadline_ms) {
+                ++sv->refused;
+                return PANACHE_EBUSY;
+            }
+        }
         j.ticket = sv->next_ticket++;
         j.t_submit = now_ms();
         if (!sv->submitted) sv->t_first = j.t_submit;
         ++sv->submitted;
+        sv->queued_wl += w;
         *ticket = j.ticket;
         sv->queue.push_back(std::move(j));
     }
@@ -220,6 +389,9 @@ int panache_server_create(const panache_config *cfg, int32_t slots, uint64_t hbm
         sv->ctxs.push_back(c);
     }
     for (int s = 0; s < slots; ++s) sv->workers.emplace_back(&panache_server::worker, sv.get(), s);
+    sv->n_stream_workers = std::max(2, slots);
+    for (int s = 0; s < sv->n_stream_workers; ++s)
+        sv->stream_workers.emplace_back(&panache_server::stream_worker, sv.get());
     *out = sv.release();
     return PANACHE_OK;
 }
@@ -228,10 +400,13 @@ void panache_server_destroy(panache_server *sv) {
     if (!sv) return;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
+        std::lock_guard<std::mutex> ls(sv->streams_mu);
         sv->stop = true;
     }
     sv->cv_work.notify_all();
+    sv->cv_stream.notify_all();
     for (auto &t : sv->workers) t.join();
+    for (auto &t : sv->stream_workers) t.join();     // pending stream ops are applied first
     cudaSetDevice(sv->device);
     {
         std::lock_guard<std::mutex> lk(sv->streams_mu);
@@ -282,7 +457,7 @@ int panache_server_stream_open(panache_server *sv, int32_t m_min, int32_t m_max,
                                uint64_t *stream_id) {
     if (!sv || !stream_id) return PANACHE_EINVAL;
     if (m_min < 3 || m_max < m_min || m_max > 1024 || k < 1 || excl < 1) return PANACHE_EINVAL;
-    std::unique_ptr<LiveStream> ls(new (std::nothrow) LiveStream());
+    std::shared_ptr<LiveStream> ls(new (std::nothrow) LiveStream());
     if (!ls) return PANACHE_ENOMEM;
     ls->m_min = m_min;
     ls->m_max = m_max;
@@ -300,25 +475,44 @@ int panache_server_stream_open(panache_server *sv, int32_t m_min, int32_t m_max,
     return PANACHE_OK;
 }
 
-static LiveStream *find_stream(panache_server *sv, uint64_t id) {
+static std::shared_ptr<LiveStream> find_stream(panache_server *sv, uint64_t id) {
     std::lock_guard<std::mutex> lk(sv->streams_mu);
     auto it = sv->streams.find(id);
-    return it == sv->streams.end() ? nullptr : it->second.get();
+    return it == sv->streams.end() ? nullptr : it->second;
+}
+
+// Queues an op and puts the stream on the work list (ops_mu held by the caller).
+static void schedule(panache_server *sv, const std::shared_ptr<LiveStream> &ls) {
+    if (ls->scheduled) return;
+    ls->scheduled = true;
+    {
+        std::lock_guard<std::mutex> lk(sv->streams_mu);
+        sv->stream_work.push_back(ls);
+    }
+    sv->cv_stream.notify_one();
 }
 
 int panache_server_append(panache_server *sv, uint64_t stream_id, const void *chunk, int32_t dtype, int64_t len) {
     if (!sv || len < 0 || (len > 0 && !chunk)) return PANACHE_EINVAL;
     const int dt = dtype & 0xFF;
     if ((dt != PANACHE_F32 && dt != PANACHE_F64) || (dtype & PANACHE_DEVICE)) return PANACHE_EINVAL;
-    LiveStream *ls = find_stream(sv, stream_id);
+    std::shared_ptr<LiveStream> ls = find_stream(sv, stream_id);
     if (!ls) return PANACHE_EINVAL;
     if (!len) return PANACHE_OK;
-    cudaSetDevice(sv->device);
-    std::lock_guard<std::mutex> lk(ls->mu);
-    const int64_t have = panache_stream_length(ls->h), cap = pn_rt::stream_capacity(ls->h);
-    const int64_t ncap = pn_rt::grow_capacity(cap, have + len);
-    if (ncap != cap) {
-        // reserve the grown state (and its snapshot row copy) before growing
+    StreamOp op;
+    op.samples.resize((size_t)len);
+    if (dt == PANACHE_F32) {
+        const float *f = static_cast<const float *>(chunk);
+        for (int64_t t = 0; t < len; ++t) op.samples[t] = (double)f[t];
+    } else {
+        memcpy(op.samples.data(), chunk, sizeof(double) * (size_t)len);
+    }
+    std::lock_guard<std::mutex> o(ls->ops_mu);
+    if (ls->err != PANACHE_OK) return ls->err;
+    if (ls->accepted + len > PN_STREAM_MAX_LEN) return PANACHE_EINVAL;
+    const int64_t ncap = pn_rt::grow_capacity(ls->planned_cap, ls->accepted + len);
+    if (ncap != ls->planned_cap) {
+        // reserve the grown state (and its snapshot row copy) before accepting
         uint64_t fp = 0;
         const PnSeriesIn s{chunk, dt, ncap, ls->m_min, ls->m_max, ls->k, ls->excl};
         int rc = pn_rt::footprint(ls->ctx, s, &fp);
@@ -329,51 +523,46 @@ int panache_server_append(panache_server *sv, uint64_t stream_id, const void *ch
         sv->in_use = sv->in_use - ls->reserved + fp;
         sv->peak_in_use = std::max(sv->peak_in_use, sv->in_use);
         ls->reserved = fp;
+        ls->planned_cap = ncap;
     }
-    return panache_append(ls->h, chunk, dtype, len);
+    ls->accepted += len;
+    op.cap_after = ls->planned_cap;
+    ls->ops.push_back(std::move(op));
+    schedule(sv, ls);
+    return PANACHE_OK;
 }
 
 int panache_server_stream_topk(panache_server *sv, uint64_t stream_id, uint64_t *ticket) {
     if (!sv || !ticket) return PANACHE_EINVAL;
-    LiveStream *ls = find_stream(sv, stream_id);
+    std::shared_ptr<LiveStream> ls = find_stream(sv, stream_id);
     if (!ls) return PANACHE_EINVAL;
-    cudaSetDevice(sv->device);
-    const double t0 = now_ms();
-    Result r;
-    int64_t n = 0;
-    {
-        std::lock_guard<std::mutex> lk(ls->mu);
-        n = panache_stream_length(ls->h);
-        if (n == 0) return PANACHE_ESTATE;
-        std::vector<panache_motif> out((size_t)ls->k * (size_t)(ls->m_max - ls->m_min + 1));
-        int64_t got = 0;
-        r.rc = panache_stream_topk(ls->h, out.data(), (int64_t)out.size(), &got);
-        if (r.rc == PANACHE_OK) r.motifs.assign(out.begin(), out.begin() + got);
-    }
-    const double t = now_ms();
-    r.latency_ms = t - t0;
+    StreamOp op;
+    op.snapshot = true;
+    op.t_enq = now_ms();
+    std::lock_guard<std::mutex> o(ls->ops_mu);
+    if (ls->accepted == 0) return PANACHE_ESTATE;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        *ticket = sv->next_ticket++;
-        if (!sv->submitted) sv->t_first = t0;
-        ++sv->submitted;
-        if (r.rc == PANACHE_OK) {
-            ++sv->completed;
-            sv->wl += (uint64_t)windows_lengths(PnSeriesIn{nullptr, 0, n, ls->m_min, ls->m_max, ls->k, ls->excl});
-            sv->latencies.push_back(r.latency_ms);
-        } else {
-            ++sv->failed;
+        // a snapshot waits for those queued before it, served by the stream workers
+        if (sv->deadline_ms > 0.0 && sv->snap_ms > 0.0 &&
+            (double)(sv->snaps_queued + 1) * sv->snap_ms / (double)sv->n_stream_workers > sv->deadline_ms) {
+            ++sv->refused_snaps;
+            return PANACHE_EBUSY;
         }
-        sv->t_last = t;
-        sv->done[*ticket] = std::move(r);
+        ++sv->snaps_queued;
+        op.ticket = sv->next_ticket++;
+        if (!sv->submitted) sv->t_first = op.t_enq;
+        ++sv->submitted;
     }
-    sv->cv_done.notify_all();
+    *ticket = op.ticket;
+    ls->ops.push_back(std::move(op));
+    schedule(sv, ls);
     return PANACHE_OK;
 }
 
 int panache_server_stream_close(panache_server *sv, uint64_t stream_id) {
     if (!sv) return PANACHE_EINVAL;
-    std::unique_ptr<LiveStream> ls;
+    std::shared_ptr<LiveStream> ls;
     {
         std::lock_guard<std::mutex> lk(sv->streams_mu);
         auto it = sv->streams.find(stream_id);
@@ -381,14 +570,34 @@ int panache_server_stream_close(panache_server *sv, uint64_t stream_id) {
         ls = std::move(it->second);
         sv->streams.erase(it);
     }
-    {
-        std::lock_guard<std::mutex> lk(ls->mu);     // no append or snapshot of this stream in flight
+    // the stream's pending ops are applied first (a snapshot asked for before
+    // the close still gets its result)
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> ex(ls->exec_mu);
+            std::lock_guard<std::mutex> o(ls->ops_mu);
+            if (ls->ops.empty() && !ls->scheduled) break;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     cudaSetDevice(sv->device);
     const uint64_t r = ls->reserved;
-    ls.reset();
+    {
+        std::lock_guard<std::mutex> ex(ls->exec_mu);
+        if (ls->h) panache_stream_close(ls->h);
+        ls->h = nullptr;
+        if (ls->ctx) panache_destroy(ls->ctx);
+        ls->ctx = nullptr;
+    }
     std::lock_guard<std::mutex> g(sv->mu);
     sv->in_use -= r;
+    return PANACHE_OK;
+}
+
+int panache_server_set_deadline(panache_server *sv, double deadline_ms) {
+    if (!sv || !(deadline_ms >= 0.0)) return PANACHE_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->deadline_ms = deadline_ms;
     return PANACHE_OK;
 }
 
@@ -406,19 +615,24 @@ int panache_server_get_stats(panache_server *sv, panache_server_stats *out) {
     out->peak_reserved_bytes = sv->peak_in_use;
     out->max_concurrent_batches = (uint32_t)sv->max_concurrent;
     out->span_ms = sv->completed ? sv->t_last - sv->t_first : 0.0;
-    if (!sv->latencies.empty()) {
-        std::vector<double> l = sv->latencies;
+    out->refused = sv->refused;
+    out->refused_snapshots = sv->refused_snaps;
+    auto pct = [](std::vector<double> l, double p) {
         std::sort(l.begin(), l.end());
-        auto pct = [&](double p) {
-            const double pos = p * (double)(l.size() - 1);
-            const size_t lo = (size_t)pos, hi = std::min(lo + 1, l.size() - 1);
-            return l[lo] + (l[hi] - l[lo]) * (pos - (double)lo);
-        };
-        out->p50_ms = pct(0.50);
-        out->p99_ms = pct(0.99);
+        const double pos = p * (double)(l.size() - 1);
+        const size_t lo = (size_t)pos, hi = std::min(lo + 1, l.size() - 1);
+        return l[lo] + (l[hi] - l[lo]) * (pos - (double)lo);
+    };
+    if (!sv->latencies.empty()) {
+        out->p50_ms = pct(sv->latencies, 0.50);
+        out->p99_ms = pct(sv->latencies, 0.99);
         double s = 0;
-        for (double v : l) s += v;
-        out->mean_ms = s / (double)l.size();
+        for (double v : sv->latencies) s += v;
+        out->mean_ms = s / (double)sv->latencies.size();
+    }
+    if (!sv->snap_latencies.empty()) {
+        out->snap_p50_ms = pct(sv->snap_latencies, 0.50);
+        out->snap_p99_ms = pct(sv->snap_latencies, 0.99);
     }
     return PANACHE_OK;
 }

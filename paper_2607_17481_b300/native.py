@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpanache.so")
 
 OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETRUNC, ESTATE, EPOOL, ENODEV, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+EBUSY = -10
 F32, F64, DEVICE = 1, 2, 0x100
 PLAIN_FP64, MIXED = 0, 1
 TOPK_GLOBAL, TOPK_PER_LENGTH = 0, 1
@@ -37,7 +38,7 @@ EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "pana
             "panache_topk_row_noalloc", "panache_alu_peak", "panache_kernel_times", "panache_inject_fault",
             "panache_server_create", "panache_server_destroy", "panache_server_submit", "panache_server_wait",
             "panache_server_stream_open", "panache_server_append", "panache_server_stream_topk",
-            "panache_server_stream_close", "panache_server_get_stats")
+            "panache_server_stream_close", "panache_server_get_stats", "panache_server_set_deadline")
 
 
 class Config(ctypes.Structure):
@@ -82,7 +83,9 @@ class ServerStats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in (
         "submitted", "completed", "failed", "queued", "batches", "windows_lengths", "budget_bytes",
         "peak_reserved_bytes")] + [("max_concurrent_batches", ctypes.c_uint32), ("_pad", ctypes.c_uint32)] + \
-        [(name, ctypes.c_double) for name in ("span_ms", "p50_ms", "p99_ms", "mean_ms")]
+        [(name, ctypes.c_double) for name in ("span_ms", "p50_ms", "p99_ms", "mean_ms")] + \
+        [("refused", ctypes.c_uint64), ("snap_p50_ms", ctypes.c_double), ("snap_p99_ms", ctypes.c_double),
+         ("refused_snapshots", ctypes.c_uint64)]
 
 
 _lib = None
@@ -135,6 +138,7 @@ def lib():
         L.panache_server_stream_topk.argtypes = [vp, ctypes.c_uint64, u64p]
         L.panache_server_stream_close.argtypes = [vp, ctypes.c_uint64]
         L.panache_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.panache_server_set_deadline.argtypes = [vp, ctypes.c_double]
         L.panache_calibrate_width.argtypes = [vp, vp, i32, i64, i32, i32, ctypes.c_double, ctypes.POINTER(i32),
                                               vp, vp]
         L.panache_strerror.argtypes = [ctypes.c_int]
@@ -426,6 +430,10 @@ class Server:
     def stream_close(self, sid: int):
         _check(lib().panache_server_stream_close(self._h, sid), "stream_close")
         self._caps.pop(("s", sid), None)
+
+    def set_deadline(self, deadline_ms: float):
+        """Deadline admission: submissions predicted to wait longer are refused (EBUSY); 0 turns it off."""
+        _check(lib().panache_server_set_deadline(self._h, deadline_ms), "set_deadline")
 
     def stats(self) -> dict:
         s = ServerStats()

@@ -135,3 +135,45 @@ def test_request_that_cannot_fit_beside_streams_is_refused(pn):
     got, _ = sv.wait(sv.submit(big.x, big.m_min, big.m_max, big.k, big.excl), timeout_ms=60_000)
     assert len(got) > 0
     sv.close()
+
+
+def test_deadline_sheds_load(pn):
+    """With a deadline, a submission whose predicted wait (queued work over the
+    measured throughput) exceeds it is refused with EBUSY and counted; with
+    the deadline off the same request is admitted and served."""
+    reqs = _series(3, seed=41)
+    sv = pn.Server(slots=1)
+    q0, q1 = reqs[0], reqs[1]
+    sv.wait(sv.submit(q0.x, q0.m_min, q0.m_max, q0.k, q0.excl))    # a throughput estimate exists
+    sv.set_deadline(1e-6)
+    with pytest.raises(pn.PanacheError) as e:
+        sv.submit(q1.x, q1.m_min, q1.m_max, q1.k, q1.excl)
+    assert e.value.code == pn.native.EBUSY
+    assert sv.stats()["refused"] == 1
+    sv.set_deadline(0.0)
+    got, _ = sv.wait(sv.submit(q1.x, q1.m_min, q1.m_max, q1.k, q1.excl))
+    assert np.array_equal(got, pn.Context().pmp(q1.x, q1.m_min, q1.m_max, q1.k, q1.excl))
+    sv.close()
+
+
+def test_many_small_appends_coalesce(pn):
+    """Hundreds of small appends queued faster than they are applied: the
+    stream workers apply runs of them as one append; snapshots taken in
+    between see exactly the samples accepted before them."""
+    s = workloads.planted_random_walk()
+    sv = pn.Server(slots=1, topk_mode=0)
+    sid = sv.stream_open(s.m_min, s.m_max, s.k, s.excl)
+    snaps = []
+    for pos in range(0, s.x.shape[0], 37):
+        sv.append(sid, s.x[pos:pos + 37])
+        if pos in (2997, 5994):
+            snaps.append((sv.stream_topk(sid), min(pos + 37, s.x.shape[0])))
+    snaps.append((sv.stream_topk(sid), s.x.shape[0]))
+    ctx = pn.Context(topk_mode=0)
+    for t, n in snaps:
+        got, lat = sv.wait(t)
+        assert np.array_equal(got, ctx.pmp(s.x[:n], s.m_min, s.m_max, s.k, s.excl)), n
+    st = sv.stats()
+    assert st["snap_p50_ms"] > 0
+    sv.stream_close(sid)
+    sv.close()

@@ -33,3 +33,15 @@ def test_batched_subset_matches_full():
         assert 2000 <= s.x.shape[0] <= 20000
         assert 16 <= s.m_min <= 128 and 20 <= s.m_max - s.m_min + 1 <= 64
         assert s.excl == s.m_max and s.k == 10
+
+
+def test_autotune_shape_key_classes():
+    """Requests of one shape class (length to the nearest power of two, the
+    length interval, the sample type) share one tuned configuration."""
+    import numpy as np
+    from paper_2607_17481_b300 import autotune
+    k = autotune.shape_key
+    assert k(40_000, 100, 150, np.float32) == k(45_000, 100, 150, np.float32)
+    assert k(40_000, 100, 150, np.float32) != k(80_000, 100, 150, np.float32)
+    assert k(40_000, 100, 150, np.float32) != k(40_000, 100, 151, np.float32)
+    assert k(40_000, 100, 150, np.float32) != k(40_000, 100, 150, np.float64)
