@@ -724,8 +724,11 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
     const int grid = ctx->sm_count * (int)c.grid_mult;
     int32_t ncls = 0;
     if ((stages & PN_EMIT_SIEVE) && !(c.flags & PANACHE_FLAG_NO_SIEVE)) {
-        PN_CU(pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w,
-                               (c.flags & PANACHE_FLAG_EXHAUSTIVE_SIEVE) ? 1 : 0, grid, R.a_max, st, &ncls));
+        // exhaustive sieve: 1 with the tensor-core Gram filter, 2 every pair exactly
+        const int exhaustive = !(c.flags & PANACHE_FLAG_EXHAUSTIVE_SIEVE) ? 0
+                               : (c.flags & PANACHE_FLAG_SIEVE_GRAM) ? 1 : 2;
+        PN_CU(pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w, exhaustive, grid, R.a_max, st,
+                               &ncls));
         ctx->launches += 6 + (ncls ? 4 + 2 * 12 : 0);
     }
     ctx->stats.hot_classes = (uint64_t)ncls;

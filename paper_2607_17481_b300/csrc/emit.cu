@@ -973,6 +973,7 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             pn_kt_begin(v.kt, PN_KT_SIEVE, st);
             // after the class sort, keys[p] is the class of member p
             if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
+            else if (exhaustive == 1 && !v.Fh) e = launch_sieve_gram(v, cls, ncls, vals, grid_blocks, st);
             else if (exhaustive && v.x1) e = sieve_tiles_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);
             else if (exhaustive) e = sieve_tiles_t<ZMix2>(v, cls, ncls, vals, grid_blocks, st);
             else if (w <= SB_WMAX && v.x1) e = sieve_band_t<ZMix1>(v, cls, nmem, keys, vals, w, grid_blocks, st);

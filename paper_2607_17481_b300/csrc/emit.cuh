@@ -44,6 +44,11 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
                          int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out);
 cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved,
                             int grid_blocks, cudaStream_t st);
+// Exhaustive sieve of the mixed form with FP32 feature rows, every valid
+// pair of each hot class bounded through a tensor-core Gram block and only
+// the survivors evaluated exactly (gram.cu).
+cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals,
+                              int grid_blocks, cudaStream_t st);
 // Exact row refinement: each target cell (series, m, i) scanned against
 // every valid partner at its length; `improved` set when a cell decreased.
 // max_windows bounds the partners of any target (the longest series).

@@ -99,6 +99,27 @@ def test_prefix_per_length_paper_stride(pn, wafer, golden):
     assert r["bad_dist"] == 0
 
 
+def test_prefix_gram_sieve_matches_dense(pn, wafer):
+    """On the wafer-like prefix (thousands of hot classes): the Gram-filtered
+    exhaustive sieve's rows equal the dense exhaustive sieve's within FP32
+    rounding, with a fraction of its exact evaluations."""
+    x = np.ascontiguousarray(wafer.x[:200_000])
+    off = pn.FLAG_NO_COMPLETION | pn.FLAG_NO_REFINE | pn.FLAG_EXHAUSTIVE_SIEVE
+    g = pn.Context(precision=1, topk_mode=0, flags=off | pn.FLAG_SIEVE_GRAM | pn.FLAG_TIMING)
+    g.pmp(x, 100, 150, 20, 150)
+    d = pn.Context(precision=1, topk_mode=0, flags=off | pn.FLAG_TIMING)
+    d.pmp(x, 100, 150, 20, 150)
+    dg, _ = pn.unpack_keys(g.profile_rows(0, x.shape[0], 51))
+    dd, _ = pn.unpack_keys(d.profile_rows(0, x.shape[0], 51))
+    assert np.array_equal(np.isfinite(dg), np.isfinite(dd))
+    fin = np.isfinite(dd)
+    assert np.all(np.abs(dg[fin] - dd[fin]) <= 2e-5 * dd[fin] + 2e-5)
+    eg, ed = g.stats()["exact_sieve"], d.stats()["exact_sieve"]
+    assert eg < ed
+    print(f"wafer prefix exhaustive sieve: Gram {eg} exact pairs in {g.kernel_times()['sieve'][0]:.1f} ms, "
+          f"dense {ed} in {d.kernel_times()['sieve'][0]:.1f} ms")
+
+
 def test_5m_reported_cells_are_exact(pn):
     """The benchmark's workload (5,000,000 samples, mixed precision): every
     reported motif's distance is the oracle's exact nearest-neighbour distance
