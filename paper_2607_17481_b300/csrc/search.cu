@@ -48,7 +48,10 @@ constexpr int SR_WARM = 32;    // candidates a query's warm start inspects
 // exact distance of an admitted pair.  The final profile is unchanged (it
 // is the minimum over the admitted pairs); only the number of pairs the
 // bound lets through drops.
-constexpr int SR_TILE = 4;     // queries a warp takes from the work queue at a time
+#ifndef PN_SR_TILE
+#define PN_SR_TILE 8
+#endif
+constexpr int SR_TILE = PN_SR_TILE;   // queries a warp takes from the work queue at a time
 
 // A persistent kernel: SMs x grid_mult blocks, and each warp takes the next
 // SR_TILE queries of the query order from a global work counter until the
