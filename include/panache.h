@@ -91,11 +91,15 @@ extern "C" {
 #define PANACHE_FLAG_INDEX_ONLY 0x10       /* build features, keys and directories, then stop (no motifs) */
 #define PANACHE_FLAG_FP64_ANCHORS 0x20     /* mixed form: chunk anchors by FP64 direct DFT instead of the
                                               tensor cores (3xTF32 tcgen05 contraction, the default) */
-#define PANACHE_FLAG_GRAPH 0x40           /* capture the index and search steps of a request into a CUDA
-                                              graph and replay it while requests keep the same shape
-                                              (series lengths, dtypes, length intervals, k, excl): the
-                                              context keeps that request's buffers, copies each new
-                                              request's samples into them and launches the graph once */
+#define PANACHE_FLAG_GRAPH 0x40           /* capture a request into two CUDA graphs and replay them while
+                                              requests keep the same shape (series lengths, dtypes, length
+                                              intervals, k, excl): the index and search steps, and the emit
+                                              stage after the hot-class sieve (completion rounds, row
+                                              refinement and final selection, whose rounds are decided on
+                                              the device); the sieve, which sizes its buffers from counts it
+                                              reads back, runs between them.  The context keeps that
+                                              request's buffers, copies each new request's samples into
+                                              them and launches each graph once */
 #define PANACHE_FLAG_HALF_FEATURES 0x80   /* mixed form: the feature-row cache (Sec. 3.2) held in half
                                               precision, 64 B per window and anchor instead of 128 B.  The
                                               rows are the FP32 rows rounded to nearest; the keys and the

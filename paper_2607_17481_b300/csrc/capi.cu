@@ -87,6 +87,35 @@ __global__ void k_put(const void *src, int32_t dtype, int64_t n, int64_t off, do
 
 }  // namespace
 
+// Device buffers of one selection group set: the groups, the picks
+// [ngroups][kmax] and their counts, kept with the request so that the
+// launches can be replayed.
+struct SelBufs {
+    PnSelGroup *dg = nullptr;
+    PnPick *out = nullptr;
+    int32_t *cnt = nullptr;
+    int32_t ng = 0, kmax = 1, cap = 0;
+};
+
+// The emit stage after the sieve: its control words, the seed, refinement
+// and final selection groups, and the seed and target lists.  Built once per
+// request (kept with the request when the stage is replayed from a graph).
+enum { C_GATE = 0, C_FLAG, C_NSEED, C_ROUNDS, R_GATE, R_FLAG, R_NTG, R_PASSES, OV_FINAL, OV_OTHER, C_WORDS };
+struct EmitPlan {
+    int32_t *ctl = nullptr;
+    SelBufs sb, rb, fb;
+    PnSeed *dseeds = nullptr, *dtg = nullptr, *ddone = nullptr;
+    int32_t *ndone = nullptr;
+    int32_t done_cap = 0;
+    int64_t max_windows = 0;
+    int m_top = 3;
+    bool completion = false, refine = false;
+    void *pin = nullptr;               // graph replay: the pinned result buffer its copies write to
+    ~EmitPlan() {
+        if (pin) cudaFreeHost(pin);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // One request: tables, device buffers and results.
 // ---------------------------------------------------------------------------
@@ -130,12 +159,14 @@ struct PnRequest {
     uint32_t *dir_keys = nullptr, *dir_vals = nullptr, *bstart = nullptr;
     unsigned long long *prof = nullptr, *stats = nullptr;
     int *flagbuf = nullptr;
+    EmitPlan *emit = nullptr;          // the emit stage's buffers, kept for graph replay
 
     // Buffers come from the stream-ordered pool of the request's stream and
     // go back to it in stream order, so requests on different streams never
     // synchronise the device through allocation.
     ~PnRequest() {
         for (void *p : allocs) cudaFreeAsync(p, st);
+        delete emit;
     }
 
     template <class T>
@@ -164,17 +195,35 @@ struct panache_ctx {
     // PANACHE_FLAG_GRAPH: the captured index + search steps of `last`, the
     // request shape they were captured for, and the persistent input staging
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec_emit = nullptr;  // the emit stage after the sieve, same shape
     std::vector<PnSeriesIn> gshape;
     unsigned char *gstage = nullptr;
     std::vector<int64_t> gstage_off;
-    uint64_t glaunches = 0;
+    uint64_t glaunches = 0, glaunches_emit = 0;
+    // pinned host buffers the emit stage's results are copied into
+    void *pin = nullptr;
+    size_t pin_bytes = 0;
 
     void drop_graph() {
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (gexec_emit) cudaGraphExecDestroy(gexec_emit);
         gexec = nullptr;
+        gexec_emit = nullptr;
         gshape.clear();
         gstage = nullptr;            // owned by `last` (allocated through it)
         gstage_off.clear();
+    }
+
+    int pinned(size_t bytes, void **out) {
+        if (bytes > pin_bytes) {
+            if (pin) cudaFreeHost(pin);
+            pin = nullptr;
+            pin_bytes = 0;
+            if (cudaMallocHost(&pin, bytes) != cudaSuccess) return PANACHE_ENOMEM;
+            pin_bytes = bytes;
+        }
+        *out = pin;
+        return PANACHE_OK;
     }
 
     const std::vector<float> &proj(int a) {
@@ -458,51 +507,47 @@ GroupSet make_groups(const PnRequest &R, int mode, const std::vector<int> &k_of_
     return gs;
 }
 
-// Runs the selection of `gs` and returns the picks per group on the host.
-int run_select(panache_ctx *ctx, PnRequest &R, const PnView &v, const GroupSet &gs, bool strict,
-               std::vector<std::vector<PnPick>> &picks) {
-    picks.assign(gs.g.size(), {});
-    if (gs.g.empty()) return PANACHE_OK;
+// Sizes the pool (k (m_max + 1) plus slack, capped at 8192 cells; EINVAL
+// beyond that when strict) and uploads the groups.
+int sel_prepare(PnRequest &R, const GroupSet &gs, bool strict, SelBufs &b) {
+    b.ng = (int32_t)gs.g.size();
+    if (!b.ng) return PANACHE_OK;
     uint32_t need_max = 0;
-    int32_t kmax = 1;
+    b.kmax = 1;
     for (auto &G : gs.g) {
         need_max = std::max(need_max, G.need);
-        kmax = std::max(kmax, G.k);
+        b.kmax = std::max(b.kmax, G.k);
     }
     int64_t cap = next_pow2((int64_t)need_max + need_max / 4 + 256);
     if (cap > 8192) {
         if (strict) return PANACHE_EINVAL;
         cap = 8192;
     }
-    const int32_t ng = (int32_t)gs.g.size();
-    PnSelGroup *dg = nullptr;
-    PnPick *dout = nullptr;
-    int32_t *dcnt = nullptr;
-    cudaStream_t st = ctx->st;
-    PN_CU(cudaMallocAsync((void **)&dg, sizeof(PnSelGroup) * ng, st));
-    PN_CU(cudaMallocAsync((void **)&dout, sizeof(PnPick) * (size_t)ng * kmax, st));
-    PN_CU(cudaMallocAsync((void **)&dcnt, sizeof(int32_t) * ng, st));
-    PN_CU(cudaMemcpyAsync(dg, gs.g.data(), sizeof(PnSelGroup) * ng, cudaMemcpyHostToDevice, st));
-    PN_CU(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
-    pn_kt_begin(v.kt, PN_KT_SELECT, st);
-    PN_CU(pn::launch_select(v, dg, ng, 0, R.total_cells, (int32_t)cap, ctx->cfg.eps0, kmax, dout, dcnt, R.flagbuf,
-                            ctx->sm_count * 8, st));
-    pn_kt_end(v.kt, PN_KT_SELECT, st);
-    ctx->launches += 10;
-    std::vector<PnPick> hout((size_t)ng * kmax);
-    std::vector<int32_t> hcnt(ng);
-    int overflow = 0;
-    PN_CU(cudaMemcpyAsync(hout.data(), dout, sizeof(PnPick) * hout.size(), cudaMemcpyDeviceToHost, st));
-    PN_CU(cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int32_t) * ng, cudaMemcpyDeviceToHost, st));
-    PN_CU(cudaMemcpyAsync(&overflow, R.flagbuf, sizeof(int), cudaMemcpyDeviceToHost, st));
-    PN_CU(cudaFreeAsync(dg, st));
-    PN_CU(cudaFreeAsync(dout, st));
-    PN_CU(cudaFreeAsync(dcnt, st));
-    PN_CU(cudaStreamSynchronize(st));
-    if (overflow && strict) return PANACHE_EPOOL;
-    for (int32_t gi = 0; gi < ng; ++gi)
-        picks[gi].assign(hout.begin() + (size_t)gi * kmax, hout.begin() + (size_t)gi * kmax + hcnt[gi]);
+    b.cap = (int32_t)cap;
+    PN_CU(R.alloc(b.dg, b.ng));
+    PN_CU(R.alloc(b.out, (int64_t)b.ng * b.kmax));
+    PN_CU(R.alloc(b.cnt, b.ng));
+    PN_CU(cudaMemcpyAsync(b.dg, gs.g.data(), sizeof(PnSelGroup) * b.ng, cudaMemcpyHostToDevice, R.st));
+    PN_CU(cudaMemsetAsync(b.cnt, 0, sizeof(int32_t) * b.ng, R.st));
     return PANACHE_OK;
+}
+
+// Enqueues one selection of `b` (its kernels honour v.gate).
+int sel_launch(panache_ctx *ctx, PnRequest &R, const PnView &v, const SelBufs &b, int *overflow) {
+    if (!b.ng) return PANACHE_OK;
+    pn_kt_begin(v.kt, PN_KT_SELECT, R.st);
+    PN_CU(pn::launch_select(v, b.dg, b.ng, 0, R.total_cells, b.cap, ctx->cfg.eps0, b.kmax, b.out, b.cnt, overflow,
+                            ctx->sm_count * 8, R.st));
+    pn_kt_end(v.kt, PN_KT_SELECT, R.st);
+    ctx->launches += 10;
+    return PANACHE_OK;
+}
+
+constexpr int kRefinePasses = 8;   // most row-refinement passes of one request
+
+__global__ void k_fill_i32(int32_t *p, int32_t n, int32_t value) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) p[t] = value;
 }
 
 // CUDA events between the steps of a request (PANACHE_FLAG_TIMING).
@@ -641,61 +686,105 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables, 
     return PANACHE_OK;
 }
 
-// Exact row refinement of the top list (refine.cu): the top refine_mult*k
-// cells of every selection group are each scanned against all valid partners at
-// their length, then the list is reselected and any cell not yet scanned is
-// scanned, until a pass finds no new cell or lowers none.  The final top-k is
-// a prefix of that list (the same greedy rule), so every reported cell ends
-// with its exact nearest neighbour.
-int refine_rows(panache_ctx *ctx, PnRequest &R, const PnView &v, const GroupSet &groups) {
-    cudaStream_t st = R.st;
-    int64_t max_windows = 0;
-    int m_top = 3;
-    for (auto &S : R.ser) {
-        max_windows = std::max<int64_t>(max_windows, S.n - S.m_min + 1);
-        m_top = std::max(m_top, (int)S.m_max);
+// Buffers and uploads of the emit stage after the sieve (no launches).
+int emit_prepare(panache_ctx *ctx, PnRequest &R, const GroupSet &seed_groups, const GroupSet &ref_groups,
+                 const GroupSet &out_groups, EmitPlan &E) {
+    const panache_config &c = ctx->cfg;
+    PN_CU(R.alloc(E.ctl, C_WORDS));
+    E.completion = !(c.flags & PANACHE_FLAG_NO_COMPLETION) && c.rounds > 0;
+    E.refine = !(c.flags & PANACHE_FLAG_NO_REFINE);
+    if (E.completion) {
+        PN_TRY(sel_prepare(R, seed_groups, false, E.sb));
+        if (E.sb.ng) PN_CU(R.alloc(E.dseeds, (int64_t)E.sb.ng * E.sb.kmax));
     }
-    std::set<std::tuple<int32_t, int32_t, int64_t>> done;
-    PnSeed *dtg = nullptr;
-    size_t tg_cap = 0;
-    int rc = PANACHE_OK;
-    for (int pass = 0; pass < 16 && rc == PANACHE_OK; ++pass) {
-        std::vector<std::vector<PnPick>> picks;
-        rc = run_select(ctx, R, v, groups, false, picks);
-        if (rc != PANACHE_OK) break;
-        std::vector<PnSeed> tg;
-        for (auto &gp : picks)
-            for (auto &p : gp)
-                if (done.insert(std::make_tuple(p.series, p.m, p.i)).second) tg.push_back(PnSeed{p.series, p.m, p.i, p.j});
-        if (tg.empty()) break;
-        if (tg.size() > tg_cap) {
-            if (dtg) cudaFreeAsync(dtg, st);
-            dtg = nullptr;
-            tg_cap = tg.size();
-            rc = from_cuda(cudaMallocAsync((void **)&dtg, sizeof(PnSeed) * tg_cap, st));
-            if (rc != PANACHE_OK) break;
+    if (E.refine) {
+        PN_TRY(sel_prepare(R, ref_groups, false, E.rb));
+        if (E.rb.ng) {
+            E.done_cap = E.rb.kmax * kRefinePasses;
+            PN_CU(R.alloc(E.dtg, (int64_t)E.rb.ng * E.rb.kmax));
+            PN_CU(R.alloc(E.ddone, (int64_t)E.rb.ng * E.done_cap));
+            PN_CU(R.alloc(E.ndone, E.rb.ng));
         }
-        rc = from_cuda(cudaMemcpyAsync(dtg, tg.data(), sizeof(PnSeed) * tg.size(), cudaMemcpyHostToDevice, st));
-        if (rc == PANACHE_OK) rc = from_cuda(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
-        pn_kt_begin(v.kt, PN_KT_REFINE, st);
-        if (rc == PANACHE_OK)
-            rc = from_cuda(pn::launch_refine(v, dtg, (int32_t)tg.size(), max_windows, m_top, R.flagbuf,
-                                             ctx->sm_count * 2, st));
-        pn_kt_end(v.kt, PN_KT_REFINE, st);
-        ctx->launches += 1;
-        int improved = 0;
-        if (rc == PANACHE_OK) rc = from_cuda(cudaMemcpyAsync(&improved, R.flagbuf, sizeof(int), cudaMemcpyDeviceToHost, st));
-        if (rc == PANACHE_OK) rc = from_cuda(cudaStreamSynchronize(st));
-        ctx->stats.refine_passes = pass + 1;
-        if (!improved) break;
+        for (auto &S : R.ser) {
+            E.max_windows = std::max<int64_t>(E.max_windows, S.n - S.m_min + 1);
+            E.m_top = std::max(E.m_top, (int)S.m_max);
+        }
     }
-    if (dtg) cudaFreeAsync(dtg, st);
-    return rc;
+    PN_TRY(sel_prepare(R, out_groups, true, E.fb));
+    return PANACHE_OK;
 }
 
-// Algorithm 2 on the profile rows `v.prof`: hot-class sieve, completion
-// rounds, the row refinement and the final selection; then the counters and
-// the error word.
+// Every launch of the emit stage after the sieve, with the results copied
+// to the pinned host buffers: no host wait, so it can be captured.
+// Algorithm 2's rounds are driven on the device: every round is enqueued,
+// and a gate word in device memory closes the remaining rounds once the
+// seeds run out or nothing improves.  Control words: 0-3 completion (gate,
+// improved, seeds, rounds run), 4-7 refinement (gate, improved, targets,
+// passes run), 8 the final selection's pool overflow, 9 the others'
+// (ignored).
+int emit_launch(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm, EmitPlan &E, PnPick *hout,
+                int32_t *hcnt, int32_t *hctl) {
+    const panache_config &c = ctx->cfg;
+    cudaStream_t st = R.st;
+    const int grid = ctx->sm_count * (int)c.grid_mult;
+    int32_t *ctl = E.ctl;
+    PN_CU(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * C_WORDS, st));
+    if (E.completion && E.sb.ng) {
+        const int32_t nmax = E.sb.ng * E.sb.kmax;
+        k_fill_i32<<<1, 32, 0, st>>>(ctl + C_GATE, 1, 1);
+        PnView vg = v;
+        vg.gate = ctl + C_GATE;
+        for (uint32_t round = 0; round < c.rounds; ++round) {
+            PN_CU(pn::launch_round_begin(ctl + C_GATE, ctl + C_FLAG, ctl + C_NSEED, st));
+            PN_TRY(sel_launch(ctx, R, vg, E.sb, ctl + OV_OTHER));
+            PN_CU(pn::launch_picks_to_seeds(E.sb.out, E.sb.cnt, E.sb.ng, E.sb.kmax, E.dseeds, ctl + C_NSEED,
+                                            ctl + C_GATE, st));
+            PN_CU(pn::launch_gate_if_empty(ctl + C_GATE, ctl + C_NSEED, st));
+            pn_kt_begin(v.kt, PN_KT_COMPLETE, st);
+            PN_CU(pn::launch_complete(vg, E.dseeds, nmax, ctl + C_NSEED, (int)c.dm, (int)c.dp, ctl + C_FLAG, grid, st));
+            pn_kt_end(v.kt, PN_KT_COMPLETE, st);
+            PN_CU(pn::launch_round_end(ctl + C_GATE, ctl + C_FLAG, ctl + C_ROUNDS, st));
+            ctx->launches += 6;
+        }
+    }
+    // Exact row refinement of the top list (refine.cu): the top
+    // refine_mult*k cells of every selection group are each scanned against
+    // all valid partners at their length; the list is reselected and cells
+    // not scanned before are scanned, until a pass finds no new cell or
+    // lowers none.  The final top-k is a prefix of that list (the same
+    // greedy rule), so every reported cell ends with its exact nearest
+    // neighbour.
+    if (E.refine && E.rb.ng) {
+        const int32_t nmax = E.rb.ng * E.rb.kmax;
+        PN_CU(cudaMemsetAsync(E.ndone, 0, sizeof(int32_t) * E.rb.ng, st));
+        k_fill_i32<<<1, 32, 0, st>>>(ctl + R_GATE, 1, 1);
+        PnView vr = v;
+        vr.gate = ctl + R_GATE;
+        for (int pass = 0; pass < kRefinePasses; ++pass) {
+            PN_CU(pn::launch_round_begin(ctl + R_GATE, ctl + R_FLAG, ctl + R_NTG, st));
+            PN_TRY(sel_launch(ctx, R, vr, E.rb, ctl + OV_OTHER));
+            PN_CU(pn::launch_new_targets(E.rb.out, E.rb.cnt, E.rb.ng, E.rb.kmax, E.ddone, E.ndone, E.done_cap, E.dtg,
+                                         ctl + R_NTG, ctl + R_GATE, st));
+            PN_CU(pn::launch_gate_if_empty(ctl + R_GATE, ctl + R_NTG, st));
+            pn_kt_begin(v.kt, PN_KT_REFINE, st);
+            PN_CU(pn::launch_refine(vr, E.dtg, nmax, ctl + R_NTG, E.max_windows, E.m_top, ctl + R_FLAG,
+                                    ctx->sm_count * 2, st));
+            pn_kt_end(v.kt, PN_KT_REFINE, st);
+            PN_CU(pn::launch_round_end(ctl + R_GATE, ctl + R_FLAG, ctl + R_PASSES, st));
+            ctx->launches += 5;
+        }
+    }
+    PN_TRY(tm.mark(7));
+    PN_TRY(sel_launch(ctx, R, v, E.fb, ctl + OV_FINAL));
+    if (E.fb.ng) {
+        PN_CU(cudaMemcpyAsync(hout, E.fb.out, sizeof(PnPick) * (size_t)E.fb.ng * E.fb.kmax, cudaMemcpyDeviceToHost,
+                              st));
+        PN_CU(cudaMemcpyAsync(hcnt, E.fb.cnt, sizeof(int32_t) * E.fb.ng, cudaMemcpyDeviceToHost, st));
+    }
+    PN_CU(cudaMemcpyAsync(hctl, ctl, sizeof(int32_t) * C_WORDS, cudaMemcpyDeviceToHost, st));
+    return PANACHE_OK;
+}
+
 enum { PN_EMIT_SIEVE = 1, PN_EMIT_REST = 2, PN_EMIT_ALL = 3 };
 
 int read_counters(panache_ctx *ctx, PnRequest &R) {
@@ -756,39 +845,63 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
     // prefix of that length's own greedy list, and no length contributes
     // more than kseed cells to it.
     const GroupSet seed_mode = make_groups(R, (int)c.topk_mode, kseed);
-    if (!(c.flags & PANACHE_FLAG_NO_COMPLETION)) {
-        PnSeed *dseeds = nullptr;
-        size_t seeds_cap = 0;
-        for (uint32_t round = 0; round < c.rounds; ++round) {
-            std::vector<PnSeed> seeds;
-            std::vector<std::vector<PnPick>> picks;
-            PN_TRY(run_select(ctx, R, v, seed_mode, false, picks));
-            for (auto &gp : picks)
-                for (auto &p : gp) seeds.push_back(PnSeed{p.series, p.m, p.i, p.j});
-            if (seeds.empty()) break;
-            if (seeds.size() > seeds_cap) {
-                if (dseeds) PN_CU(cudaFreeAsync(dseeds, st));
-                seeds_cap = seeds.size();
-                PN_CU(cudaMallocAsync((void **)&dseeds, sizeof(PnSeed) * seeds_cap, st));
-            }
-            PN_CU(cudaMemcpyAsync(dseeds, seeds.data(), sizeof(PnSeed) * seeds.size(), cudaMemcpyHostToDevice, st));
-            PN_CU(cudaMemsetAsync(R.flagbuf, 0, sizeof(int), st));
-            pn_kt_begin(v.kt, PN_KT_COMPLETE, st);
-            PN_CU(pn::launch_complete(v, dseeds, (int32_t)seeds.size(), (int)c.dm, (int)c.dp, R.flagbuf, grid, st));
-            pn_kt_end(v.kt, PN_KT_COMPLETE, st);
-            ctx->launches += 1;
-            int improved = 0;
-            PN_CU(cudaMemcpyAsync(&improved, R.flagbuf, sizeof(int), cudaMemcpyDeviceToHost, st));
-            PN_CU(cudaStreamSynchronize(st));
-            ctx->stats.completion_rounds = round + 1;
-            if (!improved) break;
-        }
-        if (dseeds) PN_CU(cudaFreeAsync(dseeds, st));
+    // The rest of Algorithm 2 (completion rounds, the row refinement, the
+    // final selection) runs without the host: buffers first, then the
+    // launches, replayed from a captured graph when the request's shape
+    // repeats, then one wait for the results.
+    const bool graph = (c.flags & PANACHE_FLAG_GRAPH) && !(c.flags & (PANACHE_FLAG_TIMING | PANACHE_FLAG_INDEX_ONLY)) &&
+                       ctx->last == &R;
+    if (!R.emit || !graph) {
+        delete R.emit;
+        R.emit = new (std::nothrow) EmitPlan();
+        if (!R.emit) return PANACHE_ENOMEM;
+        PN_TRY(emit_prepare(ctx, R, seed_mode, make_groups(R, (int)c.topk_mode, kref), out_groups, *R.emit));
     }
-    if (!(c.flags & PANACHE_FLAG_NO_REFINE)) PN_TRY(refine_rows(ctx, R, v, make_groups(R, (int)c.topk_mode, kref)));
-    PN_TRY(tm.mark(7));
-    std::vector<std::vector<PnPick>> picks;
-    PN_TRY(run_select(ctx, R, v, out_groups, true, picks));
+    EmitPlan &E = *R.emit;
+    const size_t out_bytes = sizeof(PnPick) * (size_t)E.fb.ng * E.fb.kmax;
+    const size_t pin_bytes = out_bytes + sizeof(int32_t) * ((size_t)E.fb.ng + C_WORDS);
+    void *pin = nullptr;
+    if (graph) {
+        // the captured copies write to a buffer of the plan's own, which
+        // lives as long as the graph
+        if (!E.pin && cudaMallocHost(&E.pin, std::max<size_t>(pin_bytes, 64)) != cudaSuccess) return PANACHE_ENOMEM;
+        pin = E.pin;
+    } else {
+        PN_TRY(ctx->pinned(std::max<size_t>(pin_bytes, 64), &pin));
+    }
+    PnPick *hout = static_cast<PnPick *>(pin);
+    int32_t *hcnt = reinterpret_cast<int32_t *>(static_cast<unsigned char *>(pin) + out_bytes);
+    int32_t *hctl = hcnt + E.fb.ng;
+    if (graph && ctx->gexec_emit) {
+        PN_CU(cudaGraphLaunch(ctx->gexec_emit, st));
+        ctx->launches += ctx->glaunches_emit;
+    } else if (graph) {
+        // capture once; later requests of the same shape launch it
+        const uint64_t l0 = ctx->launches;
+        cudaGraph_t g = nullptr;
+        PN_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl);
+        const cudaError_t ec = cudaStreamEndCapture(st, &g);
+        if (rc == PANACHE_OK) rc = from_cuda(ec);
+        if (rc == PANACHE_OK) rc = from_cuda(cudaGraphInstantiate(&ctx->gexec_emit, g, 0));
+        if (g) cudaGraphDestroy(g);
+        if (rc != PANACHE_OK) {
+            ctx->drop_graph();
+            return rc;
+        }
+        ctx->glaunches_emit = ctx->launches - l0;
+        PN_CU(cudaGraphLaunch(ctx->gexec_emit, st));
+    } else {
+        PN_TRY(emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl));
+    }
+    PN_CU(cudaStreamSynchronize(st));
+    if (hctl[OV_FINAL]) return PANACHE_EPOOL;
+    ctx->stats.completion_rounds = (uint64_t)hctl[C_ROUNDS];
+    ctx->stats.refine_passes = (uint64_t)hctl[R_PASSES];
+    const SelBufs &fb = E.fb;
+    std::vector<std::vector<PnPick>> picks(fb.ng);
+    for (int32_t gi = 0; gi < fb.ng; ++gi)
+        picks[gi].assign(hout + (size_t)gi * fb.kmax, hout + (size_t)gi * fb.kmax + hcnt[gi]);
     PN_TRY(tm.mark(8));
     PN_TRY(tm.read(ctx->stats.step_ms));
     ctx->kt.collect();
@@ -1311,6 +1424,7 @@ void panache_destroy(panache_ctx *ctx) {
     if (ctx->st) cudaStreamSynchronize(ctx->st);
     ctx->drop_graph();
     delete ctx->last;
+    if (ctx->pin) cudaFreeHost(ctx->pin);
     if (ctx->own) cudaStreamDestroy(ctx->own);
     delete ctx;
 }

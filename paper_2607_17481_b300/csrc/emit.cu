@@ -517,7 +517,10 @@ __global__ void __launch_bounds__(256) k_sieve_tiles(PnView v, const PnClass *cl
 // box's (2dm+1)(2dp+1) windows on each side are normalised once into shared
 // memory (FP64 moments), then every triple reads its two windows from there.
 // ---------------------------------------------------------------------------
-__global__ void k_complete(PnView v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved) {
+__global__ void k_complete(PnView v, const PnSeed *seeds, int32_t nseeds_max, const int32_t *nseeds_dev, int dm,
+                           int dp, int *improved) {
+    if (pn_gated(v)) return;
+    const int32_t nseeds = nseeds_dev ? min(*nseeds_dev, nseeds_max) : nseeds_max;
     extern __shared__ __align__(16) unsigned char csm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -604,6 +607,7 @@ __device__ __forceinline__ int group_of(const PnView &v, const PnSelGroup *grp, 
 __global__ void __launch_bounds__(256) k_sel_hist(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_t total,
                                                   double eps0, int level, const uint32_t *b1, uint32_t *hist,
                                                   int64_t per_block) {
+    if (pn_gated(v)) return;
     __shared__ uint32_t sh[4096];
     const int64_t lo = (int64_t)blockIdx.x * per_block;
     const int64_t hi = min(total, lo + per_block);
@@ -711,6 +715,7 @@ __global__ void k_sel_pick(const PnSelGroup *grp, int32_t ngrp, const uint32_t *
 __global__ void k_sel_pool(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_t total, double eps0,
                            const uint32_t *b1, const uint32_t *b2, PnPoolEntry *pool, uint32_t *pool_cnt,
                            int32_t cap, int *overflow) {
+    if (pn_gated(v)) return;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
     unsigned long long key = v.prof[t];
@@ -735,6 +740,7 @@ __global__ void k_sel_pool(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_
 // FP64 two-pass distance of every pooled cell (one warp per entry).
 __global__ void k_sel_verify(PnView v, const PnSelGroup *grp, int32_t ngrp, PnPoolEntry *pool,
                              const uint32_t *pool_cnt, int32_t cap, double eps0) {
+    if (pn_gated(v)) return;
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -782,6 +788,7 @@ __device__ __forceinline__ bool pool_less(const PnPoolEntry &a, const PnPoolEntr
 // greedy scan by warp 0 under the m/2 rule.
 __global__ void k_sel_greedy(PnView v, const PnSelGroup *grp, const PnPoolEntry *pool, const uint32_t *pool_cnt,
                              int32_t cap, int32_t npow2, PnPick *out, int32_t *out_cnt, int32_t kmax) {
+    if (pn_gated(v)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     PnPoolEntry *e = reinterpret_cast<PnPoolEntry *>(smem);
     int32_t *acc_m = reinterpret_cast<int32_t *>(e + npow2);
@@ -996,14 +1003,127 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
     return e;
 }
 
-cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved,
-                            int grid_blocks, cudaStream_t st) {
+cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, const int32_t *nseeds_dev, int dm,
+                            int dp, int *improved, int grid_blocks, cudaStream_t st) {
     if (nseeds <= 0) return cudaSuccess;
     int g = nseeds < grid_blocks ? nseeds : grid_blocks;
     const size_t sm = sizeof(PnWin) * 2 * (size_t)(2 * dm + 1) * (2 * dp + 1);
     cudaError_t e = pn_allow_smem(k_complete, sm);
     if (e != cudaSuccess) return e;
-    k_complete<<<g, 256, sm, st>>>(v, seeds, nseeds, dm, dp, improved);
+    k_complete<<<g, 256, sm, st>>>(v, seeds, nseeds, nseeds_dev, dm, dp, improved);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Device-driven rounds of the emit stage.  A round (completion) or pass
+// (refinement) is enqueued in full; a gate word decides on the device
+// whether its kernels run, so the host enqueues the maximum number of
+// rounds without waiting for any of them.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Opens a round when the gate is open: its flag and target count start at 0.
+__global__ void k_round_begin(const int *gate, int *flag, int32_t *count) {
+    if (*gate) {
+        *flag = 0;
+        *count = 0;
+    }
+}
+
+// Closes the gate when the round has nothing to do.
+__global__ void k_gate_if_empty(int *gate, const int32_t *count) {
+    if (*gate && *count == 0) *gate = 0;
+}
+
+// Counts the round and closes the gate when nothing improved.
+__global__ void k_round_end(int *gate, const int *flag, int32_t *rounds) {
+    if (*gate) {
+        ++*rounds;
+        if (!*flag) *gate = 0;
+    }
+}
+
+// Completion seeds from a selection's picks (group g's at picks[g kmax ...]).
+__global__ void k_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *seeds,
+                                 int32_t *nseeds, const int *gate) {
+    if (!*gate) return;
+    const int gi = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (gi >= ng) return;
+    const int c = cnt[gi];
+    int base = 0;
+    if (lane == 0 && c > 0) base = atomicAdd(nseeds, c);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int t = lane; t < c; t += 32) {
+        const PnPick p = picks[(int64_t)gi * kmax + t];
+        seeds[base + t] = PnSeed{p.series, p.m, p.i, p.j};
+    }
+}
+
+// Refinement targets: the picks of group g not refined in an earlier pass
+// (done[g][0 .. ndone[g])), appended to the group's done list and to the
+// targets.  One warp per group, so a group's list has one writer.
+__global__ void k_new_targets(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *done,
+                              int32_t *ndone, int32_t done_cap, PnSeed *targets, int32_t *ntargets, const int *gate) {
+    if (!*gate) return;
+    const int gi = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (gi >= ng) return;
+    const int c = cnt[gi];
+    PnSeed *dl = done + (int64_t)gi * done_cap;
+    int nd = ndone[gi];
+    for (int t0 = 0; t0 < c; t0 += 32) {
+        const int t = t0 + lane;
+        PnSeed sd{0, 0, 0, 0};
+        bool fresh = false;
+        if (t < c) {
+            const PnPick p = picks[(int64_t)gi * kmax + t];
+            sd = PnSeed{p.series, p.m, p.i, p.j};
+            fresh = true;
+            for (int e = 0; e < nd && fresh; ++e)
+                if (dl[e].m == p.m && dl[e].i == p.i) fresh = false;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, fresh);
+        const int nf = __popc(bal);
+        if (nf == 0) continue;
+        const int rank = __popc(bal & ((1u << lane) - 1u));
+        int base = 0;
+        if (lane == 0) base = atomicAdd(ntargets, nf);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (fresh) {
+            targets[base + rank] = sd;
+            if (nd + rank < done_cap) dl[nd + rank] = sd;
+        }
+        nd = min(done_cap, nd + nf);
+        __syncwarp();
+    }
+    if (lane == 0) ndone[gi] = nd;
+}
+
+}  // namespace
+
+cudaError_t launch_round_begin(const int *gate, int *flag, int32_t *count, cudaStream_t st) {
+    k_round_begin<<<1, 1, 0, st>>>(gate, flag, count);
+    return cudaGetLastError();
+}
+cudaError_t launch_gate_if_empty(int *gate, const int32_t *count, cudaStream_t st) {
+    k_gate_if_empty<<<1, 1, 0, st>>>(gate, count);
+    return cudaGetLastError();
+}
+cudaError_t launch_round_end(int *gate, const int *flag, int32_t *rounds, cudaStream_t st) {
+    k_round_end<<<1, 1, 0, st>>>(gate, flag, rounds);
+    return cudaGetLastError();
+}
+cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *seeds,
+                                  int32_t *nseeds, const int *gate, cudaStream_t st) {
+    if (ng <= 0) return cudaSuccess;
+    k_picks_to_seeds<<<grid_for((int64_t)ng * 32, 256), 256, 0, st>>>(picks, cnt, ng, kmax, seeds, nseeds, gate);
+    return cudaGetLastError();
+}
+cudaError_t launch_new_targets(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *done,
+                               int32_t *ndone, int32_t done_cap, PnSeed *targets, int32_t *ntargets, const int *gate,
+                               cudaStream_t st) {
+    if (ng <= 0) return cudaSuccess;
+    k_new_targets<<<grid_for((int64_t)ng * 32, 256), 256, 0, st>>>(picks, cnt, ng, kmax, done, ndone, done_cap,
+                                                                     targets, ntargets, gate);
     return cudaGetLastError();
 }
 

@@ -42,8 +42,19 @@ struct PnPick {           // one selected motif
 namespace pn {
 cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t total_slots, int w, int exhaustive,
                          int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out);
-cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, int dm, int dp, int *improved,
-                            int grid_blocks, cudaStream_t st);
+// nseeds: seeds in the array (host); nseeds_dev (device, may be null): how
+// many of them the kernel takes.
+cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, const int32_t *nseeds_dev, int dm,
+                            int dp, int *improved, int grid_blocks, cudaStream_t st);
+// Device-driven rounds (see emit.cu).
+cudaError_t launch_round_begin(const int *gate, int *flag, int32_t *count, cudaStream_t st);
+cudaError_t launch_gate_if_empty(int *gate, const int32_t *count, cudaStream_t st);
+cudaError_t launch_round_end(int *gate, const int *flag, int32_t *rounds, cudaStream_t st);
+cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *seeds,
+                                  int32_t *nseeds, const int *gate, cudaStream_t st);
+cudaError_t launch_new_targets(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *done,
+                               int32_t *ndone, int32_t done_cap, PnSeed *targets, int32_t *ntargets, const int *gate,
+                               cudaStream_t st);
 // Exhaustive sieve of the mixed form with FP32 feature rows, every valid
 // pair of each hot class bounded through a tensor-core Gram block and only
 // the survivors evaluated exactly (gram.cu).
@@ -52,8 +63,8 @@ cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls,
 // Exact row refinement: each target cell (series, m, i) scanned against
 // every valid partner at its length; `improved` set when a cell decreased.
 // max_windows bounds the partners of any target (the longest series).
-cudaError_t launch_refine(const PnView &v, const PnSeed *tg, int32_t ntg, int64_t max_windows, int m_max,
-                          int *improved, int blocks_per_target, cudaStream_t st);
+cudaError_t launch_refine(const PnView &v, const PnSeed *tg, int32_t ntg, const int32_t *ntg_dev, int64_t max_windows,
+                          int m_max, int *improved, int blocks_per_target, cudaStream_t st);
 cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ngrp, int64_t cell_begin,
                           int64_t cell_end, int32_t cap, double eps0, int32_t kmax, PnPick *out, int32_t *out_cnt,
                           int *overflow, int grid_blocks, cudaStream_t st);

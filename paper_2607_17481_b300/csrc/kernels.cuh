@@ -62,7 +62,13 @@ struct PnView {
     unsigned long long *stats;
     // per-kernel event timer of the request (host object; null unless timing)
     PnKTimer *kt;
+    // device-driven rounds of the emit stage: the kernels of a completion
+    // round or refinement pass return at once when *gate is 0 (null: run)
+    const int *gate;
 };
+
+// True when the current device-driven round has been closed.
+__device__ __forceinline__ bool pn_gated(const PnView &v) { return v.gate && *(volatile const int *)v.gate == 0; }
 
 #define PN_FT_CHUNKS 4         // chunks (one warp each) per block of the feature kernel
 #define PN_ERR_TC_TIMEOUT 1   // a tensor-core anchor tile's bounded wait ran out

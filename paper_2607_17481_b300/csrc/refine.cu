@@ -18,6 +18,8 @@
 // Window moments come from the FP64 prefix sums at the target's length with
 // the moment table's arithmetic (mu, sigma^2 = Q/m - mu^2; the mixed form
 // takes 1/sigma in FP32), so any length works, anchored or not.
+#include <algorithm>
+
 #include "emit.cuh"
 #include "zops.cuh"
 
@@ -65,87 +67,98 @@ __device__ __forceinline__ float2 ref_moments<ZMix1>(const PnView &v, const PnSe
     return ref_moments_mixed<ZMix1>(v, S, s, j, m);
 }
 
-// Block (x, y): target y, partners j = x * RF_THREADS + tid (+ grid stride).
+// A persistent kernel: work item w is part (w mod parts) of target
+// (w / parts); a part scans partners j = part * RF_THREADS + tid + k parts
+// RF_THREADS.  The target count may live on the device (device-driven
+// passes), so the grid is fixed and the items are counted there.
 template <class Z>
-__global__ void __launch_bounds__(RF_THREADS) k_refine(PnView v, const PnSeed *tg, int *improved) {
+__global__ void __launch_bounds__(RF_THREADS) k_refine(PnView v, const PnSeed *tg, int32_t ntg_max,
+                                                       const int32_t *ntg_dev, int32_t parts, int *improved) {
     using ZT = typename Z::T;
+    if (pn_gated(v)) return;
     extern __shared__ __align__(16) unsigned char rsm[];
     ZT *zq = reinterpret_cast<ZT *>(rsm);
     __shared__ unsigned long long wbest[RF_THREADS / 32];
-    const PnSeed t = tg[blockIdx.y];
-    const int s = t.series, m = t.m;
-    const PnSeries &S = v.series[s];
-    const int64_t i = t.i, last = S.n - m;
-    const auto mq = ref_moments<Z>(v, S, s, i, m);
-    if (Z::degenerate(mq)) return;                         // block-uniform
-    const auto *xi = Z::samples(v, S.x_off + i);
-    for (int r = threadIdx.x; r < m; r += RF_THREADS) zq[r] = Z::z(mq, xi[r]);
-    __syncthreads();
-    unsigned long long best = PN_EMPTY_KEY;
-    unsigned long long n_ex = 0;
-    for (int64_t j = (int64_t)blockIdx.x * RF_THREADS + threadIdx.x; j <= last;
-         j += (int64_t)gridDim.x * RF_THREADS) {
-        if (j - i < S.excl && i - j < S.excl) continue;
-        const auto mj = ref_moments<Z>(v, S, s, j, m);
-        if (Z::degenerate(mj)) continue;
-        const auto *xj = Z::samples(v, S.x_off + j);
-        ZT acc = 0;
-#pragma unroll 4
-        for (int r = 0; r < m; ++r) {
-            const ZT d = zq[r] - Z::z(mj, xj[r]);
-            acc = fma(d, d, acc);
-        }
-        const unsigned long long key = Z::pack(Z::root(acc), (uint32_t)j);
-        best = key < best ? key : best;
-        n_ex += 1;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-        best = other < best ? other : best;
-    }
+    const int32_t ntg = ntg_dev ? min(*ntg_dev, ntg_max) : ntg_max;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) wbest[warp] = best;
+    unsigned long long n_ex = 0;
+    for (int64_t w = blockIdx.x; w < (int64_t)ntg * parts; w += gridDim.x) {
+        const PnSeed t = tg[w / parts];
+        const int part = (int)(w % parts);
+        const int s = t.series, m = t.m;
+        const PnSeries &S = v.series[s];
+        const int64_t i = t.i, last = S.n - m;
+        const auto mq = ref_moments<Z>(v, S, s, i, m);
+        if (Z::degenerate(mq)) continue;                     // block-uniform
+        __syncthreads();                                     // the previous item's window is no longer read
+        const auto *xi = Z::samples(v, S.x_off + i);
+        for (int r = threadIdx.x; r < m; r += RF_THREADS) zq[r] = Z::z(mq, xi[r]);
+        __syncthreads();
+        unsigned long long best = PN_EMPTY_KEY;
+        for (int64_t j = (int64_t)part * RF_THREADS + threadIdx.x; j <= last; j += (int64_t)parts * RF_THREADS) {
+            if (j - i < S.excl && i - j < S.excl) continue;
+            const auto mj = ref_moments<Z>(v, S, s, j, m);
+            if (Z::degenerate(mj)) continue;
+            const auto *xj = Z::samples(v, S.x_off + j);
+            ZT acc = 0;
+#pragma unroll 4
+            for (int r = 0; r < m; ++r) {
+                const ZT d = zq[r] - Z::z(mj, xj[r]);
+                acc = fma(d, d, acc);
+            }
+            const unsigned long long key = Z::pack(Z::root(acc), (uint32_t)j);
+            best = key < best ? key : best;
+            n_ex += 1;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other < best ? other : best;
+        }
+        if (lane == 0) wbest[warp] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = wbest[0];
+            for (int q = 1; q < RF_THREADS / 32; ++q) b = wbest[q] < b ? wbest[q] : b;
+            if (b != PN_EMPTY_KEY) {
+                unsigned long long *row = v.prof + S.row_off + (int64_t)(m - S.m_min) * S.ld;
+                if (atomicMin(&row[i], b) > b) atomicExch(improved, 1);
+            }
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n_ex += __shfl_xor_sync(0xffffffffu, n_ex, o);
     if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_REFINE], n_ex);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long b = wbest[0];
-        for (int w = 1; w < RF_THREADS / 32; ++w) b = wbest[w] < b ? wbest[w] : b;
-        if (b != PN_EMPTY_KEY) {
-            unsigned long long *row = v.prof + S.row_off + (int64_t)(m - S.m_min) * S.ld;
-            if (atomicMin(&row[i], b) > b) atomicExch(improved, 1);
-        }
-    }
 }
 
 template <class Z>
-cudaError_t refine_t(const PnView &v, const PnSeed *tg, int32_t ntg, int64_t max_windows, int m_max, int *improved,
-                     int blocks_per_target, cudaStream_t st) {
+cudaError_t refine_t(const PnView &v, const PnSeed *tg, int32_t ntg, const int32_t *ntg_dev, int64_t max_windows,
+                     int m_max, int *improved, int blocks_per_target, cudaStream_t st) {
     const size_t sm = sizeof(typename Z::T) * (size_t)m_max;
     cudaError_t e = pn_allow_smem(k_refine<Z>, sm);
     if (e != cudaSuccess) return e;
-    int64_t bx = (max_windows + RF_THREADS - 1) / RF_THREADS;
-    if (bx > blocks_per_target) bx = blocks_per_target;
-    if (bx < 1) bx = 1;
-    for (int32_t t0 = 0; t0 < ntg; t0 += 65535) {
-        const int32_t cnt = ntg - t0 < 65535 ? ntg - t0 : 65535;
-        k_refine<Z><<<dim3((unsigned)bx, (unsigned)cnt), RF_THREADS, sm, st>>>(v, tg + t0, improved);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    int64_t parts = (max_windows + RF_THREADS - 1) / RF_THREADS;
+    if (parts > blocks_per_target) parts = blocks_per_target;
+    if (parts < 1) parts = 1;
+    // enough resident blocks for every SM; the items beyond are looped over
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t items = (int64_t)ntg * parts;
+    const int64_t grid = std::min<int64_t>(items, (int64_t)sms * 8);
+    k_refine<Z><<<(unsigned)std::max<int64_t>(1, grid), RF_THREADS, sm, st>>>(v, tg, ntg, ntg_dev, (int32_t)parts,
+                                                                          improved);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_refine(const PnView &v, const PnSeed *tg, int32_t ntg, int64_t max_windows, int m_max,
-                          int *improved, int blocks_per_target, cudaStream_t st) {
+cudaError_t launch_refine(const PnView &v, const PnSeed *tg, int32_t ntg, const int32_t *ntg_dev, int64_t max_windows,
+                          int m_max, int *improved, int blocks_per_target, cudaStream_t st) {
     if (ntg <= 0 || max_windows <= 0) return cudaSuccess;
-    if (v.precision == 0) return refine_t<ZPlain>(v, tg, ntg, max_windows, m_max, improved, blocks_per_target, st);
-    if (v.x1) return refine_t<ZMix1>(v, tg, ntg, max_windows, m_max, improved, blocks_per_target, st);
-    return refine_t<ZMix2>(v, tg, ntg, max_windows, m_max, improved, blocks_per_target, st);
+    if (v.precision == 0)
+        return refine_t<ZPlain>(v, tg, ntg, ntg_dev, max_windows, m_max, improved, blocks_per_target, st);
+    if (v.x1) return refine_t<ZMix1>(v, tg, ntg, ntg_dev, max_windows, m_max, improved, blocks_per_target, st);
+    return refine_t<ZMix2>(v, tg, ntg, ntg_dev, max_windows, m_max, improved, blocks_per_target, st);
 }
 
 }  // namespace pn

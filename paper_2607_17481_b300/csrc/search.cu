@@ -56,8 +56,12 @@ constexpr int SR_TILE = PN_SR_TILE;   // queries a warp takes from the work queu
 // A persistent kernel: SMs x grid_mult blocks, and each warp takes the next
 // SR_TILE queries of the query order from a global work counter until the
 // order is exhausted, so warps that draw cheap queries take more of them.
+#ifndef PN_SR_MINB
+#define PN_SR_MINB 5
+#endif
+
 template <class Z, bool HALF, bool WARM>
-__global__ void __launch_bounds__(SR_THREADS, 4) k_search(PnView v, int64_t total, int zcap,
+__global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int64_t total, int zcap,
                                                         unsigned long long *work) {
     using ZT = typename Z::T;
     __shared__ __align__(16) float sF[SR_WARPS][PN_FEAT];
