@@ -462,7 +462,8 @@ int panache_server_get_stats(panache_server *sv, panache_server_stats *out);
  * -- the windows x lengths queued ahead of it plus its own, over the
  * server's measured request throughput (what completed in the last two
  * seconds; before that, a smoothed per-batch rate times the slots) --
- * exceeds deadline_ms is refused at submission with EBUSY.  A stream
+ * exceeds three quarters of deadline_ms (the rest covers the estimate's
+ * error) is refused at submission with EBUSY.  A stream
  * snapshot is refused with EBUSY when the snapshots queued ahead of it and
  * itself, at the measured time per snapshot spread over the stream workers,
  * exceed the deadline.  Above its capacity the server then sheds load

@@ -722,8 +722,18 @@ int emit_prepare(panache_ctx *ctx, PnRequest &R, const GroupSet &seed_groups, co
 // improved, seeds, rounds run), 4-7 refinement (gate, improved, targets,
 // passes run), 8 the final selection's pool overflow, 9 the others'
 // (ignored).
+// With `batch` > 0 (not while capturing) the rounds are enqueued `batch` at
+// a time and the host reads the gate between batches, so a request whose
+// rounds end early does not launch the rest.
+int gate_open(cudaStream_t st, const int32_t *gate, int32_t *host, bool *open) {
+    PN_CU(cudaMemcpyAsync(host, gate, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PN_CU(cudaStreamSynchronize(st));
+    *open = *host != 0;
+    return PANACHE_OK;
+}
+
 int emit_launch(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm, EmitPlan &E, PnPick *hout,
-                int32_t *hcnt, int32_t *hctl) {
+                int32_t *hcnt, int32_t *hctl, int batch) {
     const panache_config &c = ctx->cfg;
     cudaStream_t st = R.st;
     const int grid = ctx->sm_count * (int)c.grid_mult;
@@ -735,16 +745,19 @@ int emit_launch(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm, 
         PnView vg = v;
         vg.gate = ctl + C_GATE;
         for (uint32_t round = 0; round < c.rounds; ++round) {
-            PN_CU(pn::launch_round_begin(ctl + C_GATE, ctl + C_FLAG, ctl + C_NSEED, st));
+            if (batch > 0 && round > 0 && round % batch == 0) {
+                bool open = true;
+                PN_TRY(gate_open(st, ctl + C_GATE, hctl + C_GATE, &open));
+                if (!open) break;
+            }
             PN_TRY(sel_launch(ctx, R, vg, E.sb, ctl + OV_OTHER));
             PN_CU(pn::launch_picks_to_seeds(E.sb.out, E.sb.cnt, E.sb.ng, E.sb.kmax, E.dseeds, ctl + C_NSEED,
                                             ctl + C_GATE, st));
-            PN_CU(pn::launch_gate_if_empty(ctl + C_GATE, ctl + C_NSEED, st));
             pn_kt_begin(v.kt, PN_KT_COMPLETE, st);
             PN_CU(pn::launch_complete(vg, E.dseeds, nmax, ctl + C_NSEED, (int)c.dm, (int)c.dp, ctl + C_FLAG, grid, st));
             pn_kt_end(v.kt, PN_KT_COMPLETE, st);
-            PN_CU(pn::launch_round_end(ctl + C_GATE, ctl + C_FLAG, ctl + C_ROUNDS, st));
-            ctx->launches += 6;
+            PN_CU(pn::launch_round_end(ctl + C_GATE, ctl + C_FLAG, ctl + C_NSEED, ctl + C_ROUNDS, st));
+            ctx->launches += 3;
         }
     }
     // Exact row refinement of the top list (refine.cu): the top
@@ -761,17 +774,20 @@ int emit_launch(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm, 
         PnView vr = v;
         vr.gate = ctl + R_GATE;
         for (int pass = 0; pass < kRefinePasses; ++pass) {
-            PN_CU(pn::launch_round_begin(ctl + R_GATE, ctl + R_FLAG, ctl + R_NTG, st));
+            if (batch > 0 && pass > 0 && pass % batch == 0) {
+                bool open = true;
+                PN_TRY(gate_open(st, ctl + R_GATE, hctl + R_GATE, &open));
+                if (!open) break;
+            }
             PN_TRY(sel_launch(ctx, R, vr, E.rb, ctl + OV_OTHER));
             PN_CU(pn::launch_new_targets(E.rb.out, E.rb.cnt, E.rb.ng, E.rb.kmax, E.ddone, E.ndone, E.done_cap, E.dtg,
                                          ctl + R_NTG, ctl + R_GATE, st));
-            PN_CU(pn::launch_gate_if_empty(ctl + R_GATE, ctl + R_NTG, st));
             pn_kt_begin(v.kt, PN_KT_REFINE, st);
             PN_CU(pn::launch_refine(vr, E.dtg, nmax, ctl + R_NTG, E.max_windows, E.m_top, ctl + R_FLAG,
                                     ctx->sm_count * 2, st));
             pn_kt_end(v.kt, PN_KT_REFINE, st);
-            PN_CU(pn::launch_round_end(ctl + R_GATE, ctl + R_FLAG, ctl + R_PASSES, st));
-            ctx->launches += 5;
+            PN_CU(pn::launch_round_end(ctl + R_GATE, ctl + R_FLAG, ctl + R_NTG, ctl + R_PASSES, st));
+            ctx->launches += 3;
         }
     }
     PN_TRY(tm.mark(7));
@@ -880,7 +896,7 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
         const uint64_t l0 = ctx->launches;
         cudaGraph_t g = nullptr;
         PN_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        int rc = emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl);
+        int rc = emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl, 0);
         const cudaError_t ec = cudaStreamEndCapture(st, &g);
         if (rc == PANACHE_OK) rc = from_cuda(ec);
         if (rc == PANACHE_OK) rc = from_cuda(cudaGraphInstantiate(&ctx->gexec_emit, g, 0));
@@ -892,7 +908,7 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
         ctx->glaunches_emit = ctx->launches - l0;
         PN_CU(cudaGraphLaunch(ctx->gexec_emit, st));
     } else {
-        PN_TRY(emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl));
+        PN_TRY(emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl, 2));
     }
     PN_CU(cudaStreamSynchronize(st));
     if (hctl[OV_FINAL]) return PANACHE_EPOOL;

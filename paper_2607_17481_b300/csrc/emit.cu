@@ -716,25 +716,26 @@ __global__ void k_sel_pool(PnView v, const PnSelGroup *grp, int32_t ngrp, int64_
                            const uint32_t *b1, const uint32_t *b2, PnPoolEntry *pool, uint32_t *pool_cnt,
                            int32_t cap, int *overflow) {
     if (pn_gated(v)) return;
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    unsigned long long key = v.prof[t];
-    if (key == PN_EMPTY_KEY) return;
-    int gi = group_of(v, grp, ngrp, t);
-    if (t >= grp[gi].cell_off + grp[gi].ncell) return;
-    uint32_t h = (sel_bits(key, eps0, 0) << 12) | sel_bits(key, eps0, 1);
-    uint32_t thr = (b1[gi] << 12) | b2[gi];
-    if (h > thr + 1u) return;
-    uint32_t slot = atomicAdd(&pool_cnt[gi], 1u);
-    if ((int32_t)slot >= cap) {
-        atomicExch(overflow, 1);
-        return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const unsigned long long key = v.prof[t];
+        if (key == PN_EMPTY_KEY) continue;
+        const int gi = group_of(v, grp, ngrp, t);
+        if (t >= grp[gi].cell_off + grp[gi].ncell) continue;
+        const uint32_t h = (sel_bits(key, eps0, 0) << 12) | sel_bits(key, eps0, 1);
+        const uint32_t thr = (b1[gi] << 12) | b2[gi];
+        if (h > thr + 1u) continue;
+        const uint32_t slot = atomicAdd(&pool_cnt[gi], 1u);
+        if ((int32_t)slot >= cap) {
+            atomicExch(overflow, 1);
+            continue;
+        }
+        PnPoolEntry e;
+        e.cell = (uint32_t)(t - grp[gi].cell_off);
+        e.j = pn_key_idx(key);
+        e.d = pn_key_dist(key);
+        pool[(int64_t)gi * cap + slot] = e;
     }
-    PnPoolEntry e;
-    e.cell = (uint32_t)(t - grp[gi].cell_off);
-    e.j = pn_key_idx(key);
-    e.d = pn_key_dist(key);
-    pool[(int64_t)gi * cap + slot] = e;
 }
 
 // FP64 two-pass distance of every pooled cell (one warp per entry).
@@ -1022,24 +1023,19 @@ cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds
 // ---------------------------------------------------------------------------
 namespace {
 
-// Opens a round when the gate is open: its flag and target count start at 0.
-__global__ void k_round_begin(const int *gate, int *flag, int32_t *count) {
+// Ends a round: an empty round closes the gate, a round that ran is
+// counted and closes the gate when nothing improved; the flag and the
+// count start again at 0 for the next round.
+__global__ void k_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds) {
     if (*gate) {
+        if (*count == 0) {
+            *gate = 0;
+        } else {
+            ++*rounds;
+            if (!*flag) *gate = 0;
+        }
         *flag = 0;
         *count = 0;
-    }
-}
-
-// Closes the gate when the round has nothing to do.
-__global__ void k_gate_if_empty(int *gate, const int32_t *count) {
-    if (*gate && *count == 0) *gate = 0;
-}
-
-// Counts the round and closes the gate when nothing improved.
-__global__ void k_round_end(int *gate, const int *flag, int32_t *rounds) {
-    if (*gate) {
-        ++*rounds;
-        if (!*flag) *gate = 0;
     }
 }
 
@@ -1100,16 +1096,8 @@ __global__ void k_new_targets(const PnPick *picks, const int32_t *cnt, int32_t n
 
 }  // namespace
 
-cudaError_t launch_round_begin(const int *gate, int *flag, int32_t *count, cudaStream_t st) {
-    k_round_begin<<<1, 1, 0, st>>>(gate, flag, count);
-    return cudaGetLastError();
-}
-cudaError_t launch_gate_if_empty(int *gate, const int32_t *count, cudaStream_t st) {
-    k_gate_if_empty<<<1, 1, 0, st>>>(gate, count);
-    return cudaGetLastError();
-}
-cudaError_t launch_round_end(int *gate, const int *flag, int32_t *rounds, cudaStream_t st) {
-    k_round_end<<<1, 1, 0, st>>>(gate, flag, rounds);
+cudaError_t launch_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, cudaStream_t st) {
+    k_round_end<<<1, 1, 0, st>>>(gate, flag, count, rounds);
     return cudaGetLastError();
 }
 cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *seeds,
@@ -1158,8 +1146,9 @@ cudaError_t launch_select(const PnView &v, const PnSelGroup *grp_dev, int32_t ng
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(pcnt, 0, 4 * ngrp, st);
     if (e == cudaSuccess) {
-        k_sel_pool<<<grid_for(total, 256), 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, b1, b2, pool, pcnt, cap,
-                                                          overflow);
+        const int64_t pool_blocks = std::min<int64_t>(grid_for(total, 256), (int64_t)grid_blocks * 4);
+        k_sel_pool<<<(unsigned)pool_blocks, 256, 0, st>>>(v, grp_dev, ngrp, total, eps0, b1, b2, pool, pcnt, cap,
+                                                           overflow);
         int64_t vw = (int64_t)ngrp * cap;
         int64_t vb = (vw + 7) / 8;
         if (vb > grid_blocks) vb = grid_blocks;

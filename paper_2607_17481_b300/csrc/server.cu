@@ -41,6 +41,10 @@
 
 #define PN_STREAM_MAX_LEN ((int64_t)((1ull << 26) - 1))
 
+// Share of a deadline that a predicted wait may use (the rest covers the
+// error of the throughput estimate).
+static constexpr double kDeadlineShare = 0.75;
+
 namespace {
 
 double now_ms() {
@@ -344,8 +348,10 @@ static int enqueue(panache_server *sv, Job &&j, uint64_t *ticket) {
         const double rate = sv->request_rate(now_ms());
         if (sv->deadline_ms > 0.0 && rate > 0.0) {
             // predicted wait: the work queued ahead and this request's own, at
-            // the server's measured throughput
-            if ((double)(sv->queued_wl + w) / rate > sv->deadline_ms) {
+            // the server's measured throughput; a quarter of the deadline is
+            // kept for the error of that estimate (the live streams share the
+            // GPU and move the rate)
+            if ((double)(sv->queued_wl + w) / rate > kDeadlineShare * sv->deadline_ms) {
                 ++sv->refused;
                 return PANACHE_EBUSY;
             }
@@ -545,7 +551,7 @@ int panache_server_stream_topk(panache_server *sv, uint64_t stream_id, uint64_t 
         std::lock_guard<std::mutex> lk(sv->mu);
         // a snapshot waits for those queued before it, served by the stream workers
         if (sv->deadline_ms > 0.0 && sv->snap_ms > 0.0 &&
-            (double)(sv->snaps_queued + 1) * sv->snap_ms / (double)sv->n_stream_workers > sv->deadline_ms) {
+            (double)(sv->snaps_queued + 1) * sv->snap_ms / (double)sv->n_stream_workers > kDeadlineShare * sv->deadline_ms) {
             ++sv->refused_snaps;
             return PANACHE_EBUSY;
         }
