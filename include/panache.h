@@ -346,6 +346,19 @@ int panache_inject_fault(int32_t kind, int32_t after);
 #define PANACHE_KERNEL_TIMES 7
 int panache_kernel_times(const panache_ctx *ctx, double *ms, uint64_t *launches, int32_t cap);
 
+/* The budgeted candidate list (Sec. 3.4) each listed query window q[i] of
+ * anchor `anchor_index` of series `series_index` in the last request is
+ * searched with, built on the device by the search kernel's own code: the
+ * exact d-bit prefix bucket of its key, then its Hamming-1 buckets in
+ * increasing projection margin, each bucket's valid entries (start <=
+ * q - excl, ascending) taken in full while the budget R allows, else the
+ * evenly spaced half then the most recent half.  cand[i * cap ...] receives
+ * up to cap window starts, counts[i] the list's length (-1 for a window the
+ * search skips: constant, or q < excl).  Host arrays.  Used by the parity
+ * tests.  Errors: EINVAL, ESTATE with no request yet. */
+int panache_query_candidates(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, const int64_t *q,
+                             int32_t nq, uint32_t *cand, int32_t cap, int32_t *counts);
+
 /* Directory population and global depth that every window of anchor
  * `anchor_index` of series `series_index` in the last request is searched
  * with (Sec. 3.5 and Prop. 4): samples arrive in batches of beta, every

@@ -1709,6 +1709,36 @@ int panache_kernel_times(const panache_ctx *ctx, double *ms, uint64_t *launches,
     return PANACHE_OK;
 }
 
+int panache_query_candidates(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, const int64_t *q,
+                             int32_t nq, uint32_t *cand, int32_t cap, int32_t *counts) {
+    if (!ctx || nq < 0 || cap < 1 || (nq > 0 && (!q || !cand || !counts))) return PANACHE_EINVAL;
+    if (!ctx->last) return PANACHE_ESTATE;
+    PnRequest &R = *ctx->last;
+    if (series_index < 0 || series_index >= (int32_t)R.ser.size()) return PANACHE_EINVAL;
+    const PnSeries &S = R.ser[series_index];
+    if (anchor_index < 0 || anchor_index >= S.anchor_count) return PANACHE_EINVAL;
+    if (nq == 0) return PANACHE_OK;
+    const int32_t ai = S.anchor_begin + anchor_index;
+    cudaStream_t st = ctx->st;
+    int64_t *dq = nullptr;
+    uint32_t *dc = nullptr;
+    int32_t *dn = nullptr;
+    PN_CU(cudaMallocAsync((void **)&dq, sizeof(int64_t) * nq, st));
+    PN_CU(cudaMallocAsync((void **)&dc, sizeof(uint32_t) * (size_t)nq * cap, st));
+    PN_CU(cudaMallocAsync((void **)&dn, sizeof(int32_t) * nq, st));
+    int rc = from_cuda(cudaMemcpyAsync(dq, q, sizeof(int64_t) * nq, cudaMemcpyHostToDevice, st));
+    const PnView v = make_view(const_cast<panache_ctx *>(ctx), R);
+    if (rc == PANACHE_OK) rc = from_cuda(pn::launch_query_candidates(v, ai, dq, nq, dc, cap, dn, st));
+    if (rc == PANACHE_OK)
+        rc = from_cuda(cudaMemcpyAsync(cand, dc, sizeof(uint32_t) * (size_t)nq * cap, cudaMemcpyDeviceToHost, st));
+    if (rc == PANACHE_OK) rc = from_cuda(cudaMemcpyAsync(counts, dn, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st));
+    cudaFreeAsync(dq, st);
+    cudaFreeAsync(dc, st);
+    cudaFreeAsync(dn, st);
+    if (rc == PANACHE_OK) rc = from_cuda(cudaStreamSynchronize(st));
+    return rc;
+}
+
 int panache_query_levels(const panache_ctx *ctx, int32_t series_index, int32_t anchor_index, int32_t *population,
                          int32_t *depth, int64_t cap_windows) {
     if (!ctx || !population || !depth) return PANACHE_EINVAL;

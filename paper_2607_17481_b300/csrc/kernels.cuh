@@ -213,4 +213,8 @@ cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_block
 // no valid earlier window).
 cudaError_t launch_query_levels(const PnView &v, int32_t anchor, int64_t nw, int32_t *population, int32_t *depth,
                                 cudaStream_t st);
+// The candidate list each listed query of anchor `anchor` is searched with,
+// by the search's own rule (counts[i] = -1 for windows the search skips).
+cudaError_t launch_query_candidates(const PnView &v, int32_t anchor, const int64_t *qs, int32_t nq, uint32_t *cand,
+                                    int32_t cap, int32_t *counts, cudaStream_t st);
 }  // namespace pn

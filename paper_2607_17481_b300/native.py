@@ -34,7 +34,7 @@ EXPORTED = ("panache_default_config", "panache_create", "panache_destroy", "pana
             "panache_pmp_batch", "panache_pmp_anchor_shard", "panache_pmp_from_rows", "panache_stream_open", "panache_append", "panache_stream_topk",
             "panache_stream_length", "panache_stream_close", "panache_stream_checkpoint", "panache_last_stats",
             "panache_profile_rows",
-            "panache_anchor_state", "panache_query_levels", "panache_projections", "panache_calibrate_width",
+            "panache_anchor_state", "panache_query_levels", "panache_query_candidates", "panache_projections", "panache_calibrate_width",
             "panache_strerror",
             "panache_topk_row_noalloc", "panache_alu_peak", "panache_kernel_times", "panache_inject_fault",
             "panache_server_create", "panache_server_destroy", "panache_server_submit", "panache_server_wait",
@@ -122,6 +122,7 @@ def lib():
         L.panache_profile_rows.argtypes = [vp, i32, vp, i64]
         L.panache_anchor_state.argtypes = [vp, i32, i32, ctypes.POINTER(i32), vp, vp, i64]
         L.panache_query_levels.argtypes = [vp, i32, i32, vp, vp, i64]
+        L.panache_query_candidates.argtypes = [vp, i32, i32, vp, i32, vp, i32, vp]
         L.panache_kernel_times.argtypes = [vp, vp, vp, i32]
         L.panache_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.panache_inject_fault.argtypes = [i32, i32]
@@ -311,6 +312,16 @@ class Context:
         _check(lib().panache_query_levels(self._h, series_index, anchor_index, pop.ctypes.data_as(ctypes.c_void_p),
                                           dep.ctypes.data_as(ctypes.c_void_p), nw), "query_levels")
         return pop[:nw], dep[:nw]
+
+    def query_candidates(self, series_index: int, anchor_index: int, qs, cap: int = 512):
+        """Candidate lists of the listed queries of one anchor of the last request: list of arrays (None if skipped)."""
+        qs = np.ascontiguousarray(qs, dtype=np.int64)
+        cand = np.zeros((max(1, len(qs)), cap), dtype=np.uint32)
+        cnt = np.zeros(max(1, len(qs)), dtype=np.int32)
+        _check(lib().panache_query_candidates(self._h, series_index, anchor_index, qs.ctypes.data_as(ctypes.c_void_p),
+                                              len(qs), cand.ctypes.data_as(ctypes.c_void_p), cap,
+                                              cnt.ctypes.data_as(ctypes.c_void_p)), "query_candidates")
+        return [None if cnt[i] < 0 else cand[i, :min(cap, cnt[i])].copy() for i in range(len(qs))]
 
     def projections(self, a: int) -> np.ndarray:
         return projections(a, self.config)

@@ -105,6 +105,58 @@ def test_query_levels_match_stream_population(pn, small, beta):
         assert np.array_equal(dep[searched], want_d), a
 
 
+@pytest.mark.parametrize("alpha", [16, 4])
+def test_candidate_lists_match_oracle(pn, small, alpha):
+    """Every sampled query's candidate list -- probe order, valid prefixes,
+    budget split (Sec. 3.4) -- read back through panache_query_candidates,
+    equals the list the oracle's probe_buckets and budget_select build over
+    the directory level the query sees (the first alpha 2^d non-constant
+    windows in stream order, bucketed by the d-bit prefix of their keys, in
+    ascending start).  The keys and rows are the device's (their own parity
+    is tested above); queries whose margin ranking is within rounding of a
+    tie are skipped.  alpha = 4 (R = 32) makes most lists overflow a bucket."""
+    s = small
+    ctx = pn.Context(precision=1, topk_mode=0, stride=2, alpha=alpha)
+    ctx.pmp(s.x, s.m_min, s.m_max, s.k, s.excl)
+    cfg = ctx.config
+    R = cfg.gamma * cfg.alpha
+    n = s.x.shape[0]
+    rng = np.random.default_rng(11)
+    checked = 0
+    for ai in (0, 8, 16):
+        a = spectral.anchors(s.m_min, s.m_max)[ai]
+        nw = n - a + 1
+        _, F, sig = ctx.anchor_state(0, ai, nw)
+        g = ctx.projections(a).astype(np.float64)
+        W = np.lib.stride_tricks.sliding_window_view(s.x, a)
+        nonconst = W.max(axis=1) != W.min(axis=1)
+        pre = np.concatenate([[0], np.cumsum(nonconst)])
+        order = np.nonzero(nonconst)[0]                     # stream order of the non-constant windows
+        qs = rng.choice(np.arange(s.excl, nw), size=150, replace=False)
+        got = ctx.query_candidates(0, ai, qs, cap=512)
+        for q, lst in zip(qs, got):
+            assert lst is not None
+            P = spectral.stream_population(int(q), a, n, s.excl, pre)
+            d = spectral.depth(P, cfg.alpha, cfg.B)
+            marg = F[q, :30].astype(np.float64) @ g[:cfg.B, :30].T
+            mag = np.sort(np.abs(marg[:d]))
+            if d > 1 and np.any(np.diff(mag) <= 1e-4 * (mag[1:] + 1e-12)):
+                continue                                    # a near-tie of margins: either order is right
+            members = order[:min(len(order), cfg.alpha << d)]
+            pref = (sig[members].astype(np.int64) >> (cfg.B - d)) if d > 0 else np.zeros(len(members), np.int64)
+            want, taken = [], 0
+            for b in spectral.probe_buckets(int(sig[q]), marg, d, cfg.B, cfg.d0, cfg.probe_cap):
+                if taken >= R:
+                    break
+                valid = np.sort(members[(pref == b) & (members <= q - s.excl)])
+                pos = spectral.budget_select(len(valid), R - taken)
+                want.extend(int(valid[p]) for p in pos)
+                taken += len(pos)
+            assert list(lst) == want, (ai, int(q), d)
+            checked += 1
+    assert checked >= 300
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_profile_rows_are_sound(pn, small, small_exact, precision):
     """Every finite cell is the exact distance of a valid neighbour and never below the exact profile (Prop. 1)."""
