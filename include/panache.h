@@ -437,7 +437,7 @@ typedef struct {
 } panache_server_stats;
 
 /* hbm_budget_bytes 0: 60% of the free device memory.  1 <= slots <= 64.
- * The server also runs max(2, slots) stream worker threads. */
+ * The server also runs max(4, 2 slots) stream worker threads. */
 int panache_server_create(const panache_config *cfg, int32_t slots, uint64_t hbm_budget_bytes,
                           panache_server **out);
 /* Drains the queue, stops the workers and frees everything. */

@@ -395,7 +395,7 @@ int panache_server_create(const panache_config *cfg, int32_t slots, uint64_t hbm
         sv->ctxs.push_back(c);
     }
     for (int s = 0; s < slots; ++s) sv->workers.emplace_back(&panache_server::worker, sv.get(), s);
-    sv->n_stream_workers = std::max(2, slots);
+    sv->n_stream_workers = std::max(4, 2 * slots);
     for (int s = 0; s < sv->n_stream_workers; ++s)
         sv->stream_workers.emplace_back(&panache_server::stream_worker, sv.get());
     *out = sv.release();
