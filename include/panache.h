@@ -120,6 +120,22 @@ extern "C" {
                                               whose cells mostly hold large distances (the wafer-like series)
                                               the bound passes the same pairs and the extra pass costs more
                                               than it saves, so it is off by default. */
+#define PANACHE_FLAG_GRAM_SEARCH 0x800     /* mixed form: run the streaming search with a tensor-core Gram filter
+                                              instead of the per-query Parseval test of Lemma 2.  Both evaluate
+                                              exactly every listed pair that can still lower a cell, with the
+                                              same FP32 arithmetic, so the profile rows and motifs are the same
+                                              bit for bit.  The Gram search merges the lists of up to 16 queries
+                                              that probe the same bucket first, estimates every listed pair's
+                                              squared distance |z_q|^2 + |z_c|^2 - 2 <z_q, z_c> from FP16
+                                              windows on the tensor cores (tcgen05, kind::f16) with an error
+                                              margin 2^-9 (|z_q|^2 + |z_c|^2), and evaluates a pair only when
+                                              that estimate can still lower a cell and is within twice the
+                                              margin of its row's or column's best.  On the 200,000-sample
+                                              wafer-like prefix it evaluates 8% fewer pairs but runs 3.6
+                                              times slower (its block-wide merge, staging and MMA steps leave
+                                              the SMs waiting on memory), so it is not the default.  Anchors
+                                              longer than 192 samples, budgets above 128, the warm start and
+                                              the plain form use the per-query search in any case. */
 #define PANACHE_FLAG_NO_REFINE 0x200      /* skip the exact row refinement of the top list.  After local
                                               completion, every cell of the top refine_mult*k list (per group)
                                               is scanned against all its valid partners at its length with the

@@ -958,13 +958,41 @@ int stage_inputs(panache_ctx *ctx, const std::vector<SeriesIn> &in) {
     return PANACHE_OK;
 }
 
+// The tensor-core Gram search when asked for and supported (mixed form,
+// anchors of at most 192 samples, R <= 128, no warm start).
+bool use_gram_search(const panache_ctx *ctx, const PnView &v, int a_max) {
+    const uint32_t f = ctx->cfg.flags;
+    return (f & PANACHE_FLAG_GRAM_SEARCH) && !(f & PANACHE_FLAG_WARM_START) && pn::search_gram_supported(v, a_max);
+}
+
+// The streaming search over the query order (Algorithm 1 phase B): the Gram
+// search when `qkeys` (the sorted bucket keys, freed here) is given, else the
+// per-query Parseval search.
+int run_search(panache_ctx *ctx, const PnView &v, int64_t total, int a_max, cudaStream_t st, uint32_t *qkeys) {
+    const panache_config &c = ctx->cfg;
+    pn_kt_begin(v.kt, PN_KT_SEARCH, st);
+    cudaError_t e;
+    if (qkeys) {
+        e = pn::launch_search_gram(v, qkeys, total, ctx->sm_count, a_max, st);
+        const cudaError_t ef = cudaFreeAsync(qkeys, st);
+        if (e == cudaSuccess) e = ef;
+        ctx->launches += 7;
+    } else {
+        e = pn::launch_search(v, total, ctx->sm_count * (int)c.grid_mult, a_max, st,
+                              (c.flags & PANACHE_FLAG_WARM_START) != 0);
+        ctx->launches += 1 + ((c.flags & PANACHE_FLAG_WARM_START) ? 1 : 0);
+    }
+    pn_kt_end(v.kt, PN_KT_SEARCH, st);
+    PN_CU(e);
+    return PANACHE_OK;
+}
+
 // Algorithm 1 over every anchor of every series (conversion of the staged
 // samples, moments, anchors, features and keys, ranks, directory, query
 // order) and the streaming search: the part of a request whose launches
 // depend only on its shape.
 int index_and_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const PnConv *dcv, int32_t ncv,
                      StepTimer &tm, bool search) {
-    const panache_config &c = ctx->cfg;
     cudaStream_t st = R.st;
     if (R.total_samples > 0) {
         k_convert<<<(unsigned)((R.total_samples + 255) / 256), 256, 0, st>>>(dcv, ncv, R.total_samples, R.x, R.xs,
@@ -994,17 +1022,17 @@ int index_and_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const PnCo
     PN_TRY(tm.mark(3));
     PN_CU(pn::launch_ranks(v, R.total_windows, st));
     PN_CU(pn::launch_directory(v, R.total_items, R.total_buckets, st));
-    PN_CU(pn::launch_query_order(v, R.total_windows, R.total_buckets, st));
-    PN_TRY(tm.mark(4));
+    const bool gram = search && use_gram_search(ctx, v, R.a_max);
+    uint32_t *qkeys = nullptr;
+    PN_CU(pn::launch_query_order(v, R.total_windows, R.total_buckets, st, nullptr, 0, gram ? &qkeys : nullptr));
+    const int mrc = tm.mark(4);
+    if (mrc != PANACHE_OK) {
+        if (qkeys) cudaFreeAsync(qkeys, st);
+        return mrc;
+    }
     ctx->launches += 3 + 5 + 1 + 5 + 2 + 4 * 3;
     if (!search) return PANACHE_OK;
-    if (c.flags & PANACHE_FLAG_WARM_START) ctx->launches += 1;
-    pn_kt_begin(v.kt, PN_KT_SEARCH, st);
-    PN_CU(pn::launch_search(v, R.total_windows, ctx->sm_count * (int)c.grid_mult, R.a_max, st,
-                            (c.flags & PANACHE_FLAG_WARM_START) != 0));
-    pn_kt_end(v.kt, PN_KT_SEARCH, st);
-    ctx->launches += 1;
-    return PANACHE_OK;
+    return run_search(ctx, v, R.total_windows, R.a_max, st, qkeys);
 }
 
 // The whole path for a list of series; results per series.
@@ -1208,12 +1236,13 @@ int stream_search(panache_ctx *ctx, PnRequest &R, const PnView &v, const std::ve
     if (!total) return PANACHE_OK;
     PnQRange *drng = nullptr;
     PN_TRY(upload_tmp(R.st, rng, drng));
-    PN_CU(pn::launch_query_order(v, total, R.total_buckets, R.st, drng, (int32_t)rng.size()));
-    PN_CU(pn::launch_search(v, total, ctx->sm_count * (int)ctx->cfg.grid_mult, R.a_max, R.st,
-                            (ctx->cfg.flags & PANACHE_FLAG_WARM_START) != 0));
+    uint32_t *qkeys = nullptr;
+    const bool gram = use_gram_search(ctx, v, R.a_max);
+    PN_CU(pn::launch_query_order(v, total, R.total_buckets, R.st, drng, (int32_t)rng.size(), gram ? &qkeys : nullptr));
+    ctx->launches += 1 + 4 * 3;
+    const int rc = run_search(ctx, v, total, R.a_max, R.st, qkeys);
     PN_CU(cudaFreeAsync(drng, R.st));
-    ctx->launches += 2 + 4 * 3 + ((ctx->cfg.flags & PANACHE_FLAG_WARM_START) ? 1 : 0);
-    return PANACHE_OK;
+    return rc;
 }
 
 // Brings the resident index up to the samples present: moments, features of

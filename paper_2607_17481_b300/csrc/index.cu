@@ -425,7 +425,8 @@ cudaError_t launch_directory(const PnView &v, int64_t total_items, int64_t total
 }
 
 cudaError_t launch_query_order(const PnView &v, int64_t total, int64_t total_buckets, cudaStream_t st,
-                               const PnQRange *rng, int32_t nrng) {
+                               const PnQRange *rng, int32_t nrng, uint32_t **keys_out) {
+    if (keys_out) *keys_out = nullptr;
     if (total <= 0) return cudaSuccess;
     uint32_t *keys = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&keys, sizeof(uint32_t) * total, st);
@@ -435,7 +436,8 @@ cudaError_t launch_query_order(const PnView &v, int64_t total, int64_t total_buc
     int bits = 1;
     while (bits < 32 && ((int64_t)1 << bits) <= total_buckets) ++bits;
     if (e == cudaSuccess) e = radix_sort_pairs(keys, v.qorder, total, bits, st);
-    cudaFreeAsync(keys, st);
+    if (e == cudaSuccess && keys_out) *keys_out = keys;
+    else cudaFreeAsync(keys, st);
     return e;
 }
 

@@ -197,8 +197,11 @@ size_t anchor_tc_smem();
 cudaError_t launch_twiddles(const PnAnchor *anc_dev, int32_t nanc, int32_t ld, float *tw, cudaStream_t st);
 cudaError_t launch_anchor_tc(const PnView &v, const int32_t *tile_anchor, const int32_t *tile_row0, int32_t ntiles,
                              cudaStream_t st);
+// The search order (v.qorder) by first-probed bucket.  With keys_out, the
+// sorted bucket keys are handed to the caller (a stream-ordered allocation
+// it frees) instead of being freed: the Gram search groups queries by them.
 cudaError_t launch_query_order(const PnView &v, int64_t total_queries, int64_t total_buckets, cudaStream_t st,
-                               const PnQRange *rng = nullptr, int32_t nrng = 0);
+                               const PnQRange *rng = nullptr, int32_t nrng = 0, uint32_t **keys_out = nullptr);
 int search_max_budget();
 // Spectral-width calibration statistics: out[0..14] energy means and
 // out[15..29] collision-probability means for K = 2..16, out[30] pairs.
@@ -208,6 +211,14 @@ cudaError_t launch_calibration(const double *x, const PnCalWin *win, int nwin, c
 // (one exact distance per query, within its admitted candidates) runs first.
 cudaError_t launch_search(const PnView &v, int64_t total_queries, int grid_blocks, int a_max, cudaStream_t st,
                           bool warm);
+// Whether the opt-in tensor-core Gram search can serve this request (mixed
+// form, anchors of at most 192 samples, budget R <= 128).
+bool search_gram_supported(const PnView &v, int a_max);
+// The same search (same admitted pairs, same profile rows) with the
+// tensor-core Gram filter in place of the per-query Parseval test; `keys`
+// are the sorted bucket keys of the query order.
+cudaError_t launch_search_gram(const PnView &v, const uint32_t *keys, int64_t total_queries, int sm_count,
+                               int a_max, cudaStream_t st);
 // Population and depth every window of anchor `anchor` would probe with, by
 // the search's own rule; -1 for windows that are not searched (constant, or
 // no valid earlier window).
