@@ -59,6 +59,22 @@ constexpr int SR_TILE = PN_SR_TILE;   // queries a warp takes from the work queu
 #define PN_SR_MINB 5
 #endif
 
+// Byte offsets of the search kernel's per-block dynamic shared memory: each
+// array holds SR_WARPS per-warp slices, every array 16-byte aligned.
+template <class Z>
+struct SrLayout {
+    size_t snap, zq, cand, mom, sum, bytes;
+    __host__ __device__ SrLayout(int R, int zcap) {
+        auto up = [](size_t b) { return (b + 15) & ~(size_t)15; };
+        snap = 0;
+        zq = up(snap + sizeof(unsigned long long) * (size_t)R * SR_WARPS);
+        cand = up(zq + sizeof(typename Z::Q) * (size_t)zcap * SR_WARPS);
+        mom = up(cand + sizeof(uint32_t) * (size_t)R * SR_WARPS);
+        sum = up(mom + sizeof(typename Z::M) * (size_t)R * SR_WARPS);
+        bytes = up(sum + sizeof(typename Z::T) * (size_t)R * SR_WARPS);
+    }
+};
+
 template <class Z, bool HALF, bool WARM>
 __global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int64_t total, int zcap,
                                                         unsigned long long *work) {
@@ -69,11 +85,17 @@ __global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int
     extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int R = v.R;
-    unsigned long long *snap = reinterpret_cast<unsigned long long *>(dsm) + warp * R;
     using ZQ = typename Z::Q;
-    ZQ *zq = reinterpret_cast<ZQ *>(reinterpret_cast<unsigned long long *>(dsm) + SR_WARPS * R) + warp * zcap;
-    uint32_t *scand = reinterpret_cast<uint32_t *>(reinterpret_cast<ZQ *>(reinterpret_cast<unsigned long long *>(dsm) +
-                                                                        SR_WARPS * R) + SR_WARPS * zcap) + warp * R;
+    using ZM = typename Z::M;
+    // per warp: survivor snapshots, staged query window, candidate list
+    // (survivors compacted at its front), survivor moments and sums
+    const SrLayout<Z> lay(R, zcap);
+    unsigned long long *snap = reinterpret_cast<unsigned long long *>(dsm + lay.snap) + warp * R;
+    ZQ *zq = reinterpret_cast<ZQ *>(dsm + lay.zq) + warp * zcap;
+    uint32_t *scand = reinterpret_cast<uint32_t *>(dsm + lay.cand) + warp * R;
+    ZM *smom = reinterpret_cast<ZM *>(dsm + lay.mom) + warp * R;
+    ZT *ssum = reinterpret_cast<ZT *>(dsm + lay.sum) + warp * R;
+    const auto *xb = Z::samples(v, 0);
     if (threadIdx.x < 3) s_stat[threadIdx.x] = 0ull;
     __syncthreads();
     unsigned long long n_q = 0, n_c = 0, n_lb = 0;
@@ -131,6 +153,7 @@ __global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int
         }
         __syncwarp();
         unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
+        const auto *xs = xb + S.x_off;
         const float4 fq = reinterpret_cast<const float4 *>(sF[warp])[lane & 7];
         const float2 nfxy = make_float2(-fq.x, -fq.y), nfzw = make_float2(-fq.z, -fq.w);
         unsigned long long bestkey = PN_EMPTY_KEY;
@@ -232,18 +255,24 @@ __global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int
                 const int rank = __popc(sm & ((1u << lane) - 1u));
                 scand[nsurv + rank] = c;
                 snap[nsurv + rank] = kc;
+                smom[nsurv + rank] = Z::load(v, A.win_off + c);
             }
             nsurv += __popc(sm);
             __syncwarp();
+            // full batches of four now; a remainder waits for the next block
+            const int h0 = head;
             while (nsurv - head >= 4) {
-                eval_batch<Z>(v, zq, scand + head, snap + head, 4, S.x_off, A.win_off, a, (uint32_t)q, prow,
-                              bestkey, lane);
+                eval_sums<Z>(zq, xs, scand + head, smom + head, 4, a, ssum + head, lane);
                 head += 4;
             }
+            __syncwarp();
+            if (head > h0) eval_finish<Z>(ssum, scand, snap, smom, h0, head, (uint32_t)q, prow, bestkey, lane);
         }
-        if (nsurv > head)
-            eval_batch<Z>(v, zq, scand + head, snap + head, nsurv - head, S.x_off, A.win_off, a, (uint32_t)q, prow,
-                          bestkey, lane);
+        if (nsurv > head) {
+            eval_sums<Z>(zq, xs, scand + head, smom + head, nsurv - head, a, ssum + head, lane);
+            __syncwarp();
+            eval_finish<Z>(ssum, scand, snap, smom, head, nsurv, (uint32_t)q, prow, bestkey, lane);
+        }
         n_lb += nsurv;
         if (lane == 0 && bestkey != PN_EMPTY_KEY) atomicMin(&prow[q], bestkey);
         __syncwarp();
@@ -265,8 +294,7 @@ template <class Z, bool HALF, bool WARM>
 cudaError_t launch_one(const PnView &v, int64_t total, int grid_blocks, int a_max, cudaStream_t st,
                        unsigned long long *work) {
     const int zcap = (a_max + 3) & ~3;
-    const size_t sm = (sizeof(unsigned long long) + sizeof(uint32_t)) * (size_t)v.R * SR_WARPS +
-                      sizeof(typename Z::Q) * (size_t)zcap * SR_WARPS;
+    const size_t sm = SrLayout<Z>(v.R, zcap).bytes;
     cudaError_t e = pn_allow_smem(k_search<Z, HALF, WARM>, sm);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
