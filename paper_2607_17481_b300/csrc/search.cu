@@ -12,6 +12,8 @@
 // evaluated exactly iff (1 - lambda) LB < max(best_q, P[c]) (Lemma 2, the
 // threshold of Algorithm 1), where best_q also takes the live value of the
 // query's own cell; both cells receive the distance by packed atomicMin.
+// The test is taken on squares, (1 - lambda)^2 LB^2 < threshold^2, with no
+// root: FP32 rounding of either form is far inside the lambda slack.
 //
 // The final profile does not depend on the schedule: a pair is skipped only
 // when its distance exceeds, by the factor 1/(1 - lambda), the current value
@@ -101,6 +103,7 @@ __global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int
     unsigned long long n_q = 0, n_c = 0, n_lb = 0;
     const int dims = 2 * (v.K - 1);
     const float shrink = 1.0f - v.lam;
+    const float shrink2 = shrink * shrink;
     // anchor of the previous query and its window range [a_lo, a_hi): the
     // query order keeps each anchor's queries together, so the search over
     // the anchor table is mostly skipped
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int
             float lbs = __int_as_float(0x7f800000);
             if (lane < nblk) {
                 kc = __ldcg(&prow[c]);
-                lbs = shrink * sqrtf(lbscale * lbsq);
+                lbs = shrink2 * (lbscale * lbsq);            // ((1 - lambda) LB)^2
             }
             const ZT cq = Z::cell(__ldcg(&prow[q]));
             // best-first start: while the query has no distance yet, the block's
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int
                 const unsigned long long kb = __shfl_sync(0xffffffffu, kc, bl);
                 ZT tb = Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kb));
                 if constexpr (HALF) tb += lbmargin;
-                if (bl < nblk && (ZT)bm < tb) {
+                if (bl < nblk && (ZT)bm < tb * tb) {
                     eval_one<Z>(v, zq, cb, kb, S.x_off, A.win_off, a, (uint32_t)q, prow, bestkey, lane);
                     n_lb += 1;
                 }
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(SR_THREADS, PN_SR_MINB) k_search(PnView v, int
             if (lane < nblk) {
                 ZT tc = Z::fmx(Z::fmn(Z::cell(bestkey), cq), Z::cell(kc));
                 if constexpr (HALF) tc += lbmargin;
-                surv = (ZT)lbs < tc;
+                surv = (ZT)lbs < tc * tc;
             }
             const uint32_t sm = __ballot_sync(0xffffffffu, surv);
             __syncwarp();
