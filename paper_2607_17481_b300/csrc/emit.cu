@@ -1026,17 +1026,32 @@ namespace {
 // Ends a round: an empty round closes the gate, a round that ran is
 // counted and closes the gate when nothing improved; the flag and the
 // count start again at 0 for the next round.
-__global__ void k_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds) {
+__global__ void k_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, int *sticky) {
     if (*gate) {
         if (*count == 0) {
             *gate = 0;
         } else {
             ++*rounds;
             if (!*flag) *gate = 0;
+            else if (sticky) *sticky = 1;
         }
         *flag = 0;
         *count = 0;
     }
+}
+
+// A cycle of the emit stage (completion rounds, then refinement passes)
+// opens both phases' gates when the cycle gate is open; at its end the cycle
+// gate stays open only if a round or pass of the cycle lowered a cell.
+__global__ void k_cycle_begin(const int *cycle_gate, int *completion_gate, int *refine_gate, int32_t *cycles) {
+    completion_gate[0] = *cycle_gate;
+    refine_gate[0] = *cycle_gate;
+    if (*cycle_gate) ++*cycles;
+}
+
+__global__ void k_cycle_end(int *cycle_gate, int *cycle_flag) {
+    if (!*cycle_flag) *cycle_gate = 0;
+    *cycle_flag = 0;
 }
 
 // Completion seeds from a selection's picks (group g's at picks[g kmax ...]).
@@ -1096,8 +1111,17 @@ __global__ void k_new_targets(const PnPick *picks, const int32_t *cnt, int32_t n
 
 }  // namespace
 
-cudaError_t launch_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, cudaStream_t st) {
-    k_round_end<<<1, 1, 0, st>>>(gate, flag, count, rounds);
+cudaError_t launch_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, cudaStream_t st, int *sticky) {
+    k_round_end<<<1, 1, 0, st>>>(gate, flag, count, rounds, sticky);
+    return cudaGetLastError();
+}
+cudaError_t launch_cycle_begin(const int *cycle_gate, int *completion_gate, int *refine_gate, int32_t *cycles,
+                               cudaStream_t st) {
+    k_cycle_begin<<<1, 1, 0, st>>>(cycle_gate, completion_gate, refine_gate, cycles);
+    return cudaGetLastError();
+}
+cudaError_t launch_cycle_end(int *cycle_gate, int *cycle_flag, cudaStream_t st) {
+    k_cycle_end<<<1, 1, 0, st>>>(cycle_gate, cycle_flag);
     return cudaGetLastError();
 }
 cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *seeds,

@@ -47,7 +47,12 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
 cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, const int32_t *nseeds_dev, int dm,
                             int dp, int *improved, int grid_blocks, cudaStream_t st);
 // Device-driven rounds (see emit.cu).
-cudaError_t launch_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, cudaStream_t st);
+// A round or pass that lowered a cell also sets *sticky (when given).
+cudaError_t launch_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, cudaStream_t st,
+                             int *sticky = nullptr);
+cudaError_t launch_cycle_begin(const int *cycle_gate, int *completion_gate, int *refine_gate, int32_t *cycles,
+                               cudaStream_t st);
+cudaError_t launch_cycle_end(int *cycle_gate, int *cycle_flag, cudaStream_t st);
 cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *seeds,
                                   int32_t *nseeds, const int *gate, cudaStream_t st);
 cudaError_t launch_new_targets(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *done,
