@@ -76,14 +76,15 @@ extern "C" {
 
 /* ---- flags ---- */
 #define PANACHE_FLAG_EXHAUSTIVE_SIEVE 0x1  /* every valid pair of a hot class, not only w sort-neighbours */
-#define PANACHE_FLAG_SIEVE_GRAM 0x400      /* with the exhaustive sieve, mixed form, FP32 rows: bound each 128 x
-                                              128 block of a class's pairs through a tensor-core Gram block of
-                                              the feature rows (3xTF32 tcgen05, LB^2 = (2/a)(|F_u|^2 + |F_v|^2
-                                              - 2 <F_u, F_v>) with an additive margin for its rounding) and
-                                              evaluate exactly only the pairs the Parseval bound keeps.  Same
-                                              rows as evaluating every pair; on the wafer-like series about 19%
-                                              of the pairs survive the bound and the survivors' scattered
-                                              evaluation is slower than the dense tiles, so it is not the
+#define PANACHE_FLAG_SIEVE_GRAM 0x400      /* with the exhaustive sieve, mixed form, anchors of at most 192
+                                              samples: estimate every pair of each 128 x 128 block of a class
+                                              on the tensor cores (FP16 Gram block of the z-windows shifted by
+                                              a reference window, tcgen05 kind::f16, with an error margin) and
+                                              evaluate exactly only the pairs that can still lower a cell.
+                                              Same rows as evaluating every pair, up to FP32 rounding; on the
+                                              wafer-like prefix 1.9% of the pairs are evaluated, but the kernel
+                                              is latency-bound (two 4-warp blocks per SM) and takes 143 ms
+                                              against 58 ms for the dense CUDA-core tiles, so it is not the
                                               default */
 #define PANACHE_FLAG_NO_SIEVE 0x2          /* skip the hot-class sieve (S_hot) */
 #define PANACHE_FLAG_NO_COMPLETION 0x4     /* skip local completion (S_local) */

@@ -364,11 +364,21 @@ __global__ void __launch_bounds__(SB_U) k_sieve_band(PnView v, const PnClass *cl
 constexpr int ST_B = 64;          // members per tile side
 constexpr int ST_K = 32;          // samples staged per step
 
-__global__ void k_tile_count(const PnClass *cls, int32_t ncls, uint32_t *cnt) {
+// Tiles per class; a class above 2^31 tiles, or a total above 2^31, sets
+// *overflow and the launcher refuses the request (no truncated table).
+__global__ void k_tile_count(const PnClass *cls, int32_t ncls, uint32_t *cnt, unsigned long long *total,
+                             int *overflow) {
     const int ci = blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= ncls) return;
-    const uint32_t nb = (cls[ci].size + ST_B - 1) / ST_B;
-    cnt[ci] = nb * (nb + 1) / 2;
+    const uint64_t nb = (cls[ci].size + ST_B - 1) / ST_B;
+    const uint64_t t = nb * (nb + 1) / 2;
+    if (t > 0x7FFFFFFFull) {
+        atomicExch(overflow, 1);
+        cnt[ci] = 0;
+        return;
+    }
+    cnt[ci] = (uint32_t)t;
+    atomicAdd(total, (unsigned long long)t);
 }
 
 // One warp per class writes its tiles (class, bu, bv) at the class's offset.
@@ -377,16 +387,12 @@ __global__ void k_tile_fill(const PnClass *cls, int32_t ncls, const uint32_t *of
     const int lane = threadIdx.x & 31;
     if (ci >= ncls) return;
     const uint32_t nb = (cls[ci].size + ST_B - 1) / ST_B;
-    const uint32_t total = nb * (nb + 1) / 2;
+    const uint32_t total = (uint32_t)(((uint64_t)nb * (nb + 1)) / 2);
     for (uint32_t t = lane; t < total; t += 32) {
-        // row bu holds nb - bu tiles; find bu for the t-th tile
-        uint32_t bu = 0, rem = t;
-        while (rem >= nb - bu) {
-            rem -= nb - bu;
-            ++bu;
-        }
-        const uint32_t bv = bu + rem;
-        uint4 *dst = reinterpret_cast<uint4 *>(tiles) + off[ci] + t;
+        // row bu holds nb - bu tiles; bu of the t-th tile by bisection
+        const uint32_t bu = tri_row(t, nb);
+        const uint32_t bv = bu + (t - (uint32_t)((uint64_t)bu * nb - ((uint64_t)bu * (bu - 1)) / 2));
+        uint4 *dst = reinterpret_cast<uint4 *>(tiles) + (int64_t)off[ci] + t;
         *dst = make_uint4((uint32_t)ci, bu, bv, 0u);
     }
 }
@@ -886,17 +892,22 @@ template <class Z>
 cudaError_t sieve_tiles_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int grid_blocks,
                           cudaStream_t st) {
     uint32_t *cnt = nullptr, *off = nullptr, *tot = nullptr, *tiles = nullptr;
+    unsigned long long *tot64 = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&cnt, 4 * (size_t)ncls, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&off, 4 * (size_t)ncls, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot, 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot64, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tot64, 0, 2 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) {
-        k_tile_count<<<grid_for(ncls, 256), 256, 0, st>>>(cls, ncls, cnt);
+        k_tile_count<<<grid_for(ncls, 256), 256, 0, st>>>(cls, ncls, cnt, tot64, reinterpret_cast<int *>(tot64 + 1));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = excl_scan_u32(cnt, off, ncls, tot, st);
-    uint32_t ntiles = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ntiles, tot, 4, cudaMemcpyDeviceToHost, st);
+    unsigned long long h64[2] = {0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h64, tot64, sizeof(h64), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && (h64[1] != 0ull || h64[0] > 0x7FFFFFFFull)) e = cudaErrorMemoryAllocation;
+    const uint32_t ntiles = e == cudaSuccess ? (uint32_t)h64[0] : 0u;
     if (e == cudaSuccess && ntiles > 0) e = cudaMallocAsync((void **)&tiles, sizeof(uint4) * (size_t)ntiles, st);
     if (e == cudaSuccess && ntiles > 0) {
         k_tile_fill<<<grid_for((int64_t)ncls * 32, 256), 256, 0, st>>>(cls, ncls, off, tiles);
@@ -904,7 +915,7 @@ cudaError_t sieve_tiles_t(const PnView &v, const PnClass *cls, int32_t ncls, con
         k_sieve_tiles<Z><<<(unsigned)g, 256, 0, st>>>(v, cls, reinterpret_cast<const uint4 *>(tiles), ntiles, vals);
         e = cudaGetLastError();
     }
-    for (void *p : {(void *)cnt, (void *)off, (void *)tot, (void *)tiles})
+    for (void *p : {(void *)cnt, (void *)off, (void *)tot, (void *)tot64, (void *)tiles})
         if (p) cudaFreeAsync(p, st);
     return e;
 }
@@ -981,7 +992,8 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             pn_kt_begin(v.kt, PN_KT_SIEVE, st);
             // after the class sort, keys[p] is the class of member p
             if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
-            else if (exhaustive == 1 && !v.Fh) e = launch_sieve_gram(v, cls, ncls, vals, grid_blocks, st);
+            else if (exhaustive == 1 && sieve_gram_supported(a_max))
+                e = launch_sieve_gram(v, cls, ncls, vals, a_max, grid_blocks, st);
             else if (exhaustive && v.x1) e = sieve_tiles_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);
             else if (exhaustive) e = sieve_tiles_t<ZMix2>(v, cls, ncls, vals, grid_blocks, st);
             else if (w <= SB_WMAX && v.x1) e = sieve_band_t<ZMix1>(v, cls, nmem, keys, vals, w, grid_blocks, st);

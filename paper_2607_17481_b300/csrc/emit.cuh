@@ -2,6 +2,18 @@
 #pragma once
 #include "kernels.cuh"
 
+// Row of the t-th tile of an nb x nb upper triangle enumerated row by row
+// (row bu holds nb - bu tiles): the largest bu with bu nb - bu (bu - 1) / 2
+// <= t, by bisection.
+__host__ __device__ __forceinline__ uint32_t tri_row(uint32_t t, uint32_t nb) {
+    uint32_t lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if ((uint64_t)mid * nb - ((uint64_t)mid * (mid - 1)) / 2 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 struct PnClass {          // one hot class: a final-depth bucket larger than R
     int32_t anchor;
     uint32_t lo;          // first sorted directory item of the bucket
@@ -58,10 +70,12 @@ cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32
 cudaError_t launch_new_targets(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *done,
                                int32_t *ndone, int32_t done_cap, PnSeed *targets, int32_t *ntargets, const int *gate,
                                cudaStream_t st);
-// Exhaustive sieve of the mixed form with FP32 feature rows, every valid
-// pair of each hot class bounded through a tensor-core Gram block and only
-// the survivors evaluated exactly (gram.cu).
-cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals,
+// Exhaustive sieve of the mixed form on the tensor cores: every valid pair
+// of each hot class estimated through an FP16 Gram block of the z-windows
+// and only the pairs that can still lower a cell evaluated exactly
+// (gram.cu); anchors of at most 192 samples.
+bool sieve_gram_supported(int a_max);
+cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int a_max,
                               int grid_blocks, cudaStream_t st);
 // Exact row refinement: each target cell (series, m, i) scanned against
 // every valid partner at its length; `improved` set when a cell decreased.

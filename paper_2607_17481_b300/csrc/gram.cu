@@ -1,33 +1,57 @@
-// Exhaustive hot-class sieve with a tensor-core Gram filter (Sec. 3.6's
-// hot-class sieve, every valid pair of each class; the Parseval bound of
-// Lemma 2 decides which pairs are evaluated exactly).
+// Exhaustive hot-class sieve on the tensor cores (Sec. 3.6's hot-class
+// sieve, every valid pair of each class), mixed form.
 //
-// For a tile of 128 x 128 members (u, v) of one class at anchor length a,
-// the bound is LB^2 = (2/a) (|F_u|^2 + |F_v|^2 - 2 <F_u, F_v>) over the 30
-// stored feature floats.  The Gram block <F_u, F_v> is one dense
-// contraction [128 x 32] x [32 x 128]: the rows are staged in shared memory
-// in the K-major no-swizzle canonical layout, split into TF32 hi + lo
-// parts, and one thread issues 4 K-steps x 3 tcgen05.mma kind::tf32
-// (hi*hi + hi*lo + lo*hi) into a 128 x 128 FP32 accumulator in tensor
-// memory.  Each warp then reads its 32 rows back with tcgen05.ld and tests
-// every pair against max(P[u], P[v]) with the (1 - lambda) shrink of
-// Algorithm 1 and an additive error margin; the survivors are evaluated
-// exactly (FP32, the search's arithmetic) and lower both cells.
+// A class's members are windows of one anchor length a.  For a tile of
+// 128 x 128 members (u, v) the squared distances are a dense contraction:
+// with y = z - z_r for one reference window r of the row block (the
+// z-normalised windows shifted by a common vector, which leaves every
+// difference unchanged), d^2(u, v) = |y_u|^2 + |y_v|^2 - 2 <y_u, y_v>.  The
+// shift keeps the cancellation small where it matters: a hot class of
+// near-copies of one pattern has |y|^2 of the order of the distances
+// themselves instead of a.  Both blocks are staged in shared memory as FP16
+// y-values (K-major, 128-byte swizzle, zero past a), one thread issues a/16
+// tcgen05.mma kind::f16 (M = N = 128, K = 16 each) into a 128 x 128 FP32
+// accumulator in tensor memory, and each warp reads its 32 rows back with
+// tcgen05.ld.  The estimate decides which pairs are evaluated exactly (FP32
+// differences, the search's arithmetic); the survivors lower both cells.
 //
-// Error margin.  With x = hi + lo, hi = rna-TF32(x) (|x - hi| <= 2^-11|x|)
-// and lo truncated to TF32 by the MMA (<= 2^-21 |x|), each product is
-// carried to within ~2^-19.7 |x_k y_k|; FP32 accumulation of the 96 partial
-// products adds at most 96 * 2^-24 of their magnitudes.  So
-// |G - <F_u, F_v>| <= 2^-17 |F_u||F_v| <= 2^-17 (n_u + n_v) / 2, and the
-// FP32 norms n = |F|^2 are within 2^-19 n.  The computed LB^2 is therefore
-// within (2/a)(n_u + n_v)(2^-17 + 2^-19) of the exact one; the test uses
-// the margin (2/a)(n_u + n_v) 2^-15, about three times that.  A pair is
-// skipped only when (1 - lambda)^2 (LB^2 - margin) >= max(P[u], P[v])^2, so
-// every pair the exact bound keeps is evaluated.
+// Error of the estimate.  y is the FP32 difference of FP32 z-values (|y| <=
+// 2 sqrt(a) < 28), y~ its FP16 rounding, |y~ - y| <= 2^-11 |y| + 2^-25, so
+// each product is off by at most (2^-10 + 2^-22) |y_u y_v| plus a subnormal
+// term below a 2^-19 in total; FP16 products are exact in FP32 and the
+// accumulation of a <= 192 of them adds at most a 2^-23 of their
+// magnitudes; Cauchy-Schwarz gives sum |y_u y_v| <= (|y_u|^2 + |y_v|^2) / 2;
+// the norms are FP32 sums; y_u - y_v differs from z_u - z_v by the rounding
+// of the two subtractions (<= 2^-23 |z| each), which moves the squared
+// distance by less than a 2^-16; and the exact pass's FP32 sum of squares is
+// within a 2^-24 of <= 2 (|y_u|^2 + |y_v|^2).  Together |d~^2 - d_f^2| <=
+// 2^-9.9 (|y_u|^2 + |y_v|^2) + a 2^-16, with d_f the distance the exact pass
+// would store; the tests use M = 2^-9 (|y_u|^2 + |y_v|^2) + a 2^-14.
 //
-// Waits on the MMA's completion are bounded: on timeout the kernel records
+// Which pairs are evaluated.  Pair (u, v) is evaluated iff
+//   [d~^2 - M < P[u]^2 and d~^2 <= rowmin(u) + 2 M_row]  or
+//   [d~^2 - M < P[v]^2 and d~^2 <= colmin(v) + 2 M_col],
+// P the cells' current values (read when the block is staged: a stale,
+// larger value keeps more pairs), rowmin / colmin the smallest estimate of
+// the row / column in this tile, M_row (M_col) the margin with the row's
+// (column's) own norm and the largest norm of the other block.  A pair
+// failing the first part of a clause has d_f > P, so it cannot lower that
+// cell; a pair failing the second has d_f above the best pair of its row
+// (column) in the tile, which wins that cell against it.  So every pair
+// whose key could end in a cell is evaluated, and the rows equal those of
+// evaluating every pair, up to the FP32 rounding order of the distances.
+//
+// Column minima: each warp reduces a 32 x 32 block of estimates to its 32
+// column minima with a transposing butterfly (31 shuffles), then one shared
+// atomicMin per column and warp.
+//
+// Tiles are handed out by a work counter in runs of consecutive tiles of a
+// class row, so a block restages only the column block when the row block
+// is unchanged.  Waits on the MMA are bounded: on timeout the kernel records
 // the error word, waits once more (bounded), frees its tensor memory and
 // returns; the request reports ETIMEOUT.
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "emit.cuh"
@@ -38,44 +62,131 @@
 namespace pn {
 namespace {
 
-constexpr int GR_B = 128;          // members per tile side (MMA M and N)
-constexpr int GR_K = 32;           // feature floats per row (30 used)
-constexpr int GR_THREADS = 128;    // 4 warps: warp w owns tile rows / TMEM lanes 32w..32w+31
-constexpr int GR_Q = 256;          // survivor queue per warp
-constexpr int GR_SPIN = 1 << 22;   // try_wait iterations before giving up
+constexpr int ZG_B = 128;           // members per tile side (MMA M and N)
+constexpr int ZG_THREADS = 128;     // 4 warps: warp w owns tile rows / TMEM lanes 32w..32w+31
+constexpr int ZG_Q = 256;           // survivor queue per warp
+constexpr int ZG_RUN = 4;           // tiles a block draws at a time
+constexpr int ZG_SPIN = 1 << 22;    // try_wait iterations before giving up
+constexpr int ZG_AMAX = 192;        // longest anchor served (three K atoms)
+constexpr int ZG_TMEM_COLS = 128;
 
-__global__ void k_gram_tile_count(const PnClass *cls, int32_t ncls, uint32_t *cnt) {
+// Tiles per class (upper triangle of 128-member blocks).  A class with more
+// than 2^31 tiles, or a total above 2^31, sets *overflow: the launcher
+// refuses such a request instead of enumerating a truncated table.
+__global__ void k_zg_tile_count(const PnClass *cls, int32_t ncls, uint32_t *cnt, unsigned long long *total,
+                                int *overflow) {
     const int ci = blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= ncls) return;
-    const uint32_t nb = (cls[ci].size + GR_B - 1) / GR_B;
-    cnt[ci] = nb * (nb + 1) / 2;
+    const uint64_t nb = (cls[ci].size + ZG_B - 1) / ZG_B;
+    const uint64_t t = nb * (nb + 1) / 2;
+    if (t > 0x7FFFFFFFull) {
+        atomicExch(overflow, 1);
+        cnt[ci] = 0;
+        return;
+    }
+    cnt[ci] = (uint32_t)t;
+    atomicAdd(total, (unsigned long long)t);
 }
 
-// One warp per class writes its upper-triangular tiles (class, bu, bv).
-__global__ void k_gram_tile_fill(const PnClass *cls, int32_t ncls, const uint32_t *off, uint4 *tiles) {
+// One warp per class writes its tiles (class, bu, bv), bu-major.
+__global__ void k_zg_tile_fill(const PnClass *cls, int32_t ncls, const uint32_t *off, uint4 *tiles) {
     const int ci = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (ci >= ncls) return;
-    const uint32_t nb = (cls[ci].size + GR_B - 1) / GR_B;
-    const uint32_t total = nb * (nb + 1) / 2;
+    const uint32_t nb = (cls[ci].size + ZG_B - 1) / ZG_B;
+    const uint32_t total = (uint32_t)(((uint64_t)nb * (nb + 1)) / 2);
     for (uint32_t t = lane; t < total; t += 32) {
-        uint32_t bu = 0, rem = t;
-        while (rem >= nb - bu) {
-            rem -= nb - bu;
-            ++bu;
+        const uint32_t bu = tri_row(t, nb);
+        const uint32_t before = (uint32_t)((uint64_t)bu * nb - ((uint64_t)bu * (bu - 1)) / 2);
+        tiles[(int64_t)off[ci] + t] = make_uint4((uint32_t)ci, bu, bu + (t - before), 0u);
+    }
+}
+
+struct ZgSide {
+    uint32_t s[ZG_B];        // member window start (0 past the block)
+    float2 m[ZG_B];          // (1/sigma, -mu/sigma); x = 0 for a degenerate window or past the block
+    float n[ZG_B];           // |y|^2, y = z - z_ref
+    float t[ZG_B];           // the cell's distance when staged
+};
+
+struct ZgShared {
+    ZgSide A, B;
+    float zref[ZG_AMAX];                       // z-values of the row block's reference window
+    int colmin[ZG_B];                          // float bits
+    unsigned long long rkey[ZG_B], ckey[ZG_B]; // exact keys of this tile, flushed to the cells once
+    uint32_t queue[ZG_THREADS / 32][ZG_Q];
+    int nmax_a, nmax_b;                        // float bits
+    int fail;
+    uint32_t taddr;
+    __align__(8) uint64_t mbar;
+    unsigned long long run;
+};
+
+// Stages block `first .. first + n` of class members into a swizzled FP16
+// tile, as y = z - z_ref (the row block's reference window), and its side
+// tables (n = |y|^2); each warp takes four rows at a time, so every lane has
+// eight sample loads in flight.
+template <class Z>
+__device__ __forceinline__ void zg_stage(const PnView &v, const PnAnchor &A, const PnSeries &S, const uint32_t *members,
+                                         int64_t first, int n, int a, int kp, unsigned char *tile, ZgSide &side,
+                                         int *nmax, const unsigned long long *prow, const float *zref, int warp,
+                                         int lane) {
+    for (int r0 = warp * 4; r0 < ZG_B; r0 += 4 * (ZG_THREADS / 32)) {
+        uint32_t c = 0;
+        float2 mm = make_float2(0.0f, 0.0f);
+        if (lane < 4 && r0 + lane < n) {
+            c = members[first + r0 + lane];
+            const auto m = Z::load(v, A.win_off + c);
+            mm = make_float2(m.x, m.y);
         }
-        tiles[off[ci] + t] = make_uint4((uint32_t)ci, bu, bu + rem, 0u);
+        uint32_t cr[4];
+        typename Z::M mr[4];
+        const typename Z::X *xr[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            cr[r] = __shfl_sync(0xffffffffu, c, r);
+            mr[r].x = __shfl_sync(0xffffffffu, mm.x, r);
+            mr[r].y = __shfl_sync(0xffffffffu, mm.y, r);
+            xr[r] = Z::samples(v, S.x_off + cr[r]);
+        }
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int k = 2 * lane; k < kp; k += 64) {
+            float z0[4], z1[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool ok = r0 + r < n;
+                z0[r] = (ok && k < a) ? Z::z(mr[r], xr[r][k]) - zref[k] : 0.0f;
+                z1[r] = (ok && k + 1 < a) ? Z::z(mr[r], xr[r][k + 1]) - zref[k + 1] : 0.0f;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                acc[r] = fmaf(z0[r], z0[r], fmaf(z1[r], z1[r], acc[r]));
+                *reinterpret_cast<__half2 *>(tile + sw128_off(r0 + r, k, ZG_B)) = __floats2half2_rn(z0[r], z1[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float nr = pn_warp_sum(acc[r]);
+            if (lane == r) {
+                const int row = r0 + r;
+                const bool ok = row < n;
+                side.s[row] = ok ? cr[r] : 0u;
+                side.m[row] = ok ? make_float2(mr[r].x, mr[r].y) : make_float2(0.0f, 0.0f);
+                side.n[row] = nr;
+                side.t[row] = ok ? pn_key_distf(__ldcg(&prow[cr[r]])) : 0.0f;
+                if (ok && mr[r].x != 0.0f) atomicMax(nmax, __float_as_int(nr));
+            }
+        }
     }
 }
 
 // Exact distances of up to four queued pairs at once, by the whole warp
 // (lanes over samples, four independent sums); each key lowers the tile's
-// shared row and column minima, which are written to the cells once per tile.
+// shared row and column minima, written to the cells once per tile.
 template <class Z>
-__device__ __forceinline__ void gram_eval4(const typename Z::X *xs, int a, const uint32_t *q, int nq,
-                                           const uint32_t *su, const uint32_t *sv, const float2 *mA,
-                                           const float2 *mB, unsigned long long *rmin, unsigned long long *cmin,
-                                           int lane) {
+__device__ __forceinline__ void zg_eval4(const typename Z::X *xs, int a, const uint32_t *q, int nq,
+                                         const ZgShared &sh, unsigned long long *rkey, unsigned long long *ckey,
+                                         int lane) {
     typename Z::M zu[4], zv[4];
     uint32_t uu[4], vv[4];
 #pragma unroll
@@ -83,16 +194,16 @@ __device__ __forceinline__ void gram_eval4(const typename Z::X *xs, int a, const
         const uint32_t e = q[p < nq ? p : 0];
         uu[p] = e >> 16;
         vv[p] = e & 0xFFFFu;
-        zu[p].x = mA[uu[p]].x;
-        zu[p].y = mA[uu[p]].y;
-        zv[p].x = mB[vv[p]].x;
-        zv[p].y = mB[vv[p]].y;
+        zu[p].x = sh.A.m[uu[p]].x;
+        zu[p].y = sh.A.m[uu[p]].y;
+        zv[p].x = sh.B.m[vv[p]].x;
+        zv[p].y = sh.B.m[vv[p]].y;
     }
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int r = lane; r < a; r += 32) {
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-            const float d = Z::z(zu[p], xs[su[uu[p]] + r]) - Z::z(zv[p], xs[sv[vv[p]] + r]);
+            const float d = Z::z(zu[p], xs[sh.A.s[uu[p]] + r]) - Z::z(zv[p], xs[sh.B.s[vv[p]] + r]);
             acc[p] = fmaf(d, d, acc[p]);
         }
     }
@@ -100,253 +211,287 @@ __device__ __forceinline__ void gram_eval4(const typename Z::X *xs, int a, const
     for (int p = 0; p < 4; ++p) {
         const float d = sqrtf(pn_warp_sum(acc[p]));
         if (lane == p && p < nq) {
-            atomicMin(&rmin[uu[p]], pn_pack_f(d, sv[vv[p]]));
-            atomicMin(&cmin[vv[p]], pn_pack_f(d, su[uu[p]]));
+            atomicMin(&rkey[uu[p]], pn_pack_f(d, sh.B.s[vv[p]]));
+            atomicMin(&ckey[vv[p]], pn_pack_f(d, sh.A.s[uu[p]]));
         }
     }
 }
 
-template <class Z>
-__global__ void __launch_bounds__(GR_THREADS) k_sieve_gram(PnView v, const PnClass *cls, const uint4 *tiles,
-                                                        int64_t ntiles, const uint32_t *members) {
-    extern __shared__ __align__(128) float gsm[];
-    float *Ahi = gsm;                                 // [128 x 32] canonical, each
-    float *Alo = Ahi + GR_B * GR_K;
-    float *Bhi = Alo + GR_B * GR_K;
-    float *Blo = Bhi + GR_B * GR_K;
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ uint32_t taddr_s;
-    __shared__ int fail_s;
-    __shared__ float nA[GR_B], nB[GR_B], tA[GR_B], tB[GR_B];
-    __shared__ uint32_t su[GR_B], sv[GR_B];
-    __shared__ float2 mA[GR_B], mB[GR_B];
-    __shared__ uint32_t queue[GR_THREADS / 32][GR_Q];
-    __shared__ unsigned long long rmin[GR_B], cmin[GR_B];
+// Column minima of a warp's 32 x 32 block: lane L ends with the minimum of
+// column L over the warp's 32 rows (five butterfly stages, each lane keeping
+// the half of its remaining columns selected by its own lane bit).
+__device__ __forceinline__ float zg_colmin32(float (&dd)[32], int lane) {
+#pragma unroll
+    for (int h = 16; h >= 1; h >>= 1) {
+        const bool up = (lane & h) != 0;
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+            const float send = up ? dd[j] : dd[j + h];
+            const float keep = up ? dd[j + h] : dd[j];
+            dd[j] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, h));
+        }
+    }
+    return dd[0];
+}
 
+template <class Z>
+__global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnClass *cls, const uint4 *tiles,
+                                                            int64_t ntiles, const uint32_t *members, int kpad_max,
+                                                            unsigned long long *work) {
+    extern __shared__ __align__(1024) unsigned char zsm_raw[];
+    __shared__ ZgShared sh;
+    unsigned char *zsm = zsm_raw + ((1024 - (smem_u32(zsm_raw) & 1023)) & 1023);
+    const int atoms = (kpad_max + 63) >> 6;
+    unsigned char *tA = zsm;
+    unsigned char *tB = tA + atoms * ZG_B * 128;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int kg = GR_K / 4;
     if (tid == 0) {
-        fail_s = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+        sh.fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh.mbar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
-                     "r"(GR_B));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.taddr)),
+                     "r"(ZG_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t taddr = taddr_s;
-    const uint32_t idesc = umma_idesc_tf32(GR_B, GR_B);
-    const float shrink = 1.0f - v.lam;
-    const float shrink2 = shrink * shrink;
+    const uint32_t taddr = sh.taddr;
+    const uint32_t idesc = umma_idesc_f16(ZG_B, ZG_B);
+    const float inf = __int_as_float(0x7f800000);
     uint32_t phase = 0;
-    bool ok = true;
     unsigned long long n_ex = 0;
+    uint32_t staged_cls = 0xFFFFFFFFu, staged_bu = 0xFFFFFFFFu;
 
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const uint4 tl = tiles[t];
-        const PnClass c = cls[tl.x];
-        const PnAnchor &A = v.anchors[c.anchor];
-        const PnSeries &S = v.series[A.series];
-        const int a = A.a;
-        const int u0 = (int)tl.y * GR_B, v0 = (int)tl.z * GR_B;
-        const int nu = min(GR_B, (int)c.size - u0), nv = min(GR_B, (int)c.size - v0);
-        const bool diag = tl.y == tl.z;
-        unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
-        const float *Fa = v.F + A.row_off * PN_FEAT;
-        const uint32_t nch = (uint32_t)A.nchunk;
-        __syncthreads();                                  // the previous tile's staging and queues are done
-        {
-            const int i = tid;                            // GR_THREADS == GR_B: one member per side per thread
-            const uint32_t xu = i < nu ? members[c.moff + u0 + i] : 0u;
-            const uint32_t xv = i < nv ? members[c.moff + v0 + i] : 0u;
-            su[i] = xu;
-            sv[i] = xv;
-            const auto mu = Z::load(v, A.win_off + xu), mv = Z::load(v, A.win_off + xv);
-            mA[i] = i < nu ? make_float2(mu.x, mu.y) : make_float2(0.0f, 0.0f);
-            mB[i] = i < nv ? make_float2(mv.x, mv.y) : make_float2(0.0f, 0.0f);
-            tA[i] = i < nu ? pn_key_distf(__ldcg(&prow[xu])) : 0.0f;
-            tB[i] = i < nv ? pn_key_distf(__ldcg(&prow[xv])) : 0.0f;
-            // squared row norms (fixed FMA order)
-            float na = 0.0f, nb = 0.0f;
-            if (i < nu) {
-                const float4 *r4 = reinterpret_cast<const float4 *>(Fa + (size_t)pn_row32(xu, v.cshift, nch) * PN_FEAT);
-#pragma unroll
-                for (int k = 0; k < GR_K / 4; ++k) {
-                    const float4 f = r4[k];
-                    na = fmaf(f.x, f.x, fmaf(f.y, f.y, fmaf(f.z, f.z, fmaf(f.w, f.w, na))));
-                }
-            }
-            if (i < nv) {
-                const float4 *r4 = reinterpret_cast<const float4 *>(Fa + (size_t)pn_row32(xv, v.cshift, nch) * PN_FEAT);
-#pragma unroll
-                for (int k = 0; k < GR_K / 4; ++k) {
-                    const float4 f = r4[k];
-                    nb = fmaf(f.x, f.x, fmaf(f.y, f.y, fmaf(f.z, f.z, fmaf(f.w, f.w, nb))));
-                }
-            }
-            nA[i] = na;
-            nB[i] = nb;
-            rmin[i] = PN_EMPTY_KEY;
-            cmin[i] = PN_EMPTY_KEY;
-        }
+    for (;;) {
         __syncthreads();
-        // operands: member rows split into TF32 hi + lo (zero rows past the class)
-        for (int e = tid; e < GR_B * GR_K; e += GR_THREADS) {
-            const int i = e / GR_K, k = e - i * GR_K;
-            const float fu = i < nu ? Fa[(size_t)pn_row32(su[i], v.cshift, nch) * PN_FEAT + k] : 0.0f;
-            const float fv = i < nv ? Fa[(size_t)pn_row32(sv[i], v.cshift, nch) * PN_FEAT + k] : 0.0f;
-            const float hu = tf32_hi(fu), hv = tf32_hi(fv);
-            Ahi[kmaj(i, k, kg)] = hu;
-            Alo[kmaj(i, k, kg)] = fu - hu;
-            Bhi[kmaj(i, k, kg)] = hv;
-            Blo[kmaj(i, k, kg)] = fv - hv;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (tid == 0) sh.run = atomicAdd(work, (unsigned long long)ZG_RUN);
         __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            const uint32_t lbo = 128, sbo = kg * 128;
-            for (int s = 0; s < GR_K / 8; ++s) {
-                const uint32_t off = (uint32_t)(s * 2 * 32 * sizeof(float));
-                const uint64_t ah = umma_desc(smem_u32(Ahi) + off, lbo, sbo);
-                const uint64_t al = umma_desc(smem_u32(Alo) + off, lbo, sbo);
-                const uint64_t bh = umma_desc(smem_u32(Bhi) + off, lbo, sbo);
-                const uint64_t bl = umma_desc(smem_u32(Blo) + off, lbo, sbo);
-                const uint32_t acc0 = s > 0 ? 1u : 0u;
-                asm volatile("{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }"
-                             ::"r"(taddr), "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(taddr), "l"(ah), "l"(bl),
-                             "r"(idesc));
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(taddr), "l"(al), "l"(bh),
-                             "r"(idesc));
+        const int64_t run0 = (int64_t)sh.run;
+        if (run0 >= ntiles || sh.fail) break;
+        const int64_t run1 = min(ntiles, run0 + ZG_RUN);
+        for (int64_t t = run0; t < run1; ++t) {
+            const uint4 tl = tiles[t];
+            const PnClass c = cls[tl.x];
+            const PnAnchor &A = v.anchors[c.anchor];
+            const PnSeries &S = v.series[A.series];
+            const int a = A.a;
+            const int kp = (a + 15) & ~15;
+            const int u0 = (int)tl.y * ZG_B, v0 = (int)tl.z * ZG_B;
+            const int nu = min(ZG_B, (int)c.size - u0), nv = min(ZG_B, (int)c.size - v0);
+            const bool diag = tl.y == tl.z;
+            unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
+            __syncthreads();                            // the previous tile's reads of both blocks are done
+            const bool new_row = tl.x != staged_cls || tl.y != staged_bu;
+            if (tid == 0) {
+                if (new_row) sh.nmax_a = 0;
+                sh.nmax_b = 0;
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&mbar))
-                         : "memory");
-        }
-        if (!mbar_wait(smem_u32(&mbar), phase, GR_SPIN)) {
-            if (lane == 0) atomicExch(&fail_s, 1);
-        }
-        phase ^= 1u;
-        __syncthreads();
-        if (fail_s) {
-            ok = false;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: row u = 32 warp + lane against the tile's columns
-        const int u = warp * 32 + lane;
-        const bool urow = u < nu && mA[u].x != 0.0f;
-        const float nu_ = nA[u], tu = tA[u];
-        const int64_t pu = (int64_t)su[u];
-        const float scale = 2.0f / (float)a;
-        const auto *xs = Z::samples(v, S.x_off);
-        int qn = 0;
-        for (int c0 = 0; c0 < nv; c0 += 32) {
-            uint32_t r[32];
-            const uint32_t ta = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
-                "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            sh.rkey[tid] = PN_EMPTY_KEY;
+            sh.ckey[tid] = PN_EMPTY_KEY;
+            sh.colmin[tid] = 0x7f800000;
+            __syncthreads();
+            if (new_row) {
+                // reference: the row block's first member (both blocks of a tile share it)
+                const uint32_t cr = members[(int64_t)c.moff + u0];
+                const auto mref = Z::load(v, A.win_off + cr);
+                const auto *xref = Z::samples(v, S.x_off + cr);
+                for (int k = tid; k < kp; k += ZG_THREADS) sh.zref[k] = k < a ? Z::z(mref, xref[k]) : 0.0f;
+                __syncthreads();
+                zg_stage<Z>(v, A, S, members, (int64_t)c.moff + u0, nu, a, kp, tA, sh.A, &sh.nmax_a, prow, sh.zref,
+                            warp, lane);
+            }
+            zg_stage<Z>(v, A, S, members, (int64_t)c.moff + v0, nv, a, kp, tB, sh.B, &sh.nmax_b, prow, sh.zref, warp,
+                        lane);
+            staged_cls = tl.x;
+            staged_bu = tl.y;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid == 0) {
+                const uint32_t a0 = smem_u32(tA), b0 = smem_u32(tB);
+                for (int s = 0; s < kp / 16; ++s) {
+                    const uint32_t off = (uint32_t)((s >> 2) * ZG_B * 128 + (s & 3) * 32);
+                    const uint64_t ad = sw128_desc(a0 + off), bd = sw128_desc(b0 + off);
+                    const uint32_t acc = s > 0 ? 1u : 0u;
+                    asm volatile("{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
+                                 ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&sh.mbar))
+                             : "memory");
+            }
+            if (!mbar_wait(smem_u32(&sh.mbar), phase, ZG_SPIN)) {
+                if (lane == 0) atomicExch(&sh.fail, 1);
+            }
+            phase ^= 1u;
+            __syncthreads();
+            if (sh.fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+            // ---- pass 1: row minima (per thread) and column minima (butterfly + shared atomics)
+            const int u = warp * 32 + lane;
+            const bool urow = u < nu && sh.A.m[u].x != 0.0f;
+            const float nu_ = sh.A.n[u];
+            const int64_t pu = (int64_t)sh.A.s[u];
+            const uint32_t tbase = taddr + ((uint32_t)(warp * 32) << 16);
+            float rmin = inf;
+            for (int c0 = 0; c0 < ZG_B; c0 += 32) {
+                uint32_t r[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(tbase + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float dd[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int vc = c0 + j;
-                bool s = urow && vc < nv && (!diag || u < vc) && mB[vc].x != 0.0f;
-                if (s) s = llabs(pu - (int64_t)sv[vc]) >= S.excl;
-                if (s) {
-                    const float n2 = nu_ + nB[vc];
-                    const float lb2 = fmaxf(0.0f, scale * (n2 - 2.0f * __uint_as_float(r[j])));
-                    const float margin = scale * n2 * 3.0517578e-5f;          // (2/a)(n_u + n_v) 2^-15
-                    const float thr = fmaxf(tu, tB[vc]);
-                    s = !(shrink2 * (lb2 - margin) >= thr * thr);            // an infinite threshold keeps it
+                for (int j = 0; j < 32; ++j) {
+                    const int vc = c0 + j;
+                    bool ok = urow && vc < nv && (!diag || u < vc) && sh.B.m[vc].x != 0.0f;
+                    if (ok) ok = llabs(pu - (int64_t)sh.B.s[vc]) >= S.excl;
+                    dd[j] = ok ? fmaxf(0.0f, nu_ + sh.B.n[vc] - 2.0f * __uint_as_float(r[j])) : inf;
+                    rmin = fminf(rmin, dd[j]);
                 }
-                const uint32_t bal = __ballot_sync(0xffffffffu, s);
-                if (s) queue[warp][qn + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)u << 16) | (uint32_t)vc;
-                qn += __popc(bal);
-                if (qn > GR_Q - 32) {                     // warp-uniform: evaluate the queued pairs
-                    __syncwarp();
-                    for (int e = 0; e < qn; e += 4)
-                        gram_eval4<Z>(xs, a, &queue[warp][e], min(4, qn - e), su, sv, mA, mB, rmin, cmin, lane);
-                    n_ex += (unsigned long long)qn;
-                    qn = 0;
-                    __syncwarp();
+                const float cm = zg_colmin32(dd, lane);
+                if (cm < inf) atomicMin(&sh.colmin[c0 + lane], __float_as_int(cm));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+            // ---- pass 2: the pairs that can still lower a cell, evaluated exactly
+            const float nmax_a = __int_as_float(sh.nmax_a), nmax_b = __int_as_float(sh.nmax_b);
+            const float tu2 = sh.A.t[u] * sh.A.t[u];
+            const float mabs = (float)a * 6.1035156e-05f;           // a 2^-14
+            const float tol_row = 0.00390625f * (nu_ + nmax_b) + 2.0f * mabs;   // 2 M_row
+            const auto *xs = Z::samples(v, S.x_off);
+            int qn = 0;
+            for (int c0 = 0; c0 < ZG_B; c0 += 32) {
+                uint32_t r[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(tbase + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int vc = c0 + j;
+                    bool s = urow && vc < nv && (!diag || u < vc) && sh.B.m[vc].x != 0.0f;
+                    if (s) s = llabs(pu - (int64_t)sh.B.s[vc]) >= S.excl;
+                    if (s) {
+                        const float nv_ = sh.B.n[vc];
+                        const float dd = fmaxf(0.0f, nu_ + nv_ - 2.0f * __uint_as_float(r[j]));
+                        const float M = 0.001953125f * (nu_ + nv_) + mabs;     // 2^-9 (|y_u|^2 + |y_v|^2) + a 2^-14
+                        const float tv = sh.B.t[vc];
+                        const bool keep_u = dd - M < tu2 && dd <= rmin + tol_row;
+                        const bool keep_v = dd - M < tv * tv && dd <= __int_as_float(sh.colmin[vc]) +
+                                                                          0.00390625f * (nv_ + nmax_a) + 2.0f * mabs;
+                        s = keep_u || keep_v;
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, s);
+                    if (s) sh.queue[warp][qn + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)u << 16) | (uint32_t)vc;
+                    qn += __popc(bal);
+                    if (qn > ZG_Q - 32) {                     // warp-uniform: evaluate the queued pairs
+                        __syncwarp();
+                        for (int e = 0; e < qn; e += 4)
+                            zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh, sh.rkey, sh.ckey, lane);
+                        n_ex += (unsigned long long)qn;
+                        qn = 0;
+                        __syncwarp();
+                    }
                 }
             }
+            __syncwarp();
+            for (int e = 0; e < qn; e += 4)
+                zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh, sh.rkey, sh.ckey, lane);
+            n_ex += (unsigned long long)qn;
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();                               // every warp's keys are in the tile minima
+            if (sh.rkey[tid] != PN_EMPTY_KEY) atomicMin(&prow[sh.A.s[tid]], sh.rkey[tid]);
+            if (sh.ckey[tid] != PN_EMPTY_KEY) atomicMin(&prow[sh.B.s[tid]], sh.ckey[tid]);
         }
-        __syncwarp();
-        for (int e = 0; e < qn; e += 4)
-            gram_eval4<Z>(xs, a, &queue[warp][e], min(4, qn - e), su, sv, mA, mB, rmin, cmin, lane);
-        n_ex += (unsigned long long)qn;
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();                                   // every warp's keys are in the tile minima
-        if (rmin[tid] != PN_EMPTY_KEY) atomicMin(&prow[su[tid]], rmin[tid]);
-        if (cmin[tid] != PN_EMPTY_KEY) atomicMin(&prow[sv[tid]], cmin[tid]);
+        if (sh.fail) break;
     }
-    if (!ok && tid == 0) {
+    __syncthreads();
+    if (sh.fail && tid == 0) {
         atomicExch(v.err, PN_ERR_TC_TIMEOUT);
-        mbar_wait(smem_u32(&mbar), phase ^ 1u, GR_SPIN);   // let an MMA still in flight finish (bounded)
+        mbar_wait(smem_u32(&sh.mbar), phase ^ 1u, ZG_SPIN);   // an MMA still in flight finishes (bounded)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(GR_B));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ZG_TMEM_COLS));
     if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);
 }
 
 template <class Z>
-cudaError_t sieve_gram_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int grid_blocks,
-                         cudaStream_t st) {
+cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int a_max,
+                          int grid_blocks, cudaStream_t st) {
     uint32_t *cnt = nullptr, *off = nullptr, *tot = nullptr;
+    unsigned long long *tot64 = nullptr;
     uint4 *tiles = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&cnt, 4 * (size_t)ncls, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&off, 4 * (size_t)ncls, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot, 4, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot64, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tot64, 0, 2 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) {
-        k_gram_tile_count<<<(unsigned)((ncls + 255) / 256), 256, 0, st>>>(cls, ncls, cnt);
+        k_zg_tile_count<<<(unsigned)((ncls + 255) / 256), 256, 0, st>>>(cls, ncls, cnt, tot64,
+                                                                     reinterpret_cast<int *>(tot64 + 1));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = excl_scan_u32(cnt, off, ncls, tot, st);
-    uint32_t ntiles = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&ntiles, tot, 4, cudaMemcpyDeviceToHost, st);
+    unsigned long long h[2] = {0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, tot64, sizeof(h), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const int64_t ntiles = (int64_t)h[0];
+    if (e == cudaSuccess && (h[1] != 0ull || ntiles > 0x7FFFFFFFll)) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess && ntiles > 0) e = cudaMallocAsync((void **)&tiles, sizeof(uint4) * (size_t)ntiles, st);
+    unsigned long long *work = tot64;
+    if (e == cudaSuccess && ntiles > 0) e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess && ntiles > 0) {
-        k_gram_tile_fill<<<(unsigned)(((int64_t)ncls * 32 + 255) / 256), 256, 0, st>>>(cls, ncls, off, tiles);
+        k_zg_tile_fill<<<(unsigned)(((int64_t)ncls * 32 + 255) / 256), 256, 0, st>>>(cls, ncls, off, tiles);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && ntiles > 0) {
-        const size_t sm = sizeof(float) * 4 * GR_B * GR_K;
-        e = pn_allow_smem(k_sieve_gram<Z>, sm);
+        const int kpad = (a_max + 15) & ~15;
+        const int atoms = (kpad + 63) >> 6;
+        const size_t sm = 1024 + (size_t)atoms * 2 * ZG_B * 128;
+        e = pn_allow_smem(k_sieve_zgram<Z>, sm);
         if (e == cudaSuccess) {
-            const int64_t g = std::min<int64_t>((int64_t)ntiles, (int64_t)grid_blocks);
-            k_sieve_gram<Z><<<(unsigned)g, GR_THREADS, sm, st>>>(v, cls, tiles, (int64_t)ntiles, vals);
+            const int64_t g = std::min<int64_t>((ntiles + ZG_RUN - 1) / ZG_RUN, (int64_t)grid_blocks);
+            k_sieve_zgram<Z><<<(unsigned)g, ZG_THREADS, sm, st>>>(v, cls, tiles, ntiles, vals, kpad, work);
             e = cudaGetLastError();
         }
     }
-    for (void *p : {(void *)cnt, (void *)off, (void *)tot, (void *)tiles})
+    for (void *p : {(void *)cnt, (void *)off, (void *)tot, (void *)tot64, (void *)tiles})
         if (p) cudaFreeAsync(p, st);
     return e;
 }
 
 }  // namespace
 
-cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals,
+bool sieve_gram_supported(int a_max) { return a_max <= ZG_AMAX; }
+
+cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int a_max,
                               int grid_blocks, cudaStream_t st) {
     if (ncls <= 0) return cudaSuccess;
-    if (v.x1) return sieve_gram_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);
-    return sieve_gram_t<ZMix2>(v, cls, ncls, vals, grid_blocks, st);
+    if (v.x1) return sieve_zgram_t<ZMix1>(v, cls, ncls, vals, a_max, grid_blocks, st);
+    return sieve_zgram_t<ZMix2>(v, cls, ncls, vals, a_max, grid_blocks, st);
 }
 
 }  // namespace pn

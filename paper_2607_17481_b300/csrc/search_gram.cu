@@ -94,30 +94,6 @@ constexpr int GS_TMEM_COLS = 32;
 static_assert(GS_GQ * GS_RMAX <= GS_HT, "the table holds every listed window");
 static_assert(GS_GQ * GS_SQ * 12 <= GS_GQ * GS_RMAX * 4, "survivor queues fit in the list area");
 
-// Byte offset of element (row, k) in a K-major 128-byte-swizzled tile of
-// `rows` rows (atoms of 64 16-bit values along K, rows x 128 bytes each).
-__device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows) {
-    const int kk = k & 63;
-    return (uint32_t)((k >> 6) * rows * 128 + row * 128 + ((((kk >> 3) ^ (row & 7))) << 4) + (kk & 7) * 2);
-}
-
-// tcgen05 shared-memory descriptor of a K-major 128-byte-swizzled operand:
-// stride 1024 bytes between eight-row groups, layout type 2 (128B swizzle).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;                          // leading offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;                // stride offset
-    d |= (uint64_t)1 << 46;                          // descriptor version
-    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: D F32, A and B f16, both K-major, M x N.
-__device__ __forceinline__ uint32_t umma_idesc_f16(int M, int N) {
-    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 __device__ __forceinline__ uint32_t gs_hash(uint32_t c) { return (c * 2654435761u) >> (32 - 11); }
 
 __device__ __forceinline__ float gs_warp_min(float x) {

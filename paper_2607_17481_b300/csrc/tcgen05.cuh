@@ -1,8 +1,8 @@
 // tcgen05 helpers shared by the tensor-core kernels (sm_103a): shared-memory
 // matrix and instruction descriptors of the PTX ISA's documented bit
 // layout, the K-major no-swizzle canonical operand layout (8-row x 16-byte
-// core matrices), TF32 rounding for the hi + lo operand split, and a
-// bounded mbarrier wait.
+// core matrices) and the K-major 128-byte-swizzled one, TF32 rounding for
+// the hi + lo operand split, and a bounded mbarrier wait.
 #pragma once
 #include <stdint.h>
 
@@ -35,6 +35,30 @@ __device__ __forceinline__ float tf32_hi(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
+}
+
+// Byte offset of element (row, k) in a K-major 128-byte-swizzled tile of
+// `rows` rows (atoms of 64 16-bit values along K, rows x 128 bytes each).
+__device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows) {
+    const int kk = k & 63;
+    return (uint32_t)((k >> 6) * rows * 128 + row * 128 + ((((kk >> 3) ^ (row & 7))) << 4) + (kk & 7) * 2);
+}
+
+// tcgen05 shared-memory descriptor of a K-major 128-byte-swizzled operand:
+// stride 1024 bytes between eight-row groups, layout type 2 (128B swizzle).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                          // leading offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride offset
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D F32, A and B f16, both K-major, M x N.
+__device__ __forceinline__ uint32_t umma_idesc_f16(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, int spin) {
