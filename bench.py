@@ -662,8 +662,7 @@ def main():
     if args.fast_steps > 0:
         fast = {}
         for name, over in (("s6_alpha4_rounds1", dict(stride=6, alpha=4, rounds=1)),
-                           ("s6_alpha4_rounds1_exhaustive_sieve", dict(stride=6, alpha=4, rounds=1,
-                                                                       flags=pn.FLAG_EXHAUSTIVE_SIEVE)),
+                           ("exhaustive_sieve", dict(flags=pn.FLAG_EXHAUSTIVE_SIEVE)),
                            ("K4_s8", dict(K=4, stride=8))):
             fctx = make_ctx(args.precision, **over)
             fms, fst, fmot = timed(fctx, args.fast_steps, 1, x_dev)
@@ -674,7 +673,14 @@ def main():
             fast[name] = {"value": W * world / (statistics.mean(fms) / 1e3), "ms_per_step": statistics.mean(fms),
                           "same_motifs": bool(np.array_equal(fmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                           "recall_vs_default": len(ref_cells & got_cells) / max(1, len(ref_cells)),
+                          "best_d": float(fmot["d"][0]) if len(fmot) else None,
+                          "kth_d": float(fmot["d"][-1]) if len(fmot) else None,
                           "config": over}
+            if name == "exhaustive_sieve":
+                # every pair of each hot class evaluated: the default's cells it
+                # also reports, and the k-th distances of both lists
+                fast[name]["default_recall_vs_this"] = fast[name]["recall_vs_default"]
+                fast[name]["default_kth_d"] = float(motifs["d"][-1]) if len(motifs) else None
     walk = run_walk(pn, stream) if rank == 0 else None
     batched = run_batched(pn, stream, args.batched, args.batched_loop) if args.batched > 0 else None
     served = run_served(pn, args) if args.served_seconds > 0 and rank == 0 else None
