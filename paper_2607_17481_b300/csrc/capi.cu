@@ -100,14 +100,14 @@ struct SelBufs {
 // The emit stage after the sieve: its control words, the seed, refinement
 // and final selection groups, and the seed and target lists.  Built once per
 // request (kept with the request when the stage is replayed from a graph).
-enum { C_GATE = 0, C_FLAG, C_NSEED, C_ROUNDS, R_GATE, R_FLAG, R_NTG, R_PASSES, OV_FINAL, OV_OTHER, Y_GATE, Y_FLAG,
-       Y_CYCLES, C_WORDS };
+enum { C_GATE = 0, C_FLAG, C_NSEED, C_ROUNDS, R_GATE, R_FLAG, R_NTG, R_PASSES, OV_FINAL, OV_OTHER, R_NNEAR, C_WORDS };
 struct EmitPlan {
     int32_t *ctl = nullptr;
     SelBufs sb, rb, fb;
-    PnSeed *dseeds = nullptr, *dtg = nullptr, *ddone = nullptr;
+    PnSeed *dseeds = nullptr, *dtg = nullptr, *ddone = nullptr, *dnear = nullptr;
     int32_t *ndone = nullptr;
     int32_t done_cap = 0;
+    int32_t knear = 0;                 // picks per group whose new targets seed a completion
     int64_t max_windows = 0;
     int m_top = 3;
     bool completion = false, refine = false;
@@ -544,8 +544,7 @@ int sel_launch(panache_ctx *ctx, PnRequest &R, const PnView &v, const SelBufs &b
     return PANACHE_OK;
 }
 
-constexpr int kRefinePasses = 8;   // most row-refinement passes of one cycle
-constexpr int kEmitCycles = 4;     // most completion + refinement cycles of one request
+constexpr int kRefinePasses = 8;   // most row-refinement passes of one request
 
 __global__ void k_fill_i32(int32_t *p, int32_t n, int32_t value) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -702,8 +701,14 @@ int emit_prepare(panache_ctx *ctx, PnRequest &R, const GroupSet &seed_groups, co
     if (E.refine) {
         PN_TRY(sel_prepare(R, ref_groups, false, E.rb));
         if (E.rb.ng) {
-            E.done_cap = E.rb.kmax * kRefinePasses * kEmitCycles;
+            E.done_cap = E.rb.kmax * kRefinePasses;
             PN_CU(R.alloc(E.dtg, (int64_t)E.rb.ng * E.rb.kmax));
+            if (E.completion) PN_CU(R.alloc(E.dnear, (int64_t)E.rb.ng * E.rb.kmax));
+            // global lists: the completion seeds' count (seed_mult k); per-length
+            // lists: k per length
+            E.knear = c.topk_mode == PANACHE_TOPK_GLOBAL && E.completion && E.sb.ng
+                          ? E.sb.kmax
+                          : (int32_t)std::max<int64_t>(1, E.rb.kmax / std::max<uint32_t>(1, c.refine_mult));
             PN_CU(R.alloc(E.ddone, (int64_t)E.rb.ng * E.done_cap));
             PN_CU(R.alloc(E.ndone, E.rb.ng));
         }
@@ -741,77 +746,69 @@ int emit_launch(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm, 
     const int grid = ctx->sm_count * (int)c.grid_mult;
     int32_t *ctl = E.ctl;
     PN_CU(cudaMemsetAsync(ctl, 0, sizeof(int32_t) * C_WORDS, st));
-    // Cycles of completion rounds and refinement passes: the refinement
-    // brings cells into the top list (a row's exact nearest neighbour) whose
-    // neighbourhood no completion round has seen, so the next cycle completes
-    // around the new picks and refines again, until a cycle lowers nothing.
-    const bool any = (E.completion && E.sb.ng) || (E.refine && E.rb.ng);
-    if (any) {
-        k_fill_i32<<<1, 32, 0, st>>>(ctl + Y_GATE, 1, 1);
-        if (E.refine && E.rb.ng) PN_CU(cudaMemsetAsync(E.ndone, 0, sizeof(int32_t) * E.rb.ng, st));
-        ctx->launches += 1;
-    }
-    for (int cycle = 0; any && cycle < kEmitCycles; ++cycle) {
-        if (batch > 0 && cycle > 0) {
-            bool open = true;
-            PN_TRY(gate_open(st, ctl + Y_GATE, hctl + Y_GATE, &open));
-            if (!open) break;
+    if (E.completion && E.sb.ng) {
+        const int32_t nmax = E.sb.ng * E.sb.kmax;
+        k_fill_i32<<<1, 32, 0, st>>>(ctl + C_GATE, 1, 1);
+        PnView vg = v;
+        vg.gate = ctl + C_GATE;
+        for (uint32_t round = 0; round < c.rounds; ++round) {
+            if (batch > 0 && round > 0 && round % batch == 0) {
+                bool open = true;
+                PN_TRY(gate_open(st, ctl + C_GATE, hctl + C_GATE, &open));
+                if (!open) break;
+            }
+            PN_TRY(sel_launch(ctx, R, vg, E.sb, ctl + OV_OTHER));
+            PN_CU(pn::launch_picks_to_seeds(E.sb.out, E.sb.cnt, E.sb.ng, E.sb.kmax, E.dseeds, ctl + C_NSEED,
+                                            ctl + C_GATE, st));
+            pn_kt_begin(v.kt, PN_KT_COMPLETE, st);
+            PN_CU(pn::launch_complete(vg, E.dseeds, nmax, ctl + C_NSEED, (int)c.dm, (int)c.dp, ctl + C_FLAG, grid, st));
+            pn_kt_end(v.kt, PN_KT_COMPLETE, st);
+            PN_CU(pn::launch_round_end(ctl + C_GATE, ctl + C_FLAG, ctl + C_NSEED, ctl + C_ROUNDS, st));
+            ctx->launches += 3;
         }
-        PN_CU(pn::launch_cycle_begin(ctl + Y_GATE, ctl + C_GATE, ctl + R_GATE, ctl + Y_CYCLES, st));
-        ctx->launches += 1;
-        if (E.completion && E.sb.ng) {
-            const int32_t nmax = E.sb.ng * E.sb.kmax;
-            PnView vg = v;
-            vg.gate = ctl + C_GATE;
-            for (uint32_t round = 0; round < c.rounds; ++round) {
-                if (batch > 0 && round > 0 && round % batch == 0) {
-                    bool open = true;
-                    PN_TRY(gate_open(st, ctl + C_GATE, hctl + C_GATE, &open));
-                    if (!open) break;
-                }
-                PN_TRY(sel_launch(ctx, R, vg, E.sb, ctl + OV_OTHER));
-                PN_CU(pn::launch_picks_to_seeds(E.sb.out, E.sb.cnt, E.sb.ng, E.sb.kmax, E.dseeds, ctl + C_NSEED,
-                                                ctl + C_GATE, st));
+    }
+    // Exact row refinement of the top list (refine.cu): the top
+    // refine_mult*k cells of every selection group are each scanned against
+    // all valid partners at their length; the list is reselected and cells
+    // not scanned before are scanned, until a pass finds no new cell or
+    // lowers none.  The final top-k is a prefix of that list (the same
+    // greedy rule), so every reported cell ends with its exact nearest
+    // neighbour.  Each pass then completes around the refined pairs of its
+    // targets among the first k picks of their group (partners read back from
+    // the cells): a row brought into the list by its exact neighbour has a box
+    // no completion round has seen, and a cell that box lowers enters the next
+    // pass's list.
+    if (E.refine && E.rb.ng) {
+        const int32_t nmax = E.rb.ng * E.rb.kmax;
+        PN_CU(cudaMemsetAsync(E.ndone, 0, sizeof(int32_t) * E.rb.ng, st));
+        k_fill_i32<<<1, 32, 0, st>>>(ctl + R_GATE, 1, 1);
+        PnView vr = v;
+        vr.gate = ctl + R_GATE;
+        for (int pass = 0; pass < kRefinePasses; ++pass) {
+            if (batch > 0 && pass > 0 && pass % batch == 0) {
+                bool open = true;
+                PN_TRY(gate_open(st, ctl + R_GATE, hctl + R_GATE, &open));
+                if (!open) break;
+            }
+            PN_TRY(sel_launch(ctx, R, vr, E.rb, ctl + OV_OTHER));
+            PN_CU(pn::launch_new_targets(E.rb.out, E.rb.cnt, E.rb.ng, E.rb.kmax, E.ddone, E.ndone, E.done_cap, E.dtg,
+                                         ctl + R_NTG, ctl + R_GATE, st, E.completion ? E.dnear : nullptr,
+                                         ctl + R_NNEAR, E.knear));
+            pn_kt_begin(v.kt, PN_KT_REFINE, st);
+            PN_CU(pn::launch_refine(vr, E.dtg, nmax, ctl + R_NTG, E.max_windows, E.m_top, ctl + R_FLAG,
+                                    ctx->sm_count * 2, st));
+            pn_kt_end(v.kt, PN_KT_REFINE, st);
+            if (E.completion) {
+                PN_CU(pn::launch_seeds_refresh(vr, E.dnear, nmax, ctl + R_NNEAR, st));
                 pn_kt_begin(v.kt, PN_KT_COMPLETE, st);
-                PN_CU(pn::launch_complete(vg, E.dseeds, nmax, ctl + C_NSEED, (int)c.dm, (int)c.dp, ctl + C_FLAG, grid,
+                PN_CU(pn::launch_complete(vr, E.dnear, nmax, ctl + R_NNEAR, (int)c.dm, (int)c.dp, ctl + R_FLAG, grid,
                                           st));
                 pn_kt_end(v.kt, PN_KT_COMPLETE, st);
-                PN_CU(pn::launch_round_end(ctl + C_GATE, ctl + C_FLAG, ctl + C_NSEED, ctl + C_ROUNDS, st,
-                                           ctl + Y_FLAG));
-                ctx->launches += 3;
+                ctx->launches += 2;
             }
+            PN_CU(pn::launch_round_end(ctl + R_GATE, ctl + R_FLAG, ctl + R_NTG, ctl + R_PASSES, st, ctl + R_NNEAR));
+            ctx->launches += 3;
         }
-        // Exact row refinement of the top list (refine.cu): the top
-        // refine_mult*k cells of every selection group are each scanned
-        // against all valid partners at their length; the list is reselected
-        // and cells not scanned before (in any cycle) are scanned, until a
-        // pass finds no new cell or lowers none.  The final top-k is a prefix
-        // of that list (the same greedy rule), so every reported cell ends
-        // with its exact nearest neighbour.
-        if (E.refine && E.rb.ng) {
-            const int32_t nmax = E.rb.ng * E.rb.kmax;
-            PnView vr = v;
-            vr.gate = ctl + R_GATE;
-            for (int pass = 0; pass < kRefinePasses; ++pass) {
-                if (batch > 0 && pass > 0 && pass % batch == 0) {
-                    bool open = true;
-                    PN_TRY(gate_open(st, ctl + R_GATE, hctl + R_GATE, &open));
-                    if (!open) break;
-                }
-                PN_TRY(sel_launch(ctx, R, vr, E.rb, ctl + OV_OTHER));
-                PN_CU(pn::launch_new_targets(E.rb.out, E.rb.cnt, E.rb.ng, E.rb.kmax, E.ddone, E.ndone, E.done_cap,
-                                             E.dtg, ctl + R_NTG, ctl + R_GATE, st));
-                pn_kt_begin(v.kt, PN_KT_REFINE, st);
-                PN_CU(pn::launch_refine(vr, E.dtg, nmax, ctl + R_NTG, E.max_windows, E.m_top, ctl + R_FLAG,
-                                        ctx->sm_count * 2, st));
-                pn_kt_end(v.kt, PN_KT_REFINE, st);
-                PN_CU(pn::launch_round_end(ctl + R_GATE, ctl + R_FLAG, ctl + R_NTG, ctl + R_PASSES, st,
-                                           ctl + Y_FLAG));
-                ctx->launches += 3;
-            }
-        }
-        PN_CU(pn::launch_cycle_end(ctl + Y_GATE, ctl + Y_FLAG, st));
-        ctx->launches += 1;
     }
     PN_TRY(tm.mark(7));
     PN_TRY(sel_launch(ctx, R, v, E.fb, ctl + OV_FINAL));

@@ -1038,32 +1038,34 @@ namespace {
 // Ends a round: an empty round closes the gate, a round that ran is
 // counted and closes the gate when nothing improved; the flag and the
 // count start again at 0 for the next round.
-__global__ void k_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, int *sticky) {
+__global__ void k_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, int32_t *count2) {
+    if (count2) *count2 = 0;
     if (*gate) {
         if (*count == 0) {
             *gate = 0;
         } else {
             ++*rounds;
             if (!*flag) *gate = 0;
-            else if (sticky) *sticky = 1;
         }
         *flag = 0;
         *count = 0;
     }
 }
 
-// A cycle of the emit stage (completion rounds, then refinement passes)
-// opens both phases' gates when the cycle gate is open; at its end the cycle
-// gate stays open only if a round or pass of the cycle lowered a cell.
-__global__ void k_cycle_begin(const int *cycle_gate, int *completion_gate, int *refine_gate, int32_t *cycles) {
-    completion_gate[0] = *cycle_gate;
-    refine_gate[0] = *cycle_gate;
-    if (*cycle_gate) ++*cycles;
-}
-
-__global__ void k_cycle_end(int *cycle_gate, int *cycle_flag) {
-    if (!*cycle_flag) *cycle_gate = 0;
-    *cycle_flag = 0;
+// Refreshed completion seeds: each target's partner j read back from its
+// cell (m, i), so a box is re-cut around the pair the cell now holds.
+__global__ void k_seeds_refresh(PnView v, PnSeed *seeds, int32_t nmax, const int32_t *n_dev) {
+    if (pn_gated(v)) return;
+    const int32_t n = min(*n_dev, nmax);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    PnSeed sd = seeds[t];
+    const PnSeries &S = v.series[sd.series];
+    const unsigned long long key = v.prof[S.row_off + (int64_t)(sd.m - S.m_min) * S.ld + sd.i];
+    if (key != PN_EMPTY_KEY) {
+        sd.j = (int64_t)pn_key_idx(key);
+        seeds[t] = sd;
+    }
 }
 
 // Completion seeds from a selection's picks (group g's at picks[g kmax ...]).
@@ -1084,9 +1086,12 @@ __global__ void k_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_
 
 // Refinement targets: the picks of group g not refined in an earlier pass
 // (done[g][0 .. ndone[g])), appended to the group's done list and to the
-// targets.  One warp per group, so a group's list has one writer.
+// targets; those among the group's first knear picks also to `near` (the
+// cells whose boxes the pass completes).  One warp per group, so a group's
+// list has one writer.
 __global__ void k_new_targets(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *done,
-                              int32_t *ndone, int32_t done_cap, PnSeed *targets, int32_t *ntargets, const int *gate) {
+                              int32_t *ndone, int32_t done_cap, PnSeed *targets, int32_t *ntargets, const int *gate,
+                              PnSeed *near, int32_t *nnear, int32_t knear) {
     if (!*gate) return;
     const int gi = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (gi >= ng) return;
@@ -1115,6 +1120,16 @@ __global__ void k_new_targets(const PnPick *picks, const int32_t *cnt, int32_t n
             targets[base + rank] = sd;
             if (nd + rank < done_cap) dl[nd + rank] = sd;
         }
+        // the fresh targets among the group's first knear picks also seed
+        // the pass's completion
+        const bool is_near = fresh && t < knear;
+        const uint32_t nb = __ballot_sync(0xffffffffu, is_near);
+        if (near && nb) {
+            int nbase = 0;
+            if (lane == 0) nbase = atomicAdd(nnear, __popc(nb));
+            nbase = __shfl_sync(0xffffffffu, nbase, 0);
+            if (is_near) near[nbase + __popc(nb & ((1u << lane) - 1u))] = sd;
+        }
         nd = min(done_cap, nd + nf);
         __syncwarp();
     }
@@ -1123,17 +1138,14 @@ __global__ void k_new_targets(const PnPick *picks, const int32_t *cnt, int32_t n
 
 }  // namespace
 
-cudaError_t launch_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, cudaStream_t st, int *sticky) {
-    k_round_end<<<1, 1, 0, st>>>(gate, flag, count, rounds, sticky);
+cudaError_t launch_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, cudaStream_t st,
+                             int32_t *count2) {
+    k_round_end<<<1, 1, 0, st>>>(gate, flag, count, rounds, count2);
     return cudaGetLastError();
 }
-cudaError_t launch_cycle_begin(const int *cycle_gate, int *completion_gate, int *refine_gate, int32_t *cycles,
-                               cudaStream_t st) {
-    k_cycle_begin<<<1, 1, 0, st>>>(cycle_gate, completion_gate, refine_gate, cycles);
-    return cudaGetLastError();
-}
-cudaError_t launch_cycle_end(int *cycle_gate, int *cycle_flag, cudaStream_t st) {
-    k_cycle_end<<<1, 1, 0, st>>>(cycle_gate, cycle_flag);
+cudaError_t launch_seeds_refresh(const PnView &v, PnSeed *seeds, int32_t nmax, const int32_t *n_dev, cudaStream_t st) {
+    if (nmax <= 0) return cudaSuccess;
+    k_seeds_refresh<<<grid_for(nmax, 256), 256, 0, st>>>(v, seeds, nmax, n_dev);
     return cudaGetLastError();
 }
 cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *seeds,
@@ -1144,10 +1156,10 @@ cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32
 }
 cudaError_t launch_new_targets(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *done,
                                int32_t *ndone, int32_t done_cap, PnSeed *targets, int32_t *ntargets, const int *gate,
-                               cudaStream_t st) {
+                               cudaStream_t st, PnSeed *near, int32_t *nnear, int32_t knear) {
     if (ng <= 0) return cudaSuccess;
     k_new_targets<<<grid_for((int64_t)ng * 32, 256), 256, 0, st>>>(picks, cnt, ng, kmax, done, ndone, done_cap,
-                                                                     targets, ntargets, gate);
+                                                                     targets, ntargets, gate, near, nnear, knear);
     return cudaGetLastError();
 }
 

@@ -59,17 +59,18 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
 cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, const int32_t *nseeds_dev, int dm,
                             int dp, int *improved, int grid_blocks, cudaStream_t st);
 // Device-driven rounds (see emit.cu).
-// A round or pass that lowered a cell also sets *sticky (when given).
+// Closes the round's gate when it had no work or lowered no cell; zeroes the
+// work count (and *count2 when given).
 cudaError_t launch_round_end(int *gate, int *flag, int32_t *count, int32_t *rounds, cudaStream_t st,
-                             int *sticky = nullptr);
-cudaError_t launch_cycle_begin(const int *cycle_gate, int *completion_gate, int *refine_gate, int32_t *cycles,
-                               cudaStream_t st);
-cudaError_t launch_cycle_end(int *cycle_gate, int *cycle_flag, cudaStream_t st);
+                             int32_t *count2 = nullptr);
+// Sets each of the first *n_dev seeds' partner j to its cell's current
+// neighbour (gated like the round it belongs to).
+cudaError_t launch_seeds_refresh(const PnView &v, PnSeed *seeds, int32_t nmax, const int32_t *n_dev, cudaStream_t st);
 cudaError_t launch_picks_to_seeds(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *seeds,
                                   int32_t *nseeds, const int *gate, cudaStream_t st);
 cudaError_t launch_new_targets(const PnPick *picks, const int32_t *cnt, int32_t ng, int32_t kmax, PnSeed *done,
                                int32_t *ndone, int32_t done_cap, PnSeed *targets, int32_t *ntargets, const int *gate,
-                               cudaStream_t st);
+                               cudaStream_t st, PnSeed *near = nullptr, int32_t *nnear = nullptr, int32_t knear = 0);
 // Exhaustive sieve of the mixed form on the tensor cores: every valid pair
 // of each hot class estimated through an FP16 Gram block of the z-windows
 // and only the pairs that can still lower a cell evaluated exactly

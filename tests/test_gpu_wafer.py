@@ -165,10 +165,10 @@ def test_full_size_completion_boxes_are_complete(pn, wafer):
     of its re-cut box (m +- 6, i +- 4, j +- 4; the oracle's
     completion_triples), both cells (m', i') and (m', j') hold a distance no
     larger than the pair's exact FP64 distance (within the FP32 rounding of
-    the in-stream distances).  Before the emit stage ran in cycles, a row
-    brought into the list by the refinement never had its box completed: on
-    the 5,000,000-sample series the pair one sample off the best motif was
-    0.0075 closer."""
+    the in-stream distances).  Before every refinement pass also completed
+    around its refined pairs, a row brought into the list by the refinement
+    never had its box completed: on the 5,000,000-sample series the pair one
+    sample off the best motif was 0.0075 closer."""
     from oracle import spectral
     n = wafer.x.shape[0]
     ctx = pn.Context(precision=1, topk_mode=0)
