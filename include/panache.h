@@ -137,6 +137,14 @@ extern "C" {
                                               the SMs waiting on memory), so it is not the default.  Anchors
                                               longer than 192 samples, budgets above 128, the warm start and
                                               the plain form use the per-query search in any case. */
+#define PANACHE_FLAG_TOPK_SIEVE 0x1000     /* mixed form, anchors of at most 192 samples: after the emit stage,
+                                              estimate every pair of every hot class on the tensor cores (the
+                                              Gram blocks of PANACHE_FLAG_SIEVE_GRAM) against the largest
+                                              distance of the refined top lists, evaluate exactly the pairs
+                                              that can fall below it and below one of their cells, and run
+                                              the rest of the emit stage again.  It finds the near-copy pairs
+                                              of large hot classes that the band of w sort neighbours misses;
+                                              not captured in a graph. */
 #define PANACHE_FLAG_NO_REFINE 0x200      /* skip the exact row refinement of the top list.  After local
                                               completion, every cell of the top refine_mult*k list (per group)
                                               is scanned against all its valid partners at its length with the

@@ -1,6 +1,7 @@
 // Host runtime and C ABI: planning, admission, device buffers and the
 // order of the steps (Algorithm 1 over all anchors, then Algorithm 2).
 #include <algorithm>
+#include <limits>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -885,8 +886,10 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
     // final selection) runs without the host: buffers first, then the
     // launches, replayed from a captured graph when the request's shape
     // repeats, then one wait for the results.
+    const bool topk_sieve = (c.flags & PANACHE_FLAG_TOPK_SIEVE) && c.precision == PANACHE_MIXED &&
+                            !(c.flags & PANACHE_FLAG_NO_SIEVE) && pn::sieve_gram_supported(R.a_max);
     const bool graph = (c.flags & PANACHE_FLAG_GRAPH) && !(c.flags & (PANACHE_FLAG_TIMING | PANACHE_FLAG_INDEX_ONLY)) &&
-                       ctx->last == &R;
+                       ctx->last == &R && !topk_sieve;
     if (!R.emit || !graph) {
         delete R.emit;
         R.emit = new (std::nothrow) EmitPlan();
@@ -932,6 +935,34 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
     }
     PN_CU(cudaStreamSynchronize(st));
     if (hctl[OV_FINAL]) return PANACHE_EPOOL;
+    if (topk_sieve) {
+        // The top-k sieve: every hot class's pairs estimated on the tensor
+        // cores against the largest distance of the refined lists (the
+        // reported lists when there is no refinement), the pairs that can
+        // enter a list evaluated exactly, then the rest of the emit stage
+        // once more on the lowered cells.
+        double thr = 0.0;
+        const SelBufs &lb = E.refine && E.rb.ng ? E.rb : E.fb;
+        std::vector<PnPick> lp((size_t)lb.ng * lb.kmax);
+        std::vector<int32_t> lc((size_t)lb.ng);
+        if (lb.ng) {
+            PN_CU(cudaMemcpyAsync(lp.data(), lb.out, sizeof(PnPick) * lp.size(), cudaMemcpyDeviceToHost, st));
+            PN_CU(cudaMemcpyAsync(lc.data(), lb.cnt, sizeof(int32_t) * lc.size(), cudaMemcpyDeviceToHost, st));
+            PN_CU(cudaStreamSynchronize(st));
+        }
+        bool short_list = false;
+        for (int32_t gi = 0; gi < lb.ng; ++gi) {
+            if (lc[gi] < lb.kmax) short_list = true;     // a short list takes any pair: no threshold
+            if (lc[gi] > 0) thr = std::max(thr, lp[(size_t)gi * lb.kmax + lc[gi] - 1].d);
+        }
+        if (short_list) thr = std::numeric_limits<double>::max();
+        int32_t ncls2 = 0;
+        PN_CU(pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w, 0, grid, R.a_max, st, &ncls2, thr));
+        ctx->launches += 6 + (ncls2 ? 4 + 2 * 12 + 6 : 0);
+        PN_TRY(emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl, 2));
+        PN_CU(cudaStreamSynchronize(st));
+        if (hctl[OV_FINAL]) return PANACHE_EPOOL;
+    }
     ctx->stats.completion_rounds = (uint64_t)hctl[C_ROUNDS];
     ctx->stats.refine_passes = (uint64_t)hctl[R_PASSES];
     const SelBufs &fb = E.fb;

@@ -944,7 +944,7 @@ cudaError_t sieve_t(const PnView &v, const PnClass *cls, int64_t nmem, const uin
 
 // ---------------------------------------------------------------------------
 cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t total_slots, int w, int exhaustive,
-                         int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out) {
+                         int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out, double topk_thr) {
     *n_classes_out = 0;
     if (total_slots <= 0) return cudaSuccess;
     uint32_t *flag = nullptr, *size = nullptr, *cid = nullptr, *moff = nullptr, *tot = nullptr;
@@ -991,7 +991,8 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             const int zcap = (a_max + 3) & ~3;
             pn_kt_begin(v.kt, PN_KT_SIEVE, st);
             // after the class sort, keys[p] is the class of member p
-            if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
+            if (topk_thr >= 0.0) e = launch_sieve_gram(v, cls, ncls, vals, a_max, grid_blocks, st, topk_thr);
+            else if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             else if (exhaustive == 1 && sieve_gram_supported(a_max))
                 e = launch_sieve_gram(v, cls, ncls, vals, a_max, grid_blocks, st);
             else if (exhaustive && v.x1) e = sieve_tiles_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);

@@ -126,12 +126,12 @@ struct ZgShared {
 // tile, as y = z - z_ref (the row block's reference window), and its side
 // tables (n = |y|^2); each warp takes four rows at a time, so every lane has
 // eight sample loads in flight.
-template <class Z>
+template <class Z, int NW = ZG_THREADS / 32>
 __device__ __forceinline__ void zg_stage(const PnView &v, const PnAnchor &A, const PnSeries &S, const uint32_t *members,
                                          int64_t first, int n, int a, int kp, unsigned char *tile, ZgSide &side,
                                          int *nmax, const unsigned long long *prow, const float *zref, int warp,
                                          int lane) {
-    for (int r0 = warp * 4; r0 < ZG_B; r0 += 4 * (ZG_THREADS / 32)) {
+    for (int r0 = warp * 4; r0 < ZG_B; r0 += 4 * NW) {
         uint32_t c = 0;
         float2 mm = make_float2(0.0f, 0.0f);
         if (lane < 4 && r0 + lane < n) {
@@ -185,8 +185,8 @@ __device__ __forceinline__ void zg_stage(const PnView &v, const PnAnchor &A, con
 // shared row and column minima, written to the cells once per tile.
 template <class Z>
 __device__ __forceinline__ void zg_eval4(const typename Z::X *xs, int a, const uint32_t *q, int nq,
-                                         const ZgShared &sh, unsigned long long *rkey, unsigned long long *ckey,
-                                         int lane) {
+                                         const ZgSide &SA, const ZgSide &SB, unsigned long long *rkey,
+                                         unsigned long long *ckey, int lane) {
     typename Z::M zu[4], zv[4];
     uint32_t uu[4], vv[4];
 #pragma unroll
@@ -194,16 +194,16 @@ __device__ __forceinline__ void zg_eval4(const typename Z::X *xs, int a, const u
         const uint32_t e = q[p < nq ? p : 0];
         uu[p] = e >> 16;
         vv[p] = e & 0xFFFFu;
-        zu[p].x = sh.A.m[uu[p]].x;
-        zu[p].y = sh.A.m[uu[p]].y;
-        zv[p].x = sh.B.m[vv[p]].x;
-        zv[p].y = sh.B.m[vv[p]].y;
+        zu[p].x = SA.m[uu[p]].x;
+        zu[p].y = SA.m[uu[p]].y;
+        zv[p].x = SB.m[vv[p]].x;
+        zv[p].y = SB.m[vv[p]].y;
     }
     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int r = lane; r < a; r += 32) {
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-            const float d = Z::z(zu[p], xs[sh.A.s[uu[p]] + r]) - Z::z(zv[p], xs[sh.B.s[vv[p]] + r]);
+            const float d = Z::z(zu[p], xs[SA.s[uu[p]] + r]) - Z::z(zv[p], xs[SB.s[vv[p]] + r]);
             acc[p] = fmaf(d, d, acc[p]);
         }
     }
@@ -211,8 +211,8 @@ __device__ __forceinline__ void zg_eval4(const typename Z::X *xs, int a, const u
     for (int p = 0; p < 4; ++p) {
         const float d = sqrtf(pn_warp_sum(acc[p]));
         if (lane == p && p < nq) {
-            atomicMin(&rkey[uu[p]], pn_pack_f(d, sh.B.s[vv[p]]));
-            atomicMin(&ckey[vv[p]], pn_pack_f(d, sh.A.s[uu[p]]));
+            atomicMin(&rkey[uu[p]], pn_pack_f(d, SB.s[vv[p]]));
+            atomicMin(&ckey[vv[p]], pn_pack_f(d, SA.s[uu[p]]));
         }
     }
 }
@@ -234,10 +234,14 @@ __device__ __forceinline__ float zg_colmin32(float (&dd)[32], int lane) {
     return dd[0];
 }
 
-template <class Z>
+// TOPK: the top-k sieve.  Instead of the row and column rules, a pair is
+// evaluated exactly only when its estimate minus the margin is below thr2
+// (the square of a distance the top list already holds) and below one of
+// its two cells: the pass looks only for pairs that can enter the list.
+template <class Z, bool TOPK>
 __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnClass *cls, const uint4 *tiles,
                                                             int64_t ntiles, const uint32_t *members, int kpad_max,
-                                                            unsigned long long *work) {
+                                                            unsigned long long *work, float thr2) {
     extern __shared__ __align__(1024) unsigned char zsm_raw[];
     __shared__ ZgShared sh;
     unsigned char *zsm = zsm_raw + ((1024 - (smem_u32(zsm_raw) & 1023)) & 1023);
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
             const int64_t pu = (int64_t)sh.A.s[u];
             const uint32_t tbase = taddr + ((uint32_t)(warp * 32) << 16);
             float rmin = inf;
-            for (int c0 = 0; c0 < ZG_B; c0 += 32) {
+            for (int c0 = 0; !TOPK && c0 < ZG_B; c0 += 32) {
                 uint32_t r[32];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
@@ -397,10 +401,14 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
                         const float dd = fmaxf(0.0f, nu_ + nv_ - 2.0f * __uint_as_float(r[j]));
                         const float M = 0.001953125f * (nu_ + nv_) + mabs;     // 2^-9 (|y_u|^2 + |y_v|^2) + a 2^-14
                         const float tv = sh.B.t[vc];
-                        const bool keep_u = dd - M < tu2 && dd <= rmin + tol_row;
-                        const bool keep_v = dd - M < tv * tv && dd <= __int_as_float(sh.colmin[vc]) +
-                                                                          0.00390625f * (nv_ + nmax_a) + 2.0f * mabs;
-                        s = keep_u || keep_v;
+                        if constexpr (TOPK) {
+                            s = dd - M < thr2 && (dd - M < tu2 || dd - M < tv * tv);
+                        } else {
+                            const bool keep_u = dd - M < tu2 && dd <= rmin + tol_row;
+                            const bool keep_v = dd - M < tv * tv && dd <= __int_as_float(sh.colmin[vc]) +
+                                                                              0.00390625f * (nv_ + nmax_a) + 2.0f * mabs;
+                            s = keep_u || keep_v;
+                        }
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, s);
                     if (s) sh.queue[warp][qn + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)u << 16) | (uint32_t)vc;
@@ -408,7 +416,7 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
                     if (qn > ZG_Q - 32) {                     // warp-uniform: evaluate the queued pairs
                         __syncwarp();
                         for (int e = 0; e < qn; e += 4)
-                            zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh, sh.rkey, sh.ckey, lane);
+                            zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh.A, sh.B, sh.rkey, sh.ckey, lane);
                         n_ex += (unsigned long long)qn;
                         qn = 0;
                         __syncwarp();
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
             }
             __syncwarp();
             for (int e = 0; e < qn; e += 4)
-                zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh, sh.rkey, sh.ckey, lane);
+                zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh.A, sh.B, sh.rkey, sh.ckey, lane);
             n_ex += (unsigned long long)qn;
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();                               // every warp's keys are in the tile minima
@@ -438,9 +446,214 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
     if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);
 }
 
+// The top-k sieve as its own kernel: eight warps (warps w and w + 4 read the
+// same accumulator lanes, columns 0-63 and 64-127), and a fast test per pair
+// -- one multiply-add against a per-row constant -- whose rare hits take the
+// full test.  The fast test is the exact one rearranged:
+// d~^2 - M < thr2  <=>  (1 - 2^-9) |y_v|^2 - 2 G < thr2 + a 2^-14 - (1 - 2^-9) |y_u|^2,
+// with a relative slack of 2^-20 on the right for the rearranged rounding.
+constexpr int ZT_THREADS = 256;
+constexpr int ZT_WARPS = ZT_THREADS / 32;
+constexpr int ZT_Q = 128;
+
+struct ZtShared {
+    ZgSide A, B;
+    float zref[ZG_AMAX];
+    float nbs[ZG_B];                           // (1 - 2^-9) |y_v|^2 of the column block
+    unsigned long long rkey[ZG_B], ckey[ZG_B];
+    uint32_t queue[ZT_WARPS][ZT_Q];
+    int nmax_a, nmax_b;
+    int fail;
+    uint32_t taddr;
+    __align__(8) uint64_t mbar;
+    unsigned long long run;
+};
+
 template <class Z>
+__global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnClass *cls, const uint4 *tiles,
+                                                           int64_t ntiles, const uint32_t *members, int kpad_max,
+                                                           unsigned long long *work, float thr2) {
+    extern __shared__ __align__(1024) unsigned char ztm_raw[];
+    __shared__ ZtShared sh;
+    unsigned char *ztm = ztm_raw + ((1024 - (smem_u32(ztm_raw) & 1023)) & 1023);
+    const int atoms = (kpad_max + 63) >> 6;
+    unsigned char *tA = ztm;
+    unsigned char *tB = tA + atoms * ZG_B * 128;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        sh.fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh.mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.taddr)),
+                     "r"(ZG_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = sh.taddr;
+    const uint32_t idesc = umma_idesc_f16(ZG_B, ZG_B);
+    uint32_t phase = 0;
+    unsigned long long n_ex = 0;
+    uint32_t staged_cls = 0xFFFFFFFFu, staged_bu = 0xFFFFFFFFu;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int u = quarter * 32 + lane;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sh.run = atomicAdd(work, (unsigned long long)ZG_RUN);
+        __syncthreads();
+        const int64_t run0 = (int64_t)sh.run;
+        if (run0 >= ntiles || sh.fail) break;
+        const int64_t run1 = min(ntiles, run0 + ZG_RUN);
+        for (int64_t t = run0; t < run1; ++t) {
+            const uint4 tl = tiles[t];
+            const PnClass c = cls[tl.x];
+            const PnAnchor &A = v.anchors[c.anchor];
+            const PnSeries &S = v.series[A.series];
+            const int a = A.a;
+            const int kp = (a + 15) & ~15;
+            const int excl = S.excl;
+            const int u0 = (int)tl.y * ZG_B, v0 = (int)tl.z * ZG_B;
+            const int nu = min(ZG_B, (int)c.size - u0), nv = min(ZG_B, (int)c.size - v0);
+            const bool diag = tl.y == tl.z;
+            unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
+            __syncthreads();
+            const bool new_row = tl.x != staged_cls || tl.y != staged_bu;
+            if (tid == 0) {
+                if (new_row) sh.nmax_a = 0;
+                sh.nmax_b = 0;
+            }
+            if (tid < ZG_B) {
+                sh.rkey[tid] = PN_EMPTY_KEY;
+                sh.ckey[tid] = PN_EMPTY_KEY;
+            }
+            if (new_row) {
+                const uint32_t cr = members[(int64_t)c.moff + u0];
+                const auto mref = Z::load(v, A.win_off + cr);
+                const auto *xref = Z::samples(v, S.x_off + cr);
+                for (int k = tid; k < kp; k += ZT_THREADS) sh.zref[k] = k < a ? Z::z(mref, xref[k]) : 0.0f;
+                __syncthreads();
+                zg_stage<Z, ZT_WARPS>(v, A, S, members, (int64_t)c.moff + u0, nu, a, kp, tA, sh.A, &sh.nmax_a, prow,
+                                      sh.zref, warp, lane);
+            } else {
+                __syncthreads();
+            }
+            zg_stage<Z, ZT_WARPS>(v, A, S, members, (int64_t)c.moff + v0, nv, a, kp, tB, sh.B, &sh.nmax_b, prow,
+                                  sh.zref, warp, lane);
+            staged_cls = tl.x;
+            staged_bu = tl.y;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid < ZG_B) sh.nbs[tid] = 0.998046875f * sh.B.n[tid];       // (1 - 2^-9) |y_v|^2
+            if (tid == 0) {
+                const uint32_t a0 = smem_u32(tA), b0 = smem_u32(tB);
+                for (int s2 = 0; s2 < kp / 16; ++s2) {
+                    const uint32_t off = (uint32_t)((s2 >> 2) * ZG_B * 128 + (s2 & 3) * 32);
+                    const uint64_t ad = sw128_desc(a0 + off), bd = sw128_desc(b0 + off);
+                    const uint32_t acc = s2 > 0 ? 1u : 0u;
+                    asm volatile("{ .reg .pred p; setp.ne.u32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
+                                 ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&sh.mbar))
+                             : "memory");
+            }
+            if (!mbar_wait(smem_u32(&sh.mbar), phase, ZG_SPIN)) {
+                if (lane == 0) atomicExch(&sh.fail, 1);
+            }
+            phase ^= 1u;
+            __syncthreads();
+            if (sh.fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+            const bool urow = u < nu && sh.A.m[u].x != 0.0f;
+            const float nu_ = sh.A.n[u];
+            const float mabs = (float)a * 6.1035156e-05f;                    // a 2^-14
+            // fast bound: (1 - 2^-9) |y_v|^2 - 2 G < ku  (+ slack)
+            const float ku = urow ? (thr2 + mabs - 0.998046875f * nu_) * (1.0f + 9.5367432e-07f) +
+                                        9.5367432e-07f * (thr2 + mabs + nu_)
+                                  : -__int_as_float(0x7f800000);
+            const float tu2 = sh.A.t[u] * sh.A.t[u];
+            const int64_t pu = (int64_t)sh.A.s[u];
+            const auto *xs = Z::samples(v, S.x_off);
+            const uint32_t tbase = taddr + ((uint32_t)(quarter * 32) << 16);
+            int qn = 0;
+            for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
+                uint32_t r[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                    "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(tbase + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                uint32_t hit = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    hit |= (fmaf(-2.0f, __uint_as_float(r[j]), sh.nbs[c0 + j]) < ku ? 1u : 0u) << j;
+                if (!__any_sync(0xffffffffu, hit != 0u)) continue;        // the common case: no pair near the list
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int vc = c0 + j;
+                    bool keep = ((hit >> j) & 1u) && vc < nv && (!diag || u < vc) && sh.B.m[vc].x != 0.0f;
+                    if (keep) keep = llabs(pu - (int64_t)sh.B.s[vc]) >= excl;
+                    if (keep) {
+                        const float nv_ = sh.B.n[vc];
+                        const float dd = fmaxf(0.0f, nu_ + nv_ - 2.0f * __uint_as_float(r[j]));
+                        const float M = 0.001953125f * (nu_ + nv_) + mabs;
+                        const float tv = sh.B.t[vc];
+                        keep = dd - M < thr2 && (dd - M < tu2 || dd - M < tv * tv);
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+                    if (keep) sh.queue[warp][qn + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)u << 16) | (uint32_t)vc;
+                    qn += __popc(bal);
+                    if (qn > ZT_Q - 32) {
+                        __syncwarp();
+                        for (int e = 0; e < qn; e += 4)
+                            zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh.A, sh.B, sh.rkey, sh.ckey, lane);
+                        n_ex += (unsigned long long)qn;
+                        qn = 0;
+                        __syncwarp();
+                    }
+                }
+            }
+            __syncwarp();
+            for (int e = 0; e < qn; e += 4)
+                zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh.A, sh.B, sh.rkey, sh.ckey, lane);
+            n_ex += (unsigned long long)qn;
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tid < ZG_B) {
+                if (sh.rkey[tid] != PN_EMPTY_KEY) atomicMin(&prow[sh.A.s[tid]], sh.rkey[tid]);
+                if (sh.ckey[tid] != PN_EMPTY_KEY) atomicMin(&prow[sh.B.s[tid]], sh.ckey[tid]);
+            }
+        }
+        if (sh.fail) break;
+    }
+    __syncthreads();
+    if (sh.fail && tid == 0) {
+        atomicExch(v.err, PN_ERR_TC_TIMEOUT);
+        mbar_wait(smem_u32(&sh.mbar), phase ^ 1u, ZG_SPIN);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ZG_TMEM_COLS));
+    if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);
+}
+
+template <class Z, bool TOPK>
 cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int a_max,
-                          int grid_blocks, cudaStream_t st) {
+                          int grid_blocks, float thr2, cudaStream_t st) {
     uint32_t *cnt = nullptr, *off = nullptr, *tot = nullptr;
     unsigned long long *tot64 = nullptr;
     uint4 *tiles = nullptr;
@@ -471,11 +684,20 @@ cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, con
         const int kpad = (a_max + 15) & ~15;
         const int atoms = (kpad + 63) >> 6;
         const size_t sm = 1024 + (size_t)atoms * 2 * ZG_B * 128;
-        e = pn_allow_smem(k_sieve_zgram<Z>, sm);
-        if (e == cudaSuccess) {
-            const int64_t g = std::min<int64_t>((ntiles + ZG_RUN - 1) / ZG_RUN, (int64_t)grid_blocks);
-            k_sieve_zgram<Z><<<(unsigned)g, ZG_THREADS, sm, st>>>(v, cls, tiles, ntiles, vals, kpad, work);
-            e = cudaGetLastError();
+        const int64_t g = std::min<int64_t>((ntiles + ZG_RUN - 1) / ZG_RUN, (int64_t)grid_blocks);
+        if constexpr (TOPK) {
+            e = pn_allow_smem(k_sieve_topk<Z>, sm);
+            if (e == cudaSuccess) {
+                k_sieve_topk<Z><<<(unsigned)g, ZT_THREADS, sm, st>>>(v, cls, tiles, ntiles, vals, kpad, work, thr2);
+                e = cudaGetLastError();
+            }
+        } else {
+            e = pn_allow_smem(k_sieve_zgram<Z, false>, sm);
+            if (e == cudaSuccess) {
+                k_sieve_zgram<Z, false><<<(unsigned)g, ZG_THREADS, sm, st>>>(v, cls, tiles, ntiles, vals, kpad, work,
+                                                                             thr2);
+                e = cudaGetLastError();
+            }
         }
     }
     for (void *p : {(void *)cnt, (void *)off, (void *)tot, (void *)tot64, (void *)tiles})
@@ -488,10 +710,16 @@ cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, con
 bool sieve_gram_supported(int a_max) { return a_max <= ZG_AMAX; }
 
 cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int a_max,
-                              int grid_blocks, cudaStream_t st) {
+                              int grid_blocks, cudaStream_t st, double topk_thr) {
     if (ncls <= 0) return cudaSuccess;
-    if (v.x1) return sieve_zgram_t<ZMix1>(v, cls, ncls, vals, a_max, grid_blocks, st);
-    return sieve_zgram_t<ZMix2>(v, cls, ncls, vals, a_max, grid_blocks, st);
+    if (topk_thr >= 0.0) {
+        const float t = (float)topk_thr;
+        const float thr2 = t * t * (1.0f + 1e-6f) + 1e-12f;       // FP32 rounding of the square
+        if (v.x1) return sieve_zgram_t<ZMix1, true>(v, cls, ncls, vals, a_max, grid_blocks, thr2, st);
+        return sieve_zgram_t<ZMix2, true>(v, cls, ncls, vals, a_max, grid_blocks, thr2, st);
+    }
+    if (v.x1) return sieve_zgram_t<ZMix1, false>(v, cls, ncls, vals, a_max, grid_blocks, 0.0f, st);
+    return sieve_zgram_t<ZMix2, false>(v, cls, ncls, vals, a_max, grid_blocks, 0.0f, st);
 }
 
 }  // namespace pn

@@ -120,6 +120,23 @@ def test_prefix_gram_sieve_matches_dense(pn, wafer):
           f"dense {ed} in {d.kernel_times()['sieve'][0]:.1f} ms")
 
 
+def test_prefix_topk_sieve_matches_exhaustive(pn, wafer):
+    """The top-k sieve (tensor-core Gram blocks of every hot class against
+    the refined list's largest distance) reports the motifs of the dense
+    exhaustive sieve, which evaluates every pair of every hot class, with a
+    small fraction of its exact evaluations; on the prefix and on 1M."""
+    for n in (200_000, 1_000_000):
+        x = np.ascontiguousarray(wafer.x[:n])
+        t = pn.Context(precision=1, topk_mode=0, flags=pn.FLAG_TOPK_SIEVE)
+        mt = t.pmp(x, 100, 150, 20, 150)
+        d = pn.Context(precision=1, topk_mode=0, flags=pn.FLAG_EXHAUSTIVE_SIEVE)
+        md = d.pmp(x, 100, 150, 20, 150)
+        assert np.array_equal(mt[["m", "i", "j"]], md[["m", "i", "j"]]), n
+        assert np.allclose(mt["d"], md["d"], rtol=1e-12, atol=0)
+        assert t.stats()["exact_sieve"] < d.stats()["exact_sieve"] / 10
+        print(f"n={n}: top-k sieve {t.stats()['exact_sieve']} exact pairs, exhaustive {d.stats()['exact_sieve']}")
+
+
 def test_5m_reported_cells_are_exact(pn):
     """The benchmark's workload (5,000,000 samples, mixed precision): every
     reported motif's distance is the oracle's exact nearest-neighbour distance
