@@ -131,24 +131,36 @@ __device__ __forceinline__ void zg_stage(const PnView &v, const PnAnchor &A, con
                                          int64_t first, int n, int a, int kp, unsigned char *tile, ZgSide &side,
                                          int *nmax, const unsigned long long *prow, const float *zref, int warp,
                                          int lane) {
-    for (int r0 = warp * 4; r0 < ZG_B; r0 += 4 * NW) {
-        uint32_t c = 0;
-        float2 mm = make_float2(0.0f, 0.0f);
-        if (lane < 4 && r0 + lane < n) {
-            c = members[first + r0 + lane];
-            const auto m = Z::load(v, A.win_off + c);
-            mm = make_float2(m.x, m.y);
+    // every row of this warp (rows warp*4 + 4*NW*g + r) has its member and
+    // moments loaded up front, one per lane, so that only the sample loads
+    // wait inside the row loop
+    constexpr int RPW = ZG_B / NW;                 // rows per warp
+    static_assert(RPW <= 32, "one lane per row of the warp");
+    uint32_t c_l = 0;
+    float2 m_l = make_float2(0.0f, 0.0f);
+    unsigned long long k_l = PN_EMPTY_KEY;
+    {
+        const int g = lane >> 2, r = lane & 3;
+        const int row = warp * 4 + 4 * NW * g + r;
+        if (lane < RPW && row < n) {
+            c_l = members[first + row];
+            const auto m = Z::load(v, A.win_off + c_l);
+            m_l = make_float2(m.x, m.y);
+            k_l = __ldcg(&prow[c_l]);
         }
+    }
+    for (int r0 = warp * 4, gi = 0; r0 < ZG_B; r0 += 4 * NW, ++gi) {
         uint32_t cr[4];
         typename Z::M mr[4];
         const typename Z::X *xr[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            cr[r] = __shfl_sync(0xffffffffu, c, r);
-            mr[r].x = __shfl_sync(0xffffffffu, mm.x, r);
-            mr[r].y = __shfl_sync(0xffffffffu, mm.y, r);
+            cr[r] = __shfl_sync(0xffffffffu, c_l, gi * 4 + r);
+            mr[r].x = __shfl_sync(0xffffffffu, m_l.x, gi * 4 + r);
+            mr[r].y = __shfl_sync(0xffffffffu, m_l.y, gi * 4 + r);
             xr[r] = Z::samples(v, S.x_off + cr[r]);
         }
+        const unsigned long long kr = __shfl_sync(0xffffffffu, k_l, gi * 4 + (lane & 3));
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int k = 2 * lane; k < kp; k += 64) {
             float z0[4], z1[4];
@@ -173,7 +185,7 @@ __device__ __forceinline__ void zg_stage(const PnView &v, const PnAnchor &A, con
                 side.s[row] = ok ? cr[r] : 0u;
                 side.m[row] = ok ? make_float2(mr[r].x, mr[r].y) : make_float2(0.0f, 0.0f);
                 side.n[row] = nr;
-                side.t[row] = ok ? pn_key_distf(__ldcg(&prow[cr[r]])) : 0.0f;
+                side.t[row] = ok ? pn_key_distf(kr) : 0.0f;
                 if (ok && mr[r].x != 0.0f) atomicMax(nmax, __float_as_int(nr));
             }
         }
@@ -455,11 +467,12 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
 constexpr int ZT_THREADS = 256;
 constexpr int ZT_WARPS = ZT_THREADS / 32;
 constexpr int ZT_Q = 128;
+constexpr int ZT_RUN = 16;          // tiles a block draws at a time (one row block mostly: A staged once)
 
 struct ZtShared {
     ZgSide A, B;
     float zref[ZG_AMAX];
-    float nbs[ZG_B];                           // (1 - 2^-9) |y_v|^2 of the column block
+    float2 nbt[ZG_B];                          // ((1 - 2^-9) |y_v|^2, P[v]^2) of the column block
     unsigned long long rkey[ZG_B], ckey[ZG_B];
     uint32_t queue[ZT_WARPS][ZT_Q];
     int nmax_a, nmax_b;
@@ -504,11 +517,11 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
 
     for (;;) {
         __syncthreads();
-        if (tid == 0) sh.run = atomicAdd(work, (unsigned long long)ZG_RUN);
+        if (tid == 0) sh.run = atomicAdd(work, (unsigned long long)ZT_RUN);
         __syncthreads();
         const int64_t run0 = (int64_t)sh.run;
         if (run0 >= ntiles || sh.fail) break;
-        const int64_t run1 = min(ntiles, run0 + ZG_RUN);
+        const int64_t run1 = min(ntiles, run0 + ZT_RUN);
         for (int64_t t = run0; t < run1; ++t) {
             const uint4 tl = tiles[t];
             const PnClass c = cls[tl.x];
@@ -550,7 +563,7 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (tid < ZG_B) sh.nbs[tid] = 0.998046875f * sh.B.n[tid];       // (1 - 2^-9) |y_v|^2
+            if (tid < ZG_B) sh.nbt[tid] = make_float2(0.998046875f * sh.B.n[tid], sh.B.t[tid] * sh.B.t[tid]);
             if (tid == 0) {
                 const uint32_t a0 = smem_u32(tA), b0 = smem_u32(tB);
                 for (int s2 = 0; s2 < kp / 16; ++s2) {
@@ -575,11 +588,12 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
             const bool urow = u < nu && sh.A.m[u].x != 0.0f;
             const float nu_ = sh.A.n[u];
             const float mabs = (float)a * 6.1035156e-05f;                    // a 2^-14
-            // fast bound: (1 - 2^-9) |y_v|^2 - 2 G < ku  (+ slack)
-            const float ku = urow ? (thr2 + mabs - 0.998046875f * nu_) * (1.0f + 9.5367432e-07f) +
-                                        9.5367432e-07f * (thr2 + mabs + nu_)
-                                  : -__int_as_float(0x7f800000);
             const float tu2 = sh.A.t[u] * sh.A.t[u];
+            // fast bound: (1 - 2^-9) |y_v|^2 - 2 G < min(thr2, max(P[u]^2, P[v]^2)) + cu, with
+            // cu = a 2^-14 - (1 - 2^-9) |y_u|^2 and a slack of 2^-20 of the magnitudes involved
+            const float slack = 9.5367432e-07f * (thr2 + mabs + nu_ + 1.0f);
+            const float cu = urow ? mabs - 0.998046875f * nu_ + slack : -__int_as_float(0x7f800000);
+            const float kt = thr2 + cu, ku = tu2 + cu;
             const int64_t pu = (int64_t)sh.A.s[u];
             const auto *xs = Z::samples(v, S.x_off);
             const uint32_t tbase = taddr + ((uint32_t)(quarter * 32) << 16);
@@ -598,8 +612,11 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 uint32_t hit = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    hit |= (fmaf(-2.0f, __uint_as_float(r[j]), sh.nbs[c0 + j]) < ku ? 1u : 0u) << j;
+                for (int j = 0; j < 32; ++j) {
+                    const float2 nt = sh.nbt[c0 + j];
+                    const float lim = fminf(kt, fmaxf(ku, nt.y + cu));
+                    hit |= (fmaf(-2.0f, __uint_as_float(r[j]), nt.x) < lim ? 1u : 0u) << j;
+                }
                 if (!__any_sync(0xffffffffu, hit != 0u)) continue;        // the common case: no pair near the list
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -684,7 +701,8 @@ cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, con
         const int kpad = (a_max + 15) & ~15;
         const int atoms = (kpad + 63) >> 6;
         const size_t sm = 1024 + (size_t)atoms * 2 * ZG_B * 128;
-        const int64_t g = std::min<int64_t>((ntiles + ZG_RUN - 1) / ZG_RUN, (int64_t)grid_blocks);
+        const int run = TOPK ? ZT_RUN : ZG_RUN;
+        const int64_t g = std::min<int64_t>((ntiles + run - 1) / run, (int64_t)grid_blocks);
         if constexpr (TOPK) {
             e = pn_allow_smem(k_sieve_topk<Z>, sm);
             if (e == cudaSuccess) {
