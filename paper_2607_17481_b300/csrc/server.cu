@@ -7,8 +7,8 @@
 // estimate) from the server budget before it runs and releases it when its
 // results are on the host; a request larger than the whole budget is refused
 // at submission (PANACHE_EBUDGET).  With a deadline set, a request whose
-// predicted wait -- the work queued ahead of it and its own, in
-// windows x lengths, over the server's measured throughput -- exceeds the
+// predicted wait -- the work on the GPU and queued ahead of it and its own,
+// in windows x lengths, over the server's measured throughput -- exceeds the
 // deadline is refused at submission (PANACHE_EBUSY): above capacity the
 // server sheds load instead of letting every request's latency grow.  A
 // stream snapshot is refused the same way when the snapshots queued ahead
@@ -120,9 +120,10 @@ struct panache_server {
     std::deque<std::shared_ptr<LiveStream>> stream_work;
     std::condition_variable cv_stream;
     std::vector<std::thread> stream_workers;
-    // deadline admission: queued work and the measured throughput
+    // deadline admission: work in flight and queued, and the measured throughput
     double deadline_ms = 0.0;
     uint64_t queued_wl = 0;
+    uint64_t inflight_wl = 0;                // windows x lengths of the batches on the GPU
     double rate_wl_per_ms = 0.0;             // per batch, smoothed; times the slots for the server
     std::deque<std::pair<double, uint64_t>> recent;   // (completion time, windows x lengths), last 2 s
     uint64_t snaps_queued = 0;               // snapshots accepted and not yet served
@@ -189,6 +190,7 @@ void panache_server::worker(int slot) {
                 if (!fits || !in_share) break;
                 fp += j.footprint;
                 queued_wl -= std::min<uint64_t>(queued_wl, (uint64_t)windows_lengths(j.s));
+                inflight_wl += (uint64_t)windows_lengths(j.s);
                 batch.push_back(std::move(queue.front()));
                 queue.pop_front();
             }
@@ -212,6 +214,7 @@ void panache_server::worker(int slot) {
             std::lock_guard<std::mutex> lk(mu);
             in_use -= fp;
             --running;
+            for (auto &j : batch) inflight_wl -= std::min<uint64_t>(inflight_wl, (uint64_t)windows_lengths(j.s));
             if (rc == PANACHE_OK && t > t_start) {
                 uint64_t bw = 0;
                 for (auto &j : batch) bw += (uint64_t)windows_lengths(j.s);
@@ -347,11 +350,11 @@ static int enqueue(panache_server *sv, Job &&j, uint64_t *ticket) {
         std::lock_guard<std::mutex> lk(sv->mu);
         const double rate = sv->request_rate(now_ms());
         if (sv->deadline_ms > 0.0 && rate > 0.0) {
-            // predicted wait: the work queued ahead and this request's own, at
-            // the server's measured throughput; a quarter of the deadline is
-            // kept for the error of that estimate (the live streams share the
-            // GPU and move the rate)
-            if ((double)(sv->queued_wl + w) / rate > kDeadlineShare * sv->deadline_ms) {
+            // predicted wait: the work on the GPU and queued ahead and this
+            // request's own, at the server's measured throughput; a quarter of
+            // the deadline is kept for the error of that estimate (the live
+            // streams share the GPU and move the rate)
+            if ((double)(sv->inflight_wl + sv->queued_wl + w) / rate > kDeadlineShare * sv->deadline_ms) {
                 ++sv->refused;
                 return PANACHE_EBUSY;
             }
