@@ -124,24 +124,23 @@ struct ZgShared {
 
 // Stages block `first .. first + n` of class members into a swizzled FP16
 // tile, as y = z - z_ref (the row block's reference window), and its side
-// tables (n = |y|^2); each warp takes four rows at a time, so every lane has
-// eight sample loads in flight.
-template <class Z, int NW = ZG_THREADS / 32>
+// tables (n = |y|^2).  NW warps take RPG rows at a time each (rows
+// warp RPG + RPG NW g + r), so every lane has 2 RPG sample loads in flight;
+// each warp's rows have their member, moments and cell loaded up front, one
+// per lane, so that only the sample loads wait inside the row loop.
+template <class Z, int NW = ZG_THREADS / 32, int RPG = 4>
 __device__ __forceinline__ void zg_stage(const PnView &v, const PnAnchor &A, const PnSeries &S, const uint32_t *members,
                                          int64_t first, int n, int a, int kp, unsigned char *tile, ZgSide &side,
                                          int *nmax, const unsigned long long *prow, const float *zref, int warp,
                                          int lane) {
-    // every row of this warp (rows warp*4 + 4*NW*g + r) has its member and
-    // moments loaded up front, one per lane, so that only the sample loads
-    // wait inside the row loop
     constexpr int RPW = ZG_B / NW;                 // rows per warp
-    static_assert(RPW <= 32, "one lane per row of the warp");
+    static_assert(RPW <= 32 && RPW % RPG == 0, "one lane per row of the warp");
     uint32_t c_l = 0;
     float2 m_l = make_float2(0.0f, 0.0f);
     unsigned long long k_l = PN_EMPTY_KEY;
     {
-        const int g = lane >> 2, r = lane & 3;
-        const int row = warp * 4 + 4 * NW * g + r;
+        const int g = lane / RPG, r = lane % RPG;
+        const int row = warp * RPG + RPG * NW * g + r;
         if (lane < RPW && row < n) {
             c_l = members[first + row];
             const auto m = Z::load(v, A.win_off + c_l);
@@ -149,35 +148,37 @@ __device__ __forceinline__ void zg_stage(const PnView &v, const PnAnchor &A, con
             k_l = __ldcg(&prow[c_l]);
         }
     }
-    for (int r0 = warp * 4, gi = 0; r0 < ZG_B; r0 += 4 * NW, ++gi) {
-        uint32_t cr[4];
-        typename Z::M mr[4];
-        const typename Z::X *xr[4];
+    for (int r0 = warp * RPG, gi = 0; r0 < ZG_B; r0 += RPG * NW, ++gi) {
+        uint32_t cr[RPG];
+        typename Z::M mr[RPG];
+        const typename Z::X *xr[RPG];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            cr[r] = __shfl_sync(0xffffffffu, c_l, gi * 4 + r);
-            mr[r].x = __shfl_sync(0xffffffffu, m_l.x, gi * 4 + r);
-            mr[r].y = __shfl_sync(0xffffffffu, m_l.y, gi * 4 + r);
+        for (int r = 0; r < RPG; ++r) {
+            cr[r] = __shfl_sync(0xffffffffu, c_l, gi * RPG + r);
+            mr[r].x = __shfl_sync(0xffffffffu, m_l.x, gi * RPG + r);
+            mr[r].y = __shfl_sync(0xffffffffu, m_l.y, gi * RPG + r);
             xr[r] = Z::samples(v, S.x_off + cr[r]);
         }
-        const unsigned long long kr = __shfl_sync(0xffffffffu, k_l, gi * 4 + (lane & 3));
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int k = 2 * lane; k < kp; k += 64) {
-            float z0[4], z1[4];
+        const unsigned long long kr = __shfl_sync(0xffffffffu, k_l, gi * RPG + (lane % RPG));
+        float acc[RPG];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < RPG; ++r) acc[r] = 0.0f;
+        for (int k = 2 * lane; k < kp; k += 64) {
+            float z0[RPG], z1[RPG];
+#pragma unroll
+            for (int r = 0; r < RPG; ++r) {
                 const bool ok = r0 + r < n;
                 z0[r] = (ok && k < a) ? Z::z(mr[r], xr[r][k]) - zref[k] : 0.0f;
                 z1[r] = (ok && k + 1 < a) ? Z::z(mr[r], xr[r][k + 1]) - zref[k + 1] : 0.0f;
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < RPG; ++r) {
                 acc[r] = fmaf(z0[r], z0[r], fmaf(z1[r], z1[r], acc[r]));
                 *reinterpret_cast<__half2 *>(tile + sw128_off(r0 + r, k, ZG_B)) = __floats2half2_rn(z0[r], z1[r]);
             }
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < RPG; ++r) {
             const float nr = pn_warp_sum(acc[r]);
             if (lane == r) {
                 const int row = r0 + r;
@@ -186,7 +187,7 @@ __device__ __forceinline__ void zg_stage(const PnView &v, const PnAnchor &A, con
                 side.m[row] = ok ? make_float2(mr[r].x, mr[r].y) : make_float2(0.0f, 0.0f);
                 side.n[row] = nr;
                 side.t[row] = ok ? pn_key_distf(kr) : 0.0f;
-                if (ok && mr[r].x != 0.0f) atomicMax(nmax, __float_as_int(nr));
+                if (nmax && ok && mr[r].x != 0.0f) atomicMax(nmax, __float_as_int(nr));
             }
         }
     }
