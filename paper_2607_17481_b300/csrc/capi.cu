@@ -591,9 +591,11 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables, 
         // the emit stage alone reads samples, prefix sums, run lengths and rows
         PN_CU(R.alloc(R.d_ser, nser));
         PN_CU(R.alloc(R.x, R.total_samples));
-        PN_CU(R.alloc(R.xs, R.total_samples));
-        if (want_x1) PN_CU(R.alloc(R.x1, R.total_samples));
+        PN_CU(R.alloc(R.xs, R.total_samples + PN_SAMPLE_PAD));
+        if (want_x1) PN_CU(R.alloc(R.x1, R.total_samples + PN_SAMPLE_PAD));
         PN_CU(R.alloc(R.sq, R.total_samples + nser));
+        PN_CU(cudaMemsetAsync(R.xs + R.total_samples, 0, sizeof(float2) * PN_SAMPLE_PAD, st));
+        if (want_x1) PN_CU(cudaMemsetAsync(R.x1 + R.total_samples, 0, sizeof(float) * PN_SAMPLE_PAD, st));
         PN_CU(R.alloc(R.shift, nser));
         PN_CU(R.alloc(R.runlen, R.total_samples));
         PN_CU(R.alloc(R.prof, R.total_cells));
@@ -610,9 +612,11 @@ int alloc_state(panache_ctx *ctx, PnRequest &R, bool want_x1, bool full_tables, 
     PN_CU(R.alloc(R.d_lev, (int64_t)R.lev.size()));
     PN_CU(R.alloc(R.d_slot_off, nanc));
     PN_CU(R.alloc(R.x, R.total_samples));
-    PN_CU(R.alloc(R.xs, R.total_samples));
-    if (want_x1) PN_CU(R.alloc(R.x1, R.total_samples));
+    PN_CU(R.alloc(R.xs, R.total_samples + PN_SAMPLE_PAD));
+    if (want_x1) PN_CU(R.alloc(R.x1, R.total_samples + PN_SAMPLE_PAD));
     PN_CU(R.alloc(R.sq, R.total_samples + nser));
+    PN_CU(cudaMemsetAsync(R.xs + R.total_samples, 0, sizeof(float2) * PN_SAMPLE_PAD, st));
+    if (want_x1) PN_CU(cudaMemsetAsync(R.x1 + R.total_samples, 0, sizeof(float) * PN_SAMPLE_PAD, st));
     PN_CU(R.alloc(R.shift, nser));
     PN_CU(R.alloc(R.runlen, R.total_samples));
     if (c.flags & PANACHE_FLAG_HALF_FEATURES) PN_CU(R.alloc(R.Fh, R.total_rows * PN_FEAT));

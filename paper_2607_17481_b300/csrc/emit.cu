@@ -991,10 +991,10 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             const int zcap = (a_max + 3) & ~3;
             pn_kt_begin(v.kt, PN_KT_SIEVE, st);
             // after the class sort, keys[p] is the class of member p
-            if (topk_thr >= 0.0) e = launch_sieve_gram(v, cls, ncls, vals, a_max, grid_blocks, st, topk_thr);
+            if (topk_thr >= 0.0) e = launch_sieve_gram(v, cls, ncls, vals, nmem, a_max, grid_blocks, st, topk_thr);
             else if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             else if (exhaustive == 1 && sieve_gram_supported(a_max))
-                e = launch_sieve_gram(v, cls, ncls, vals, a_max, grid_blocks, st);
+                e = launch_sieve_gram(v, cls, ncls, vals, nmem, a_max, grid_blocks, st);
             else if (exhaustive && v.x1) e = sieve_tiles_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);
             else if (exhaustive) e = sieve_tiles_t<ZMix2>(v, cls, ncls, vals, grid_blocks, st);
             else if (w <= SB_WMAX && v.x1) e = sieve_band_t<ZMix1>(v, cls, nmem, keys, vals, w, grid_blocks, st);

@@ -78,9 +78,10 @@ cudaError_t launch_new_targets(const PnPick *picks, const int32_t *cnt, int32_t 
 // (gram.cu); anchors of at most 192 samples.
 bool sieve_gram_supported(int a_max);
 // With topk_thr >= 0, the top-k sieve: only pairs whose estimate can fall
-// below topk_thr (and below one of their cells) are evaluated.
-cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int a_max,
-                              int grid_blocks, cudaStream_t st, double topk_thr = -1.0);
+// below topk_thr (and below one of their cells) are evaluated, over the
+// tiles that the pivot order leaves (nmem members in all classes).
+cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int64_t nmem,
+                              int a_max, int grid_blocks, cudaStream_t st, double topk_thr = -1.0);
 // Exact row refinement: each target cell (series, m, i) scanned against
 // every valid partner at its length; `improved` set when a cell decreased.
 // max_windows bounds the partners of any target (the longest series).

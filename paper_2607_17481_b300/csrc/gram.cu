@@ -102,6 +102,139 @@ __global__ void k_zg_tile_fill(const PnClass *cls, int32_t ncls, const uint32_t 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pivot order of the top-k sieve.  Each member p of a class gets
+// r_p = |z_p - z_c|, its distance to the class's first member c in the exact
+// pass's FP32 z-values, and every class is re-sorted by r.  A pair (u, v) is
+// at least |r_u - r_v| apart (triangle inequality), so in r order a column
+// block bv whose smallest r exceeds row block bu's largest by more than T
+// holds no pair of bu closer than T, and neither does any later column
+// block: the tile table lists, per row block, only the column blocks before
+// the first such one.
+//
+// Rounding: r~ is an FP32 norm of FP32 differences (a warp tree over at
+// most 192 squares), |r~ - r| <= 2^-19 r for the z-values the exact pass
+// uses, and the exact pass's distance d_f is within 2^-19 d of their true
+// distance d.  A block pair is skipped only when
+//   lo (1 - 2^-12) - hi (1 + 2^-12) > T (1 + 2^-12) + 2^-12,
+// which leaves every skipped pair with d_f above the list threshold's FP32
+// square root (T (1 + 5e-7) + 1e-6) by a wide margin.
+// ---------------------------------------------------------------------------
+constexpr float ZT_PIV_SLACK = 2.44140625e-4f;     // 2^-12
+
+__device__ __forceinline__ bool zt_far(float lo, float hi, float T) {
+    return lo * (1.0f - ZT_PIV_SLACK) - hi * (1.0f + ZT_PIV_SLACK) > T * (1.0f + ZT_PIV_SLACK) + ZT_PIV_SLACK;
+}
+
+// One warp per member: r (by position in the class-sorted member list), the
+// sort key (the bits of r >= 0 order like r) and the position itself.
+template <class Z>
+__global__ void k_zt_pivot(PnView v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int64_t nmem, float *r,
+                           uint32_t *keys, uint32_t *idx) {
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= nmem) return;
+    const int ci = pn_find(cls, ncls, p, [](const PnClass &c) { return (int64_t)c.moff; });
+    const PnClass c = cls[ci];
+    const PnAnchor &A = v.anchors[c.anchor];
+    const PnSeries &S = v.series[A.series];
+    const uint32_t su = vals[p], sc = vals[c.moff];
+    const auto mu = Z::load(v, A.win_off + su), mc = Z::load(v, A.win_off + sc);
+    const auto *xu = Z::samples(v, S.x_off + su);
+    const auto *xc = Z::samples(v, S.x_off + sc);
+    float acc = 0.0f;
+    for (int k = lane; k < A.a; k += 32) {
+        const float d = Z::z(mu, xu[k]) - Z::z(mc, xc[k]);
+        acc = fmaf(d, d, acc);
+    }
+    const float rr = sqrtf(pn_warp_sum(acc));
+    if (lane == 0) {
+        r[p] = rr;
+        keys[p] = __float_as_uint(rr);
+        idx[p] = (uint32_t)p;
+    }
+}
+
+// After the sort by r: the class of each position, for the stable class sort.
+__global__ void k_zt_rekey(const PnClass *cls, int32_t ncls, int64_t nmem, uint32_t *keys, const uint32_t *idx) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nmem) return;
+    keys[q] = (uint32_t)pn_find(cls, ncls, (int64_t)idx[q], [](const PnClass &c) { return (int64_t)c.moff; });
+}
+
+// After the class sort: position q's record (start, 1/sigma, -mu/sigma, r),
+// the one 16-byte load a staging lane needs per row.
+template <class Z>
+__global__ void k_zt_records(PnView v, const PnClass *cls, const uint32_t *vals, const float *r, const uint32_t *idx,
+                             const uint32_t *cid, int64_t nmem, uint4 *rec) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nmem) return;
+    const uint32_t p = idx[q];
+    const uint32_t s = vals[p];
+    const auto m = Z::load(v, v.anchors[cls[cid[q]].anchor].win_off + s);
+    rec[q] = make_uint4(s, __float_as_uint(m.x), __float_as_uint(m.y), __float_as_uint(r[p]));
+}
+
+__global__ void k_zt_blocks(const PnClass *cls, int32_t ncls, uint32_t *nb) {
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci < ncls) nb[ci] = (cls[ci].size + ZG_B - 1) / ZG_B;
+}
+
+// Row g = (class, bu): its tiles are bv = bu .. e, e the last column block
+// not far from bu (far is monotone in bv: the blocks' smallest r ascend).
+__device__ __forceinline__ float zt_r(const uint4 *rec, int64_t q) { return __uint_as_float(rec[q].w); }
+
+__device__ __forceinline__ void zt_row(const PnClass *cls, int32_t ncls, const uint32_t *roff, const uint4 *rec,
+                                       float T, int64_t g, int &ci, uint32_t &bu, uint32_t &e) {
+    ci = pn_find(roff, ncls, g, [](uint32_t o) { return (int64_t)o; });
+    const PnClass c = cls[ci];
+    const uint32_t nb = (c.size + ZG_B - 1) / ZG_B;
+    bu = (uint32_t)(g - roff[ci]);
+    const float hi = zt_r(rec, (int64_t)c.moff + min((int64_t)c.size, ((int64_t)bu + 1) * ZG_B) - 1);
+    uint32_t lo_b = bu, hi_b = nb - 1;                  // zt_far(lo(bu), hi) is false
+    while (lo_b < hi_b) {
+        const uint32_t mid = (lo_b + hi_b + 1) >> 1;
+        if (zt_far(zt_r(rec, (int64_t)c.moff + (int64_t)mid * ZG_B), hi, T)) hi_b = mid - 1; else lo_b = mid;
+    }
+    e = lo_b;
+}
+
+__global__ void k_zt_row_count(const PnClass *cls, int32_t ncls, const uint32_t *roff, const uint32_t *nrows,
+                               int64_t nrows_max, const uint4 *rec, float T, uint32_t *tcnt,
+                               unsigned long long *total) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nrows_max) return;
+    if (g >= (int64_t)*nrows) {
+        tcnt[g] = 0;
+        return;
+    }
+    int ci;
+    uint32_t bu, e;
+    zt_row(cls, ncls, roff, rec, T, g, ci, bu, e);
+    tcnt[g] = e - bu + 1;
+    atomicAdd(total, (unsigned long long)(e - bu + 1));
+}
+
+// One warp per row writes its tiles: class, first record of the row and of
+// the column block, rows | columns << 8 | diagonal << 16.
+__global__ void k_zt_row_fill(const PnClass *cls, int32_t ncls, const uint32_t *roff, const uint32_t *nrows,
+                              const uint4 *rec, float T, const uint32_t *toff, uint4 *tiles) {
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= (int64_t)*nrows) return;
+    int ci;
+    uint32_t bu, e;
+    zt_row(cls, ncls, roff, rec, T, g, ci, bu, e);
+    const PnClass c = cls[ci];
+    const uint32_t nu = min((uint32_t)ZG_B, c.size - bu * ZG_B);
+    for (uint32_t t = lane; t <= e - bu; t += 32) {
+        const uint32_t bv = bu + t;
+        const uint32_t nv = min((uint32_t)ZG_B, c.size - bv * ZG_B);
+        tiles[(int64_t)toff[g] + t] =
+            make_uint4((uint32_t)ci, c.moff + bu * ZG_B, c.moff + bv * ZG_B, nu | (nv << 8) | ((t == 0 ? 1u : 0u) << 16));
+    }
+}
+
 struct ZgSide {
     uint32_t s[ZG_B];        // member window start (0 past the block)
     float2 m[ZG_B];          // (1/sigma, -mu/sigma); x = 0 for a degenerate window or past the block
@@ -247,14 +380,10 @@ __device__ __forceinline__ float zg_colmin32(float (&dd)[32], int lane) {
     return dd[0];
 }
 
-// TOPK: the top-k sieve.  Instead of the row and column rules, a pair is
-// evaluated exactly only when its estimate minus the margin is below thr2
-// (the square of a distance the top list already holds) and below one of
-// its two cells: the pass looks only for pairs that can enter the list.
-template <class Z, bool TOPK>
+template <class Z>
 __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnClass *cls, const uint4 *tiles,
                                                             int64_t ntiles, const uint32_t *members, int kpad_max,
-                                                            unsigned long long *work, float thr2) {
+                                                            unsigned long long *work) {
     extern __shared__ __align__(1024) unsigned char zsm_raw[];
     __shared__ ZgShared sh;
     unsigned char *zsm = zsm_raw + ((1024 - (smem_u32(zsm_raw) & 1023)) & 1023);
@@ -357,7 +486,7 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
             const int64_t pu = (int64_t)sh.A.s[u];
             const uint32_t tbase = taddr + ((uint32_t)(warp * 32) << 16);
             float rmin = inf;
-            for (int c0 = 0; !TOPK && c0 < ZG_B; c0 += 32) {
+            for (int c0 = 0; c0 < ZG_B; c0 += 32) {
                 uint32_t r[32];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
@@ -414,14 +543,10 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
                         const float dd = fmaxf(0.0f, nu_ + nv_ - 2.0f * __uint_as_float(r[j]));
                         const float M = 0.001953125f * (nu_ + nv_) + mabs;     // 2^-9 (|y_u|^2 + |y_v|^2) + a 2^-14
                         const float tv = sh.B.t[vc];
-                        if constexpr (TOPK) {
-                            s = dd - M < thr2 && (dd - M < tu2 || dd - M < tv * tv);
-                        } else {
-                            const bool keep_u = dd - M < tu2 && dd <= rmin + tol_row;
-                            const bool keep_v = dd - M < tv * tv && dd <= __int_as_float(sh.colmin[vc]) +
-                                                                              0.00390625f * (nv_ + nmax_a) + 2.0f * mabs;
-                            s = keep_u || keep_v;
-                        }
+                        const bool keep_u = dd - M < tu2 && dd <= rmin + tol_row;
+                        const bool keep_v = dd - M < tv * tv && dd <= __int_as_float(sh.colmin[vc]) +
+                                                                          0.00390625f * (nv_ + nmax_a) + 2.0f * mabs;
+                        s = keep_u || keep_v;
                     }
                     const uint32_t bal = __ballot_sync(0xffffffffu, s);
                     if (s) sh.queue[warp][qn + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)u << 16) | (uint32_t)vc;
@@ -459,8 +584,11 @@ __global__ void __launch_bounds__(ZG_THREADS) k_sieve_zgram(PnView v, const PnCl
     if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);
 }
 
-// The top-k sieve as its own kernel: eight warps (warps w and w + 4 read the
-// same accumulator lanes, columns 0-63 and 64-127), and a fast test per pair
+// The top-k sieve.  Instead of the row and column rules, a pair is evaluated
+// exactly only when its estimate minus the margin is below thr2 (the square
+// of a distance the top list already holds) and below one of its two cells:
+// the pass looks only for pairs that can enter the list.  Eight warps (warps
+// w and w + 4 read the same accumulator lanes, columns 0-63 and 64-127), and a fast test per pair
 // -- one multiply-add against a per-row constant -- whose rare hits take the
 // full test.  The fast test is the exact one rearranged:
 // d~^2 - M < thr2  <=>  (1 - 2^-9) |y_v|^2 - 2 G < thr2 + a 2^-14 - (1 - 2^-9) |y_u|^2,
@@ -472,7 +600,8 @@ constexpr int ZT_RUN = 16;          // tiles a block draws at a time (one row bl
 
 struct ZtShared {
     ZgSide A, B;
-    float zref[ZG_AMAX];
+    __align__(16) float zref[ZG_AMAX];
+    __align__(16) float nbx[ZG_B];             // (1 - 2^-9) |y_v|^2 of the column block
     float2 nbt[ZG_B];                          // ((1 - 2^-9) |y_v|^2, P[v]^2) of the column block
     unsigned long long rkey[ZG_B], ckey[ZG_B];
     uint32_t queue[ZT_WARPS][ZT_Q];
@@ -483,9 +612,106 @@ struct ZtShared {
     unsigned long long run;
 };
 
+// Stages a block of class members for the top-k sieve as y = z - z_ref in
+// FP16 (the layout and side tables of zg_stage).  Warp w owns rows
+// 16 w .. 16 w + 15 and takes U of them at a time, the whole warp on each
+// row: lane l holds the sample pairs k = 2 l + 64 j, so a load instruction
+// reads 256 consecutive bytes of a row, every lane stores one FP16 pair per
+// step at an offset fixed per row (the 128-byte swizzle of row r puts the
+// pair of lane l at r 128 + ((l / 4) xor (r mod 8)) 16 + (l mod 4) 4 in each
+// 64-column atom), and all loads of a group are issued before the first is
+// used.  The loads take whole steps without bounds (a window's last step
+// reads at most 192 samples past its start, inside the sample buffer's
+// zero padding past the last series) and the samples past the window's end
+// are masked.  Lane l < 16 brings row 16 w + l's record (start, 1/sigma,
+// -mu/sigma), loaded one tile ahead; the cells are read here, early, and
+// used last.  |y|^2 is the FP32 warp sum of the row's squares.
+template <class Z, int U>
+__device__ __forceinline__ void zt_stage(const typename Z::X *xs, uint4 rl, int n, int a, int kp,
+                                         unsigned char *tile, ZgSide &side, int *nmax,
+                                         const unsigned long long *prow, const float *zref, int warp, int lane) {
+    constexpr int RPW = ZG_B / ZT_WARPS;        // 16 rows per warp
+    constexpr int JP = (ZG_AMAX + 63) / 64;     // pair steps per row
+    static_assert(RPW % U == 0, "row groups");
+    static_assert(64 * JP <= PN_SAMPLE_PAD, "unbounded steps stay inside the padding");
+    const bool mine = lane < RPW && warp * RPW + lane < n;
+    const unsigned long long k_l = mine ? __ldcg(&prow[rl.x]) : PN_EMPTY_KEY;
+    float2 zr[JP];
+    bool in0[JP], in1[JP];
+#pragma unroll
+    for (int j = 0; j < JP; ++j) {
+        const int k = 2 * lane + 64 * j;
+        zr[j] = k < kp ? *reinterpret_cast<const float2 *>(zref + k) : make_float2(0.0f, 0.0f);
+        in0[j] = k < a;
+        in1[j] = k + 1 < a;
+    }
+    const uint32_t lane_off = (uint32_t)(lane & 3) * 4u;
+    for (int g = 0; g < RPW; g += U) {
+        int row[U];
+        bool ok[U];
+        uint32_t cr[U];
+        typename Z::M mr[U];
+        typename Z::X xv[U][JP][2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            row[u] = warp * RPW + g + u;
+            ok[u] = row[u] < n;
+            cr[u] = __shfl_sync(0xffffffffu, rl.x, g + u);
+            mr[u].x = __uint_as_float(__shfl_sync(0xffffffffu, rl.y, g + u));
+            mr[u].y = __uint_as_float(__shfl_sync(0xffffffffu, rl.z, g + u));
+            const typename Z::X *xr = xs + cr[u] + 2 * lane;
+#pragma unroll
+            for (int j = 0; j < JP; ++j) {
+                if (64 * j < kp) {
+                    xv[u][j][0] = __ldg(xr + 64 * j);
+                    xv[u][j][1] = __ldg(xr + 64 * j + 1);
+                } else {
+                    xv[u][j][0] = typename Z::X{};
+                    xv[u][j][1] = typename Z::X{};
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t roff = (uint32_t)row[u] * 128u + ((((uint32_t)lane >> 2) ^ ((uint32_t)row[u] & 7u)) << 4) +
+                                  lane_off;
+            float acc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < JP; ++j) {
+                const float z0 = Z::z(mr[u], xv[u][j][0]) - zr[j].x;
+                const float z1 = Z::z(mr[u], xv[u][j][1]) - zr[j].y;
+                const float y0 = ok[u] && in0[j] ? z0 : 0.0f;
+                const float y1 = ok[u] && in1[j] ? z1 : 0.0f;
+                acc = fmaf(y0, y0, fmaf(y1, y1, acc));
+                if (64 * j < kp)
+                    *reinterpret_cast<__half2 *>(tile + roff + (uint32_t)j * (ZG_B * 128)) = __floats2half2_rn(y0, y1);
+            }
+            const float nr = pn_warp_sum(acc);
+            const unsigned long long kr = __shfl_sync(0xffffffffu, k_l, g + u);
+            if (lane == 0) {
+                side.s[row[u]] = ok[u] ? cr[u] : 0u;
+                side.m[row[u]] = ok[u] ? make_float2(mr[u].x, mr[u].y) : make_float2(0.0f, 0.0f);
+                side.n[row[u]] = nr;
+                side.t[row[u]] = ok[u] ? pn_key_distf(kr) : 0.0f;
+                if (nmax && ok[u] && mr[u].x != 0.0f) atomicMax(nmax, __float_as_int(nr));
+            }
+        }
+    }
+}
+
+constexpr int ZT_U = 4;              // rows per half-warp in flight while staging
+
+// Row-lane record of a block: lane l < 16 of warp w holds row 16 w + l's.
+__device__ __forceinline__ uint4 zt_record(const uint4 *rec, uint32_t first, int n, int warp, int lane) {
+    const int row = warp * (ZG_B / ZT_WARPS) + lane;
+    return (lane < ZG_B / ZT_WARPS && row < n) ? __ldg(&rec[(int64_t)first + row]) : make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Tiles: x = class, y / z = first record of the row / column block,
+// w = rows | columns << 8 | diagonal << 16.
 template <class Z>
-__global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnClass *cls, const uint4 *tiles,
-                                                           int64_t ntiles, const uint32_t *members, int kpad_max,
+__global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const PnClass *cls, const uint4 *tiles,
+                                                           int64_t ntiles, const uint4 *rec, int kpad_max,
                                                            unsigned long long *work, float thr2) {
     extern __shared__ __align__(1024) unsigned char ztm_raw[];
     __shared__ ZtShared sh;
@@ -512,7 +738,7 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
     const uint32_t idesc = umma_idesc_f16(ZG_B, ZG_B);
     uint32_t phase = 0;
     unsigned long long n_ex = 0;
-    uint32_t staged_cls = 0xFFFFFFFFu, staged_bu = 0xFFFFFFFFu;
+    uint32_t staged_a = 0xFFFFFFFFu;                 // first record of the staged row block
     const int quarter = warp & 3, half = warp >> 2;
     const int u = quarter * 32 + lane;
 
@@ -523,20 +749,24 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
         const int64_t run0 = (int64_t)sh.run;
         if (run0 >= ntiles || sh.fail) break;
         const int64_t run1 = min(ntiles, run0 + ZT_RUN);
+        uint4 tl = tiles[run0];
+        uint4 ra = zt_record(rec, tl.y, (int)(tl.w & 0xFFu), warp, lane);
+        uint4 rb = zt_record(rec, tl.z, (int)((tl.w >> 8) & 0xFFu), warp, lane);
         for (int64_t t = run0; t < run1; ++t) {
-            const uint4 tl = tiles[t];
+            // the next tile's coordinates, loaded now and used after this tile's staging
+            const uint4 tn = t + 1 < run1 ? tiles[t + 1] : make_uint4(0u, 0u, 0u, 0u);
             const PnClass c = cls[tl.x];
             const PnAnchor &A = v.anchors[c.anchor];
             const PnSeries &S = v.series[A.series];
             const int a = A.a;
             const int kp = (a + 15) & ~15;
             const int excl = S.excl;
-            const int u0 = (int)tl.y * ZG_B, v0 = (int)tl.z * ZG_B;
-            const int nu = min(ZG_B, (int)c.size - u0), nv = min(ZG_B, (int)c.size - v0);
-            const bool diag = tl.y == tl.z;
+            const int nu = (int)(tl.w & 0xFFu), nv = (int)((tl.w >> 8) & 0xFFu);
+            const bool diag = (tl.w >> 16) & 1u;
             unsigned long long *prow = v.prof + S.row_off + (int64_t)(a - S.m_min) * S.ld;
+            const auto *xs = Z::samples(v, S.x_off);
             __syncthreads();
-            const bool new_row = tl.x != staged_cls || tl.y != staged_bu;
+            const bool new_row = tl.y != staged_a;
             if (tid == 0) {
                 if (new_row) sh.nmax_a = 0;
                 sh.nmax_b = 0;
@@ -546,25 +776,36 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
                 sh.ckey[tid] = PN_EMPTY_KEY;
             }
             if (new_row) {
-                const uint32_t cr = members[(int64_t)c.moff + u0];
-                const auto mref = Z::load(v, A.win_off + cr);
-                const auto *xref = Z::samples(v, S.x_off + cr);
+                // reference: the row block's first member (both blocks of a tile share it)
+                const uint4 r0 = __ldg(&rec[tl.y]);
+                typename Z::M mref;
+                mref.x = __uint_as_float(r0.y);
+                mref.y = __uint_as_float(r0.z);
+                const auto *xref = Z::samples(v, S.x_off + r0.x);
                 for (int k = tid; k < kp; k += ZT_THREADS) sh.zref[k] = k < a ? Z::z(mref, xref[k]) : 0.0f;
                 __syncthreads();
-                zg_stage<Z, ZT_WARPS>(v, A, S, members, (int64_t)c.moff + u0, nu, a, kp, tA, sh.A, &sh.nmax_a, prow,
-                                      sh.zref, warp, lane);
+                zt_stage<Z, ZT_U>(xs, ra, nu, a, kp, tA, sh.A, &sh.nmax_a, prow, sh.zref, warp, lane);
             } else {
                 __syncthreads();
             }
-            zg_stage<Z, ZT_WARPS>(v, A, S, members, (int64_t)c.moff + v0, nv, a, kp, tB, sh.B, &sh.nmax_b, prow,
-                                  sh.zref, warp, lane);
-            staged_cls = tl.x;
-            staged_bu = tl.y;
+            zt_stage<Z, ZT_U>(xs, rb, nv, a, kp, tB, sh.B, &sh.nmax_b, prow, sh.zref, warp, lane);
+            staged_a = tl.y;
+            // the next tile's records, in flight during this tile's product and epilogue
+            if (t + 1 < run1) {
+                ra = tn.y != tl.y ? zt_record(rec, tn.y, (int)(tn.w & 0xFFu), warp, lane) : ra;
+                rb = zt_record(rec, tn.z, (int)((tn.w >> 8) & 0xFFu), warp, lane);
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (tid < ZG_B) sh.nbt[tid] = make_float2(0.998046875f * sh.B.n[tid], sh.B.t[tid] * sh.B.t[tid]);
+            if (tid < ZG_B) {
+                // columns past the block and degenerate windows never pass the fast test
+                const bool colok = tid < nv && sh.B.m[tid].x != 0.0f;
+                const float nb_ = colok ? 0.998046875f * sh.B.n[tid] : __int_as_float(0x7f800000);
+                sh.nbx[tid] = nb_;
+                sh.nbt[tid] = make_float2(nb_, sh.B.t[tid] * sh.B.t[tid]);
+            }
             if (tid == 0) {
                 const uint32_t a0 = smem_u32(tA), b0 = smem_u32(tB);
                 for (int s2 = 0; s2 < kp / 16; ++s2) {
@@ -595,8 +836,11 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
             const float slack = 9.5367432e-07f * (thr2 + mabs + nu_ + 1.0f);
             const float cu = urow ? mabs - 0.998046875f * nu_ + slack : -__int_as_float(0x7f800000);
             const float kt = thr2 + cu, ku = tu2 + cu;
+            // no row of the warp holds a cell below the list threshold: the
+            // fast test is e < kt alone, and a column group without any
+            // e = (1 - 2^-9) |y_v|^2 - 2 G below kt is passed by a running minimum
+            const bool rows_above = __all_sync(0xffffffffu, !urow || ku >= kt);
             const int64_t pu = (int64_t)sh.A.s[u];
-            const auto *xs = Z::samples(v, S.x_off);
             const uint32_t tbase = taddr + ((uint32_t)(quarter * 32) << 16);
             int qn = 0;
             for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
@@ -611,6 +855,15 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
                       "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                     : "r"(tbase + (uint32_t)c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (rows_above) {
+                    float e4[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) e4[j] = fmaf(-2.0f, __uint_as_float(r[j]), sh.nbx[c0 + j]);
+#pragma unroll
+                    for (int j = 4; j < 32; ++j)
+                        e4[j & 3] = fminf(e4[j & 3], fmaf(-2.0f, __uint_as_float(r[j]), sh.nbx[c0 + j]));
+                    if (!__any_sync(0xffffffffu, fminf(fminf(e4[0], e4[1]), fminf(e4[2], e4[3])) < kt)) continue;
+                }
                 uint32_t hit = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -654,6 +907,7 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
                 if (sh.rkey[tid] != PN_EMPTY_KEY) atomicMin(&prow[sh.A.s[tid]], sh.rkey[tid]);
                 if (sh.ckey[tid] != PN_EMPTY_KEY) atomicMin(&prow[sh.B.s[tid]], sh.ckey[tid]);
             }
+            tl = tn;
         }
         if (sh.fail) break;
     }
@@ -669,9 +923,9 @@ __global__ void __launch_bounds__(ZT_THREADS) k_sieve_topk(PnView v, const PnCla
     if (lane == 0 && v.stats && n_ex) atomicAdd(&v.stats[PN_ST_EXACT_SIEVE], n_ex);
 }
 
-template <class Z, bool TOPK>
+template <class Z>
 cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int a_max,
-                          int grid_blocks, float thr2, cudaStream_t st) {
+                          int grid_blocks, cudaStream_t st) {
     uint32_t *cnt = nullptr, *off = nullptr, *tot = nullptr;
     unsigned long long *tot64 = nullptr;
     uint4 *tiles = nullptr;
@@ -702,24 +956,93 @@ cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, con
         const int kpad = (a_max + 15) & ~15;
         const int atoms = (kpad + 63) >> 6;
         const size_t sm = 1024 + (size_t)atoms * 2 * ZG_B * 128;
-        const int run = TOPK ? ZT_RUN : ZG_RUN;
-        const int64_t g = std::min<int64_t>((ntiles + run - 1) / run, (int64_t)grid_blocks);
-        if constexpr (TOPK) {
-            e = pn_allow_smem(k_sieve_topk<Z>, sm);
-            if (e == cudaSuccess) {
-                k_sieve_topk<Z><<<(unsigned)g, ZT_THREADS, sm, st>>>(v, cls, tiles, ntiles, vals, kpad, work, thr2);
-                e = cudaGetLastError();
-            }
-        } else {
-            e = pn_allow_smem(k_sieve_zgram<Z, false>, sm);
-            if (e == cudaSuccess) {
-                k_sieve_zgram<Z, false><<<(unsigned)g, ZG_THREADS, sm, st>>>(v, cls, tiles, ntiles, vals, kpad, work,
-                                                                             thr2);
-                e = cudaGetLastError();
-            }
+        const int64_t g = std::min<int64_t>((ntiles + ZG_RUN - 1) / ZG_RUN, (int64_t)grid_blocks);
+        e = pn_allow_smem(k_sieve_zgram<Z>, sm);
+        if (e == cudaSuccess) {
+            k_sieve_zgram<Z><<<(unsigned)g, ZG_THREADS, sm, st>>>(v, cls, tiles, ntiles, vals, kpad, work);
+            e = cudaGetLastError();
         }
     }
     for (void *p : {(void *)cnt, (void *)off, (void *)tot, (void *)tot64, (void *)tiles})
+        if (p) cudaFreeAsync(p, st);
+    return e;
+}
+
+// The top-k sieve: members re-sorted by their pivot distance, the tile table
+// pruned by the triangle inequality, then k_sieve_topk over the kept tiles.
+template <class Z>
+cudaError_t sieve_topk_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int64_t nmem,
+                         int a_max, int grid_blocks, double thr, cudaStream_t st) {
+    if (nmem <= 0) return cudaSuccess;
+    const float t = (float)thr;
+    const float thr2 = t * t * (1.0f + 1e-6f) + 1e-12f;        // FP32 rounding of the square
+    const int64_t nrows_max = nmem / ZG_B + ncls + 1;           // sum of ceil(size / 128) over the classes
+    float *r = nullptr;
+    uint32_t *keys = nullptr, *idx = nullptr, *nb = nullptr, *roff = nullptr, *tot = nullptr;
+    uint32_t *tcnt = nullptr, *toff = nullptr;
+    unsigned long long *tot64 = nullptr;
+    uint4 *rec = nullptr, *tiles = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&r, 4 * (size_t)nmem, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&keys, 4 * (size_t)nmem, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&idx, 4 * (size_t)nmem, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&rec, sizeof(uint4) * (size_t)nmem, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&nb, 4 * (size_t)ncls, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&roff, 4 * (size_t)ncls, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot, 8, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tcnt, 4 * (size_t)nrows_max, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&toff, 4 * (size_t)nrows_max, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot64, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tot64, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        k_zt_pivot<Z><<<(unsigned)((nmem * 32 + 255) / 256), 256, 0, st>>>(v, cls, ncls, vals, nmem, r, keys, idx);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, idx, nmem, 32, st);
+    int cbits = 1;
+    while (cbits < 32 && ((int64_t)1 << cbits) <= ncls) ++cbits;
+    if (e == cudaSuccess) {
+        k_zt_rekey<<<(unsigned)((nmem + 255) / 256), 256, 0, st>>>(cls, ncls, nmem, keys, idx);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, idx, nmem, cbits, st);
+    if (e == cudaSuccess) {
+        // after the class sort keys[q] is the class of position q
+        k_zt_records<Z><<<(unsigned)((nmem + 255) / 256), 256, 0, st>>>(v, cls, vals, r, idx, keys, nmem, rec);
+        k_zt_blocks<<<(unsigned)((ncls + 255) / 256), 256, 0, st>>>(cls, ncls, nb);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = excl_scan_u32(nb, roff, ncls, tot, st);             // tot[0] = rows
+    if (e == cudaSuccess) {
+        k_zt_row_count<<<(unsigned)((nrows_max + 255) / 256), 256, 0, st>>>(cls, ncls, roff, tot, nrows_max, rec, t,
+                                                                           tcnt, tot64);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = excl_scan_u32(tcnt, toff, nrows_max, tot + 1, st);
+    unsigned long long h = 0ull;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, tot64, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const int64_t ntiles = (int64_t)h;
+    if (e == cudaSuccess && ntiles > 0x7FFFFFFFll) e = cudaErrorMemoryAllocation;
+    if (e == cudaSuccess && ntiles > 0) e = cudaMallocAsync((void **)&tiles, sizeof(uint4) * (size_t)ntiles, st);
+    unsigned long long *work = tot64 + 1;
+    if (e == cudaSuccess && ntiles > 0) {
+        k_zt_row_fill<<<(unsigned)((nrows_max * 32 + 255) / 256), 256, 0, st>>>(cls, ncls, roff, tot, rec, t, toff,
+                                                                               tiles);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && ntiles > 0) {
+        const int kpad = (a_max + 15) & ~15;
+        const int atoms = (kpad + 63) >> 6;
+        const size_t sm = 1024 + (size_t)atoms * 2 * ZG_B * 128;
+        const int64_t g = std::min<int64_t>((ntiles + ZT_RUN - 1) / ZT_RUN, (int64_t)grid_blocks);
+        e = pn_allow_smem(k_sieve_topk<Z>, sm);
+        if (e == cudaSuccess) {
+            k_sieve_topk<Z><<<(unsigned)g, ZT_THREADS, sm, st>>>(v, cls, tiles, ntiles, rec, kpad, work, thr2);
+            e = cudaGetLastError();
+        }
+    }
+    for (void *p : {(void *)r, (void *)keys, (void *)idx, (void *)rec, (void *)nb, (void *)roff, (void *)tot,
+                    (void *)tcnt, (void *)toff, (void *)tot64, (void *)tiles})
         if (p) cudaFreeAsync(p, st);
     return e;
 }
@@ -728,17 +1051,15 @@ cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, con
 
 bool sieve_gram_supported(int a_max) { return a_max <= ZG_AMAX; }
 
-cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int a_max,
-                              int grid_blocks, cudaStream_t st, double topk_thr) {
+cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int64_t nmem,
+                              int a_max, int grid_blocks, cudaStream_t st, double topk_thr) {
     if (ncls <= 0) return cudaSuccess;
     if (topk_thr >= 0.0) {
-        const float t = (float)topk_thr;
-        const float thr2 = t * t * (1.0f + 1e-6f) + 1e-12f;       // FP32 rounding of the square
-        if (v.x1) return sieve_zgram_t<ZMix1, true>(v, cls, ncls, vals, a_max, grid_blocks, thr2, st);
-        return sieve_zgram_t<ZMix2, true>(v, cls, ncls, vals, a_max, grid_blocks, thr2, st);
+        if (v.x1) return sieve_topk_t<ZMix1>(v, cls, ncls, vals, nmem, a_max, grid_blocks, topk_thr, st);
+        return sieve_topk_t<ZMix2>(v, cls, ncls, vals, nmem, a_max, grid_blocks, topk_thr, st);
     }
-    if (v.x1) return sieve_zgram_t<ZMix1, false>(v, cls, ncls, vals, a_max, grid_blocks, 0.0f, st);
-    return sieve_zgram_t<ZMix2, false>(v, cls, ncls, vals, a_max, grid_blocks, 0.0f, st);
+    if (v.x1) return sieve_zgram_t<ZMix1>(v, cls, ncls, vals, a_max, grid_blocks, st);
+    return sieve_zgram_t<ZMix2>(v, cls, ncls, vals, a_max, grid_blocks, st);
 }
 
 }  // namespace pn

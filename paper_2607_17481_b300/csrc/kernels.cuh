@@ -72,6 +72,10 @@ __device__ __forceinline__ bool pn_gated(const PnView &v) { return v.gate && *(v
 
 #define PN_FT_CHUNKS 4         // chunks (one warp each) per block of the feature kernel
 #define PN_ERR_TC_TIMEOUT 1   // a tensor-core anchor tile's bounded wait ran out
+// Samples allocated (zero) past the last series in the FP32 sample buffers:
+// the top-k sieve's staging reads whole 64-sample steps of a window without
+// per-sample bounds and masks the samples past the window's end.
+#define PN_SAMPLE_PAD 256
 
 enum PnStat {
     PN_ST_QUERIES = 0,
