@@ -605,7 +605,6 @@ struct ZtShared {
     float2 nbt[ZG_B];                          // ((1 - 2^-9) |y_v|^2, P[v]^2) of the column block
     unsigned long long rkey[ZG_B], ckey[ZG_B];
     uint32_t queue[ZT_WARPS][ZT_Q];
-    int nmax_a, nmax_b;
     int fail;
     uint32_t taddr;
     __align__(8) uint64_t mbar;
@@ -625,11 +624,12 @@ struct ZtShared {
 // zero padding past the last series) and the samples past the window's end
 // are masked.  Lane l < 16 brings row 16 w + l's record (start, 1/sigma,
 // -mu/sigma), loaded one tile ahead; the cells are read here, early, and
-// used last.  |y|^2 is the FP32 warp sum of the row's squares.
+// used last, when each of these lanes writes its row's side entries.
+// |y|^2 is the FP32 warp sum of the row's squares.
 template <class Z, int U>
 __device__ __forceinline__ void zt_stage(const typename Z::X *xs, uint4 rl, int n, int a, int kp,
-                                         unsigned char *tile, ZgSide &side, int *nmax,
-                                         const unsigned long long *prow, const float *zref, int warp, int lane) {
+                                         unsigned char *tile, ZgSide &side, const unsigned long long *prow,
+                                         const float *zref, int warp, int lane) {
     constexpr int RPW = ZG_B / ZT_WARPS;        // 16 rows per warp
     constexpr int JP = (ZG_AMAX + 63) / 64;     // pair steps per row
     static_assert(RPW % U == 0, "row groups");
@@ -646,6 +646,7 @@ __device__ __forceinline__ void zt_stage(const typename Z::X *xs, uint4 rl, int 
         in1[j] = k + 1 < a;
     }
     const uint32_t lane_off = (uint32_t)(lane & 3) * 4u;
+    float n_own = 0.0f;                         // |y|^2 of row 16 w + l (lanes l < 16)
     for (int g = 0; g < RPW; g += U) {
         int row[U];
         bool ok[U];
@@ -687,15 +688,16 @@ __device__ __forceinline__ void zt_stage(const typename Z::X *xs, uint4 rl, int 
                     *reinterpret_cast<__half2 *>(tile + roff + (uint32_t)j * (ZG_B * 128)) = __floats2half2_rn(y0, y1);
             }
             const float nr = pn_warp_sum(acc);
-            const unsigned long long kr = __shfl_sync(0xffffffffu, k_l, g + u);
-            if (lane == 0) {
-                side.s[row[u]] = ok[u] ? cr[u] : 0u;
-                side.m[row[u]] = ok[u] ? make_float2(mr[u].x, mr[u].y) : make_float2(0.0f, 0.0f);
-                side.n[row[u]] = nr;
-                side.t[row[u]] = ok[u] ? pn_key_distf(kr) : 0.0f;
-                if (nmax && ok[u] && mr[u].x != 0.0f) atomicMax(nmax, __float_as_int(nr));
-            }
+            if (lane == g + u) n_own = nr;
         }
+    }
+    // side tables: lane l < 16 writes its own row's entries
+    const int row = warp * RPW + lane;
+    if (lane < RPW) {
+        side.s[row] = mine ? rl.x : 0u;
+        side.m[row] = mine ? make_float2(__uint_as_float(rl.y), __uint_as_float(rl.z)) : make_float2(0.0f, 0.0f);
+        side.n[row] = n_own;
+        side.t[row] = mine ? pn_key_distf(k_l) : 0.0f;
     }
 }
 
@@ -767,10 +769,6 @@ __global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const Pn
             const auto *xs = Z::samples(v, S.x_off);
             __syncthreads();
             const bool new_row = tl.y != staged_a;
-            if (tid == 0) {
-                if (new_row) sh.nmax_a = 0;
-                sh.nmax_b = 0;
-            }
             if (tid < ZG_B) {
                 sh.rkey[tid] = PN_EMPTY_KEY;
                 sh.ckey[tid] = PN_EMPTY_KEY;
@@ -784,11 +782,11 @@ __global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const Pn
                 const auto *xref = Z::samples(v, S.x_off + r0.x);
                 for (int k = tid; k < kp; k += ZT_THREADS) sh.zref[k] = k < a ? Z::z(mref, xref[k]) : 0.0f;
                 __syncthreads();
-                zt_stage<Z, ZT_U>(xs, ra, nu, a, kp, tA, sh.A, &sh.nmax_a, prow, sh.zref, warp, lane);
+                zt_stage<Z, ZT_U>(xs, ra, nu, a, kp, tA, sh.A, prow, sh.zref, warp, lane);
             } else {
                 __syncthreads();
             }
-            zt_stage<Z, ZT_U>(xs, rb, nv, a, kp, tB, sh.B, &sh.nmax_b, prow, sh.zref, warp, lane);
+            zt_stage<Z, ZT_U>(xs, rb, nv, a, kp, tB, sh.B, prow, sh.zref, warp, lane);
             staged_a = tl.y;
             // the next tile's records, in flight during this tile's product and epilogue
             if (t + 1 < run1) {
