@@ -74,3 +74,22 @@ def test_kernel_table_arithmetic():
     assert f["flops"] == 1650.0 * nwa and f["bytes"] == 164.0 * nwa
     assert "tf32_frac" in rows["anchor_tc"] and "fp32_frac" not in rows["anchor_tc"]
     assert rows["select"]["bytes"] == 24.0 * 51 * n * 4
+
+
+def test_paper_recovery_rule():
+    """Sec. 4's recovery: position match within m/2 at the same length, else
+    value match of the length's best reported distance (5% or 0.05), else missed."""
+    import numpy as np
+    dt = [("m", "i4"), ("i", "i8"), ("j", "i8"), ("d", "f8")]
+    ref = np.array([(100, 1000, 5000, 0.30),     # reported 50 samples away: position (2*50 <= 100)
+                    (100, 2000, 6000, 0.31),     # reported 51 away only: not a position match, value 0.30 vs 0.31
+                    (120, 3000, 7000, 0.40),     # no cell at 120: missed
+                    (101, 4000, 8000, 0.20)],    # best at 101 is 0.26: |0.06| > 0.05 and > 5%: missed
+                   dtype=dt)
+    got = np.array([(100, 1050, 5050, 0.30), (100, 2051, 6051, 0.35), (101, 9000, 9900, 0.26)], dtype=dt)
+    r = bench.paper_recovery(ref, got)
+    assert r == {"position": 1, "value": 1, "missed": 2, "of": 4}
+    # the rule is per length: a cell at the right start but another length does not count
+    r2 = bench.paper_recovery(ref[:1], np.array([(101, 1000, 5000, 0.30)], dtype=dt))
+    assert r2 == {"position": 0, "value": 0, "missed": 1, "of": 1}
+    assert bench.paper_recovery(ref, ref)["position"] == 4
