@@ -703,6 +703,16 @@ __device__ __forceinline__ void zt_stage(const typename Z::X *xs, uint4 rl, int 
 
 constexpr int ZT_U = 4;              // rows per half-warp in flight while staging
 
+// The queued pairs of a warp evaluated exactly, four at a time (one copy of
+// the evaluation code for both call sites of the top-k kernel).
+template <class Z>
+__device__ __noinline__ void zt_flush(const typename Z::X *xs, int a, const uint32_t *q, int qn, const ZgSide &SA,
+                                      const ZgSide &SB, unsigned long long *rkey, unsigned long long *ckey, int lane) {
+    __syncwarp();
+    for (int e = 0; e < qn; e += 4) zg_eval4<Z>(xs, a, q + e, min(4, qn - e), SA, SB, rkey, ckey, lane);
+    __syncwarp();
+}
+
 // Row-lane record of a block: lane l < 16 of warp w holds row 16 w + l's.
 __device__ __forceinline__ uint4 zt_record(const uint4 *rec, uint32_t first, int n, int warp, int lane) {
     const int row = warp * (ZG_B / ZT_WARPS) + lane;
@@ -781,12 +791,13 @@ __global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const Pn
                 mref.y = __uint_as_float(r0.z);
                 const auto *xref = Z::samples(v, S.x_off + r0.x);
                 for (int k = tid; k < kp; k += ZT_THREADS) sh.zref[k] = k < a ? Z::z(mref, xref[k]) : 0.0f;
-                __syncthreads();
-                zt_stage<Z, ZT_U>(xs, ra, nu, a, kp, tA, sh.A, prow, sh.zref, warp, lane);
-            } else {
-                __syncthreads();
             }
-            zt_stage<Z, ZT_U>(xs, rb, nv, a, kp, tB, sh.B, prow, sh.zref, warp, lane);
+            __syncthreads();
+            // the row block (when it changed) and the column block, through one copy of the staging code
+#pragma unroll 1
+            for (int sd = new_row ? 0 : 1; sd < 2; ++sd)
+                zt_stage<Z, ZT_U>(xs, sd ? rb : ra, sd ? nv : nu, a, kp, sd ? tB : tA, sd ? sh.B : sh.A, prow, sh.zref,
+                                  warp, lane);
             staged_a = tl.y;
             // the next tile's records, in flight during this tile's product and epilogue
             if (t + 1 < run1) {
@@ -862,22 +873,24 @@ __global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const Pn
                         e4[j & 3] = fminf(e4[j & 3], fmaf(-2.0f, __uint_as_float(r[j]), sh.nbx[c0 + j]));
                     if (!__any_sync(0xffffffffu, fminf(fminf(e4[0], e4[1]), fminf(e4[2], e4[3])) < kt)) continue;
                 }
-                uint32_t hit = 0;
-#pragma unroll
+                // the full test, one column at a time (rare: a group with a pair near
+                // the list), each estimate read again from tensor memory
+#pragma unroll 1
                 for (int j = 0; j < 32; ++j) {
-                    const float2 nt = sh.nbt[c0 + j];
-                    const float lim = fminf(kt, fmaxf(ku, nt.y + cu));
-                    hit |= (fmaf(-2.0f, __uint_as_float(r[j]), nt.x) < lim ? 1u : 0u) << j;
-                }
-                if (!__any_sync(0xffffffffu, hit != 0u)) continue;        // the common case: no pair near the list
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
+                    uint32_t gj;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                                 : "=r"(gj)
+                                 : "r"(tbase + (uint32_t)(c0 + j)));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const float G = __uint_as_float(gj);
                     const int vc = c0 + j;
-                    bool keep = ((hit >> j) & 1u) && vc < nv && (!diag || u < vc) && sh.B.m[vc].x != 0.0f;
+                    const float2 nt = sh.nbt[vc];
+                    bool keep = fmaf(-2.0f, G, nt.x) < fminf(kt, fmaxf(ku, nt.y + cu)) && vc < nv && (!diag || u < vc) &&
+                                sh.B.m[vc].x != 0.0f;
                     if (keep) keep = llabs(pu - (int64_t)sh.B.s[vc]) >= excl;
                     if (keep) {
                         const float nv_ = sh.B.n[vc];
-                        const float dd = fmaxf(0.0f, nu_ + nv_ - 2.0f * __uint_as_float(r[j]));
+                        const float dd = fmaxf(0.0f, nu_ + nv_ - 2.0f * G);
                         const float M = 0.001953125f * (nu_ + nv_) + mabs;
                         const float tv = sh.B.t[vc];
                         keep = dd - M < thr2 && (dd - M < tu2 || dd - M < tv * tv);
@@ -886,19 +899,14 @@ __global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const Pn
                     if (keep) sh.queue[warp][qn + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)u << 16) | (uint32_t)vc;
                     qn += __popc(bal);
                     if (qn > ZT_Q - 32) {
-                        __syncwarp();
-                        for (int e = 0; e < qn; e += 4)
-                            zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh.A, sh.B, sh.rkey, sh.ckey, lane);
                         n_ex += (unsigned long long)qn;
+                        zt_flush<Z>(xs, a, sh.queue[warp], qn, sh.A, sh.B, sh.rkey, sh.ckey, lane);
                         qn = 0;
-                        __syncwarp();
                     }
                 }
             }
-            __syncwarp();
-            for (int e = 0; e < qn; e += 4)
-                zg_eval4<Z>(xs, a, &sh.queue[warp][e], min(4, qn - e), sh.A, sh.B, sh.rkey, sh.ckey, lane);
             n_ex += (unsigned long long)qn;
+            zt_flush<Z>(xs, a, sh.queue[warp], qn, sh.A, sh.B, sh.rkey, sh.ckey, lane);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             if (tid < ZG_B) {
