@@ -203,6 +203,21 @@ def test_topk_matches_oracle(pn, small, small_exact, mode, precision):
         ctx.query_levels(0, n_anchor, 1)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_topk_sieve_matches_oracle(pn, small, small_exact, mode):
+    """With the top-k sieve (float64 walk: the (hi, lo) sample staging, tile
+    tables pruned by pivot distances) the lists are still the oracle's."""
+    from parity import compare
+    s = small
+    P, I = small_exact
+    ref = topk.select(P, I, s.m_min, s.k, mode)
+    ctx, got = run(pn, s, precision=1, topk_mode=mode, flags=pn.FLAG_TOPK_SIEVE)
+    assert len(got) == len(ref)
+    r = compare(s.x, got, ref)
+    assert r["misses"] == 0, r["miss_list"]
+    assert r["bad_dist"] == 0
+
+
 def test_recall_at_paper_stride(pn, small, small_exact):
     """The paper's stride 2 in per-length mode: reported.  Two cells of one
     pair at length 60 are missed: the anchor's search finds the pair shifted

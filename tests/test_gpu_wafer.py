@@ -137,6 +137,22 @@ def test_prefix_topk_sieve_matches_exhaustive(pn, wafer):
         print(f"n={n}: top-k sieve {t.stats()['exact_sieve']} exact pairs, exhaustive {d.stats()['exact_sieve']}")
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_prefix_topk_sieve_float64_and_per_length(pn, wafer, mode):
+    """The top-k sieve on the prefix given as float64 samples (the (hi, lo)
+    sample path of its staging) and in both top-k modes: the dense
+    exhaustive sieve's motifs, which evaluates every pair of every hot class."""
+    x = np.ascontiguousarray(wafer.x[:200_000]).astype(np.float64)
+    t = pn.Context(precision=1, topk_mode=mode, flags=pn.FLAG_TOPK_SIEVE)
+    mt = t.pmp(x, 100, 150, 20, 150)
+    d = pn.Context(precision=1, topk_mode=mode, flags=pn.FLAG_EXHAUSTIVE_SIEVE)
+    md = d.pmp(x, 100, 150, 20, 150)
+    assert len(mt) == len(md) == (20 if mode == 0 else 20 * 51)
+    assert np.array_equal(mt[["m", "i", "j"]], md[["m", "i", "j"]])
+    assert np.allclose(mt["d"], md["d"], rtol=1e-12, atol=0)
+    assert t.stats()["exact_sieve"] < d.stats()["exact_sieve"]
+
+
 def test_5m_reported_cells_are_exact(pn):
     """The benchmark's workload (5,000,000 samples, mixed precision): every
     reported motif's distance is the oracle's exact nearest-neighbour distance
