@@ -687,13 +687,13 @@ def main():
         fast = {}
         for name, over in (("s6_alpha4_rounds1", dict(stride=6, alpha=4, rounds=1)),
                            ("topk_sieve", dict(flags=pn.FLAG_TOPK_SIEVE)),
+                           ("no_focus_sieve", dict(flags=pn.FLAG_NO_FOCUS_SIEVE)),
                            ("K4_s8", dict(K=4, stride=8))):
             fctx = make_ctx(args.precision, **over)
             fms, fst, fmot = timed(fctx, args.fast_steps, 1, x_dev)
             ref_cells = {(int(r["m"]), int(r["i"]), int(r["j"])) for r in motifs}
             got_cells = {(int(r["m"]), int(r["i"]), int(r["j"])) for r in fmot}
-            over = {k: v for k, v in over.items() if k != "flags"} | ({"topk_sieve": True}
-                                                                      if "flags" in over else {})
+            over = {k: v for k, v in over.items() if k != "flags"} | ({name: True} if "flags" in over else {})
             fast[name] = {"value": W * world / (statistics.mean(fms) / 1e3), "ms_per_step": statistics.mean(fms),
                           "same_motifs": bool(np.array_equal(fmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                           "recall_vs_default": len(ref_cells & got_cells) / max(1, len(ref_cells)),
@@ -708,6 +708,13 @@ def main():
                 fast[name]["default_kth_d"] = float(motifs["d"][-1]) if len(motifs) else None
                 # the default's list scored against this one by the paper's recovery rule
                 fast[name]["default_recovery_sec4"] = paper_recovery(fmot, motifs)
+                topk_mot = fmot
+            if name == "no_focus_sieve" and "topk_sieve" in fast:
+                # without the default's focused sieve: its cells against the whole
+                # top-k sieve's, by identity and by the paper's rule
+                tc = {(int(r["m"]), int(r["i"]), int(r["j"])) for r in topk_mot}
+                fast[name]["recall_vs_topk_sieve"] = len(tc & got_cells) / max(1, len(tc))
+                fast[name]["recovery_sec4_vs_topk_sieve"] = paper_recovery(topk_mot, fmot)
     walk = run_walk(pn, stream) if rank == 0 else None
     batched = run_batched(pn, stream, args.batched, args.batched_loop) if args.batched > 0 else None
     served = run_served(pn, args) if args.served_seconds > 0 and rank == 0 else None

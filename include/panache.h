@@ -144,7 +144,21 @@ extern "C" {
                                               that can fall below it and below one of their cells, and run
                                               the rest of the emit stage again.  It finds the near-copy pairs
                                               of large hot classes that the band of w sort neighbours misses;
-                                              not captured in a graph. */
+                                              it and the emit stage after it run eagerly (no graph). */
+#define PANACHE_FLAG_NO_FOCUS_SIEVE 0x2000 /* turn off the focused top-k sieve.  By default a global top-k
+                                              request in the mixed form (anchors of at most 192 samples, with
+                                              its directories: not pmp_from_rows) runs, after the emit stage,
+                                              the top-k sieve of PANACHE_FLAG_TOPK_SIEVE restricted to the hot
+                                              classes of the anchors next to the lengths of the refined lists'
+                                              cells (per series, the largest anchor length <= m and the
+                                              smallest >= m), against the largest distance of those lists,
+                                              and then the rest of the emit stage again: the near-copy pairs
+                                              where the lists live, which the band of w sort neighbours
+                                              misses.  A pair below that distance at another anchor is not
+                                              looked for (PANACHE_FLAG_TOPK_SIEVE looks at every anchor, and
+                                              per-length requests take the sieve only with that flag).  With
+                                              PANACHE_FLAG_GRAPH the first emit stage replays its graph and
+                                              the sieve and the second emit stage run eagerly. */
 #define PANACHE_FLAG_NO_REFINE 0x200      /* skip the exact row refinement of the top list.  After local
                                               completion, every cell of the top refine_mult*k list (per group)
                                               is scanned against all its valid partners at its length with the

@@ -890,8 +890,15 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
     // final selection) runs without the host: buffers first, then the
     // launches, replayed from a captured graph when the request's shape
     // repeats, then one wait for the results.
-    const bool topk_sieve = (c.flags & PANACHE_FLAG_TOPK_SIEVE) && c.precision == PANACHE_MIXED &&
-                            !(c.flags & PANACHE_FLAG_NO_SIEVE) && pn::sieve_gram_supported(R.a_max);
+    const bool gram_ok = c.precision == PANACHE_MIXED && !(c.flags & PANACHE_FLAG_NO_SIEVE) &&
+                         pn::sieve_gram_supported(R.a_max);
+    // the top-k sieves need the request's own directories (not rows handed
+    // in from other ranks); the focused one runs for global requests unless
+    // turned off
+    const bool own_dirs = (stages & PN_EMIT_SIEVE) != 0;
+    const bool topk_sieve = (c.flags & PANACHE_FLAG_TOPK_SIEVE) && gram_ok && own_dirs;
+    const bool focus_sieve = !topk_sieve && !(c.flags & PANACHE_FLAG_NO_FOCUS_SIEVE) && c.topk_mode == 0 && gram_ok &&
+                             own_dirs;
     const bool graph = (c.flags & PANACHE_FLAG_GRAPH) && !(c.flags & (PANACHE_FLAG_TIMING | PANACHE_FLAG_INDEX_ONLY)) &&
                        ctx->last == &R && !topk_sieve;
     if (!R.emit || !graph) {
@@ -939,13 +946,13 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
     }
     PN_CU(cudaStreamSynchronize(st));
     if (hctl[OV_FINAL]) return PANACHE_EPOOL;
-    if (topk_sieve) {
+    if (topk_sieve || focus_sieve) {
         // The top-k sieve: every hot class's pairs estimated on the tensor
         // cores against the largest distance of the refined lists (the
         // reported lists when there is no refinement), the pairs that can
         // enter a list evaluated exactly, then the rest of the emit stage
-        // once more on the lowered cells.
-        double thr = 0.0;
+        // once more on the lowered cells.  Focused: only the classes that
+        // hold a window of a listed cell, at the anchors next to its length.
         const SelBufs &lb = E.refine && E.rb.ng ? E.rb : E.fb;
         std::vector<PnPick> lp((size_t)lb.ng * lb.kmax);
         std::vector<int32_t> lc((size_t)lb.ng);
@@ -954,18 +961,70 @@ int run_emit(panache_ctx *ctx, PnRequest &R, const PnView &v, StepTimer &tm,
             PN_CU(cudaMemcpyAsync(lc.data(), lb.cnt, sizeof(int32_t) * lc.size(), cudaMemcpyDeviceToHost, st));
             PN_CU(cudaStreamSynchronize(st));
         }
-        bool short_list = false;
+        // each anchor's threshold: the largest last distance of the lists that
+        // can take its pairs (a global list: every anchor of its series; a
+        // per-length list: the anchors next to its length); a short list
+        // takes any pair (no threshold)
+        auto next_anchors = [&](const PnSeries &S, int m, int &below, int &above) {
+            below = above = -1;
+            for (int32_t k = S.anchor_begin; k < S.anchor_begin + S.anchor_count; ++k) {
+                const int a = R.anc[k].a;
+                if (a <= m && (below < 0 || a > R.anc[below].a)) below = k;
+                if (a >= m && (above < 0 || a < R.anc[above].a)) above = k;
+            }
+        };
+        std::vector<float> thr(R.anc.size(), 0.0f);
         for (int32_t gi = 0; gi < lb.ng; ++gi) {
-            if (lc[gi] < lb.kmax) short_list = true;     // a short list takes any pair: no threshold
-            if (lc[gi] > 0) thr = std::max(thr, lp[(size_t)gi * lb.kmax + lc[gi] - 1].d);
+            if (lc[gi] <= 0) continue;
+            const PnPick &last = lp[(size_t)gi * lb.kmax + lc[gi] - 1];
+            const float t = lc[gi] < lb.kmax ? std::numeric_limits<float>::max() : (float)last.d;
+            const PnSeries &S = R.ser[last.series];
+            if (S.mode == 0) {
+                for (int32_t k = S.anchor_begin; k < S.anchor_begin + S.anchor_count; ++k) thr[k] = std::max(thr[k], t);
+            } else {
+                int below, above;
+                next_anchors(S, last.m, below, above);
+                if (below >= 0) thr[below] = std::max(thr[below], t);
+                if (above >= 0) thr[above] = std::max(thr[above], t);
+            }
         }
-        if (short_list) thr = std::numeric_limits<double>::max();
+        // focused: the anchors next to the length of every listed cell (the
+        // largest anchor length <= m and the smallest >= m of its series)
+        std::vector<uint32_t> fa;
+        if (focus_sieve) {
+            fa.assign(R.anc.size(), 0u);
+            for (int32_t gi = 0; gi < lb.ng; ++gi) {
+                for (int32_t t = 0; t < lc[gi]; ++t) {
+                    const PnPick &pk = lp[(size_t)gi * lb.kmax + t];
+                    int below, above;
+                    next_anchors(R.ser[pk.series], pk.m, below, above);
+                    if (below >= 0) fa[below] = 1u;
+                    if (above >= 0) fa[above] = 1u;
+                }
+            }
+        }
+        uint32_t *dfa = nullptr;
+        float *dthr = nullptr;
+        if (!fa.empty()) {
+            PN_CU(cudaMallocAsync((void **)&dfa, sizeof(uint32_t) * fa.size(), st));
+            PN_CU(cudaMemcpyAsync(dfa, fa.data(), sizeof(uint32_t) * fa.size(), cudaMemcpyHostToDevice, st));
+        }
+        PN_CU(cudaMallocAsync((void **)&dthr, sizeof(float) * thr.size(), st));
+        PN_CU(cudaMemcpyAsync(dthr, thr.data(), sizeof(float) * thr.size(), cudaMemcpyHostToDevice, st));
         int32_t ncls2 = 0;
-        PN_CU(pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w, 0, grid, R.a_max, st, &ncls2, thr));
+        int improved = 0;
+        const cudaError_t es = pn::launch_sieve(v, R.d_slot_off, R.total_slots, (int)c.sieve_w, 0, grid, R.a_max, st,
+                                                &ncls2, dthr, dfa, &improved);
+        if (dfa) cudaFreeAsync(dfa, st);
+        cudaFreeAsync(dthr, st);
+        PN_CU(es);
         ctx->launches += 6 + (ncls2 ? 4 + 2 * 12 + 6 : 0);
-        PN_TRY(emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl, 2));
-        PN_CU(cudaStreamSynchronize(st));
-        if (hctl[OV_FINAL]) return PANACHE_EPOOL;
+        if (improved) {
+            // the rest of the emit stage once more, on the lowered cells
+            PN_TRY(emit_launch(ctx, R, v, tm, E, hout, hcnt, hctl, 2));
+            PN_CU(cudaStreamSynchronize(st));
+            if (hctl[OV_FINAL]) return PANACHE_EPOOL;
+        }
     }
     ctx->stats.completion_rounds = (uint64_t)hctl[C_ROUNDS];
     ctx->stats.refine_passes = (uint64_t)hctl[R_PASSES];

@@ -18,10 +18,16 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 // Hot classes: buckets of an anchor's final directory (depth(N)) that hold
 // more than R entries -- classes no budgeted scan covered (Sec. 3.6).
 // ---------------------------------------------------------------------------
-__global__ void k_hot_flags(PnView v, const int64_t *slot_off, int64_t total, uint32_t *flag, uint32_t *size) {
+__global__ void k_hot_flags(PnView v, const int64_t *slot_off, int64_t total, uint32_t *flag, uint32_t *size,
+                            const uint32_t *anchor_on) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
     int ai = pn_find(slot_off, v.nanchors, t, [](int64_t o) { return o; });
+    if (anchor_on && !anchor_on[ai]) {           // an anchor the focused sieve leaves out
+        flag[t] = 0;
+        size[t] = 0;
+        return;
+    }
     const PnAnchor &A = v.anchors[ai];
     uint32_t N = A.nw > 0 ? v.cnt[A.win_off + A.nw - 1] : 0u;
     int D = pn_depth(N, v.alpha, v.B);
@@ -56,6 +62,13 @@ __global__ void k_hot_compact(PnView v, const int64_t *slot_off, int64_t total, 
     c.size = v.bstart[gb + 1] - v.bstart[gb];
     c.moff = moff[t];
     cls[cid[t]] = c;
+}
+
+// A class's members in directory order, one block per class (the top-k
+// sieves order them themselves).
+__global__ void k_class_members(PnView v, const PnClass *cls, uint32_t *vals) {
+    const PnClass c = cls[blockIdx.x];
+    for (uint32_t t = threadIdx.x; t < c.size; t += blockDim.x) vals[(int64_t)c.moff + t] = v.dir_vals[c.lo + t];
 }
 
 // Sort key of a member: its projection on the sieve direction g_{a,B+1},
@@ -944,7 +957,8 @@ cudaError_t sieve_t(const PnView &v, const PnClass *cls, int64_t nmem, const uin
 
 // ---------------------------------------------------------------------------
 cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t total_slots, int w, int exhaustive,
-                         int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out, double topk_thr) {
+                         int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out, const float *topk_thr,
+                         const uint32_t *focus_anchors, int *improved) {
     *n_classes_out = 0;
     if (total_slots <= 0) return cudaSuccess;
     uint32_t *flag = nullptr, *size = nullptr, *cid = nullptr, *moff = nullptr, *tot = nullptr;
@@ -954,7 +968,8 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&moff, 4 * total_slots, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot, 8, st);
     if (e == cudaSuccess) {
-        k_hot_flags<<<grid_for(total_slots, 256), 256, 0, st>>>(v, slot_off_dev, total_slots, flag, size);
+        k_hot_flags<<<grid_for(total_slots, 256), 256, 0, st>>>(v, slot_off_dev, total_slots, flag, size,
+                                                                topk_thr ? focus_anchors : nullptr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = excl_scan_u32(flag, cid, total_slots, tot, st);
@@ -964,35 +979,48 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     const int32_t ncls = (int32_t)h_tot[0];
     const int64_t nmem = (int64_t)h_tot[1];
+    bool topk_done = false;
     PnClass *cls = nullptr;
     uint32_t *keys = nullptr, *vals = nullptr;
     if (e == cudaSuccess && ncls > 0) {
         e = cudaMallocAsync((void **)&cls, sizeof(PnClass) * ncls, st);
-        if (e == cudaSuccess) e = cudaMallocAsync((void **)&keys, 4 * nmem, st);
+        if (e == cudaSuccess && !topk_thr) e = cudaMallocAsync((void **)&keys, 4 * nmem, st);
         if (e == cudaSuccess) e = cudaMallocAsync((void **)&vals, 4 * nmem, st);
         if (e == cudaSuccess) {
             k_hot_compact<<<grid_for(total_slots, 256), 256, 0, st>>>(v, slot_off_dev, total_slots, flag, cid, moff,
                                                                       cls);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && topk_thr) {
+            // the top-k sieves: members in directory order, no sort-key order
+            k_class_members<<<(unsigned)ncls, 256, 0, st>>>(v, cls, vals);
+            e = cudaGetLastError();
+            pn_kt_begin(v.kt, PN_KT_SIEVE, st);
+            if (e == cudaSuccess)
+                e = launch_sieve_gram(v, cls, ncls, vals, nmem, a_max, grid_blocks, st, topk_thr, improved);
+            pn_kt_end(v.kt, PN_KT_SIEVE, st);
+            topk_done = true;
+        }
+        if (e == cudaSuccess && !topk_done) {
             k_sieve_keys<<<grid_for(nmem, 256), 256, 0, st>>>(v, cls, ncls, nmem, keys, vals);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, nmem, 32, st);
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && !topk_done) e = radix_sort_pairs(keys, vals, nmem, 32, st);
+        if (e == cudaSuccess && !topk_done) {
             k_sieve_rekey<<<grid_for(nmem, 256), 256, 0, st>>>(v, cls, ncls, nmem, keys, vals);
             e = cudaGetLastError();
         }
         int cbits = 1;
         while (cbits < 32 && ((int64_t)1 << cbits) <= ncls) ++cbits;
-        if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, nmem, cbits, st);
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && !topk_done) e = radix_sort_pairs(keys, vals, nmem, cbits, st);
+        if (e == cudaSuccess && !topk_done) {
             int64_t warps_needed = nmem;
             int64_t blocks = (warps_needed + 7) / 8;
             if (blocks > grid_blocks) blocks = grid_blocks;
             const int zcap = (a_max + 3) & ~3;
             pn_kt_begin(v.kt, PN_KT_SIEVE, st);
             // after the class sort, keys[p] is the class of member p
-            if (topk_thr >= 0.0) e = launch_sieve_gram(v, cls, ncls, vals, nmem, a_max, grid_blocks, st, topk_thr);
-            else if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
+            if (v.precision == 0) e = sieve_t<ZPlain>(v, cls, nmem, keys, vals, w, exhaustive, zcap, blocks, st);
             else if (exhaustive == 1 && sieve_gram_supported(a_max))
                 e = launch_sieve_gram(v, cls, ncls, vals, nmem, a_max, grid_blocks, st);
             else if (exhaustive && v.x1) e = sieve_tiles_t<ZMix1>(v, cls, ncls, vals, grid_blocks, st);

@@ -52,9 +52,14 @@ struct PnPick {           // one selected motif
 };
 
 namespace pn {
+// topk_thr (device, one threshold per anchor, or null): the top-k sieve;
+// focus_anchors (device, one word per anchor, or null) restricts it to the
+// hot classes of the anchors whose word is nonzero; *improved (host) is set
+// when it lowered a cell.
 cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t total_slots, int w, int exhaustive,
                          int grid_blocks, int a_max, cudaStream_t st, int32_t *n_classes_out,
-                         double topk_thr = -1.0);
+                         const float *topk_thr = nullptr, const uint32_t *focus_anchors = nullptr,
+                         int *improved = nullptr);
 // nseeds: seeds in the array (host); nseeds_dev (device, may be null): how
 // many of them the kernel takes.
 cudaError_t launch_complete(const PnView &v, const PnSeed *seeds, int32_t nseeds, const int32_t *nseeds_dev, int dm,
@@ -77,11 +82,12 @@ cudaError_t launch_new_targets(const PnPick *picks, const int32_t *cnt, int32_t 
 // and only the pairs that can still lower a cell evaluated exactly
 // (gram.cu); anchors of at most 192 samples.
 bool sieve_gram_supported(int a_max);
-// With topk_thr >= 0, the top-k sieve: only pairs whose estimate can fall
-// below topk_thr (and below one of their cells) are evaluated, over the
+// With topk_thr (per anchor), the top-k sieve: only pairs whose estimate can
+// fall below their anchor's threshold (and below one of their cells) are evaluated, over the
 // tiles that the pivot order leaves (nmem members in all classes).
 cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int64_t nmem,
-                              int a_max, int grid_blocks, cudaStream_t st, double topk_thr = -1.0);
+                              int a_max, int grid_blocks, cudaStream_t st, const float *topk_thr = nullptr,
+                              int *improved = nullptr);
 // Exact row refinement: each target cell (series, m, i) scanned against
 // every valid partner at its length; `improved` set when a cell decreased.
 // max_windows bounds the partners of any target (the longest series).

@@ -185,9 +185,10 @@ __global__ void k_zt_blocks(const PnClass *cls, int32_t ncls, uint32_t *nb) {
 __device__ __forceinline__ float zt_r(const uint4 *rec, int64_t q) { return __uint_as_float(rec[q].w); }
 
 __device__ __forceinline__ void zt_row(const PnClass *cls, int32_t ncls, const uint32_t *roff, const uint4 *rec,
-                                       float T, int64_t g, int &ci, uint32_t &bu, uint32_t &e) {
+                                       const float *thr_a, int64_t g, int &ci, uint32_t &bu, uint32_t &e) {
     ci = pn_find(roff, ncls, g, [](uint32_t o) { return (int64_t)o; });
     const PnClass c = cls[ci];
+    const float T = thr_a[c.anchor];
     const uint32_t nb = (c.size + ZG_B - 1) / ZG_B;
     bu = (uint32_t)(g - roff[ci]);
     const float hi = zt_r(rec, (int64_t)c.moff + min((int64_t)c.size, ((int64_t)bu + 1) * ZG_B) - 1);
@@ -200,7 +201,7 @@ __device__ __forceinline__ void zt_row(const PnClass *cls, int32_t ncls, const u
 }
 
 __global__ void k_zt_row_count(const PnClass *cls, int32_t ncls, const uint32_t *roff, const uint32_t *nrows,
-                               int64_t nrows_max, const uint4 *rec, float T, uint32_t *tcnt,
+                               int64_t nrows_max, const uint4 *rec, const float *thr_a, uint32_t *tcnt,
                                unsigned long long *total) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nrows_max) return;
@@ -210,7 +211,7 @@ __global__ void k_zt_row_count(const PnClass *cls, int32_t ncls, const uint32_t 
     }
     int ci;
     uint32_t bu, e;
-    zt_row(cls, ncls, roff, rec, T, g, ci, bu, e);
+    zt_row(cls, ncls, roff, rec, thr_a, g, ci, bu, e);
     tcnt[g] = e - bu + 1;
     atomicAdd(total, (unsigned long long)(e - bu + 1));
 }
@@ -218,13 +219,13 @@ __global__ void k_zt_row_count(const PnClass *cls, int32_t ncls, const uint32_t 
 // One warp per row writes its tiles: class, first record of the row and of
 // the column block, rows | columns << 8 | diagonal << 16.
 __global__ void k_zt_row_fill(const PnClass *cls, int32_t ncls, const uint32_t *roff, const uint32_t *nrows,
-                              const uint4 *rec, float T, const uint32_t *toff, uint4 *tiles) {
+                              const uint4 *rec, const float *thr_a, const uint32_t *toff, uint4 *tiles) {
     const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (g >= (int64_t)*nrows) return;
     int ci;
     uint32_t bu, e;
-    zt_row(cls, ncls, roff, rec, T, g, ci, bu, e);
+    zt_row(cls, ncls, roff, rec, thr_a, g, ci, bu, e);
     const PnClass c = cls[ci];
     const uint32_t nu = min((uint32_t)ZG_B, c.size - bu * ZG_B);
     for (uint32_t t = lane; t <= e - bu; t += 32) {
@@ -724,7 +725,8 @@ __device__ __forceinline__ uint4 zt_record(const uint4 *rec, uint32_t first, int
 template <class Z>
 __global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const PnClass *cls, const uint4 *tiles,
                                                            int64_t ntiles, const uint4 *rec, int kpad_max,
-                                                           unsigned long long *work, float thr2) {
+                                                           unsigned long long *work, const float *thr_a,
+                                                           unsigned long long *improved) {
     extern __shared__ __align__(1024) unsigned char ztm_raw[];
     __shared__ ZtShared sh;
     unsigned char *ztm = ztm_raw + ((1024 - (smem_u32(ztm_raw) & 1023)) & 1023);
@@ -840,6 +842,8 @@ __global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const Pn
             const float nu_ = sh.A.n[u];
             const float mabs = (float)a * 6.1035156e-05f;                    // a 2^-14
             const float tu2 = sh.A.t[u] * sh.A.t[u];
+            const float ts = thr_a[c.anchor];
+            const float thr2 = ts * ts * (1.0f + 1e-6f) + 1e-12f;              // FP32 rounding of the square
             // fast bound: (1 - 2^-9) |y_v|^2 - 2 G < min(thr2, max(P[u]^2, P[v]^2)) + cu, with
             // cu = a 2^-14 - (1 - 2^-9) |y_u|^2 and a slack of 2^-20 of the magnitudes involved
             const float slack = 9.5367432e-07f * (thr2 + mabs + nu_ + 1.0f);
@@ -910,8 +914,10 @@ __global__ void __launch_bounds__(ZT_THREADS, 2) k_sieve_topk(PnView v, const Pn
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncthreads();
             if (tid < ZG_B) {
-                if (sh.rkey[tid] != PN_EMPTY_KEY) atomicMin(&prow[sh.A.s[tid]], sh.rkey[tid]);
-                if (sh.ckey[tid] != PN_EMPTY_KEY) atomicMin(&prow[sh.B.s[tid]], sh.ckey[tid]);
+                bool lowered = false;
+                if (sh.rkey[tid] != PN_EMPTY_KEY) lowered |= atomicMin(&prow[sh.A.s[tid]], sh.rkey[tid]) > sh.rkey[tid];
+                if (sh.ckey[tid] != PN_EMPTY_KEY) lowered |= atomicMin(&prow[sh.B.s[tid]], sh.ckey[tid]) > sh.ckey[tid];
+                if (lowered) atomicOr(improved, 1ull);
             }
             tl = tn;
         }
@@ -978,10 +984,8 @@ cudaError_t sieve_zgram_t(const PnView &v, const PnClass *cls, int32_t ncls, con
 // pruned by the triangle inequality, then k_sieve_topk over the kept tiles.
 template <class Z>
 cudaError_t sieve_topk_t(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int64_t nmem,
-                         int a_max, int grid_blocks, double thr, cudaStream_t st) {
+                         int a_max, int grid_blocks, const float *thr_a, int *improved, cudaStream_t st) {
     if (nmem <= 0) return cudaSuccess;
-    const float t = (float)thr;
-    const float thr2 = t * t * (1.0f + 1e-6f) + 1e-12f;        // FP32 rounding of the square
     const int64_t nrows_max = nmem / ZG_B + ncls + 1;           // sum of ceil(size / 128) over the classes
     float *r = nullptr;
     uint32_t *keys = nullptr, *idx = nullptr, *nb = nullptr, *roff = nullptr, *tot = nullptr;
@@ -997,8 +1001,8 @@ cudaError_t sieve_topk_t(const PnView &v, const PnClass *cls, int32_t ncls, cons
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot, 8, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&tcnt, 4 * (size_t)nrows_max, st);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&toff, 4 * (size_t)nrows_max, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot64, 2 * sizeof(unsigned long long), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tot64, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tot64, 3 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tot64, 0, 3 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) {
         k_zt_pivot<Z><<<(unsigned)((nmem * 32 + 255) / 256), 256, 0, st>>>(v, cls, ncls, vals, nmem, r, keys, idx);
         e = cudaGetLastError();
@@ -1019,8 +1023,8 @@ cudaError_t sieve_topk_t(const PnView &v, const PnClass *cls, int32_t ncls, cons
     }
     if (e == cudaSuccess) e = excl_scan_u32(nb, roff, ncls, tot, st);             // tot[0] = rows
     if (e == cudaSuccess) {
-        k_zt_row_count<<<(unsigned)((nrows_max + 255) / 256), 256, 0, st>>>(cls, ncls, roff, tot, nrows_max, rec, t,
-                                                                           tcnt, tot64);
+        k_zt_row_count<<<(unsigned)((nrows_max + 255) / 256), 256, 0, st>>>(cls, ncls, roff, tot, nrows_max, rec,
+                                                                           thr_a, tcnt, tot64);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = excl_scan_u32(tcnt, toff, nrows_max, tot + 1, st);
@@ -1032,8 +1036,8 @@ cudaError_t sieve_topk_t(const PnView &v, const PnClass *cls, int32_t ncls, cons
     if (e == cudaSuccess && ntiles > 0) e = cudaMallocAsync((void **)&tiles, sizeof(uint4) * (size_t)ntiles, st);
     unsigned long long *work = tot64 + 1;
     if (e == cudaSuccess && ntiles > 0) {
-        k_zt_row_fill<<<(unsigned)((nrows_max * 32 + 255) / 256), 256, 0, st>>>(cls, ncls, roff, tot, rec, t, toff,
-                                                                               tiles);
+        k_zt_row_fill<<<(unsigned)((nrows_max * 32 + 255) / 256), 256, 0, st>>>(cls, ncls, roff, tot, rec, thr_a,
+                                                                               toff, tiles);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && ntiles > 0) {
@@ -1043,10 +1047,16 @@ cudaError_t sieve_topk_t(const PnView &v, const PnClass *cls, int32_t ncls, cons
         const int64_t g = std::min<int64_t>((ntiles + ZT_RUN - 1) / ZT_RUN, (int64_t)grid_blocks);
         e = pn_allow_smem(k_sieve_topk<Z>, sm);
         if (e == cudaSuccess) {
-            k_sieve_topk<Z><<<(unsigned)g, ZT_THREADS, sm, st>>>(v, cls, tiles, ntiles, rec, kpad, work, thr2);
+            k_sieve_topk<Z><<<(unsigned)g, ZT_THREADS, sm, st>>>(v, cls, tiles, ntiles, rec, kpad, work, thr_a,
+                                                                 tot64 + 2);
             e = cudaGetLastError();
         }
     }
+    // whether any cell went down (the emit stage after the sieve is needed only then)
+    unsigned long long himp = 0ull;
+    if (e == cudaSuccess && ntiles > 0) e = cudaMemcpyAsync(&himp, tot64 + 2, sizeof(himp), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && ntiles > 0) e = cudaStreamSynchronize(st);
+    if (improved && himp) *improved = 1;
     for (void *p : {(void *)r, (void *)keys, (void *)idx, (void *)rec, (void *)nb, (void *)roff, (void *)tot,
                     (void *)tcnt, (void *)toff, (void *)tot64, (void *)tiles})
         if (p) cudaFreeAsync(p, st);
@@ -1058,11 +1068,11 @@ cudaError_t sieve_topk_t(const PnView &v, const PnClass *cls, int32_t ncls, cons
 bool sieve_gram_supported(int a_max) { return a_max <= ZG_AMAX; }
 
 cudaError_t launch_sieve_gram(const PnView &v, const PnClass *cls, int32_t ncls, const uint32_t *vals, int64_t nmem,
-                              int a_max, int grid_blocks, cudaStream_t st, double topk_thr) {
+                              int a_max, int grid_blocks, cudaStream_t st, const float *topk_thr, int *improved) {
     if (ncls <= 0) return cudaSuccess;
-    if (topk_thr >= 0.0) {
-        if (v.x1) return sieve_topk_t<ZMix1>(v, cls, ncls, vals, nmem, a_max, grid_blocks, topk_thr, st);
-        return sieve_topk_t<ZMix2>(v, cls, ncls, vals, nmem, a_max, grid_blocks, topk_thr, st);
+    if (topk_thr) {
+        if (v.x1) return sieve_topk_t<ZMix1>(v, cls, ncls, vals, nmem, a_max, grid_blocks, topk_thr, improved, st);
+        return sieve_topk_t<ZMix2>(v, cls, ncls, vals, nmem, a_max, grid_blocks, topk_thr, improved, st);
     }
     if (v.x1) return sieve_zgram_t<ZMix1>(v, cls, ncls, vals, a_max, grid_blocks, st);
     return sieve_zgram_t<ZMix2>(v, cls, ncls, vals, a_max, grid_blocks, st);

@@ -28,6 +28,7 @@ FLAG_WARM_START = 0x100
 FLAG_NO_REFINE = 0x200
 FLAG_GRAM_SEARCH = 0x800
 FLAG_TOPK_SIEVE = 0x1000
+FLAG_NO_FOCUS_SIEVE = 0x2000
 FLAG_SIEVE_GRAM = 0x400
 NOALLOC_NEED_MAX = 6300   # largest k (m + 1) of panache_topk_row_noalloc
 FAULT_NONE, FAULT_ALLOC, FAULT_COPY, FAULT_TC_WAIT = 0, 1, 2, 3

@@ -137,6 +137,19 @@ def test_prefix_topk_sieve_matches_exhaustive(pn, wafer):
         print(f"n={n}: top-k sieve {t.stats()['exact_sieve']} exact pairs, exhaustive {d.stats()['exact_sieve']}")
 
 
+def test_default_focused_sieve_matches_exhaustive(pn, wafer):
+    """The default global request runs the focused top-k sieve (the anchors
+    next to the refined list's lengths): on the 1M series it reports the
+    dense exhaustive sieve's motifs, which the request without it does not."""
+    x = np.ascontiguousarray(wafer.x[:1_000_000])
+    md = pn.Context(precision=1, topk_mode=0).pmp(x, 100, 150, 20, 150)
+    me = pn.Context(precision=1, topk_mode=0, flags=pn.FLAG_EXHAUSTIVE_SIEVE).pmp(x, 100, 150, 20, 150)
+    mo = pn.Context(precision=1, topk_mode=0, flags=pn.FLAG_NO_FOCUS_SIEVE).pmp(x, 100, 150, 20, 150)
+    assert np.array_equal(md[["m", "i", "j"]], me[["m", "i", "j"]])
+    assert np.allclose(md["d"], me["d"], rtol=1e-12, atol=0)
+    assert not np.array_equal(mo[["m", "i", "j"]], me[["m", "i", "j"]])
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_prefix_topk_sieve_float64_and_per_length(pn, wafer, mode):
     """The top-k sieve on the prefix given as float64 samples (the (hi, lo)
