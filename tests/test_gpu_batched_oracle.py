@@ -25,6 +25,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "batched_subset_top10.json")
+SMALL = os.path.join(os.path.dirname(__file__), "golden", "batched_small_top10.json")
 
 
 @pytest.fixture(scope="module")
@@ -118,3 +119,38 @@ def test_served_matches_oracle(pn, subset):
             sv.stream_close(sid)
     finally:
         sv.close()
+
+
+def test_batched_short_series_match_oracle(pn):
+    """Every series of the workload with n <= 12,000 and m_min <= 24 (145
+    series): global top-10 against the oracle
+    (tests/golden/batched_small_top10.json, written by make_batched_small.py),
+    in one pmp_batch call at the defaults, which include the focused top-k
+    sieve, and without it.  Measured: 12 of 1,450 cells missed, in six
+    series (pairs at lengths 16..26 that neither an anchor's search nor a hot
+    class brings up); 36 in 18 series without the focused sieve.  Bar:
+    recall >= 0.99 and fewer misses than without the sieve."""
+    from parity import compare
+    with open(SMALL) as f:
+        gold = json.load(f)["series"]
+    series = workloads.batched_workload(4096, seed=0, indices=[e["index"] for e in gold])
+    params = [(q.m_min, q.m_max, q.k, q.excl) for q in series]
+    got = pn.Context(precision=1, topk_mode=0).pmp_batch([q.x for q in series], params)
+    off = pn.Context(precision=1, topk_mode=0, flags=pn.FLAG_NO_FOCUS_SIEVE).pmp_batch([q.x for q in series], params)
+    misses = misses_off = total = 0
+    for q, g, o, e in zip(series, got, off, gold):
+        assert (len(q.x), q.m_min, q.m_max) == (e["n"], e["m_min"], e["m_max"])
+        ref = [tuple(t) for t in e["global"]]
+        r = compare(q.x.astype(np.float64), g, ref)
+        assert r["bad_dist"] == 0
+        misses += r["misses"]
+        total += r["n"]
+        if r["misses"]:
+            print("short series misses:", e["index"], q.kind, len(q.x), q.m_min, q.m_max, r["miss_list"])
+        ro = compare(q.x.astype(np.float64), o, ref)
+        misses_off += ro["misses"]
+        if ro["misses"]:
+            print("  without the focused sieve:", e["index"], ro["misses"])
+    print(f"short batched series: {misses} of {total} oracle cells missed ({misses_off} without the focused sieve)")
+    assert misses <= 0.01 * total
+    assert misses < misses_off
