@@ -174,7 +174,8 @@ def kernel_table(st: dict, kt: dict, n: int, anchors: list[int], peaks: dict, al
                     exact distance of 5 flop per sample (normalise, subtract,
                     multiply-add) at the mean anchor length
       sieve eval    5 flop per sample per evaluated pair; each member's window
-                    (4 B per sample) once per band of w pairs
+                    (4 B per sample) once per band of w pairs (the exact pairs
+                    counted include the top-k sieve's, a few percent)
       k_complete    3 flop per sample per box triple (its windows are
                     normalised once in shared memory); bytes: per seed (1,053
                     triples) the two runs of m + 2 dm + 2 dp samples its box
@@ -215,6 +216,13 @@ def kernel_table(st: dict, kt: dict, n: int, anchors: list[int], peaks: dict, al
                     "tflops": sig(tf), "gbs": sig(gbs),
                     ("tf32_frac" if pipe == "tf32" else "fp32_frac"): sig(tf / peak_c),
                     "hbm_frac": sig(gbs / peaks["hbm_gbs"])})
+    ms, launches = kt.get("topk_sieve", (0.0, 0))
+    if ms > 0:
+        # the focused top-k sieve after the emit stage: its work is the kept
+        # tiles' FP16 Gram blocks, which the request counters do not give;
+        # time only (its profile summary has the counters)
+        out.append({"kernel": "topk_sieve", "launches": launches, "ms": round(ms, 3),
+                    "note": "FP16 Gram blocks of the pivot-kept tiles plus the pivot pre-pass; issue-bound"})
     return out
 
 

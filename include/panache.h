@@ -380,9 +380,10 @@ int panache_inject_fault(int32_t kind, int32_t after);
  * k = 0 tensor-core chunk anchors, 1 sliding DFT + normalisation + keys,
  * 2 streaming search, 3 hot-class sieve evaluation (without its sorts),
  * 4 local completion (without its seed selections), 5 selection (every
- * seed selection and the final top-k), 6 exact row refinement.  Zero
- * without the flag.  ETRUNC when cap < 7. */
-#define PANACHE_KERNEL_TIMES 7
+ * seed selection and the final top-k), 6 exact row refinement, 7 the
+ * top-k sieve after the emit stage (focused or at every anchor, with its
+ * pivot pre-pass).  Zero without the flag.  ETRUNC when cap < 8. */
+#define PANACHE_KERNEL_TIMES 8
 int panache_kernel_times(const panache_ctx *ctx, double *ms, uint64_t *launches, int32_t cap);
 
 /* The budgeted candidate list (Sec. 3.4) each listed query window q[i] of

@@ -995,10 +995,10 @@ cudaError_t launch_sieve(const PnView &v, const int64_t *slot_off_dev, int64_t t
             // the top-k sieves: members in directory order, no sort-key order
             k_class_members<<<(unsigned)ncls, 256, 0, st>>>(v, cls, vals);
             e = cudaGetLastError();
-            pn_kt_begin(v.kt, PN_KT_SIEVE, st);
+            pn_kt_begin(v.kt, PN_KT_TOPK, st);
             if (e == cudaSuccess)
                 e = launch_sieve_gram(v, cls, ncls, vals, nmem, a_max, grid_blocks, st, topk_thr, improved);
-            pn_kt_end(v.kt, PN_KT_SIEVE, st);
+            pn_kt_end(v.kt, PN_KT_TOPK, st);
             topk_done = true;
         }
         if (e == cudaSuccess && !topk_done) {

@@ -17,6 +17,7 @@ enum PnKernelId {
     PN_KT_COMPLETE,        // local completion rounds
     PN_KT_SELECT,          // selection kernels (seed selections and the final top-k)
     PN_KT_REFINE,          // exact row refinement of the top list
+    PN_KT_TOPK,            // top-k sieve after the emit stage (focused or every anchor; with its pre-pass)
     PN_KT_COUNT
 };
 

@@ -72,7 +72,7 @@ class Request(ctypes.Structure):
 
 
 STEP_NAMES = ("upload", "moments", "features", "directory", "search", "sieve", "completion", "select")
-KERNEL_NAMES = ("anchor_tc", "features", "search", "sieve", "complete", "select", "refine")
+KERNEL_NAMES = ("anchor_tc", "features", "search", "sieve", "complete", "select", "refine", "topk_sieve")
 KERNEL_TIMES = len(KERNEL_NAMES)
 
 
