@@ -137,6 +137,19 @@ def test_prefix_topk_sieve_matches_exhaustive(pn, wafer):
         print(f"n={n}: top-k sieve {t.stats()['exact_sieve']} exact pairs, exhaustive {d.stats()['exact_sieve']}")
 
 
+def test_graph_replay_with_focused_sieve(pn, wafer):
+    """Global requests of one shape with graph replay: the index, search and
+    first emit stage replay their graphs, the focused top-k sieve and the
+    emit stage after it run eagerly; every request equals the eager path."""
+    eager = pn.Context(precision=1, topk_mode=0)
+    graph = pn.Context(precision=1, topk_mode=0, flags=pn.FLAG_GRAPH)
+    for lo in (0, 200_000, 0, 400_000):
+        x = np.ascontiguousarray(wafer.x[lo:lo + 200_000])
+        want = eager.pmp(x, 100, 150, 20, 150)
+        got = graph.pmp(x, 100, 150, 20, 150)
+        assert np.array_equal(got, want), lo
+
+
 def test_default_focused_sieve_matches_exhaustive(pn, wafer):
     """The default global request runs the focused top-k sieve (the anchors
     next to the refined list's lengths): on the 1M series it reports the
