@@ -142,7 +142,7 @@ struct GsShared {
     unsigned long long qbest[GS_GQ];                 // best key of each query in this group
     uint32_t q[GS_GQ];                               // query window (index within its anchor)
     int cnt[GS_GQ];                                  // list length
-    int qn[GS_GQ];                                   // survivors queued this round
+    int qn[GS_GQ];                                   // survivors queued in this pass
     int ncmax, nqmax;                                // float bits
     int nu, G, ai;
     uint32_t g;

@@ -1,7 +1,7 @@
 """The request server: continuous batching, admission by HBM footprint, live streams.
 
 Results must not depend on which requests share a batch or run alongside
-(the north star's "same alone and in the mix"); the parity tolerance here is
+(each result the same alone and in the mix); the parity tolerance here is
 zero: motifs are compared bit for bit.
 """
 import numpy as np
