@@ -677,6 +677,7 @@ def main():
     if args.plain_steps > 0 and args.precision != 0:
         pctx = make_ctx(0)
         pms, pstats, pmot = timed(pctx, args.plain_steps, 1, x_dev)
+        plain_mot = pmot
         plain = {"value": W * world / (statistics.mean(pms) / 1e3), "ms_per_step": statistics.mean(pms),
                  "same_motifs": bool(np.array_equal(pmot[["m", "i", "j"]], motifs[["m", "i", "j"]])),
                  "step_ms": pstats[-1]["step_ms"]}
@@ -717,6 +718,11 @@ def main():
                 # the default's list scored against this one by the paper's recovery rule
                 fast[name]["default_recovery_sec4"] = paper_recovery(fmot, motifs)
                 topk_mot = fmot
+            if name == "no_focus_sieve" and plain is not None:
+                # the plain FP64 form has no focused sieve (it needs the FP16
+                # Gram blocks): its lists against the mixed form's without it
+                plain["same_motifs_as_mixed_without_focus"] = bool(
+                    np.array_equal(plain_mot[["m", "i", "j"]], fmot[["m", "i", "j"]]))
             if name == "no_focus_sieve" and "topk_sieve" in fast:
                 # without the default's focused sieve: its cells against the whole
                 # top-k sieve's, by identity and by the paper's rule
